@@ -278,7 +278,7 @@ class DelayScatter(torch.autograd.Function):
     Inputs: c [2, 20, 39] (tap 0 at -19), zr, zi [2, 20].  Output taps [2, 20 D + 38], tap 0 at n = -19."""
 
     @staticmethod
-    def forward(ctx, c, zr, zi, D: int):
+    def forward(ctx, c, zr, zi, D: int, L: int):
         d = delay_positions(zr.detach().numpy(), zi.detach().numpy(), D)   # [2, 20]
         ntaps = DELAY_TAPS * D + DELAY_FIR_TAPS - 1
         out = torch.zeros(2, ntaps, dtype=F64)
@@ -289,6 +289,7 @@ class DelayScatter(torch.autograd.Function):
         ctx.save_for_backward(c, zr, zi)
         ctx.d = d
         ctx.D = D
+        ctx.L = L
         return out
 
     @staticmethod
@@ -298,7 +299,10 @@ class DelayScatter(torch.autograd.Function):
         dc = torch.zeros_like(c)
         dzr = torch.zeros_like(zr)
         dzi = torch.zeros_like(zi)
-        dt = dtaps.detach().numpy()
+        dt = dtaps.detach().numpy().copy()
+        # dL/dh[t] = sum_n dL/dy[n] u[n - t] vanishes identically for lags t >= L (no overlap); drop the
+        # rounding residue there so that sgn(0) = 0 holds for slots beyond the signal
+        dt[:, ctx.L + DELAY_FIR_TAPS // 2:] = 0.0
         cc = c.detach().numpy()
         for ch in range(2):
             for m in range(DELAY_TAPS):
@@ -315,17 +319,18 @@ class DelayScatter(torch.autograd.Function):
                 tot = sg + radial
                 dzr[ch, m] = tot.real
                 dzi[ch, m] = tot.imag
-        return dc, dzr, dzi, None
+        return dc, dzr, dzi, None, None
 
 
-def delay_fir(p: torch.Tensor, D: int) -> torch.Tensor:
-    """Eq. (17) FIR of both channels from p = [ch][m][(Re z, Im z, 20 log-magnitudes)]."""
+def delay_fir(p: torch.Tensor, D: int, L: int) -> torch.Tensor:
+    """Eq. (17) FIR of both channels from p = [ch][m][(Re z, Im z, 20 log-magnitudes)], for an input of
+    L samples."""
     pp = p.reshape(2, DELAY_TAPS, 22)
     c = zero_phase_fir(pp[:, :, 2:], DELAY_FIR_TAPS)     # [2, 20, 39]
-    return DelayScatter.apply(c, pp[:, :, 0], pp[:, :, 1], D)
+    return DelayScatter.apply(c, pp[:, :, 0], pp[:, :, 1], D, L)
 
 
 def multitap_delay(u: torch.Tensor, p: torch.Tensor, D: int) -> torch.Tensor:
     """Sec. 3.7: channel-wise convolution with the per-channel multitap FIRs (first tap at n = -19)."""
-    h = delay_fir(p, D)
+    h = delay_fir(p, D, u.shape[-1])
     return fft_conv(u, h, -(DELAY_FIR_TAPS - 1) // 2)

@@ -254,7 +254,7 @@ def test_delay_straight_through_gradient():
     p[:, :, 1] = t64(rad * np.sin(ang))
     p[:, :, 2:] = t64(r.uniform(-2, 0, (2, 20, 20)))
     p.requires_grad_(True)
-    taps = P.delay_fir(p.reshape(-1), D)
+    taps = P.delay_fir(p.reshape(-1), D, 10 ** 6)
     wts = t64(r.standard_normal(taps.shape))
     (taps * wts).sum().backward()
     g = p.grad.numpy()
@@ -277,9 +277,9 @@ def test_delay_straight_through_gradient():
     eps = 1e-6
     pp = p.detach().clone()
     pp[lm_fd_idx] += eps
-    up = float((P.delay_fir(pp.reshape(-1), D) * wts).sum())
+    up = float((P.delay_fir(pp.reshape(-1), D, 10 ** 6) * wts).sum())
     pp[lm_fd_idx] -= 2 * eps
-    dn = float((P.delay_fir(pp.reshape(-1), D) * wts).sum())
+    dn = float((P.delay_fir(pp.reshape(-1), D, 10 ** 6) * wts).sum())
     assert abs((up - dn) / (2 * eps) - g[lm_fd_idx]) < 1e-6
 
 
