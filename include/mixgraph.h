@@ -1,0 +1,174 @@
+/*
+ * mixgraph.h - C ABI of the GB300 mixing-console hot path.
+ *
+ * Reverse engineering of a music mix (Sec. 1.1): given dry sources S = [s_1..s_K] and a target mix y,
+ * find the graph G and parameters P with y_hat = G(S; P) close to y under the loss L_a.  This library
+ * holds the hot path of that search: the batched forward and backward pass of the differentiable mixing
+ * console G_c (Sec. 1.2, Sec. 3, Sec. 4), its multi-resolution STFT loss and regularisers (Sec. 5.1,
+ * Sec. 6.3), Adam (Sec. 5.1), masked forwards that score pruning candidates (Alg. 2-3), and structural
+ * pruning (Alg. 3, Prune).
+ *
+ * Conventions (all entry points):
+ *  - Every call is stream-ordered on the stream given to mg_console_create and returns without waiting
+ *    for the GPU unless stated.  Device pointers passed by the caller are borrowed for the duration of
+ *    the enqueued work only when the call says "copied"; otherwise they must stay valid until the
+ *    stream reaches the call.
+ *  - The library owns all device memory it allocates; the caller owns what it passes in.
+ *  - No C++ exception crosses the ABI.  Failures return a status; mg_last_error(console) gives a message
+ *    (valid until the next call on that console).
+ *  - Processor order P ("canonical"): song -> chain (tracks 0..K-1, then subgroups 0..S-1) -> type in
+ *    chain order e c n s g d r (enabled types only).  The flat parameter vector holds every processor's
+ *    parameters in that order (g 2, s 1, e 1024, r 768, c 4, n 4, d 880; Sec. 3), followed by one
+ *    dry/wet logit q per processor in the same order; w = sigmoid(q) * mask (Sec. 5.1, Alg. 3).
+ *  - Audio is FP32, sample rate as given; stereo buffers are planar [2][L] (left row, then right row).
+ */
+#ifndef MIXGRAPH_H
+#define MIXGRAPH_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID = 1,     /* bad argument (null pointer, size mismatch, out-of-range value) */
+  MG_ERR_OOM = 2,         /* device allocation failed */
+  MG_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  MG_ERR_STATE = 4,       /* call out of order (e.g. backward without a preceding unmasked forward_loss) */
+  MG_ERR_TIMEOUT = 5,     /* a bounded wait gave up */
+  MG_ERR_UNSUPPORTED = 6  /* configuration outside the supported range */
+} mg_status;
+
+typedef struct mg_console mg_console;
+
+/* One song (Sec. 1.1 problem statement): K mono dry sources, a subgroup assignment (given a priori,
+ * Sec. 1.2) and the target stereo mix. */
+typedef struct {
+  int32_t num_tracks;          /* K >= 1 */
+  int32_t num_subgroups;       /* S >= 0 */
+  const int32_t* track_group;  /* host [K]: subgroup of each track in [0, S), or -1 = straight to the mix */
+  int64_t num_samples;         /* L >= 1 */
+  const float* sources;        /* [K][L] mono sources (input node i duplicates each to both channels); copied */
+  const float* target;         /* [2][L] target mix y, or NULL (then the losses are not defined); copied */
+  int32_t on_device;           /* 1: sources/target are device pointers, 0: host pointers */
+} mg_song_desc;
+
+/* Console and loss settings (Sec. 3, Sec. 5.1, Sec. 6.3). */
+typedef struct {
+  double sample_rate;          /* fs in Hz (e.g. 44100) */
+  uint32_t type_mask;          /* bit i enables processor type "ecnsgdr"[i] in every chain (0x7F = all) */
+  int32_t n_resolutions;       /* 1..3 STFT resolutions of Eq. (21) */
+  int32_t n_fft[3];            /* FFT sizes, powers of two in [64, 8192] (e.g. 512, 2048, 8192) */
+  int32_t hop_div;             /* hop = n_fft / hop_div (4 in Sec. 5.1) */
+  int32_t n_mels;              /* Mel bands (96 in Sec. 5.1); 0 = linear-frequency bins */
+  int32_t a_weighting;         /* 1 = A-weighting before the STFT (Sec. 5.1) */
+  int64_t warmup_samples;      /* frames starting before this sample are left out of the loss */
+  float alpha_lr, alpha_m, alpha_s;  /* Eq. (20) weights (0.5, 0.25, 0.25) */
+  float alpha_g;               /* Eq. (23) gain-staging weight (1e-3) */
+  const float* reverb_noise;   /* [n_reverbs][2][2*fs] fixed U(-1,1) noises of the reverbs in canonical order
+                                  (Sec. 3.4); required when reverbs are enabled; copied */
+  int32_t noise_on_device;     /* 1: reverb_noise is a device pointer */
+  int64_t workspace_limit_bytes;  /* bound on FFT scratch for one launch group; 0 = no bound */
+} mg_console_desc;
+
+/* Sizes of a console (layout only). */
+typedef struct {
+  int32_t n_songs;
+  int32_t n_processors;        /* P */
+  int64_t n_proc_params;       /* processor parameters; the dry/wet logits start here */
+  int64_t n_params;            /* n_proc_params + P */
+  int32_t n_reverbs;
+  int64_t total_samples;       /* sum of L over songs */
+  double track_seconds;        /* sum over songs of K * L / fs */
+  int64_t device_bytes;        /* device memory held by the console (0 from mg_plan) */
+  int32_t launches_per_step;   /* kernel launches of forward_loss + backward + adam_step (0 from mg_plan) */
+} mg_console_info;
+
+/* Host-only layout planning (no GPU needed): fills sizes for the given console. */
+mg_status mg_plan(const mg_console_desc* desc, const mg_song_desc* songs, int32_t n_songs, mg_console_info* out);
+
+/* Build a console over n_songs songs on the current CUDA device.  Allocates all device memory, uploads
+ * sources and targets, precomputes the target spectrograms and the reverb noise STFTs.  Synchronises
+ * the stream before returning.  Parameters start at zero; set them with mg_set_params. */
+mg_status mg_console_create(const mg_console_desc* desc, const mg_song_desc* songs, int32_t n_songs,
+                            cudaStream_t stream, mg_console** out);
+mg_status mg_console_destroy(mg_console* c);
+mg_status mg_console_get_info(const mg_console* c, mg_console_info* out);
+
+/* Canonical layout: types[P] (index into "ecnsgdr"), param_offset[P], song[P]; any pointer may be NULL. */
+mg_status mg_processor_layout(const mg_console* c, int32_t* types, int64_t* param_offset, int32_t* song);
+
+/* Parameter vector [n_params] in the canonical layout; copied (host or device). */
+mg_status mg_set_params(mg_console* c, const float* params, int64_t n, int32_t on_device);
+mg_status mg_get_params(const mg_console* c, float* out, int64_t n, int32_t on_device);
+/* Gradient d(sum over songs of L)/d params of the last mg_backward, same layout.  The z entries of the
+ * multitap delays hold the straight-through update direction of Eq. (19). */
+mg_status mg_get_grads(const mg_console* c, float* out, int64_t n, int32_t on_device);
+/* Sparsity weight alpha_p of Eq. (26) used by the next forward_loss / backward. */
+mg_status mg_set_alpha_p(mg_console* c, float alpha_p);
+
+/* Forward pass and objective (Alg. 1 schedule, Eqs. 2, 20-23, 26).
+ * d_mask: device {0,1}[P] multiplied into the dry/wet weights, or NULL (all ones); copied.
+ * d_losses: device [n_songs][7] = (L_a, L_lr, L_m, L_s, L_g, L_p, L) per song, or NULL.
+ * d_mix: device [sum_songs 2*L] rendered mixes (song-major, planar stereo), or NULL.
+ * A call with d_mask == NULL arms mg_backward. */
+mg_status mg_forward_loss(mg_console* c, const uint8_t* d_mask, float* d_losses, float* d_mix);
+
+/* Reverse pass of the last unmasked forward_loss: writes the parameter gradients.
+ * MG_ERR_STATE if parameters, audio or structure changed since that forward, or a masked forward or
+ * mg_prune_scores ran after it. */
+mg_status mg_backward(mg_console* c);
+
+/* Masked forwards that score pruning candidates (Alg. 2 Evaluate, Alg. 3): for every mask j in
+ * d_masks (device {0,1}[n_masks][P]) the audio loss L_a of every song with w * mask_j.
+ * d_la: device [n_masks][n_songs].  Does not touch gradients or Adam state. */
+mg_status mg_prune_scores(mg_console* c, const uint8_t* d_masks, int32_t n_masks, float* d_la);
+
+/* One Adam step (Sec. 5.1; Kingma-Ba bias correction, decoupled weight decay) on all parameters with the
+ * gradients of the last mg_backward.  Moments start at zero after create / mg_reset_optimizer. */
+mg_status mg_adam_step(mg_console* c, float lr, float beta1, float beta2, float eps, float weight_decay);
+mg_status mg_reset_optimizer(mg_console* c);
+
+/* forward_loss (unmasked) + backward + adam_step as one CUDA graph, captured on first use and replayed
+ * after; d_losses as in mg_forward_loss (the pointer is part of the captured graph: pass the same one). */
+mg_status mg_train_step(mg_console* c, float lr, float beta1, float beta2, float eps, float weight_decay,
+                        float* d_losses);
+
+/* Structural pruning (Alg. 3, Prune): processors with h_keep[i] == 0 are removed (bypassed, no work, left
+ * out of L_g and L_p; their gradients read zero).  h_keep: host {0,1}[P]; removal is permanent. */
+mg_status mg_prune(mg_console* c, const uint8_t* h_keep);
+/* Host {0,1}[P]: 1 for processors not removed by mg_prune. */
+mg_status mg_get_present(const mg_console* c, uint8_t* h_present);
+
+/* Replace the audio of one song (same K and L): sources [K][L], target [2][L] (NULL keeps the old target);
+ * recomputes the target spectrograms.  Copied (host or device). */
+mg_status mg_update_audio(mg_console* c, int32_t song, const float* sources, const float* target,
+                          int32_t on_device);
+
+/* 0: one launch per processor type over all nodes of all songs (batched, default);
+ * 1: the same kernels launched once per node (one-by-one processing, Sec. 4.1 / Fig. 2d). */
+mg_status mg_set_launch_mode(mg_console* c, int32_t per_node);
+
+/* Per-kernel timing with CUDA events around every launch (1 = on; off by default).  Times accumulate
+ * until mg_reset_kernel_times.  Kernel families: see mg_kernel_family_name. */
+mg_status mg_set_profiling(mg_console* c, int32_t on);
+int32_t mg_num_kernel_families(void);
+const char* mg_kernel_family_name(int32_t family);
+/* Waits for the stream, then returns per family: total milliseconds and launch counts. */
+mg_status mg_get_kernel_times(mg_console* c, double* ms, int64_t* launches, int32_t n_families);
+mg_status mg_reset_kernel_times(mg_console* c);
+
+/* Diagnostic read-back of one processor's buffers (synchronises the stream), for per-node parity checks.
+ * what: 0 output y [2][L], 1 FIR taps [2][Nh] (LTI processors), 2 FIR tap gradient [2][Nh], 3 input adjoint
+ * du [2][L], 4 node statistics [16], 5 output adjoint dy [2][L].  host_out must hold exactly n = rows x columns floats. */
+mg_status mg_debug_read(const mg_console* c, int32_t proc, int32_t what, float* host_out, int64_t n);
+
+const char* mg_last_error(const mg_console* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MIXGRAPH_H */

@@ -1,0 +1,1357 @@
+// Host engine and C ABI of the mixing-console hot path (see include/mixgraph.h).
+//
+// Layout (Sec. 4.3, re-designed for one GPU and many songs): every processor node of every song is one entry
+// of a flattened node table (ProcDev).  The forward pass walks the console's type string
+// i e c n s g d r m e c n s g d r o (Sec. 4.2) once: for each position one launch per kernel covers all nodes
+// of that type in all songs (work items = (node, tile)), instead of the paper's per-graph gather /
+// aggregate / store with index_select and scatter: node outputs are written once into their own slice of
+// one device arena, and every node reads its input slice in place.  The backward pass walks the string in
+// reverse.  Per-node reductions use fixed-order partial sums so results do not depend on batch composition.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mixgraph.h"
+#include "mg_internal.cuh"
+
+using namespace mg;
+
+namespace {
+
+constexpr const char* kTypeChars = "ecnsgdr";
+constexpr int kParamCount[NTYPES] = {1024, 4, 4, 1, 2, 880, 768};
+
+enum Family {
+  F_GS_FWD, F_GS_BWD, F_SUM, F_DYN_FWD, F_DYN_BWD, F_EQ_FIR, F_DLY_FIR, F_REV_FIR, F_FIR_ADJ, F_COL_FWD, F_ROW_HZ,
+  F_ROW_CONV, F_COL_OUT, F_COL_DYBAR, F_ROW_BWD2, F_COL_DU, F_COL_DH, F_LOSS_FWD, F_LOSS_BWD, F_LOSS_GATHER,
+  F_FINALIZE, F_ADAM, F_MISC, F_COUNT
+};
+const char* kFamilyNames[F_COUNT] = {
+    "gs_fwd", "gs_bwd", "sum", "dyn_fwd", "dyn_bwd", "eq_fir", "dly_fir", "rev_fir", "fir_adj", "col_fwd", "row_hz",
+    "row_conv", "col_out", "col_dybar", "row_bwd2", "col_du", "col_dh", "loss_fwd", "loss_bwd", "loss_gather",
+    "finalize", "adam", "misc"};
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline int ilog2_ceil(int64_t x) {
+  int l = 0;
+  while (((int64_t)1 << l) < x) ++l;
+  return l;
+}
+
+struct HostProc {
+  int type, song, chain, level, qidx, rev;
+  int present = 1;
+  int64_t poff;
+  int L, ld;
+  int logN = 0, logN1 = 0, logN2 = 0, colG = 0, n0 = 0, Nh = 0, nchunks = 0, nframes = 0;
+  int nfrows = 0, nbrows = 0;
+  // arena offsets (bytes)
+  size_t o_y = 0, o_stats = 0, o_fpart = 0, o_bpart = 0, o_taps = 0, o_dtaps = 0, o_aux = 0, o_carry = 0, o_rcarry = 0,
+         o_cagg = 0, o_nspec = 0;
+  size_t scratch_bytes = 0;  // T1 + T2 + Hz
+  size_t o_scratch = 0;      // offset inside the shared LTI scratch
+};
+
+struct HostChain {
+  int song, level, index, L, ld;
+  std::vector<int> procs;
+  size_t o_in = 0;           // chain input: source (track) or mix-node output (subgroup)
+  size_t o_dA = 0, o_dB = 0; // adjoint ping-pong
+};
+
+struct HostSong {
+  int K, S, L, ld;
+  std::vector<int> group;
+  int nframes[3] = {0, 0, 0}, first[3] = {0, 0, 0}, litems[3] = {0, 0, 0}, lcap = 0;
+  size_t o_mix = 0, o_dmix = 0, o_tgt = 0, o_Y[3] = {0, 0, 0}, o_dF[3] = {0, 0, 0}, o_lpart = 0, o_coef = 0,
+         o_ynorm = 0;
+  std::vector<int> tracks_chain, groups_chain;
+  int pbeg = 0, pend = 0;
+  double track_seconds = 0;
+};
+
+template <class T>
+struct DevVec {
+  std::vector<T> h;
+  T* d = nullptr;
+};
+
+// A launch list: items sorted by processor, with per-processor ranges for one-launch-per-node mode.
+struct ItemList {
+  std::vector<Item> h;
+  std::vector<int> beg;  // ranges: [beg[i], beg[i+1]) for i-th proc
+  Item* d = nullptr;
+  int maxv = 0;          // kernel-specific size bound (max N2*G or N1)
+};
+struct ProcList {
+  std::vector<int> h;
+  int* d = nullptr;
+};
+
+struct LtiGroup {
+  ProcList procs;
+  ItemList col, rowhz, rowpair, firtaps, dlyadj, revfir;
+};
+
+struct Stage {
+  int level, type;
+  ProcList procs;
+  ItemList elem;                 // g, s, c, n (tile / chunk items)
+  std::vector<LtiGroup> groups;  // e, r, d
+};
+
+}  // namespace
+
+struct mg_console {
+  mg_console_desc desc{};
+  std::vector<HostSong> songs;
+  std::vector<HostProc> procs;
+  std::vector<HostChain> chains;
+  int P = 0, nrev = 0, nres = 0;
+  int64_t npp = 0, nparams = 0;
+  double track_seconds = 0;
+  int64_t total_samples = 0;
+  cudaStream_t stream = nullptr;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  char* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  float* d_params = nullptr;
+  float* d_grads = nullptr;
+  float* d_m = nullptr;
+  float* d_v = nullptr;
+  int* d_step = nullptr;
+  float* d_hyper = nullptr;
+  float* d_alphas = nullptr;
+  uint8_t* d_mask = nullptr;
+  float* d_scratch_la = nullptr;
+  ProcDev* d_procs = nullptr;
+  SongDev* d_songs = nullptr;
+  LossRes* d_res = nullptr;
+  int64_t* d_mixoff = nullptr;
+  Tables tab{};
+  std::vector<void*> table_allocs;
+  std::vector<ProcDev> hpd;
+  std::vector<SongDev> hsd;
+  std::vector<LossRes> hres;
+  std::vector<Stage> stages;      // forward order
+  // sums
+  DevVec<float*> sum_out;
+  DevVec<const float*> sum_in;
+  DevVec<int> sum_beg, sum_L, sum_ld;
+  ItemList sum_m_items, sum_o_items;
+  int n_msum = 0;
+  ProcList all_present;
+  ProcList all_lti_present;
+  DevVec<int4> loss_items[3];
+  ItemList gather_items;
+  // state
+  bool fwd_valid = false;
+  bool per_node = false;
+  bool profiling = false;
+  float alpha_p = 0.f;
+  std::string err;
+  cudaGraphExec_t graph = nullptr;
+  float* graph_losses = nullptr;
+  bool graph_profiled = false;
+  int launches = 0;
+  int launches_step = 0;
+  // profiling
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_next = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending, graph_pairs;
+  double fam_ms[F_COUNT] = {0};
+  int64_t fam_n[F_COUNT] = {0};
+  bool capturing = false;
+  std::vector<void*> small_allocs;
+};
+
+namespace {
+
+std::string g_static_err;
+
+mg_status fail(mg_console* c, mg_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_static_err = msg;
+  return s;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(c, MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------------
+// planning (host only)
+// ------------------------------------------------------------------------------------------------
+mg_status validate(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
+  if (!d || !s || n <= 0) return fail(c, MG_ERR_INVALID, "null descriptor or no songs");
+  if (!(d->sample_rate > 1000.0 && d->sample_rate < 1e6)) return fail(c, MG_ERR_INVALID, "sample_rate out of range");
+  if (d->type_mask & ~0x7Fu) return fail(c, MG_ERR_INVALID, "type_mask has bits beyond the 7 processor types");
+  if (d->n_resolutions < 1 || d->n_resolutions > 3) return fail(c, MG_ERR_INVALID, "n_resolutions must be 1..3");
+  for (int r = 0; r < d->n_resolutions; ++r) {
+    const int nf = d->n_fft[r];
+    if (nf < 64 || nf > 8192 || (nf & (nf - 1))) return fail(c, MG_ERR_INVALID, "n_fft must be a power of two in [64, 8192]");
+    if (d->hop_div < 1 || nf % d->hop_div) return fail(c, MG_ERR_INVALID, "hop_div must divide n_fft");
+  }
+  if (d->n_mels < 0 || d->n_mels > 512) return fail(c, MG_ERR_INVALID, "n_mels must be in [0, 512]");
+  if (d->warmup_samples < 0) return fail(c, MG_ERR_INVALID, "negative warmup_samples");
+  for (int i = 0; i < n; ++i) {
+    if (s[i].num_tracks < 1 || s[i].num_subgroups < 0) return fail(c, MG_ERR_INVALID, "song needs >= 1 track");
+    if (s[i].num_samples < 1 || s[i].num_samples > (1 << 22) - 200000)
+      return fail(c, MG_ERR_UNSUPPORTED, "num_samples must be in [1, 3994304]");
+    if (!s[i].track_group) return fail(c, MG_ERR_INVALID, "track_group is null");
+    for (int k = 0; k < s[i].num_tracks; ++k)
+      if (s[i].track_group[k] < -1 || s[i].track_group[k] >= s[i].num_subgroups)
+        return fail(c, MG_ERR_INVALID, "track_group entry out of range");
+  }
+  return MG_OK;
+}
+
+void plan(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
+  c->desc = *d;
+  c->nres = d->n_resolutions;
+  const double fs = d->sample_rate;
+  const int D = (int)std::llround(0.1 * fs);
+  const int revlen = (int)std::llround(2.0 * fs);
+  std::vector<int> chain_types;
+  for (int t = 0; t < NTYPES; ++t)
+    if (d->type_mask & (1u << t)) chain_types.push_back(t);
+  int64_t poff = 0;
+  c->songs.clear();
+  c->procs.clear();
+  c->chains.clear();
+  c->nrev = 0;
+  c->track_seconds = 0;
+  c->total_samples = 0;
+  for (int si = 0; si < n; ++si) {
+    HostSong hs;
+    hs.K = s[si].num_tracks;
+    hs.S = s[si].num_subgroups;
+    hs.L = (int)s[si].num_samples;
+    hs.ld = (int)round_up(hs.L, 64);
+    hs.group.assign(s[si].track_group, s[si].track_group + hs.K);
+    hs.pbeg = (int)c->procs.size();
+    hs.track_seconds = (double)hs.K * hs.L / fs;
+    c->track_seconds += hs.track_seconds;
+    c->total_samples += hs.L;
+    for (int ch = 0; ch < hs.K + hs.S; ++ch) {
+      HostChain hc;
+      hc.song = si;
+      hc.level = ch < hs.K ? 0 : 1;
+      hc.index = ch < hs.K ? ch : ch - hs.K;
+      hc.L = hs.L;
+      hc.ld = hs.ld;
+      for (int t : chain_types) {
+        HostProc p;
+        p.type = t;
+        p.song = si;
+        p.chain = (int)c->chains.size();
+        p.level = hc.level;
+        p.qidx = (int)c->procs.size();
+        p.rev = t == T_R ? c->nrev++ : -1;
+        p.poff = poff;
+        poff += kParamCount[t];
+        p.L = hs.L;
+        p.ld = hs.ld;
+        if (t == T_E || t == T_R || t == T_D) {
+          if (t == T_E) { p.n0 = -kEqHalf; p.Nh = kEqTaps; }
+          if (t == T_D) { p.n0 = -kDlyHalf; p.Nh = kDlyTaps * D + kDlyFir - 1; }
+          if (t == T_R) { p.n0 = 0; p.Nh = revlen; p.nframes = (revlen - kRevFft) / kRevHop + 1; }
+          p.logN = std::max(12, ilog2_ceil((int64_t)p.L + p.Nh + std::abs(p.n0) + 1));
+          p.logN1 = (p.logN + 1) / 2;
+          p.logN2 = p.logN / 2;
+          p.colG = std::min(8, std::min(8192 >> p.logN2, 1 << p.logN1));
+          p.nfrows = (1 << p.logN1) / p.colG;
+          p.nbrows = p.nfrows;
+          p.scratch_bytes = (size_t)3 * ((size_t)1 << p.logN) * sizeof(float2);
+        } else if (t == T_C || t == T_N) {
+          p.nchunks = (p.L + kDynChunk - 1) / kDynChunk;
+          p.nbrows = p.nchunks;
+        } else {
+          p.nbrows = (p.L + kElemTile - 1) / kElemTile;
+        }
+        hc.procs.push_back((int)c->procs.size());
+        c->procs.push_back(p);
+      }
+      if (hc.level == 0) hs.tracks_chain.push_back((int)c->chains.size());
+      else hs.groups_chain.push_back((int)c->chains.size());
+      c->chains.push_back(hc);
+    }
+    hs.pend = (int)c->procs.size();
+    c->songs.push_back(hs);
+  }
+  c->P = (int)c->procs.size();
+  c->npp = poff;
+  c->nparams = poff + c->P;
+}
+
+// ------------------------------------------------------------------------------------------------
+// host tables (double precision, rounded once to fp32)
+// ------------------------------------------------------------------------------------------------
+double a_weight(double f) {
+  auto ra = [](double x) {
+    const double f2 = x * x;
+    return (12194.0 * 12194.0 * f2 * f2) /
+           ((f2 + 20.6 * 20.6) * std::sqrt((f2 + 107.7 * 107.7) * (f2 + 737.9 * 737.9)) * (f2 + 12194.0 * 12194.0));
+  };
+  return ra(f) / ra(1000.0);
+}
+
+void mel_bank(int nfft, int nmels, double fs, std::vector<std::vector<double>>& W) {
+  const int nb = nfft / 2 + 1;
+  auto hz2mel = [](double f) { return 2595.0 * std::log10(1.0 + f / 700.0); };
+  auto mel2hz = [](double m) { return 700.0 * (std::pow(10.0, m / 2595.0) - 1.0); };
+  std::vector<double> edges(nmels + 2);
+  const double top = hz2mel(fs / 2.0);
+  for (int i = 0; i < nmels + 2; ++i) edges[i] = mel2hz(top * i / (nmels + 1));
+  W.assign(nmels, std::vector<double>(nb, 0.0));
+  for (int b = 0; b < nmels; ++b)
+    for (int k = 0; k < nb; ++k) {
+      const double f = (double)k * fs / nfft;
+      const double lo = edges[b], ce = edges[b + 1], hi = edges[b + 2];
+      W[b][k] = std::max(0.0, std::min((f - lo) / (ce - lo), (hi - f) / (hi - ce)));
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// launching
+// ------------------------------------------------------------------------------------------------
+template <class F>
+void run(mg_console* c, int fam, F&& f) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profiling) {
+    if (c->ev_next + 2 > c->ev_pool.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+      }
+    }
+    e0 = c->ev_pool[c->ev_next++];
+    e1 = c->ev_pool[c->ev_next++];
+    cudaEventRecord(e0, c->stream);
+  }
+  f();
+  ++c->launches;
+  if (c->profiling) {
+    cudaEventRecord(e1, c->stream);
+    auto pr = std::make_pair(fam, std::make_pair(e0, e1));
+    if (c->capturing) c->graph_pairs.push_back(pr);
+    else c->pending.push_back(pr);
+  }
+}
+
+// Launch an item list: once over all items (batched) or once per processor (one-by-one).
+template <class F>
+void run_items(mg_console* c, int fam, const ItemList& L, F&& f) {
+  if (L.h.empty()) return;
+  if (!c->per_node) {
+    run(c, fam, [&] { f(L.d, (int)L.h.size()); });
+    return;
+  }
+  for (size_t i = 0; i + 1 < L.beg.size(); ++i) {
+    const int b = L.beg[i], e = L.beg[i + 1];
+    if (e > b) run(c, fam, [&] { f(L.d + b, e - b); });
+  }
+}
+template <class F>
+void run_procs(mg_console* c, int fam, const ProcList& L, F&& f) {
+  if (L.h.empty()) return;
+  if (!c->per_node) {
+    run(c, fam, [&] { f(L.d, (int)L.h.size()); });
+    return;
+  }
+  for (size_t i = 0; i < L.h.size(); ++i) run(c, fam, [&] { f(L.d + i, 1); });
+}
+
+LaunchCtx make_ctx(mg_console* c, const uint8_t* mask) {
+  LaunchCtx x{};
+  x.stream = c->stream;
+  x.procs = c->d_procs;
+  x.q = c->d_params + c->npp;
+  x.mask = mask;
+  x.hyper = c->d_hyper;
+  x.alpha_g = c->desc.alpha_g;
+  x.fs = c->desc.sample_rate;
+  x.tab = c->tab;
+  return x;
+}
+
+void lti_forward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
+  if (type == T_E) run_procs(c, F_EQ_FIR, g.procs, [&](const int* p, int n) { launch_eq_fir(x, p, n); });
+  if (type == T_D) {
+    run_procs(c, F_DLY_FIR, g.procs, [&](const int* p, int n) { launch_dly_prep(x, p, n); });
+    run_items(c, F_DLY_FIR, g.firtaps, [&](const Item* it, int n) { launch_dly_fir(x, it, n); });
+  }
+  if (type == T_R) run_items(c, F_REV_FIR, g.revfir, [&](const Item* it, int n) { launch_rev_fir(x, it, n); });
+  run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
+  run_items(c, F_ROW_HZ, g.rowhz, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowhz.maxv); });
+  run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_audio(x, it, n, g.col.maxv); });
+  run_items(c, F_ROW_CONV, g.rowpair, [&](const Item* it, int n) { launch_row_conv_fwd(x, it, n, g.rowpair.maxv, false); });
+  run_items(c, F_COL_OUT, g.col, [&](const Item* it, int n) { launch_col_inv_out(x, it, n, g.col.maxv); });
+}
+
+void lti_backward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
+  run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
+  run_items(c, F_ROW_HZ, g.rowhz, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowhz.maxv); });
+  run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_audio(x, it, n, g.col.maxv); });
+  run_items(c, F_ROW_CONV, g.rowpair, [&](const Item* it, int n) { launch_row_conv_fwd(x, it, n, g.rowpair.maxv, true); });
+  run_items(c, F_COL_DYBAR, g.col, [&](const Item* it, int n) { launch_col_dybar(x, it, n, g.col.maxv); });
+  run_items(c, F_ROW_BWD2, g.rowpair, [&](const Item* it, int n) { launch_row_bwd2(x, it, n, g.rowpair.maxv); });
+  run_items(c, F_COL_DU, g.col, [&](const Item* it, int n) { launch_col_du(x, it, n, g.col.maxv); });
+  run_items(c, F_COL_DH, g.col, [&](const Item* it, int n) { launch_col_dh(x, it, n, g.col.maxv); });
+  if (type == T_E) run_procs(c, F_FIR_ADJ, g.procs, [&](const int* p, int n) { launch_eq_fir_adj(x, p, n); });
+  if (type == T_D) run_items(c, F_FIR_ADJ, g.dlyadj, [&](const Item* it, int n) { launch_dly_adj(x, it, n); });
+  if (type == T_R) {
+    run_items(c, F_FIR_ADJ, g.revfir, [&](const Item* it, int n) { launch_rev_adj(x, it, n); });
+    run_procs(c, F_FIR_ADJ, g.procs, [&](const int* p, int n) { launch_rev_adj_fin(x, p, n); });
+  }
+}
+
+void stage_forward(mg_console* c, const LaunchCtx& x, Stage& s) {
+  switch (s.type) {
+    case T_G:
+    case T_S:
+      run_items(c, F_GS_FWD, s.elem, [&](const Item* it, int n) { launch_gs_fwd(x, it, n); });
+      break;
+    case T_C:
+    case T_N:
+      run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd_agg(x, it, n); });
+      run_procs(c, F_DYN_FWD, s.procs, [&](const int* p, int n) { launch_dyn_fwd_carry(x, p, n); });
+      run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd_apply(x, it, n); });
+      break;
+    default:
+      for (auto& g : s.groups) lti_forward(c, x, s.type, g);
+  }
+}
+
+void stage_backward(mg_console* c, const LaunchCtx& x, Stage& s) {
+  switch (s.type) {
+    case T_G:
+    case T_S:
+      run_items(c, F_GS_BWD, s.elem, [&](const Item* it, int n) { launch_gs_bwd(x, it, n); });
+      break;
+    case T_C:
+    case T_N:
+      run_items(c, F_DYN_BWD, s.elem, [&](const Item* it, int n) { launch_dyn_bwd_agg(x, it, n); });
+      run_procs(c, F_DYN_BWD, s.procs, [&](const int* p, int n) { launch_dyn_bwd_carry(x, p, n); });
+      run_items(c, F_DYN_BWD, s.elem, [&](const Item* it, int n) { launch_dyn_bwd_apply(x, it, n); });
+      break;
+    default:
+      for (auto& g : s.groups) lti_backward(c, x, s.type, g);
+  }
+}
+
+void render(mg_console* c, const LaunchCtx& x) {
+  for (int level = 0; level < 2; ++level) {
+    if (level == 1 && !c->sum_m_items.h.empty())
+      run_items(c, F_SUM, c->sum_m_items, [&](const Item* it, int n) {
+        launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n);
+      });
+    for (auto& s : c->stages)
+      if (s.level == level) stage_forward(c, x, s);
+  }
+  run_items(c, F_SUM, c->sum_o_items, [&](const Item* it, int n) {
+    launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n);
+  });
+}
+
+void loss_forward(mg_console* c, const LaunchCtx& x, int mode, float* out_losses, float* out_la, int la_stride) {
+  for (int r = 0; r < c->nres; ++r) {
+    auto& L = c->loss_items[r];
+    if (!L.h.empty())
+      run(c, F_LOSS_FWD, [&] {   // frame kernel: 0 target spectrogram, 1 loss partials (losses and trials)
+        launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), mode == 0 ? 0 : 1, 8192);
+      });
+  }
+  if (mode != 0) run_procs(c, F_FINALIZE, c->all_lti_present, [&](const int* p, int n) { launch_node_stats(x, p, n, 1); });
+  run(c, F_FINALIZE, [&] {
+    launch_loss_finalize_mode(x, c->d_songs, (int)c->songs.size(), c->d_res, c->nres, c->d_alphas, mode, out_losses,
+                              out_la, la_stride);
+  });
+}
+
+void backward_pass(mg_console* c, const LaunchCtx& x) {
+  for (int r = 0; r < c->nres; ++r) {
+    auto& L = c->loss_items[r];
+    if (!L.h.empty())
+      run(c, F_LOSS_BWD, [&] { launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), 2, 8192); });
+  }
+  run_items(c, F_LOSS_GATHER, c->gather_items,
+            [&](const Item* it, int n) { launch_loss_gather(x, c->d_songs, c->d_res, c->nres, it, n); });
+  run(c, F_MISC, [&] { cudaMemsetAsync(c->d_grads, 0, sizeof(float) * c->nparams, c->stream); });
+  for (int level = 1; level >= 0; --level)
+    for (int i = (int)c->stages.size() - 1; i >= 0; --i)
+      if (c->stages[i].level == level) stage_backward(c, x, c->stages[i]);
+  run_procs(c, F_FINALIZE, c->all_present, [&](const int* p, int n) { launch_node_stats(x, p, n, 0); });
+  run_procs(c, F_FINALIZE, c->all_present,
+            [&](const int* p, int n) { launch_grad_finalize2(x, p, n, c->d_grads + c->npp); });
+}
+
+// ------------------------------------------------------------------------------------------------
+// device layout
+// ------------------------------------------------------------------------------------------------
+struct Bump {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    off = (size_t)round_up((int64_t)off, 256);
+    const size_t o = off;
+    off += bytes;
+    return o;
+  }
+};
+
+// Device copy of a host table.  Earlier copies stay allocated until the console is destroyed (tables are
+// rebuilt only by mg_prune), so no pointer captured in a graph or kernel argument ever dangles.
+template <class T>
+mg_status upload(mg_console* c, std::vector<T>& h, T** d) {
+  *d = nullptr;
+  if (h.empty()) return MG_OK;
+  CK(cudaMalloc(d, h.size() * sizeof(T)));
+  CK(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  c->small_allocs.push_back(*d);
+  return MG_OK;
+}
+mg_status upload_items(mg_console* c, ItemList& L) { return upload(c, L.h, &L.d); }
+mg_status upload_procs(mg_console* c, ProcList& L) { return upload(c, L.h, &L.d); }
+
+// Pointers of the node table for the current structure (present processors), stage lists and launch lists.
+mg_status build_tables(mg_console* c) {
+  auto A = [&](size_t off) { return c->arena + off; };
+  c->hpd.assign(c->P, ProcDev{});
+  // forward / backward wiring per chain
+  std::vector<size_t> chain_out(c->chains.size());
+  for (size_t ci = 0; ci < c->chains.size(); ++ci) {
+    const HostChain& ch = c->chains[ci];
+    size_t cur = ch.o_in;
+    for (int pi : ch.procs) {
+      HostProc& p = c->procs[pi];
+      ProcDev& d = c->hpd[pi];
+      d.present = p.present;
+      if (!p.present) continue;
+      d.u = (const float*)A(cur);
+      d.y = (float*)A(p.o_y);
+      cur = p.o_y;
+    }
+    chain_out[ci] = cur;
+  }
+  // adjoints: chain output adjoint
+  std::vector<size_t> chain_dout(c->chains.size()), chain_din(c->chains.size());
+  for (int level = 1; level >= 0; --level) {
+    for (size_t ci = 0; ci < c->chains.size(); ++ci) {
+      const HostChain& ch = c->chains[ci];
+      if (ch.level != level) continue;
+      const HostSong& s = c->songs[ch.song];
+      size_t dout = s.o_dmix;
+      if (level == 0 && s.group[ch.index] >= 0) dout = chain_din[s.groups_chain[s.group[ch.index]]];
+      chain_dout[ci] = dout;
+      size_t cur = dout;
+      bool useA = true;
+      for (int k = (int)ch.procs.size() - 1; k >= 0; --k) {
+        const int pi = ch.procs[k];
+        if (!c->procs[pi].present) continue;
+        ProcDev& d = c->hpd[pi];
+        d.dy = (const float*)A(cur);
+        const size_t nxt = useA ? ch.o_dA : ch.o_dB;
+        d.du = (float*)A(nxt);
+        cur = nxt;
+        useA = !useA;
+      }
+      chain_din[ci] = cur;
+    }
+  }
+  for (int pi = 0; pi < c->P; ++pi) {
+    HostProc& p = c->procs[pi];
+    ProcDev& d = c->hpd[pi];
+    d.type = p.type;
+    d.song = p.song;
+    d.qidx = p.qidx;
+    d.rev = p.rev;
+    d.L = p.L;
+    d.ld = p.ld;
+    d.p = c->d_params + p.poff;
+    d.gp = c->d_grads + p.poff;
+    d.stats = (float*)A(p.o_stats);
+    d.fpart = p.nfrows ? (float*)A(p.o_fpart) : nullptr;
+    d.bpart = p.nbrows ? (float*)A(p.o_bpart) : nullptr;
+    d.nfpart = p.nfrows;
+    d.nbpart = p.nbrows;
+    d.logN = p.logN;
+    d.logN1 = p.logN1;
+    d.logN2 = p.logN2;
+    d.colG = p.colG;
+    d.n0 = p.n0;
+    d.Nh = p.Nh;
+    if (p.scratch_bytes) {
+      const size_t N = (size_t)1 << p.logN;
+      d.T1 = (float2*)(c->scratch + p.o_scratch);
+      d.T2 = d.T1 + N;
+      d.Hz = d.T2 + N;
+      d.taps = (float*)A(p.o_taps);
+      d.dtaps = (float*)A(p.o_dtaps);
+    }
+    d.aux = p.o_aux ? (float*)A(p.o_aux) : nullptr;
+    d.carry = p.nchunks ? (float*)A(p.o_carry) : nullptr;
+    d.rcarry = p.nchunks ? (float*)A(p.o_rcarry) : nullptr;
+    d.chunkagg = p.nchunks ? (float*)A(p.o_cagg) : nullptr;
+    d.nchunks = p.nchunks;
+    d.nspec = p.type == T_R ? (const float2*)A(p.o_nspec) : nullptr;
+    d.nframes = p.nframes;
+  }
+  if (upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
+
+  // sums: m per subgroup (level 1 inputs), o per song
+  c->sum_out.h.clear(); c->sum_in.h.clear(); c->sum_beg.h.clear(); c->sum_L.h.clear(); c->sum_ld.h.clear();
+  c->sum_m_items = ItemList{}; c->sum_o_items = ItemList{};
+  int sid = 0;
+  auto add_sum = [&](size_t out, const std::vector<size_t>& ins, int L, int ld, ItemList& items) {
+    c->sum_beg.h.push_back((int)c->sum_in.h.size());
+    c->sum_out.h.push_back((float*)A(out));
+    for (size_t o : ins) c->sum_in.h.push_back((const float*)A(o));
+    c->sum_L.h.push_back(L);
+    c->sum_ld.h.push_back(ld);
+    items.beg.push_back((int)items.h.size());
+    for (int t = 0; t < (L + kElemTile - 1) / kElemTile; ++t) items.h.push_back(Item{sid, t});
+    ++sid;
+  };
+  for (auto& s : c->songs)
+    for (int g = 0; g < s.S; ++g) {
+      std::vector<size_t> ins;
+      for (int k = 0; k < s.K; ++k)
+        if (s.group[k] == g) ins.push_back(chain_out[s.tracks_chain[k]]);
+      add_sum(c->chains[s.groups_chain[g]].o_in, ins, s.L, s.ld, c->sum_m_items);
+    }
+  c->sum_m_items.beg.push_back((int)c->sum_m_items.h.size());
+  for (auto& s : c->songs) {
+    std::vector<size_t> ins;
+    for (int g = 0; g < s.S; ++g) ins.push_back(chain_out[s.groups_chain[g]]);
+    for (int k = 0; k < s.K; ++k)
+      if (s.group[k] < 0) ins.push_back(chain_out[s.tracks_chain[k]]);
+    add_sum(s.o_mix, ins, s.L, s.ld, c->sum_o_items);
+  }
+  c->sum_o_items.beg.push_back((int)c->sum_o_items.h.size());
+  c->sum_beg.h.push_back((int)c->sum_in.h.size());
+  if (upload(c, c->sum_out.h, &c->sum_out.d) || upload(c, c->sum_in.h, &c->sum_in.d) ||
+      upload(c, c->sum_beg.h, &c->sum_beg.d) || upload(c, c->sum_L.h, &c->sum_L.d) ||
+      upload(c, c->sum_ld.h, &c->sum_ld.d) || upload_items(c, c->sum_m_items) || upload_items(c, c->sum_o_items))
+    return MG_ERR_CUDA;
+
+  // stages in console order: level 0 types e..r, level 1 types e..r
+  c->stages.clear();
+  c->all_present = ProcList{};
+  c->all_lti_present = ProcList{};
+  const int64_t limit = c->desc.workspace_limit_bytes > 0 ? c->desc.workspace_limit_bytes : INT64_MAX;
+  for (int level = 0; level < 2; ++level)
+    for (int t = 0; t < NTYPES; ++t) {
+      Stage st;
+      st.level = level;
+      st.type = t;
+      for (int pi = 0; pi < c->P; ++pi) {
+        const HostProc& p = c->procs[pi];
+        if (p.level != level || p.type != t || !p.present) continue;
+        st.procs.h.push_back(pi);
+        c->all_present.h.push_back(pi);
+        if (t == T_E || t == T_R || t == T_D) c->all_lti_present.h.push_back(pi);
+      }
+      if (st.procs.h.empty()) continue;
+      if (t == T_G || t == T_S || t == T_C || t == T_N) {
+        for (int pi : st.procs.h) {
+          st.elem.beg.push_back((int)st.elem.h.size());
+          const int nt = (t == T_C || t == T_N) ? c->procs[pi].nchunks : c->procs[pi].nbrows;
+          for (int i = 0; i < nt; ++i) st.elem.h.push_back(Item{pi, i});
+        }
+        st.elem.beg.push_back((int)st.elem.h.size());
+        if (upload_items(c, st.elem) || upload_procs(c, st.procs)) return MG_ERR_CUDA;
+      } else {
+        // LTI: groups under the workspace limit, each with its own scratch offsets
+        size_t used = 0;
+        LtiGroup g;
+        auto close = [&]() -> mg_status {
+          if (g.procs.h.empty()) return MG_OK;
+          for (ItemList* L : {&g.col, &g.rowhz, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
+            L->beg.push_back((int)L->h.size());
+          if (upload_procs(c, g.procs) || upload_items(c, g.col) || upload_items(c, g.rowhz) ||
+              upload_items(c, g.rowpair) || upload_items(c, g.firtaps) || upload_items(c, g.dlyadj) ||
+              upload_items(c, g.revfir))
+            return MG_ERR_CUDA;
+          st.groups.push_back(g);
+          g = LtiGroup{};
+          used = 0;
+          return MG_OK;
+        };
+        for (int pi : st.procs.h) {
+          HostProc& p = c->procs[pi];
+          if (used > 0 && (int64_t)(used + p.scratch_bytes) > limit)
+            if (close() != MG_OK) return MG_ERR_CUDA;
+          p.o_scratch = used;
+          used += p.scratch_bytes;
+          ProcDev& d = c->hpd[pi];
+          const size_t N = (size_t)1 << p.logN;
+          d.T1 = (float2*)(c->scratch + p.o_scratch);
+          d.T2 = d.T1 + N;
+          d.Hz = d.T2 + N;
+          g.procs.h.push_back(pi);
+          const int N1 = 1 << p.logN1, N2 = 1 << p.logN2;
+          for (ItemList* L : {&g.col, &g.rowhz, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
+            L->beg.push_back((int)L->h.size());
+          for (int i = 0; i < N1 / p.colG; ++i) g.col.h.push_back(Item{pi, i});
+          g.col.maxv = std::max(g.col.maxv, N2 * p.colG);
+          for (int i = 0; i < N2; ++i) g.rowhz.h.push_back(Item{pi, i});
+          g.rowhz.maxv = std::max(g.rowhz.maxv, N1);
+          for (int i = 0; i <= N2 / 2; ++i) g.rowpair.h.push_back(Item{pi, i});
+          g.rowpair.maxv = std::max(g.rowpair.maxv, N1);
+          if (t == T_D) {
+            for (int i = 0; i < (p.Nh + 255) / 256; ++i) g.firtaps.h.push_back(Item{pi, i});
+            for (int i = 0; i < 2 * kDlyTaps; ++i) g.dlyadj.h.push_back(Item{pi, i});
+          }
+          if (t == T_R) {
+            const int ng = (p.nframes + kRevFG - 1) / kRevFG;
+            for (int i = 0; i < ng; ++i) g.revfir.h.push_back(Item{pi, i});
+          }
+        }
+        if (close() != MG_OK) return MG_ERR_CUDA;
+      }
+      c->stages.push_back(st);
+    }
+  // scratch pointers changed with grouping: re-upload the node table
+  if (upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
+  if (upload_procs(c, c->all_present) || upload_procs(c, c->all_lti_present)) return MG_ERR_CUDA;
+  return MG_OK;
+}
+
+mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
+  plan(c, d, s, n);
+  init_kernel_attributes();
+  init_loss_attributes();
+  init_fir_attributes();
+  const double fs = d->sample_rate;
+  // ---- arena layout ----
+  Bump b;
+  for (auto& hs : c->songs) {
+    const size_t st = (size_t)2 * hs.ld * sizeof(float);
+    hs.o_mix = b.take(st);
+    hs.o_dmix = b.take(st);
+    hs.o_tgt = b.take(st);
+    for (int r = 0; r < c->nres; ++r) {
+      const int nf = d->n_fft[r], hop = nf / d->hop_div;
+      hs.nframes[r] = hs.L >= nf ? (hs.L - nf) / hop + 1 : 0;
+      hs.first[r] = std::min(hs.nframes[r], (int)((d->warmup_samples + hop - 1) / hop));
+      const int per = 8192 / nf;
+      hs.litems[r] = (hs.nframes[r] - hs.first[r] + per - 1) / per;
+      hs.lcap = std::max(hs.lcap, hs.litems[r]);
+      const int nbands = d->n_mels > 0 ? d->n_mels : nf / 2 + 1;
+      hs.o_Y[r] = b.take((size_t)std::max(1, hs.nframes[r]) * nbands * 4 * sizeof(float));
+      hs.o_dF[r] = b.take((size_t)std::max(1, hs.nframes[r]) * nf * sizeof(float2));
+    }
+    hs.o_lpart = b.take((size_t)3 * std::max(1, hs.lcap) * 6 * sizeof(float));
+    hs.o_coef = b.take(18 * sizeof(float));
+    hs.o_ynorm = b.take(9 * sizeof(double));
+  }
+  for (auto& ch : c->chains) {
+    const size_t st = (size_t)2 * ch.ld * sizeof(float);
+    ch.o_in = b.take(st);
+    ch.o_dA = b.take(st);
+    ch.o_dB = b.take(st);
+  }
+  size_t scratch_need = 0;
+  for (auto& p : c->procs) {
+    p.o_y = b.take((size_t)2 * p.ld * sizeof(float));
+    p.o_stats = b.take(16 * sizeof(float));
+    if (p.nfrows) p.o_fpart = b.take((size_t)p.nfrows * kNPart * sizeof(float));
+    if (p.nbrows) p.o_bpart = b.take((size_t)p.nbrows * kNPart * sizeof(float));
+    if (p.scratch_bytes) {
+      p.o_taps = b.take((size_t)2 * p.Nh * sizeof(float));
+      p.o_dtaps = b.take((size_t)2 * p.Nh * sizeof(float));
+      scratch_need = std::max(scratch_need, p.scratch_bytes);
+    }
+    if (p.type == T_D) p.o_aux = b.take((2 * kDlyTaps * kDlyFir + 2 * kDlyTaps) * sizeof(float));
+    if (p.type == T_R) {
+      const int ng = (p.nframes + kRevFG - 1) / kRevFG;
+      p.o_aux = b.take((size_t)2 * ng * kRevBins * 2 * sizeof(float));
+      p.o_nspec = b.take((size_t)2 * p.nframes * kRevBins * sizeof(float2));
+    }
+    if (p.nchunks) {
+      p.o_carry = b.take(p.nchunks * sizeof(float));
+      p.o_rcarry = b.take(p.nchunks * sizeof(float));
+      p.o_cagg = b.take(p.nchunks * sizeof(float));
+    }
+  }
+  // LTI scratch: the largest stage group (the stage lists are built later; size for the worst case)
+  {
+    const int64_t limit = d->workspace_limit_bytes > 0 ? d->workspace_limit_bytes : INT64_MAX;
+    size_t worst = 0;
+    for (int level = 0; level < 2; ++level)
+      for (int t : {T_E, T_R, T_D}) {
+        size_t used = 0;
+        for (auto& p : c->procs) {
+          if (p.level != level || p.type != t) continue;
+          if (used > 0 && (int64_t)(used + p.scratch_bytes) > limit) used = 0;
+          used += p.scratch_bytes;
+          worst = std::max(worst, used);
+        }
+      }
+    c->scratch_bytes = std::max(worst, scratch_need);
+  }
+  c->arena_bytes = b.off;
+  // ---- allocations ----
+  CK(cudaMalloc(&c->arena, c->arena_bytes));
+  CK(cudaMemsetAsync(c->arena, 0, c->arena_bytes, c->stream));
+  if (c->scratch_bytes) CK(cudaMalloc(&c->scratch, c->scratch_bytes));
+  CK(cudaMalloc(&c->d_params, sizeof(float) * c->nparams));
+  CK(cudaMalloc(&c->d_grads, sizeof(float) * c->nparams));
+  CK(cudaMalloc(&c->d_m, sizeof(float) * c->nparams));
+  CK(cudaMalloc(&c->d_v, sizeof(float) * c->nparams));
+  CK(cudaMalloc(&c->d_step, sizeof(int)));
+  CK(cudaMalloc(&c->d_hyper, 8 * sizeof(float)));
+  CK(cudaMalloc(&c->d_alphas, 4 * sizeof(float)));
+  CK(cudaMalloc(&c->d_mask, std::max(1, c->P)));
+  CK(cudaMemsetAsync(c->d_params, 0, sizeof(float) * c->nparams, c->stream));
+  CK(cudaMemsetAsync(c->d_grads, 0, sizeof(float) * c->nparams, c->stream));
+  CK(cudaMemsetAsync(c->d_m, 0, sizeof(float) * c->nparams, c->stream));
+  CK(cudaMemsetAsync(c->d_v, 0, sizeof(float) * c->nparams, c->stream));
+  CK(cudaMemsetAsync(c->d_step, 0, sizeof(int), c->stream));
+  CK(cudaMemsetAsync(c->d_hyper, 0, 8 * sizeof(float), c->stream));
+  {
+    const float al[4] = {d->alpha_lr, d->alpha_m, d->alpha_s, 0.f};
+    CK(cudaMemcpy(c->d_alphas, al, sizeof(al), cudaMemcpyHostToDevice));
+  }
+  // ---- tables ----
+  auto up_table = [&](const void* h, size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    cudaMemcpy(p, h, bytes, cudaMemcpyHostToDevice);
+    c->table_allocs.push_back(p);
+    return p;
+  };
+  {
+    const double PI = 3.14159265358979323846;
+    std::vector<float2> tw(kTwN);
+    for (int j = 0; j < kTwN; ++j) tw[j] = make_float2((float)std::cos(2 * PI * j / kTwN), (float)-std::sin(2 * PI * j / kTwN));
+    std::vector<float> ceq(kEqTaps), cdl(kDlyFir), hwin(kRevFft), heq(kEqTaps), hdl(kDlyFir);
+    for (int m = 0; m < kEqTaps; ++m) ceq[m] = (float)std::cos(2 * PI * m / kEqTaps);
+    for (int m = 0; m < kDlyFir; ++m) cdl[m] = (float)std::cos(2 * PI * m / kDlyFir);
+    for (int j = 0; j < kRevFft; ++j) hwin[j] = (float)(0.5 * (1.0 - std::cos(2 * PI * j / kRevFft)));
+    std::vector<float2> rcs(kRevFft);
+    for (int m = 0; m < kRevFft; ++m) rcs[m] = make_float2((float)std::cos(2 * PI * m / kRevFft), (float)std::sin(2 * PI * m / kRevFft));
+    for (int j = 0; j < kEqTaps; ++j) heq[j] = (float)(0.5 * (1.0 + std::cos(2 * PI * (j - kEqHalf) / (kEqTaps - 1))));
+    for (int j = 0; j < kDlyFir; ++j) hdl[j] = (float)(0.5 * (1.0 + std::cos(2 * PI * (j - kDlyHalf) / (kDlyFir - 1))));
+    const int D = (int)std::llround(0.1 * fs);
+    std::vector<float2> dw(D);
+    for (int q = 0; q < D; ++q) dw[q] = make_float2((float)std::cos(2 * PI * q / D), (float)std::sin(2 * PI * q / D));
+    c->tab.tw = (const float2*)up_table(tw.data(), tw.size() * sizeof(float2));
+    c->tab.cos_eq = (const float*)up_table(ceq.data(), ceq.size() * sizeof(float));
+    c->tab.cos_dl = (const float*)up_table(cdl.data(), cdl.size() * sizeof(float));
+    c->tab.rev_win = (const float*)up_table(hwin.data(), hwin.size() * sizeof(float));
+    c->tab.rev_cs = (const float2*)up_table(rcs.data(), rcs.size() * sizeof(float2));
+    c->tab.hann_eq = (const float*)up_table(heq.data(), heq.size() * sizeof(float));
+    c->tab.hann_dl = (const float*)up_table(hdl.data(), hdl.size() * sizeof(float));
+    c->tab.dly_w = (const float2*)up_table(dw.data(), dw.size() * sizeof(float2));
+    if (!c->tab.tw || !c->tab.dly_w) return fail(c, MG_ERR_OOM, "table allocation failed");
+  }
+  // loss resolutions
+  c->hres.assign(c->nres, LossRes{});
+  for (int r = 0; r < c->nres; ++r) {
+    const int nf = d->n_fft[r], nb = nf / 2 + 1;
+    LossRes& R = c->hres[r];
+    R.nfft = nf;
+    R.log_nfft = ilog2_ceil(nf);
+    R.hop = nf / d->hop_div;
+    std::vector<float> win(nf), aw2(nb);
+    const double PI = 3.14159265358979323846;
+    for (int j = 0; j < nf; ++j) win[j] = (float)(0.5 * (1.0 - std::cos(2 * PI * j / nf)));
+    for (int k = 0; k < nb; ++k) {
+      const double a = d->a_weighting ? a_weight((double)k * fs / nf) : 1.0;
+      aw2[k] = (float)(a * a);
+    }
+    std::vector<int> bb, bbin, kb, kband;
+    std::vector<float> bw, kw;
+    if (d->n_mels > 0) {
+      std::vector<std::vector<double>> W;
+      mel_bank(nf, d->n_mels, fs, W);
+      R.nbands = d->n_mels;
+      for (int b2 = 0; b2 < d->n_mels; ++b2) {
+        bb.push_back((int)bbin.size());
+        for (int k = 0; k < nb; ++k)
+          if (W[b2][k] > 0) { bbin.push_back(k); bw.push_back((float)W[b2][k]); }
+      }
+      bb.push_back((int)bbin.size());
+      for (int k = 0; k < nb; ++k) {
+        kb.push_back((int)kband.size());
+        for (int b2 = 0; b2 < d->n_mels; ++b2)
+          if (W[b2][k] > 0) { kband.push_back(b2); kw.push_back((float)W[b2][k]); }
+      }
+      kb.push_back((int)kband.size());
+    } else {
+      R.nbands = nb;
+      for (int k = 0; k < nb; ++k) { bb.push_back(k); bbin.push_back(k); bw.push_back(1.f); kb.push_back(k); kband.push_back(k); kw.push_back(1.f); }
+      bb.push_back(nb);
+      kb.push_back(nb);
+    }
+    if (bbin.empty()) { bbin.push_back(0); bw.push_back(0.f); }
+    if (kband.empty()) { kband.push_back(0); kw.push_back(0.f); }
+    R.win = (const float*)up_table(win.data(), win.size() * sizeof(float));
+    R.aw2 = (const float*)up_table(aw2.data(), aw2.size() * sizeof(float));
+    R.band_beg = (const int*)up_table(bb.data(), bb.size() * sizeof(int));
+    R.band_bin = (const int*)up_table(bbin.data(), bbin.size() * sizeof(int));
+    R.band_w = (const float*)up_table(bw.data(), bw.size() * sizeof(float));
+    R.bin_beg = (const int*)up_table(kb.data(), kb.size() * sizeof(int));
+    R.bin_band = (const int*)up_table(kband.data(), kband.size() * sizeof(int));
+    R.bin_w = (const float*)up_table(kw.data(), kw.size() * sizeof(float));
+  }
+  if (upload(c, c->hres, &c->d_res) != MG_OK) return MG_ERR_CUDA;
+  // songs on device
+  c->hsd.assign(c->songs.size(), SongDev{});
+  std::vector<int64_t> mixoff;
+  int64_t moff = 0;
+  for (size_t si = 0; si < c->songs.size(); ++si) {
+    HostSong& hs = c->songs[si];
+    SongDev& sd = c->hsd[si];
+    sd.L = hs.L;
+    sd.ld = hs.ld;
+    for (int r = 0; r < 3; ++r) {
+      sd.nframes[r] = hs.nframes[r];
+      sd.first_frame[r] = hs.first[r];
+      sd.litems[r] = r < c->nres ? hs.litems[r] : 0;
+      sd.Y[r] = r < c->nres ? (float*)(c->arena + hs.o_Y[r]) : nullptr;
+      sd.dF[r] = r < c->nres ? (float*)(c->arena + hs.o_dF[r]) : nullptr;
+    }
+    sd.lcap = std::max(1, hs.lcap);
+    sd.mix = (const float*)(c->arena + hs.o_mix);
+    sd.dmix = (float*)(c->arena + hs.o_dmix);
+    sd.target = (const float*)(c->arena + hs.o_tgt);
+    sd.lpart = (float*)(c->arena + hs.o_lpart);
+    sd.coef = (float*)(c->arena + hs.o_coef);
+    sd.ynorm2 = (double*)(c->arena + hs.o_ynorm);
+    sd.pbeg = hs.pbeg;
+    sd.pend = hs.pend;
+    mixoff.push_back(moff);
+    moff += 2 * (int64_t)hs.L;
+  }
+  if (upload(c, c->hsd, &c->d_songs) || upload(c, mixoff, &c->d_mixoff)) return MG_ERR_CUDA;
+  // loss items
+  for (int r = 0; r < c->nres; ++r) {
+    auto& L = c->loss_items[r];
+    L.h.clear();
+    const int per = 8192 / d->n_fft[r];
+    for (size_t si = 0; si < c->songs.size(); ++si) {
+      const HostSong& hs = c->songs[si];
+      for (int t = hs.first[r]; t < hs.nframes[r]; t += per)
+        L.h.push_back(make_int4((int)si, r, t, std::min(per, hs.nframes[r] - t)));
+    }
+    if (upload(c, L.h, &L.d) != MG_OK) return MG_ERR_CUDA;
+  }
+  c->gather_items = ItemList{};
+  for (size_t si = 0; si < c->songs.size(); ++si) {
+    c->gather_items.beg.push_back((int)c->gather_items.h.size());
+    for (int t = 0; t < (c->songs[si].L + kElemTile - 1) / kElemTile; ++t) c->gather_items.h.push_back(Item{(int)si, t});
+  }
+  c->gather_items.beg.push_back((int)c->gather_items.h.size());
+  if (upload_items(c, c->gather_items) != MG_OK) return MG_ERR_CUDA;
+  // ---- audio ----
+  {
+    float* tmp = nullptr;
+    size_t tmpn = 0;
+    for (size_t si = 0; si < c->songs.size(); ++si) {
+      const HostSong& hs = c->songs[si];
+      const size_t need = (size_t)hs.K * hs.L;
+      if (need > tmpn) {
+        if (tmp) cudaFree(tmp);
+        CK(cudaMalloc(&tmp, need * sizeof(float)));
+        tmpn = need;
+      }
+      if (!s[si].sources) return fail(c, MG_ERR_INVALID, "sources is null");
+      CK(cudaMemcpyAsync(tmp, s[si].sources, need * sizeof(float),
+                         s[si].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+      for (int k = 0; k < hs.K; ++k)
+        launch_ingest(c->stream, tmp + (size_t)k * hs.L, (float*)(c->arena + c->chains[hs.tracks_chain[k]].o_in), hs.L, hs.ld);
+      if (s[si].target) {
+        CK(cudaMemcpy2DAsync(c->arena + hs.o_tgt, (size_t)hs.ld * sizeof(float), s[si].target, (size_t)hs.L * sizeof(float),
+                             (size_t)hs.L * sizeof(float), 2,
+                             s[si].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+      }
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    if (tmp) cudaFree(tmp);
+  }
+  // ---- tables of the node structure ----
+  if (build_tables(c) != MG_OK) return MG_ERR_CUDA;
+  // ---- reverb noise spectra ----
+  if (c->nrev > 0) {
+    if (!d->reverb_noise) return fail(c, MG_ERR_INVALID, "reverb_noise is required when reverbs are enabled");
+    const int rl = (int)std::llround(2.0 * fs);
+    float* nz = nullptr;
+    const size_t bytes = (size_t)c->nrev * 2 * rl * sizeof(float);
+    CK(cudaMalloc(&nz, bytes));
+    CK(cudaMemcpyAsync(nz, d->reverb_noise, bytes, d->noise_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream));
+    ItemList it;
+    for (int pi = 0; pi < c->P; ++pi)
+      if (c->procs[pi].type == T_R)
+        for (int i = 0; i < (c->procs[pi].nframes + kRevFG - 1) / kRevFG; ++i) it.h.push_back(Item{pi, i});
+    if (upload_items(c, it) != MG_OK) return MG_ERR_CUDA;
+    LaunchCtx x = make_ctx(c, nullptr);
+    launch_rev_noise_stft(x, it.d, (int)it.h.size(), nz, rl);
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(nz);
+  }
+  // ---- target spectrograms ----
+  {
+    LaunchCtx x = make_ctx(c, nullptr);
+    const bool prof = c->profiling;
+    c->profiling = false;
+    loss_forward(c, x, 0, nullptr, nullptr, 0);
+    c->profiling = prof;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+void destroy_impl(mg_console* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (void* p : c->small_allocs) cudaFree(p);
+  for (void* p : c->table_allocs) cudaFree(p);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  cudaFree(c->arena);
+  cudaFree(c->scratch);
+  cudaFree(c->d_params);
+  cudaFree(c->d_grads);
+  cudaFree(c->d_m);
+  cudaFree(c->d_v);
+  cudaFree(c->d_step);
+  cudaFree(c->d_hyper);
+  cudaFree(c->d_alphas);
+  cudaFree(c->d_mask);
+  cudaFree(c->d_scratch_la);
+}
+
+void fill_info(const mg_console* c, mg_console_info* o) {
+  o->n_songs = (int32_t)c->songs.size();
+  o->n_processors = c->P;
+  o->n_proc_params = c->npp;
+  o->n_params = c->nparams;
+  o->n_reverbs = c->nrev;
+  o->total_samples = c->total_samples;
+  o->track_seconds = c->track_seconds;
+  o->device_bytes = (int64_t)(c->arena_bytes + c->scratch_bytes + 4 * sizeof(float) * c->nparams);
+  o->launches_per_step = c->launches_step;
+}
+
+}  // namespace
+
+// ==================================================================================================
+// C ABI
+// ==================================================================================================
+extern "C" {
+
+mg_status mg_plan(const mg_console_desc* desc, const mg_song_desc* songs, int32_t n_songs, mg_console_info* out) {
+  if (!out) return fail(nullptr, MG_ERR_INVALID, "out is null");
+  mg_console tmp;
+  mg_status st = validate(&tmp, desc, songs, n_songs);
+  if (st != MG_OK) {
+    g_static_err = tmp.err;
+    return st;
+  }
+  plan(&tmp, desc, songs, n_songs);
+  fill_info(&tmp, out);
+  out->device_bytes = 0;
+  out->launches_per_step = 0;
+  return MG_OK;
+}
+
+mg_status mg_console_create(const mg_console_desc* desc, const mg_song_desc* songs, int32_t n_songs, cudaStream_t stream,
+                            mg_console** out) {
+  if (!out) return fail(nullptr, MG_ERR_INVALID, "out is null");
+  *out = nullptr;
+  mg_console* c = new (std::nothrow) mg_console();
+  if (!c) return fail(nullptr, MG_ERR_OOM, "host allocation failed");
+  c->stream = stream;
+  mg_status st = validate(c, desc, songs, n_songs);
+  if (st == MG_OK) st = create_impl(c, desc, songs, n_songs);
+  if (st != MG_OK) {
+    g_static_err = c->err;
+    destroy_impl(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return MG_OK;
+}
+
+mg_status mg_console_destroy(mg_console* c) {
+  if (!c) return MG_ERR_INVALID;
+  cudaStreamSynchronize(c->stream);
+  destroy_impl(c);
+  delete c;
+  return MG_OK;
+}
+
+mg_status mg_console_get_info(const mg_console* c, mg_console_info* out) {
+  if (!c || !out) return MG_ERR_INVALID;
+  fill_info(c, out);
+  return MG_OK;
+}
+
+mg_status mg_processor_layout(const mg_console* c, int32_t* types, int64_t* param_offset, int32_t* song) {
+  if (!c) return MG_ERR_INVALID;
+  for (int i = 0; i < c->P; ++i) {
+    if (types) types[i] = c->procs[i].type;
+    if (param_offset) param_offset[i] = c->procs[i].poff;
+    if (song) song[i] = c->procs[i].song;
+  }
+  return MG_OK;
+}
+
+static mg_status copy_vec(mg_console* c, float* dst, const float* src, int64_t n, int on_device, bool to_dev) {
+  if (!c || !dst || !src) return fail(c, MG_ERR_INVALID, "null pointer");
+  if (n != c->nparams) return fail(c, MG_ERR_INVALID, "size must equal n_params");
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+  CK(cudaMemcpyAsync(dst, src, sizeof(float) * n, k, c->stream));
+  if (!on_device && !to_dev) CK(cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+mg_status mg_set_params(mg_console* c, const float* params, int64_t n, int32_t on_device) {
+  mg_status s = copy_vec(c, c ? c->d_params : nullptr, params, n, on_device, true);
+  if (s == MG_OK) c->fwd_valid = false;
+  return s;
+}
+mg_status mg_get_params(const mg_console* c, float* out, int64_t n, int32_t on_device) {
+  mg_console* m = const_cast<mg_console*>(c);
+  return copy_vec(m, out, m ? m->d_params : nullptr, n, on_device, false);
+}
+mg_status mg_get_grads(const mg_console* c, float* out, int64_t n, int32_t on_device) {
+  mg_console* m = const_cast<mg_console*>(c);
+  return copy_vec(m, out, m ? m->d_grads : nullptr, n, on_device, false);
+}
+
+mg_status mg_set_alpha_p(mg_console* c, float alpha_p) {
+  if (!c) return MG_ERR_INVALID;
+  c->alpha_p = alpha_p;
+  launch_set_hyper(c->stream, c->d_hyper, alpha_p, 0, 0, 0, 0, 0, 0);
+  c->fwd_valid = false;
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_forward_loss(mg_console* c, const uint8_t* d_mask, float* d_losses, float* d_mix) {
+  if (!c) return MG_ERR_INVALID;
+  if (d_mask) CK(cudaMemcpyAsync(c->d_mask, d_mask, c->P, cudaMemcpyDeviceToDevice, c->stream));
+  LaunchCtx x = make_ctx(c, d_mask ? c->d_mask : nullptr);
+  render(c, x);
+  loss_forward(c, x, 1, d_losses, nullptr, 0);
+  if (d_mix) run(c, F_MISC, [&] { launch_copy_mix(c->stream, c->d_songs, (int)c->songs.size(), d_mix, c->d_mixoff); });
+  CK(cudaGetLastError());
+  c->fwd_valid = d_mask == nullptr;
+  return MG_OK;
+}
+
+mg_status mg_backward(mg_console* c) {
+  if (!c) return MG_ERR_INVALID;
+  if (!c->fwd_valid) return fail(c, MG_ERR_STATE, "mg_backward needs a preceding unmasked mg_forward_loss with unchanged state");
+  LaunchCtx x = make_ctx(c, nullptr);
+  backward_pass(c, x);
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_prune_scores(mg_console* c, const uint8_t* d_masks, int32_t n_masks, float* d_la) {
+  if (!c || !d_masks || !d_la || n_masks < 0) return fail(c, MG_ERR_INVALID, "null pointer or negative count");
+  for (int j = 0; j < n_masks; ++j) {
+    CK(cudaMemcpyAsync(c->d_mask, d_masks + (size_t)j * c->P, c->P, cudaMemcpyDeviceToDevice, c->stream));
+    LaunchCtx x = make_ctx(c, c->d_mask);
+    render(c, x);
+    loss_forward(c, x, 2, nullptr, d_la + (size_t)j * c->songs.size(), 1);
+  }
+  c->fwd_valid = false;
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_adam_step(mg_console* c, float lr, float beta1, float beta2, float eps, float weight_decay) {
+  if (!c) return MG_ERR_INVALID;
+  launch_set_hyper(c->stream, c->d_hyper, 0, lr, beta1, beta2, eps, weight_decay, 1);
+  run(c, F_ADAM, [&] { launch_adam2(c->stream, c->d_hyper, c->d_step, c->d_params, c->d_grads, c->d_m, c->d_v, c->nparams); });
+  c->fwd_valid = false;
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_reset_optimizer(mg_console* c) {
+  if (!c) return MG_ERR_INVALID;
+  CK(cudaMemsetAsync(c->d_m, 0, sizeof(float) * c->nparams, c->stream));
+  CK(cudaMemsetAsync(c->d_v, 0, sizeof(float) * c->nparams, c->stream));
+  CK(cudaMemsetAsync(c->d_step, 0, sizeof(int), c->stream));
+  return MG_OK;
+}
+
+mg_status mg_train_step(mg_console* c, float lr, float beta1, float beta2, float eps, float weight_decay, float* d_losses) {
+  if (!c) return MG_ERR_INVALID;
+  launch_set_hyper(c->stream, c->d_hyper, 0, lr, beta1, beta2, eps, weight_decay, 1);
+  if (c->per_node) {  // one-by-one processing runs eagerly (no graph)
+    LaunchCtx x = make_ctx(c, nullptr);
+    render(c, x);
+    loss_forward(c, x, 1, d_losses, nullptr, 0);
+    backward_pass(c, x);
+    run(c, F_ADAM, [&] { launch_adam2(c->stream, c->d_hyper, c->d_step, c->d_params, c->d_grads, c->d_m, c->d_v, c->nparams); });
+    c->fwd_valid = false;
+    CK(cudaGetLastError());
+    return MG_OK;
+  }
+  if (!c->graph || c->graph_losses != d_losses || c->graph_profiled != c->profiling) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    c->graph_pairs.clear();
+    c->ev_next = 0;
+    cudaGraph_t g;
+    c->capturing = true;
+    c->launches = 0;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    LaunchCtx x = make_ctx(c, nullptr);
+    render(c, x);
+    loss_forward(c, x, 1, d_losses, nullptr, 0);
+    backward_pass(c, x);
+    run(c, F_ADAM, [&] { launch_adam2(c->stream, c->d_hyper, c->d_step, c->d_params, c->d_grads, c->d_m, c->d_v, c->nparams); });
+    c->capturing = false;
+    c->launches_step = c->launches;
+    CK(cudaStreamEndCapture(c->stream, &g));
+    CK(cudaGraphInstantiate(&c->graph, g, 0));
+    cudaGraphDestroy(g);
+    c->graph_losses = d_losses;
+    c->graph_profiled = c->profiling;
+  }
+  CK(cudaGraphLaunch(c->graph, c->stream));
+  if (c->profiling) {
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto& pr : c->graph_pairs) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, pr.second.first, pr.second.second);
+      c->fam_ms[pr.first] += ms;
+      c->fam_n[pr.first] += 1;
+    }
+  }
+  c->fwd_valid = false;
+  return MG_OK;
+}
+
+mg_status mg_prune(mg_console* c, const uint8_t* h_keep) {
+  if (!c || !h_keep) return fail(c, MG_ERR_INVALID, "null pointer");
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < c->P; ++i)
+    if (!h_keep[i]) c->procs[i].present = 0;
+  if (build_tables(c) != MG_OK) return MG_ERR_CUDA;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->fwd_valid = false;
+  CK(cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
+mg_status mg_get_present(const mg_console* c, uint8_t* h_present) {
+  if (!c || !h_present) return MG_ERR_INVALID;
+  for (int i = 0; i < c->P; ++i) h_present[i] = (uint8_t)c->procs[i].present;
+  return MG_OK;
+}
+
+mg_status mg_update_audio(mg_console* c, int32_t song, const float* sources, const float* target, int32_t on_device) {
+  if (!c || song < 0 || song >= (int)c->songs.size() || !sources) return fail(c, MG_ERR_INVALID, "bad song or null sources");
+  const HostSong& hs = c->songs[song];
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // mono sources go to the left row of each track input, then ingest duplicates them to both rows
+  for (int t = 0; t < hs.K; ++t) {
+    float* dst = (float*)(c->arena + c->chains[hs.tracks_chain[t]].o_in);
+    CK(cudaMemcpyAsync(dst, sources + (size_t)t * hs.L, sizeof(float) * hs.L, k, c->stream));
+    CK(cudaMemcpyAsync(dst + hs.ld, sources + (size_t)t * hs.L, sizeof(float) * hs.L, k, c->stream));
+  }
+  if (target) {
+    CK(cudaMemcpy2DAsync(c->arena + hs.o_tgt, (size_t)hs.ld * sizeof(float), target, (size_t)hs.L * sizeof(float),
+                         (size_t)hs.L * sizeof(float), 2, k, c->stream));
+    LaunchCtx x = make_ctx(c, nullptr);
+    const bool prof = c->profiling;
+    c->profiling = false;
+    loss_forward(c, x, 0, nullptr, nullptr, 0);
+    c->profiling = prof;
+  }
+  c->fwd_valid = false;
+  CK(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_set_launch_mode(mg_console* c, int32_t per_node) {
+  if (!c) return MG_ERR_INVALID;
+  c->per_node = per_node != 0;
+  return MG_OK;
+}
+
+mg_status mg_set_profiling(mg_console* c, int32_t on) {
+  if (!c) return MG_ERR_INVALID;
+  c->profiling = on != 0;
+  return MG_OK;
+}
+
+int32_t mg_num_kernel_families(void) { return F_COUNT; }
+const char* mg_kernel_family_name(int32_t f) { return (f >= 0 && f < F_COUNT) ? kFamilyNames[f] : ""; }
+
+mg_status mg_get_kernel_times(mg_console* c, double* ms, int64_t* launches, int32_t n) {
+  if (!c) return MG_ERR_INVALID;
+  CK(cudaStreamSynchronize(c->stream));
+  for (auto& pr : c->pending) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, pr.second.first, pr.second.second);
+    c->fam_ms[pr.first] += t;
+    c->fam_n[pr.first] += 1;
+  }
+  c->pending.clear();
+  if (!c->capturing && c->graph_pairs.empty()) c->ev_next = 0;
+  for (int i = 0; i < n && i < F_COUNT; ++i) {
+    if (ms) ms[i] = c->fam_ms[i];
+    if (launches) launches[i] = c->fam_n[i];
+  }
+  return MG_OK;
+}
+
+mg_status mg_reset_kernel_times(mg_console* c) {
+  if (!c) return MG_ERR_INVALID;
+  for (int i = 0; i < F_COUNT; ++i) {
+    c->fam_ms[i] = 0;
+    c->fam_n[i] = 0;
+  }
+  return MG_OK;
+}
+
+mg_status mg_debug_read(const mg_console* cc, int32_t proc, int32_t what, float* host_out, int64_t n) {
+  mg_console* c = const_cast<mg_console*>(cc);
+  if (!c || !host_out || proc < 0 || proc >= c->P) return fail(c, MG_ERR_INVALID, "bad processor or null output");
+  const ProcDev& d = c->hpd[proc];
+  const HostProc& p = c->procs[proc];
+  const float* src = nullptr;
+  int64_t rows = 2, cols = 0, ld = 0;
+  switch (what) {
+    case 0: src = d.y; cols = p.L; ld = p.ld; break;
+    case 1: src = d.taps; cols = p.Nh; ld = p.Nh; break;
+    case 2: src = d.dtaps; cols = p.Nh; ld = p.Nh; break;
+    case 3: src = d.du; cols = p.L; ld = p.ld; break;
+    case 4: src = d.stats; rows = 1; cols = 16; ld = 16; break;
+    case 5: src = d.dy; cols = p.L; ld = p.ld; break;
+    default: return fail(c, MG_ERR_INVALID, "unknown buffer");
+  }
+  if (!src) return fail(c, MG_ERR_INVALID, "buffer not present for this processor");
+  if (n != rows * cols) return fail(c, MG_ERR_INVALID, "size mismatch");
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy2D(host_out, cols * sizeof(float), src, ld * sizeof(float), cols * sizeof(float), rows,
+                  cudaMemcpyDeviceToHost));
+  return MG_OK;
+}
+
+const char* mg_last_error(const mg_console* c) { return c ? c->err.c_str() : g_static_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,374 @@
+// Compressor (Sec. 3.5) and noisegate (Sec. 3.6): the exact one-pole envelope recursion of Eq. (11),
+// g[n] = alpha g[n-1] + (1 - alpha) x[n], x = (u_l + u_r)^2, evaluated as a chunked linear scan:
+//   pass 1 (agg):   every 4096-sample chunk computes its zero-start end state,
+//   pass 2 (carry): one thread per node chains the chunk states (g entering each chunk),
+//   pass 3 (apply): every chunk rescans from its carried state with a warp-shuffle scan of the
+//                   per-thread states (decay alpha^16 per thread), then applies the gain law
+//                   (Eqs. 13-16) and Eq. (15), fused with the dry/wet blend.
+// The adjoint runs the same structure in reverse: lambda[n] = dL/dg[n] + alpha lambda[n+1].
+#include "mg_fft.cuh"
+
+namespace mg {
+
+namespace {
+
+constexpr int kPer = 16;   // samples per thread
+constexpr int kThreads = kDynChunk / kPer;
+
+struct DynParams {
+  float alpha, lna, T, W, R;
+  bool gate;
+};
+
+__device__ __forceinline__ DynParams dyn_params(const ProcDev& P) {
+  DynParams d;
+  const float p0 = P.p[0];
+  d.alpha = 1.f / (1.f + expf(-p0));
+  d.lna = -log1pf(expf(-p0));          // ln sigmoid(p0)
+  if (p0 < -20.f) d.lna = p0;          // log1p(exp(-p0)) = -p0 + log1p(exp(p0))
+  d.T = P.p[1];
+  d.W = expf(P.p[2]);
+  d.R = 1.f + expf(P.p[3]);
+  d.gate = P.type == T_N;
+  return d;
+}
+
+// Gain laws (Eqs. 13-14 compressor, Eq. 16 noisegate) with their partial derivatives.
+__device__ __forceinline__ float gain_law(const DynParams& d, float G, float& dG, float& dT, float& dW, float& dR) {
+  const float T = d.T, W = d.W, R = d.R;
+  if (!d.gate) {
+    if (G >= T + W) {
+      dG = 1.f / R; dT = 1.f - 1.f / R; dW = 0.f; dR = -(G - T) / (R * R);
+      return T + (G - T) / R;
+    }
+    if (G >= T - W) {
+      const float q = G - T + W, k = 1.f / R - 1.f;
+      dG = 1.f + k * q / (2.f * W); dT = -k * q / (2.f * W);
+      dW = k * (q / (2.f * W) - q * q / (4.f * W * W)); dR = -(q * q) / (4.f * W * R * R);
+      return G + k * q * q / (4.f * W);
+    }
+    dG = 1.f; dT = 0.f; dW = 0.f; dR = 0.f;
+    return G;
+  }
+  if (G >= T + W) {
+    dG = 1.f; dT = 0.f; dW = 0.f; dR = 0.f;
+    return G;
+  }
+  if (G >= T - W) {
+    const float q = G - T - W, k = 1.f - R;
+    dG = 1.f + k * q / (2.f * W); dT = -k * q / (2.f * W);
+    dW = k * (-q / (2.f * W) - q * q / (4.f * W * W)); dR = -(q * q) / (4.f * W);
+    return G + k * q * q / (4.f * W);
+  }
+  dG = R; dT = 1.f - R; dW = 0.f; dR = G - T;
+  return T + R * (G - T);
+}
+
+__device__ __forceinline__ float gain_law_v(const DynParams& d, float G) {
+  float a, b, cc, e;
+  return gain_law(d, G, a, b, cc, e);
+}
+
+// Loads this thread's 16 consecutive samples of a [2][ld] buffer (zeros at and beyond L).
+__device__ __forceinline__ void load16(const float* base, int ld, int L, int n0, float (&l)[kPer], float (&r)[kPer]) {
+#pragma unroll
+  for (int j = 0; j < kPer / 4; ++j) {
+    const int n = n0 + 4 * j;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (n < L) {
+      a = *reinterpret_cast<const float4*>(base + n);
+      b = *reinterpret_cast<const float4*>(base + ld + n);
+    }
+    l[4 * j] = a.x; l[4 * j + 1] = a.y; l[4 * j + 2] = a.z; l[4 * j + 3] = a.w;
+    r[4 * j] = b.x; r[4 * j + 1] = b.y; r[4 * j + 2] = b.z; r[4 * j + 3] = b.w;
+  }
+}
+
+__device__ __forceinline__ void store16(float* base, int ld, int L, int n0, const float (&l)[kPer], const float (&r)[kPer]) {
+#pragma unroll
+  for (int j = 0; j < kPer / 4; ++j) {
+    const int n = n0 + 4 * j;
+    if (n < L) {
+      *reinterpret_cast<float4*>(base + n) = make_float4(l[4 * j], l[4 * j + 1], l[4 * j + 2], l[4 * j + 3]);
+      *reinterpret_cast<float4*>(base + ld + n) = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+    }
+  }
+}
+
+// Exclusive forward scan over the block: returns the state entering this thread's first sample, given the
+// per-thread zero-start end states s (each spanning 16 samples) and the chunk's entering state.
+__device__ __forceinline__ float scan_fwd_excl(float s, float lna, float carry, float* sm /* >= 8 floats */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float inc = s;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float v = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += v * expf((float)(kPer * off) * lna);
+  }
+  if (lane == 31) sm[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    float t = lane < kThreads / 32 ? sm[lane] : 0.f;
+    float ti = t;
+#pragma unroll
+    for (int off = 1; off < kThreads / 32; off <<= 1) {
+      const float v = __shfl_up_sync(0xffffffffu, ti, off);
+      if (lane >= off) ti += v * expf((float)(kPer * 32 * off) * lna);
+    }
+    // exclusive warp prefix, with the chunk carry folded in
+    float ex = __shfl_up_sync(0xffffffffu, ti, 1);
+    if (lane == 0) ex = 0.f;
+    ex += carry * expf((float)(kPer * 32 * lane) * lna);
+    if (lane < kThreads / 32) sm[8 + lane] = ex;
+  }
+  __syncthreads();
+  const float win = sm[8 + wid];   // state entering the warp
+  float ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) ex = 0.f;
+  const float res = ex + win * expf((float)(kPer * lane) * lna);
+  __syncthreads();
+  return res;
+}
+
+// Exclusive reverse scan: state entering this thread's last sample from the right.
+__device__ __forceinline__ float scan_rev_excl(float r, float lna, float carry, float* sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int nw = kThreads / 32;
+  float inc = r;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const float v = __shfl_down_sync(0xffffffffu, inc, off);
+    if (lane + off < 32) inc += v * expf((float)(kPer * off) * lna);
+  }
+  if (lane == 0) sm[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    // reverse scan over warps: warp w receives sum_{w' > w} total_{w'} decayed, plus the carry
+    float t = lane < nw ? sm[lane] : 0.f;
+    float ti = t;
+#pragma unroll
+    for (int off = 1; off < nw; off <<= 1) {
+      const float v = __shfl_down_sync(0xffffffffu, ti, off);
+      if (lane + off < nw) ti += v * expf((float)(kPer * 32 * off) * lna);
+    }
+    float ex = __shfl_down_sync(0xffffffffu, ti, 1);
+    if (lane >= nw - 1) ex = 0.f;
+    ex += carry * expf((float)(kPer * 32 * (nw - 1 - lane)) * lna);
+    if (lane < nw) sm[8 + lane] = ex;
+  }
+  __syncthreads();
+  const float win = sm[8 + wid];
+  float ex = __shfl_down_sync(0xffffffffu, inc, 1);
+  if (lane == 31) ex = 0.f;
+  const float res = ex + win * expf((float)(kPer * (31 - lane)) * lna);
+  __syncthreads();
+  return res;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads) k_dyn_fwd_agg(LaunchCtx c, const Item* __restrict__ items) {
+  __shared__ float red[32];
+  const Item it = items[blockIdx.x];
+  const ProcDev& P = c.procs[it.proc];
+  const DynParams d = dyn_params(P);
+  const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
+  float l[kPer], r[kPer];
+  load16(P.u, P.ld, P.L, n0, l, r);
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const float m = l[j] + r[j];
+    s = d.alpha * s + (1.f - d.alpha) * (m * m);
+  }
+  float v[1] = {s * expf((float)(kPer * (kThreads - 1 - (int)threadIdx.x)) * d.lna)};
+  float out[1];
+  block_sum<1>(v, red, out);
+  if (threadIdx.x == 0) P.chunkagg[it.idx] = out[0];
+}
+
+__global__ void k_dyn_fwd_carry(LaunchCtx c, const int* __restrict__ procs, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ProcDev& P = c.procs[procs[i]];
+  const DynParams d = dyn_params(P);
+  const float A = expf((float)kDynChunk * d.lna);
+  float g = 0.f;
+  for (int k = 0; k < P.nchunks; ++k) {
+    P.carry[k] = g;
+    g = A * g + P.chunkagg[k];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_dyn_fwd_apply(LaunchCtx c, const Item* __restrict__ items) {
+  __shared__ float sm[16];
+  const Item it = items[blockIdx.x];
+  const ProcDev& P = c.procs[it.proc];
+  const DynParams d = dyn_params(P);
+  const float w = dry_wet_w(c, P.qidx);
+  const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
+  float l[kPer], r[kPer];
+  load16(P.u, P.ld, P.L, n0, l, r);
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const float m = l[j] + r[j];
+    s = d.alpha * s + (1.f - d.alpha) * (m * m);
+  }
+  float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const float m = l[j] + r[j];
+    g = d.alpha * g + (1.f - d.alpha) * (m * m);
+    const float Gu = logf(g + kEnvEps);
+    const float gain = expf(gain_law_v(d, Gu) - Gu);
+    l[j] = w * (gain * l[j]) + (1.f - w) * l[j];
+    r[j] = w * (gain * r[j]) + (1.f - w) * r[j];
+  }
+  store16(P.y, P.ld, P.L, n0, l, r);
+}
+
+// dL/dg at one sample, plus accumulation of the gain-law parameter partials and dw.
+struct DynAdj {
+  float dT, dW, dR, dw;
+};
+
+__device__ __forceinline__ float dyn_dg(const DynParams& d, float w, float g, float ul, float ur, float gl, float gr,
+                                        float& gain, DynAdj& acc) {
+  const float Gu = logf(g + kEnvEps);
+  float dG, dT, dW, dR;
+  const float Gy = gain_law(d, Gu, dG, dT, dW, dR);
+  gain = expf(Gy - Gu);
+  const float bl = w * gl, br = w * gr;
+  const float dE = (bl * ul + br * ur) * gain;
+  acc.dT += dE * dT;
+  acc.dW += dE * dW;
+  acc.dR += dE * dR;
+  acc.dw += gl * (gain * ul - ul) + gr * (gain * ur - ur);
+  return dE * (dG - 1.f) / (g + kEnvEps);
+}
+
+__global__ void __launch_bounds__(kThreads) k_dyn_bwd_agg(LaunchCtx c, const Item* __restrict__ items) {
+  __shared__ float sm[32];
+  const Item it = items[blockIdx.x];
+  const ProcDev& P = c.procs[it.proc];
+  const DynParams d = dyn_params(P);
+  const float w = dry_wet_w(c, P.qidx);
+  const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
+  float l[kPer], r[kPer], gl[kPer], gr[kPer];
+  load16(P.u, P.ld, P.L, n0, l, r);
+  load16(P.dy, P.ld, P.L, n0, gl, gr);
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const float m = l[j] + r[j];
+    s = d.alpha * s + (1.f - d.alpha) * (m * m);
+  }
+  float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
+  float dg[kPer];
+  DynAdj acc = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const float m = l[j] + r[j];
+    g = d.alpha * g + (1.f - d.alpha) * (m * m);
+    float gain;
+    dg[j] = dyn_dg(d, w, g, l[j], r[j], gl[j], gr[j], gain, acc);
+  }
+  float lam = 0.f;
+#pragma unroll
+  for (int j = kPer - 1; j >= 0; --j) lam = dg[j] + d.alpha * lam;
+  float v[1] = {lam * expf((float)(kPer * threadIdx.x) * d.lna)};
+  float out[1];
+  block_sum<1>(v, sm, out);
+  if (threadIdx.x == 0) P.chunkagg[it.idx] = out[0];
+}
+
+__global__ void k_dyn_bwd_carry(LaunchCtx c, const int* __restrict__ procs, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ProcDev& P = c.procs[procs[i]];
+  const DynParams d = dyn_params(P);
+  const float A = expf((float)kDynChunk * d.lna);
+  float lam = 0.f;
+  for (int k = P.nchunks - 1; k >= 0; --k) {
+    P.rcarry[k] = lam;
+    lam = P.chunkagg[k] + A * lam;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_dyn_bwd_apply(LaunchCtx c, const Item* __restrict__ items) {
+  __shared__ float sm[32 * 5];
+  const Item it = items[blockIdx.x];
+  const ProcDev& P = c.procs[it.proc];
+  const DynParams d = dyn_params(P);
+  const float w = dry_wet_w(c, P.qidx);
+  const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
+  float l[kPer], r[kPer], gl[kPer], gr[kPer];
+  load16(P.u, P.ld, P.L, n0, l, r);
+  load16(P.dy, P.ld, P.L, n0, gl, gr);
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const float m = l[j] + r[j];
+    s = d.alpha * s + (1.f - d.alpha) * (m * m);
+  }
+  const float gin = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
+  float gv[kPer], dg[kPer], gains[kPer];
+  DynAdj acc = {0.f, 0.f, 0.f, 0.f};
+  float g = gin;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const float m = l[j] + r[j];
+    g = d.alpha * g + (1.f - d.alpha) * (m * m);
+    gv[j] = g;
+    dg[j] = dyn_dg(d, w, g, l[j], r[j], gl[j], gr[j], gains[j], acc);
+  }
+  float rl = 0.f;
+#pragma unroll
+  for (int j = kPer - 1; j >= 0; --j) rl = dg[j] + d.alpha * rl;
+  float lam = scan_rev_excl(rl, d.lna, P.rcarry[it.idx], sm);   // lambda entering the last sample from the right
+  float dalpha = 0.f;
+#pragma unroll
+  for (int j = kPer - 1; j >= 0; --j) {
+    lam = dg[j] + d.alpha * lam;
+    const float m = l[j] + r[j];
+    const float x = m * m;
+    const float gprev = j > 0 ? gv[j - 1] : gin;
+    dalpha += lam * (gprev - x);
+    const float dx2m = (1.f - d.alpha) * lam * 2.f * m;
+    const float ol = (1.f - w) * gl[j] + gains[j] * (w * gl[j]) + dx2m;
+    const float orr = (1.f - w) * gr[j] + gains[j] * (w * gr[j]) + dx2m;
+    l[j] = ol;
+    r[j] = orr;
+  }
+  store16(P.du, P.ld, P.L, n0, l, r);
+  float v[5] = {dalpha, acc.dT, acc.dW, acc.dR, acc.dw};
+  float out[5];
+  block_sum<5>(v, sm, out);
+  if (threadIdx.x == 0) {
+    float* bp = P.bpart + (size_t)it.idx * kNPart;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) bp[j] = out[j];
+  }
+}
+
+void launch_dyn_fwd_agg(const LaunchCtx& c, const Item* items, int n) {
+  if (n) k_dyn_fwd_agg<<<n, kThreads, 0, c.stream>>>(c, items);
+}
+void launch_dyn_fwd_carry(const LaunchCtx& c, const int* procs, int n) {
+  if (n) k_dyn_fwd_carry<<<(n + 63) / 64, 64, 0, c.stream>>>(c, procs, n);
+}
+void launch_dyn_fwd_apply(const LaunchCtx& c, const Item* items, int n) {
+  if (n) k_dyn_fwd_apply<<<n, kThreads, 0, c.stream>>>(c, items);
+}
+void launch_dyn_bwd_agg(const LaunchCtx& c, const Item* items, int n) {
+  if (n) k_dyn_bwd_agg<<<n, kThreads, 0, c.stream>>>(c, items);
+}
+void launch_dyn_bwd_carry(const LaunchCtx& c, const int* procs, int n) {
+  if (n) k_dyn_bwd_carry<<<(n + 63) / 64, 64, 0, c.stream>>>(c, procs, n);
+}
+void launch_dyn_bwd_apply(const LaunchCtx& c, const Item* items, int n) {
+  if (n) k_dyn_bwd_apply<<<n, kThreads, 0, c.stream>>>(c, items);
+}
+
+}  // namespace mg

@@ -1,0 +1,196 @@
+// Multi-resolution STFT loss of Sec. 5.1 (Eqs. 20-21) and its adjoint.
+// Per resolution: frames t hop .. t hop + n_fft of the stereo mix (periodic Hann, no centre padding) are
+// transformed as one packed complex FFT z = left + i right; per bin the channel spectra are
+// X_L = (Z[k] + conj Z[-k]) / 2, X_R = (Z[k] - conj Z[-k]) / 2i, X_M = X_L + X_R, X_S = X_L - X_R;
+// magnitudes sqrt(A_k^2 |X|^2 + 1e-8) (A-weighting per bin) are projected on the Mel triangles (CSR by
+// band, fixed summation order), compared with the cached target spectrograms, and reduced per work item
+// (deterministic partial sums, no atomics).
+// Adjoint: the same frames are re-transformed, dL/dY_hat per band goes back to the bins through the
+// transposed Mel CSR, to the complex bins through |X|, to the packed Hermitian spectrum, and through one
+// inverse FFT to the windowed frame; a gather kernel overlap-adds the frames of all resolutions.
+#include "mg_fft.cuh"
+
+namespace mg {
+
+namespace {
+constexpr int kLossThreads = 512;
+constexpr float kLogEps = 1e-5f;
+constexpr float kMagEps = 1e-8f;
+
+// channel magnitudes^2 of bin k (|X_L|^2, |X_R|^2, |X_M|^2, |X_S|^2) and the complex X_L, X_R
+__device__ __forceinline__ void bin_spectra(const float2* Z, int k, int n, float2& XL, float2& XR) {
+  const float2 a = Z[k], b = Z[(n - k) & (n - 1)];
+  XL = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+  // (a - conj b) / 2i
+  const float2 d = make_float2(a.x - b.x, a.y + b.y);
+  XR = make_float2(0.5f * d.y, -0.5f * d.x);
+}
+
+__device__ __forceinline__ float2 chan(int c, float2 XL, float2 XR) {
+  if (c == 0) return XL;
+  if (c == 1) return XR;
+  if (c == 2) return cadd(XL, XR);
+  return csub(XL, XR);
+}
+
+__device__ __forceinline__ float band_value(const LossRes& R, const float2* Z, int b, int c) {
+  float s = 0.f;
+  for (int e = R.band_beg[b]; e < R.band_beg[b + 1]; ++e) {
+    const int k = R.band_bin[e];
+    float2 XL, XR;
+    bin_spectra(Z, k, R.nfft, XL, XR);
+    const float2 X = chan(c, XL, XR);
+    s = fmaf(R.band_w[e], sqrtf(R.aw2[k] * (X.x * X.x + X.y * X.y) + kMagEps), s);
+  }
+  return s;
+}
+
+__device__ __forceinline__ void load_frames(float2* sm, const float* x, int ld, int L, const LossRes& R, int t0, int nb) {
+  const int n = R.nfft;
+  for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
+    const int f = e >> R.log_nfft, j = e & (n - 1);
+    const int s = (t0 + f) * R.hop + j;
+    const float w = R.win[j];
+    sm[e] = (s < L) ? make_float2(x[s] * w, x[ld + s] * w) : make_float2(0.f, 0.f);
+  }
+}
+}  // namespace
+
+// item (song, res, first frame, frames); mode 0: write target spectrogram + partial sum Y^2 per set;
+// mode 1: partial sums of |dlog| and (Y - Yhat)^2 per set; mode 2: adjoint frames to dF.
+__global__ void __launch_bounds__(kLossThreads) k_loss_frames(LaunchCtx c, const SongDev* __restrict__ songs,
+                                                              const LossRes* __restrict__ resv,
+                                                              const int4* __restrict__ items, int mode) {
+  extern __shared__ float2 sm[];
+  __shared__ float red[6 * 32];
+  const int4 it = items[blockIdx.x];
+  const SongDev& S = songs[it.x];
+  const LossRes& R = resv[it.y];
+  const int t0 = it.z, nb = it.w, n = R.nfft, nbands = R.nbands;
+  const float* x = mode == 0 ? S.target : S.mix;
+  load_frames(sm, x, S.ld, S.L, R, t0, nb);
+  __syncthreads();
+  fft_smem<false, 4>(sm, R.log_nfft, nb, 1, n, c.tab.tw);
+  float* Yt = S.Y[it.y];
+  if (mode < 2) {
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int e = threadIdx.x; e < nb * nbands * 4; e += blockDim.x) {
+      const int f = e / (nbands * 4), r = e % (nbands * 4), b = r >> 2, ch = r & 3;
+      const float yh = band_value(R, sm + f * n, b, ch);
+      const int set = ch < 2 ? 0 : ch - 1;
+      float* ydst = Yt + ((size_t)(t0 + f) * nbands + b) * 4 + ch;
+      if (mode == 0) {
+        *ydst = yh;
+        acc[set] += yh * yh;
+      } else {
+        const float y = *ydst;
+        acc[2 * set] += fabsf(logf(y + kLogEps) - logf(yh + kLogEps));
+        const float d = y - yh;
+        acc[2 * set + 1] += d * d;
+      }
+    }
+    float out[6];
+    block_sum<6>(acc, red, out);
+    if (threadIdx.x == 0) {
+      // partial row: the items of one (song, resolution) cover consecutive groups of 8192 / n_fft frames
+      const int row = (t0 - S.first_frame[it.y]) / (8192 >> R.log_nfft);
+      for (int j = 0; j < 6; ++j) S.lpart[((size_t)it.y * S.lcap + row) * 6 + j] = out[j];
+    }
+    return;
+  }
+  // ---- adjoint ----
+  float* dY = reinterpret_cast<float*>(sm + nb * n);       // [nb][nbands][4]
+  const float* coef = S.coef + it.y * 6;                    // per set: (alpha / count, alpha / (|Y - Yh| |Y|))
+  for (int e = threadIdx.x; e < nb * nbands * 4; e += blockDim.x) {
+    const int f = e / (nbands * 4), r = e % (nbands * 4), b = r >> 2, ch = r & 3;
+    const float yh = band_value(R, sm + f * n, b, ch);
+    const int set = ch < 2 ? 0 : ch - 1;
+    const float y = Yt[((size_t)(t0 + f) * nbands + b) * 4 + ch];
+    const float dl = logf(yh + kLogEps) - logf(y + kLogEps);
+    const float sg = dl > 0.f ? 1.f : (dl < 0.f ? -1.f : 0.f);
+    dY[e] = coef[2 * set] * sg / (yh + kLogEps) + coef[2 * set + 1] * (yh - y);
+  }
+  __syncthreads();
+  // bins -> packed Hermitian spectrum, in place (thread owns the pair k, n - k)
+  const int half = n >> 1;
+  for (int e = threadIdx.x; e < nb * (half + 1); e += blockDim.x) {
+    const int f = e / (half + 1), k = e % (half + 1);
+    float2* Z = sm + f * n;
+    float2 XL, XR;
+    bin_spectra(Z, k, n, XL, XR);
+    const float* dYf = dY + (size_t)f * nbands * 4;
+    float2 gl = make_float2(0.f, 0.f), gr = gl;
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      float dm = 0.f;
+      for (int q = R.bin_beg[k]; q < R.bin_beg[k + 1]; ++q) dm = fmaf(R.bin_w[q], dYf[R.bin_band[q] * 4 + ch], dm);
+      const float2 X = chan(ch, XL, XR);
+      const float mag = sqrtf(R.aw2[k] * (X.x * X.x + X.y * X.y) + kMagEps);
+      const float2 g = cscale(X, dm * R.aw2[k] / mag);
+      if (ch == 0) gl = cadd(gl, g);
+      else if (ch == 1) gr = cadd(gr, g);
+      else if (ch == 2) { gl = cadd(gl, g); gr = cadd(gr, g); }
+      else { gl = cadd(gl, g); gr = csub(gr, g); }
+    }
+    if (k == 0 || k == half) {
+      Z[k] = make_float2(gl.x, gr.x);
+    } else {
+      // G_L[k] = gl/2, G_L[n-k] = conj(gl)/2 (same for R); packed P = G_L + i G_R
+      Z[k] = make_float2(0.5f * (gl.x - gr.y), 0.5f * (gl.y + gr.x));
+      Z[n - k] = make_float2(0.5f * (gl.x + gr.y), 0.5f * (gr.x - gl.y));
+    }
+  }
+  __syncthreads();
+  fft_smem<true, 4>(sm, R.log_nfft, nb, 1, n, c.tab.tw);
+  float* dF = S.dF[it.y];
+  for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
+    const int f = e >> R.log_nfft, j = e & (n - 1);
+    const float w = R.win[j];
+    reinterpret_cast<float2*>(dF)[(size_t)(t0 + f) * n + j] = cscale(sm[e], w);
+  }
+}
+
+// dmix[c][s] = sum over resolutions and covering frames of dF (overlap-add, fixed order)
+__global__ void __launch_bounds__(256) k_loss_gather(const SongDev* __restrict__ songs, const LossRes* __restrict__ resv,
+                                                    int nres, const Item* __restrict__ items) {
+  const Item it = items[blockIdx.x];
+  const SongDev& S = songs[it.proc];
+  const int s0 = it.idx * kElemTile;
+  for (int s = s0 + threadIdx.x; s < min(s0 + kElemTile, S.L); s += blockDim.x) {
+    float al = 0.f, ar = 0.f;
+    for (int r = 0; r < nres; ++r) {
+      const LossRes& R = resv[r];
+      const int tlast = min(S.nframes[r] - 1, s / R.hop);
+      int tfirst = s - R.nfft + 1 <= 0 ? 0 : (s - R.nfft + 1 + R.hop - 1) / R.hop;
+      tfirst = max(tfirst, S.first_frame[r]);
+      const float2* dF = reinterpret_cast<const float2*>(S.dF[r]);
+      for (int t = tfirst; t <= tlast; ++t) {
+        const float2 v = dF[(size_t)t * R.nfft + (s - t * R.hop)];
+        al += v.x;
+        ar += v.y;
+      }
+    }
+    S.dmix[s] = al;
+    S.dmix[S.ld + s] = ar;
+  }
+}
+
+void launch_loss_frames(const LaunchCtx& c, const SongDev* songs, const LossRes* res, const int4* items, int n,
+                        int mode, int maxfft) {
+  if (!n) return;
+  (void)maxfft;
+  const size_t smem = 8192 * sizeof(float2) + (mode == 2 ? (size_t)(4096 + 128) * 4 * sizeof(float) : 0);
+  k_loss_frames<<<n, kLossThreads, smem, c.stream>>>(c, songs, res, items, mode);
+}
+
+void launch_loss_gather(const LaunchCtx& c, const SongDev* songs, const LossRes* res, int nres, const Item* items,
+                        int n) {
+  if (n) k_loss_gather<<<n, 256, 0, c.stream>>>(songs, res, nres, items);
+}
+
+void init_loss_attributes() {
+  cudaFuncSetAttribute(k_loss_frames, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       8192 * sizeof(float2) + (4096 + 128) * 4 * sizeof(float));
+}
+
+}  // namespace mg

@@ -1,0 +1,170 @@
+// Internal declarations shared by the kernels and the host engine of the mixing-console library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mg {
+
+enum ProcType { T_E = 0, T_C = 1, T_N = 2, T_S = 3, T_G = 4, T_D = 5, T_R = 6, NTYPES = 7 };
+
+constexpr int kTwLog = 13;                 // shared twiddle table exp(-2 pi i j / 8192)
+constexpr int kTwN = 1 << kTwLog;
+constexpr int kNPart = 8;                  // partial sums per work item
+constexpr int kEqTaps = 2047;              // Sec. 3.3
+constexpr int kEqHalf = 1023;
+constexpr int kEqParams = 1024;
+constexpr int kDlyFir = 39;                // Sec. 3.7
+constexpr int kDlyHalf = 19;
+constexpr int kDlyTaps = 20;
+constexpr int kDlyPer = 22;                // Re z, Im z, 20 log-magnitudes
+constexpr int kRevFft = 384;               // Sec. 3.4
+constexpr int kRevHop = 192;
+constexpr int kRevBins = 193;
+constexpr int kRevParams = 192;
+constexpr int kRevFG = 16;                 // frames per reverb work item
+constexpr int kDynChunk = 4096;            // samples per envelope-scan work item (256 threads x 16)
+constexpr int kElemTile = 4096;            // samples per elementwise work item
+constexpr float kEnvEps = 1e-8f;           // G_u = ln(g + eps)
+
+struct Item {
+  int proc;
+  int idx;
+};
+
+// Device view of one processor node (flattened over all songs).
+struct ProcDev {
+  int type, song, qidx, L, ld;             // ld: channel stride of every [2][ld] buffer
+  int present;                             // 0 once removed by structural pruning
+  int rev;                                 // rank among reverbs (noise index), -1 otherwise
+  const float* u;                          // forward input  [2][ld]
+  float* y;                                // forward output [2][ld]
+  const float* dy;                         // adjoint of y
+  float* du;                               // adjoint of u
+  const float* p;                          // parameters of this processor
+  float* gp;                               // gradient of those parameters
+  float* fpart;                            // forward partials  [items][kNPart]
+  float* bpart;                            // backward partials [items][kNPart]
+  int nfpart, nbpart;                      // number of partial rows written by the main pass
+  float* stats;                            // [8]: 0 E_ybar_mid, 1 E_u_mid, 2 c1, 3 c2, 4.. backward sums
+  // LTI processors (e, r, d): four-step FFT convolution of size N = N1 * N2
+  int logN, logN1, logN2, colG;            // colG: columns per column-pass work item
+  int n0, Nh;                              // FIR: first tap time, number of taps
+  float2* T1;
+  float2* T2;
+  float2* Hz;
+  float* taps;                             // [2][Nh]
+  float* dtaps;                            // [2][Nh]
+  float* aux;                              // type scratch (delay: c_m and d_m; reverb: adjoint partials)
+  // envelope scans (c, n)
+  float* carry;                            // [nchunks] forward state entering each chunk
+  float* rcarry;                           // [nchunks] reverse state entering each chunk from the right
+  float* chunkagg;                         // [nchunks] per-chunk aggregates
+  int nchunks;
+  // reverb
+  const float2* nspec;                     // [2][F][193] STFT of the fixed mid/side noise
+  int nframes;                             // F
+};
+
+struct LossRes {                           // one STFT resolution of Eq. (21)
+  int nfft, log_nfft, hop, nbands;
+  const float* win;                        // [nfft] periodic Hann
+  const float* aw2;                        // [nfft/2+1] squared A-weighting gain
+  const int* band_beg;                     // [nbands+1] CSR over (bin, weight) by band
+  const int* band_bin;
+  const float* band_w;
+  const int* bin_beg;                      // [nfft/2+2] CSR over (band, weight) by bin
+  const int* bin_band;
+  const float* bin_w;
+};
+
+struct SongDev {
+  int L, ld, nframes[3], first_frame[3];
+  const float* mix;                        // [2][ld]
+  float* dmix;                             // [2][ld]
+  const float* target;
+  float* Y[3];                             // target spectrograms [frames][nbands][4] (L, R, M, S)
+  float* dF[3];                            // backward per-frame gradients [frames][nfft] (packed complex)
+  float* lpart;                            // loss partials [3][lcap][6]
+  int litems[3];                           // items per resolution
+  int lcap;
+  int pbeg, pend;                          // canonical processor range of the song
+  float* coef;                             // [3 res][3 sets][2]: backward coefficients
+  double* ynorm2;                          // [3 res][3 sets] squared Frobenius norms of the target
+};
+
+// ----------------------------------------------------------------------------------------------
+// launch wrappers (kernels live in the k_*.cu files)
+// ----------------------------------------------------------------------------------------------
+struct Tables {
+  const float2* tw;                        // exp(-2 pi i j / 8192)
+  const float* cos_eq;                     // cos(2 pi m / 2047), m < 2047
+  const float* cos_dl;                     // cos(2 pi m / 39), m < 39
+  const float* rev_win;                    // periodic Hann 384
+  const float2* rev_cs;                    // (cos, sin)(2 pi m / 384), m < 384
+  const float* hann_eq;                    // symmetric Hann v[n], n = -1023..1023
+  const float* hann_dl;                    // symmetric Hann v[n], n = -19..19
+  const float2* dly_w;                     // exp(+2 pi i q / D), q < D (delay slot length D)
+};
+
+struct LaunchCtx {
+  cudaStream_t stream;
+  const ProcDev* procs;                    // device
+  const float* q;                          // dry/wet logits [P]
+  const uint8_t* mask;                     // [P] or null (all ones)
+  const float* hyper;                      // device: 0 alpha_p, 1 lr, 2 beta1, 3 beta2, 4 eps, 5 weight decay
+  float alpha_g;
+  double fs;
+  Tables tab;
+};
+
+// elementwise processors, sums, ingest
+void launch_gs_fwd(const LaunchCtx&, const Item* items, int n);
+void launch_gs_bwd(const LaunchCtx&, const Item* items, int n);
+void launch_sum(cudaStream_t, float* const* outs, const float* const* ins, const int* in_beg, const int* L,
+                const int* ld, const Item* items, int n);
+void launch_ingest(cudaStream_t, const float* mono, float* stereo, int L, int ld);
+// envelope scans
+void launch_dyn_fwd_agg(const LaunchCtx&, const Item* items, int n);
+void launch_dyn_fwd_carry(const LaunchCtx&, const int* procs, int n);
+void launch_dyn_fwd_apply(const LaunchCtx&, const Item* items, int n);
+void launch_dyn_bwd_agg(const LaunchCtx&, const Item* items, int n);
+void launch_dyn_bwd_carry(const LaunchCtx&, const int* procs, int n);
+void launch_dyn_bwd_apply(const LaunchCtx&, const Item* items, int n);
+// LTI processors
+void launch_eq_fir(const LaunchCtx&, const int* procs, int n);
+void launch_eq_fir_adj(const LaunchCtx&, const int* procs, int n);
+void launch_dly_prep(const LaunchCtx&, const int* procs, int n);
+void launch_dly_fir(const LaunchCtx&, const Item* items, int n);
+void launch_dly_adj(const LaunchCtx&, const Item* items, int n);
+void launch_rev_fir(const LaunchCtx&, const Item* items, int n);
+void launch_rev_adj(const LaunchCtx&, const Item* items, int n);
+void launch_rev_adj_fin(const LaunchCtx&, const int* procs, int n);
+void launch_rev_noise_stft(const LaunchCtx&, const Item* items, int n, const float* noise, int noise_len);
+void init_kernel_attributes();
+void init_loss_attributes();
+void init_fir_attributes();
+void launch_col_fwd_audio(const LaunchCtx&, const Item* items, int n, int maxN2G);
+void launch_col_fwd_taps(const LaunchCtx&, const Item* items, int n, int maxN2G);
+void launch_row_fwd_hz(const LaunchCtx&, const Item* items, int n, int maxN1);
+void launch_row_conv_fwd(const LaunchCtx&, const Item* items, int n, int maxN1, bool bwd_keep_u);
+void launch_col_inv_out(const LaunchCtx&, const Item* items, int n, int maxN2G);
+void launch_col_dybar(const LaunchCtx&, const Item* items, int n, int maxN2G);
+void launch_row_bwd2(const LaunchCtx&, const Item* items, int n, int maxN1);
+void launch_col_du(const LaunchCtx&, const Item* items, int n, int maxN2G);
+void launch_col_dh(const LaunchCtx&, const Item* items, int n, int maxN2G);
+// reductions, loss, optimiser
+void launch_node_stats(const LaunchCtx&, const int* procs, int n, int fwd);
+void launch_loss_frames(const LaunchCtx&, const SongDev* songs, const LossRes* res, const int4* items, int n,
+                        int mode, int maxfft);
+void launch_loss_finalize_mode(const LaunchCtx&, const SongDev* songs, int nsongs, const LossRes* res, int nres,
+                               const float* alphas, int mode, float* out_losses, float* out_la, int la_stride);
+void launch_loss_gather(const LaunchCtx&, const SongDev* songs, const LossRes* res, int nres, const Item* items,
+                        int n);
+void launch_grad_finalize2(const LaunchCtx&, const int* procs, int n, float* gq);
+void launch_adam2(cudaStream_t, const float* hyper, int* step, float* p, const float* g, float* m, float* v,
+                  int64_t n);
+void launch_set_hyper(cudaStream_t, float* hyper, float alpha_p, float lr, float b1, float b2, float eps, float wd,
+                      int which);
+void launch_copy_mix(cudaStream_t, const SongDev* songs, int nsongs, float* out, const int64_t* offs);
+
+}  // namespace mg

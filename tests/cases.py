@@ -1,0 +1,118 @@
+"""Shared builders for parity cases: the same seeded inputs feed the FP64 oracle and the CUDA console."""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+import workloads as W
+from oracle import console as OC
+from oracle import loss as OL
+
+LOSS_FIELDS = ("La", "Llr", "Lm", "Ls", "Lg", "Lp", "total")
+
+
+@dataclasses.dataclass
+class Case:
+    layouts: List[W.SongLayout]
+    types: str
+    sources: list
+    targets: list
+    noise: Optional[np.ndarray]
+    ptypes: List[str]
+    params: np.ndarray
+    n_fft: Sequence[int]
+    n_mels: int
+    oracle: OC.Console
+
+
+def make_case(layouts: Sequence[W.SongLayout], types: str = "ecnsgdr", seed: int = 0, n_fft=(512, 2048, 8192),
+              n_mels: int = 96, a_weighting: bool = True, warmup: int = 0, param_key=None) -> Case:
+    layouts = list(layouts)
+    songs = [OC.SongSpec(l.num_tracks, l.num_subgroups, l.track_group, l.num_samples) for l in layouts]
+    sources = [W.song_sources(l, (seed, i)) for i, l in enumerate(layouts)]
+    ptypes = W.processor_types(layouts, types)
+    n_rev = sum(t == "r" for t in ptypes)
+    noise = W.reverb_noise((seed,), max(1, n_rev)) if n_rev else None
+    ldesc = OL.LossDesc(n_fft=tuple(n_fft), n_mels=n_mels, a_weighting=a_weighting, warmup_samples=warmup)
+    desc = OC.ConsoleDesc(types=types, loss=ldesc)
+    gt, keep = W.ground_truth(ptypes, (seed, 77))
+    targets = OC.Console(songs, sources, None, noise, desc).render_targets(gt, keep)
+    oracle = OC.Console(songs, sources, targets, noise, desc)
+    params = W.init_params(ptypes, (seed, 5) if param_key is None else param_key)
+    return Case(layouts, types, sources, targets, noise, ptypes, params, tuple(n_fft), n_mels, oracle)
+
+
+def gpu_console(case: Case, **cfg_kw):
+    import paper_2509_15948_gb300 as M
+    songs = [M.Song(l.num_tracks, l.num_subgroups, l.track_group, l.num_samples) for l in case.layouts]
+    cfg = M.ConsoleConfig(types=case.types, n_fft=case.n_fft, n_mels=case.n_mels, **cfg_kw)
+    con = M.Console(songs, case.sources, case.targets, case.noise, cfg)
+    return con
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a - b))
+
+
+def oracle_with_delay_taps(case: Case, alpha_p: float):
+    """Oracle losses, gradients and mixes, plus for every delay processor the oracle's dL/dh (taps) and its
+    39-tap FIRs c_m (captured from the forward/backward of the same call)."""
+    from oracle import processors as OP
+    cap = []
+    orig = OP.DelayScatter.apply
+
+    def hook(c, zr, zi, D, L):
+        t = orig(c, zr, zi, D, L)
+        if t.requires_grad:
+            t.retain_grad()
+            cap.append((t, c.detach().numpy()))
+        return t
+
+    OP.DelayScatter.apply = hook
+    try:
+        losses, grads, mixes = case.oracle.loss_and_grad(case.params, alpha_p=alpha_p)
+    finally:
+        OP.DelayScatter.apply = orig
+    dprocs = [p for p in case.oracle.procs if p.type == "d"]
+    taps = {p.index: (t.grad.numpy(), c) for p, (t, c) in zip(dprocs, cap)}
+    return losses, grads, mixes, taps
+
+
+def delay_slot_conditioning(case: Case, taps: dict, D: int = 4410):
+    """Per delay processor, channel and tap m: kappa = |g_m| / (rms(dL/dh) ||c_m|| ||s'||), the ratio of the
+    Eq. (19) inner product g_m to its Cauchy-Schwarz scale (how far g_m stands above cancellation)."""
+    from oracle import processors as OP
+    out = {}
+    for p in case.oracle.procs:
+        if p.type != "d":
+            continue
+        dh, cvals = taps[p.index]
+        kap = np.zeros((2, 20))
+        for ch in range(2):
+            rms = np.sqrt(np.mean(dh[ch] ** 2))
+            for m in range(20):
+                o = p.offset + (ch * 20 + m) * 22
+                z = complex(case.params[o], case.params[o + 1])
+                sp = OP.surrogate_impulse_dz(z / max(1.0, abs(z)), D)
+                G = np.lib.stride_tricks.sliding_window_view(dh[ch, m * D: m * D + D + 38], 39) @ cvals[ch, m]
+                scale = rms * np.linalg.norm(cvals[ch, m]) * np.linalg.norm(sp)
+                kap[ch, m] = abs(np.sum(G * np.conj(sp))) / scale if scale > 0 else 0.0
+        out[p.index] = kap
+    return out
+
+
+def grad_groups(case: Case):
+    """Index arrays of the gradient per processor type (parameters) and of the dry/wet logits."""
+    procs = case.oracle.procs
+    out = {}
+    for t in "ecnsgdr":
+        idx = [np.arange(p.offset, p.offset + p.count) for p in procs if p.type == t]
+        if idx:
+            out[t] = np.concatenate(idx)
+    out["q"] = np.arange(case.oracle.n_proc_params, case.oracle.n_params)
+    return out
