@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the mixing-console hot path: forward + loss + backward + Adam per song, in
+track-seconds of audio per second.
+
+One step = one CUDA-graph replay of forward_loss + backward + adam_step over every song of the batch (all
+processor types, dry/wet, subgroup and master sums, multi-resolution STFT loss, regularisers).  Default
+workload: 64 songs with 4-32 tracks, 1-8 subgroups and 5-30 s at 44.1 kHz (uneven batch in one persistent
+launch per processor type).  Inputs are resident in HBM and far larger than L2 (no flush needed).
+
+Multi-GPU: songs are independent, so N ranks run N independent replicas (weak scaling, no collective).
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+FS = W.FS
+STREAM_BYTES_PER_SAMPLE = 8  # one stereo FP32 sample
+
+
+# ------------------------------------------------------------------------------------------------
+# workloads
+# ------------------------------------------------------------------------------------------------
+def workload_layouts(name: str, rank: int = 0):
+    if name == "uneven":
+        return W.layout_uneven_batch(64, seed=2 + 1000 * rank), "uneven batch: 64 songs, K~U{4..32}, S~U{1..8}, 5-30 s"
+    if name == "search":
+        return [W.layout_single_search()], "single search song: 16 tracks x 10 s, 4 subgroups"
+    if name == "plain":
+        return [W.layout_plain()], "plain console: 4 tracks x 2 s, one subgroup of 2"
+    raise ValueError(name)
+
+
+def source_bank(n: int = 24, seconds: float = 30.0, key: int = 0):
+    return [W.source_track((0xBA, key, i), int(seconds * FS)) for i in range(n)]
+
+
+def song_sources_from_bank(bank, layout, song: int):
+    """Crops of the seeded bank (pink-noise bursts + decaying notes, peak -6 dBFS), one per track."""
+    out = np.empty((layout.num_tracks, layout.num_samples), np.float32)
+    for k in range(layout.num_tracks):
+        b = bank[(7 * song + 3 * k) % len(bank)]
+        off = (song * 9973 + k * 7919) % max(1, b.shape[0] - layout.num_samples + 1)
+        x = b[off: off + layout.num_samples]
+        if x.shape[0] < layout.num_samples:
+            x = np.pad(x, (0, layout.num_samples - x.shape[0]))
+        out[k] = x
+    return out
+
+
+def model_bytes(layouts, types="ecnsgdr"):
+    """Algorithmic bytes of one fwd+bwd step: 5 stereo streams per processor node (forward reads u, writes y;
+    backward reads dy and u, writes du), 2 per input plus 2 per output of each mix sum, 2 for the loss."""
+    nt = len([t for t in "ecnsgdr" if t in types])
+    tot = 0
+    per_type = {t: 0 for t in "ecnsgdr"}
+    for l in layouts:
+        chains = l.num_tracks + l.num_subgroups
+        ungrouped = sum(1 for g in l.track_group if g < 0)
+        streams = 5 * nt * chains + 2 * (l.num_tracks - ungrouped) + 2 * l.num_subgroups + 2 * (l.num_subgroups + ungrouped) + 2 + 2
+        tot += streams * l.num_samples * STREAM_BYTES_PER_SAMPLE
+        for t in "ecnsgdr":
+            if t in types:
+                per_type[t] += 5 * chains * l.num_samples * STREAM_BYTES_PER_SAMPLE
+    return tot, per_type
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampling during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, device_index: int = 0):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm)
+# ------------------------------------------------------------------------------------------------
+def oracle_sample_step(layout, seed=0):
+    """One FP64 oracle fwd+bwd on a bounded sample song; returns (seconds, track-seconds)."""
+    import torch
+    from oracle import console as OC
+    songs = [OC.SongSpec(layout.num_tracks, layout.num_subgroups, layout.track_group, layout.num_samples)]
+    bank = [W.source_track((0xBA, 0, i), layout.num_samples) for i in range(layout.num_tracks)]
+    src = [np.stack(bank)]
+    types = W.processor_types([layout])
+    noise = W.reverb_noise((seed,), sum(t == "r" for t in types))
+    gt, keep = W.ground_truth(types, (seed, 77))
+    tgt = OC.Console(songs, src, None, noise).render_targets(gt, keep)
+    con = OC.Console(songs, src, tgt, noise)
+    params = W.init_params(types, (seed, 5))
+    t0 = time.perf_counter()
+    con.loss_and_grad(params, alpha_p=1e-4)
+    dt = time.perf_counter() - t0
+    return dt, layout.num_tracks * layout.num_samples / FS, torch.get_num_threads()
+
+
+def cpu_sample_layout():
+    # a bounded sample shaped like the workload's songs: 4 tracks x 2 s, one subgroup of 2 tracks
+    return W.layout_plain(2 * FS), "4 tracks x 2 s (1 subgroup) of the workload, one fwd+bwd per step"
+
+
+def run_reference(args, metric, config):
+    import torch
+    torch.set_num_threads(os.cpu_count() or 1)
+    lay, desc = cpu_sample_layout()
+    for _ in range(max(0, args.warmup)):
+        oracle_sample_step(lay)
+    tot_t, tot_ts = 0.0, 0.0
+    for _ in range(args.steps):
+        dt, ts, cores = oracle_sample_step(lay)
+        tot_t += dt
+        tot_ts += ts
+    value = tot_ts / tot_t
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": "track-s/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config,
+            "cpu_baseline": {"value": value, "unit": "track-s/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "track-s/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def build_console(layouts, rank, per_song_seed=0):
+    import torch
+    import paper_2509_15948_gb300 as M
+    from paper_2509_15948_gb300 import build as B
+    B.build()
+    bank = source_bank(key=rank)
+    sources = [song_sources_from_bank(bank, l, s) for s, l in enumerate(layouts)]
+    songs = [M.Song(l.num_tracks, l.num_subgroups, l.track_group, l.num_samples) for l in layouts]
+    types = W.processor_types(layouts)
+    noise = W.reverb_noise((rank, 9), sum(t == "r" for t in types))
+    zeros = [np.zeros((2, l.num_samples), np.float32) for l in layouts]
+    con = M.Console(songs, sources, zeros, noise, M.ConsoleConfig())
+    # ground-truth targets rendered by the console itself (seeded graph keeping ~1/3 of the processors)
+    gt, keep = W.ground_truth(types, (rank, 77))
+    gtp = gt.copy()
+    gtp[con.n_proc_params:] = 30.0          # w = sigmoid(30) * keep = keep in FP32
+    con.set_params(gtp)
+    _, mixes = con.forward_loss(mask=keep, with_mix=True)
+    mixes = [m.cpu().numpy() for m in mixes]
+    for s in range(len(layouts)):
+        con.update_audio(s, torch.as_tensor(sources[s]), torch.as_tensor(mixes[s]))
+    con.set_params(W.init_params(types, (rank, 5)))
+    con.set_alpha_p(1e-4)
+    torch.cuda.synchronize()
+    return con, sources, mixes
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uneven", choices=["uneven", "search", "plain"])
+    ap.add_argument("--per-node-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-baseline-steps", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    metric = "console fwd+bwd track-s/s batched vs per-node GPU; search-job p50/p99 latency"
+    layouts, wdesc = workload_layouts(args.workload, rank)
+    config = {"workload": wdesc, "songs": len(layouts), "tracks": sum(l.num_tracks for l in layouts),
+              "subgroups": sum(l.num_subgroups for l in layouts),
+              "seconds": round(sum(l.num_samples for l in layouts) / FS, 2), "sample_rate": FS,
+              "types": "ecnsgdr", "loss": "MRSTFT 512/2048/8192 hop 1/4, 96 Mel, A-weighted; L_g, L_p; Adam lr 1e-2",
+              "parallelism": f"replicas x{world}", "l2": "inputs far larger than L2 (no flush needed)"}
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, metric, config)
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.cuda.current_device()
+    con, sources, mixes = build_console(layouts, rank)
+    info = con.get_info()
+    track_seconds = info["track_seconds"]
+    tot_bytes, type_bytes = model_bytes(layouts)
+
+    for _ in range(args.warmup):
+        con.train_step(lr=1e-2)
+    torch.cuda.synchronize()
+    launches_per_step = con.get_info()["launches_per_step"]
+
+    # ---------------- timed region (device time, CUDA events on the console's stream) ----------------
+    con.set_profiling(True)
+    con.train_step(lr=1e-2)               # capture the instrumented graph outside the timed region
+    torch.cuda.synchronize()
+    con.reset_kernel_times()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(con.stream)
+    for _ in range(args.steps):
+        losses = con.train_step(lr=1e-2)
+    ev1.record(con.stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    stage = con.stage_times()
+    fam = con.kernel_times()
+    con.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * track_seconds / (ms_per_step / 1e3)
+    finite = bool(torch.isfinite(losses).all().item())
+
+    # roofline of the dominant stage: algorithmic bytes (5 streams per node, fwd+bwd) / its device time
+    peak, peak_kind = measured_peaks()
+    proc_stages = {k: v for k, v in stage.items() if k in "ecnsgdr"}
+    dom = max(proc_stages, key=lambda k: proc_stages[k][0])
+    dom_ms_per_step = proc_stages[dom][0] / args.steps
+    dom_bytes = type_bytes[dom]
+    achieved = dom_bytes / (dom_ms_per_step / 1e3) / 1e9
+    step_achieved = tot_bytes / (ms_per_step / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"stage '{dom}' (all its fwd+bwd kernels)", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "step": {"achieved": step_achieved, "frac": step_achieved / peak, "model_bytes": tot_bytes}}
+
+    # ---------------- one launch per node (same kernels, one-by-one processing) ----------------
+    per_node = None
+    if args.per_node_steps > 0:
+        con.set_launch_mode(True)
+        con.train_step(lr=1e-2)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(con.stream)
+        for _ in range(args.per_node_steps):
+            con.train_step(lr=1e-2)
+        b.record(con.stream)
+        torch.cuda.synchronize()
+        pn_ms = a.elapsed_time(b) / args.per_node_steps
+        per_node = {"value": world * track_seconds / (pn_ms / 1e3), "ms_per_step": pn_ms,
+                    "batched_speedup": pn_ms / ms_per_step}
+        con.set_launch_mode(False)
+
+    # ---------------- end to end through the public API, host buffers ----------------
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned_src = [torch.as_tensor(s).pin_memory() for s in sources]
+        pinned_tgt = [torch.as_tensor(m).pin_memory() for m in mixes]
+        host_losses = torch.empty(con.n_songs, 7, dtype=torch.float32).pin_memory()
+        h2d = sum(s.numel() * 4 + t.numel() * 4 for s, t in zip(pinned_src, pinned_tgt))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for s in range(con.n_songs):
+                con.update_audio_host(s, pinned_src[s].numpy(), pinned_tgt[s].numpy())
+            l = con.train_step(lr=1e-2)
+            host_losses.copy_(l, non_blocking=False)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": world * track_seconds / e2e_s, "unit": "track-s/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(host_losses.numel() * 4), "ms_per_step": 1e3 * e2e_s}
+
+    # ---------------- CPU baseline: the oracle on a bounded sample ----------------
+    cpu = None
+    if rank == 0 and args.cpu_baseline_steps > 0:
+        torch.set_num_threads(os.cpu_count() or 1)
+        lay, desc = cpu_sample_layout()
+        tt, ts = 0.0, 0.0
+        for _ in range(args.cpu_baseline_steps):
+            dt, tsec, cores = oracle_sample_step(lay)
+            tt += dt
+            ts += tsec
+        cpu = {"value": ts / tt, "unit": "track-s/s", "cores": torch.get_num_threads(), "kind": "oracle",
+               "sample": desc + f", {args.cpu_baseline_steps} steps"}
+
+    if rank == 0:
+        line = {"metric": metric, "value": value, "unit": "track-s/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config, "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
+                "clocks": clk, "per_node": per_node, "losses_finite": finite,
+                "stages_ms_per_step": {k: v[0] / args.steps for k, v in stage.items()},
+                "kernel_families_ms_per_step": {k: v[0] / args.steps for k, v in fam.items() if v[1] > 0},
+                "device_bytes": info["device_bytes"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -160,6 +160,9 @@ const char* mg_kernel_family_name(int32_t family);
 /* Waits for the stream, then returns per family: total milliseconds and launch counts. */
 mg_status mg_get_kernel_times(mg_console* c, double* ms, int64_t* launches, int32_t n_families);
 mg_status mg_reset_kernel_times(mg_console* c);
+/* Same timings grouped by stage of the console: [0..6] processor types e c n s g d r (forward and backward),
+ * 7 loss (STFT, Mel, adjoint), 8 mix sums, 9 other (finalisation, optimiser).  n <= 10. */
+mg_status mg_get_stage_times(mg_console* c, double* ms, int64_t* launches, int32_t n);
 
 /* Diagnostic read-back of one processor's buffers (synchronises the stream), for per-node parity checks.
  * what: 0 output y [2][L], 1 FIR taps [2][Nh] (LTI processors), 2 FIR tap gradient [2][Nh], 3 input adjoint

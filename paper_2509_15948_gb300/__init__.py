@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "mg_get_kernel_times": [P, P, P, I32],
         "mg_reset_kernel_times": [P],
         "mg_debug_read": [P, I32, I32, P, I64],
+        "mg_get_stage_times": [P, P, P, I32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -376,6 +377,15 @@ class Console:
         out = np.zeros(shape, np.float32)
         self._check(self.lib.mg_debug_read(self.h, proc, what, out.ctypes.data, out.size))
         return out
+
+    STAGES = ("e", "c", "n", "s", "g", "d", "r", "loss", "sum", "other")
+
+    def stage_times(self) -> dict:
+        """Accumulated milliseconds and launches per console stage (processor types, loss, sums, other)."""
+        ms = (ctypes.c_double * 10)()
+        cnt = (ctypes.c_int64 * 10)()
+        self._check(self.lib.mg_get_stage_times(self.h, ms, cnt, 10))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(self.STAGES)}
 
     def reset_kernel_times(self):
         self._check(self.lib.mg_reset_kernel_times(self.h))

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -165,6 +166,12 @@ struct mg_console {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending, graph_pairs;
   double fam_ms[F_COUNT] = {0};
   int64_t fam_n[F_COUNT] = {0};
+  // stages: 0..6 processor types e c n s g d r, 7 loss, 8 mix sums, 9 other (optimiser, finalisation)
+  int cur_stage = 9;
+  double stage_ms[10] = {0};
+  int64_t stage_n[10] = {0};
+  // loss items of one song (per resolution: first item, count) for per-song target refresh
+  std::vector<std::array<int2, 3>> song_litems;
   bool capturing = false;
   std::vector<void*> small_allocs;
 };
@@ -321,6 +328,24 @@ void mel_bank(int nfft, int nmels, double fs, std::vector<std::vector<double>>& 
 // ------------------------------------------------------------------------------------------------
 // launching
 // ------------------------------------------------------------------------------------------------
+void accumulate_pair(mg_console* c, int code, cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  const int fam = code % F_COUNT, st = code / F_COUNT;
+  c->fam_ms[fam] += ms;
+  c->fam_n[fam] += 1;
+  c->stage_ms[st] += ms;
+  c->stage_n[st] += 1;
+}
+
+// RAII: launches inside belong to one stage of the per-stage timing.
+struct StageScope {
+  mg_console* c;
+  int prev;
+  StageScope(mg_console* cc, int st) : c(cc), prev(cc->cur_stage) { c->cur_stage = st; }
+  ~StageScope() { c->cur_stage = prev; }
+};
+
 template <class F>
 void run(mg_console* c, int fam, F&& f) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -334,13 +359,13 @@ void run(mg_console* c, int fam, F&& f) {
     }
     e0 = c->ev_pool[c->ev_next++];
     e1 = c->ev_pool[c->ev_next++];
-    cudaEventRecord(e0, c->stream);
+    cudaEventRecordWithFlags(e0, c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   }
   f();
   ++c->launches;
   if (c->profiling) {
-    cudaEventRecord(e1, c->stream);
-    auto pr = std::make_pair(fam, std::make_pair(e0, e1));
+    cudaEventRecordWithFlags(e1, c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+    auto pr = std::make_pair(fam + F_COUNT * c->cur_stage, std::make_pair(e0, e1));
     if (c->capturing) c->graph_pairs.push_back(pr);
     else c->pending.push_back(pr);
   }
@@ -414,6 +439,7 @@ void lti_backward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
 }
 
 void stage_forward(mg_console* c, const LaunchCtx& x, Stage& s) {
+  StageScope scope(c, s.type);
   switch (s.type) {
     case T_G:
     case T_S:
@@ -431,6 +457,7 @@ void stage_forward(mg_console* c, const LaunchCtx& x, Stage& s) {
 }
 
 void stage_backward(mg_console* c, const LaunchCtx& x, Stage& s) {
+  StageScope scope(c, s.type);
   switch (s.type) {
     case T_G:
     case T_S:
@@ -449,19 +476,23 @@ void stage_backward(mg_console* c, const LaunchCtx& x, Stage& s) {
 
 void render(mg_console* c, const LaunchCtx& x) {
   for (int level = 0; level < 2; ++level) {
-    if (level == 1 && !c->sum_m_items.h.empty())
+    if (level == 1 && !c->sum_m_items.h.empty()) {
+      StageScope scope(c, 8);
       run_items(c, F_SUM, c->sum_m_items, [&](const Item* it, int n) {
         launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n);
       });
+    }
     for (auto& s : c->stages)
       if (s.level == level) stage_forward(c, x, s);
   }
+  StageScope scope(c, 8);
   run_items(c, F_SUM, c->sum_o_items, [&](const Item* it, int n) {
     launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n);
   });
 }
 
 void loss_forward(mg_console* c, const LaunchCtx& x, int mode, float* out_losses, float* out_la, int la_stride) {
+  StageScope scope(c, 7);
   for (int r = 0; r < c->nres; ++r) {
     auto& L = c->loss_items[r];
     if (!L.h.empty())
@@ -477,13 +508,16 @@ void loss_forward(mg_console* c, const LaunchCtx& x, int mode, float* out_losses
 }
 
 void backward_pass(mg_console* c, const LaunchCtx& x) {
-  for (int r = 0; r < c->nres; ++r) {
-    auto& L = c->loss_items[r];
-    if (!L.h.empty())
-      run(c, F_LOSS_BWD, [&] { launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), 2, 8192); });
+  {
+    StageScope scope(c, 7);
+    for (int r = 0; r < c->nres; ++r) {
+      auto& L = c->loss_items[r];
+      if (!L.h.empty())
+        run(c, F_LOSS_BWD, [&] { launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), 2, 8192); });
+    }
+    run_items(c, F_LOSS_GATHER, c->gather_items,
+              [&](const Item* it, int n) { launch_loss_gather(x, c->d_songs, c->d_res, c->nres, it, n); });
   }
-  run_items(c, F_LOSS_GATHER, c->gather_items,
-            [&](const Item* it, int n) { launch_loss_gather(x, c->d_songs, c->d_res, c->nres, it, n); });
   run(c, F_MISC, [&] { cudaMemsetAsync(c->d_grads, 0, sizeof(float) * c->nparams, c->stream); });
   for (int level = 1; level >= 0; --level)
     for (int i = (int)c->stages.size() - 1; i >= 0; --i)
@@ -933,15 +967,18 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     moff += 2 * (int64_t)hs.L;
   }
   if (upload(c, c->hsd, &c->d_songs) || upload(c, mixoff, &c->d_mixoff)) return MG_ERR_CUDA;
-  // loss items
+  // loss items (song-major within each resolution, so one song's items are one contiguous range)
+  c->song_litems.assign(c->songs.size(), std::array<int2, 3>{});
   for (int r = 0; r < c->nres; ++r) {
     auto& L = c->loss_items[r];
     L.h.clear();
     const int per = 8192 / d->n_fft[r];
     for (size_t si = 0; si < c->songs.size(); ++si) {
       const HostSong& hs = c->songs[si];
+      const int first = (int)L.h.size();
       for (int t = hs.first[r]; t < hs.nframes[r]; t += per)
         L.h.push_back(make_int4((int)si, r, t, std::min(per, hs.nframes[r] - t)));
+      c->song_litems[si][r] = make_int2(first, (int)L.h.size() - first);
     }
     if (upload(c, L.h, &L.d) != MG_OK) return MG_ERR_CUDA;
   }
@@ -1230,12 +1267,7 @@ mg_status mg_train_step(mg_console* c, float lr, float beta1, float beta2, float
   CK(cudaGraphLaunch(c->graph, c->stream));
   if (c->profiling) {
     CK(cudaStreamSynchronize(c->stream));
-    for (auto& pr : c->graph_pairs) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, pr.second.first, pr.second.second);
-      c->fam_ms[pr.first] += ms;
-      c->fam_n[pr.first] += 1;
-    }
+    for (auto& pr : c->graph_pairs) accumulate_pair(c, pr.first, pr.second.first, pr.second.second);
   }
   c->fwd_valid = false;
   return MG_OK;
@@ -1275,11 +1307,13 @@ mg_status mg_update_audio(mg_console* c, int32_t song, const float* sources, con
   if (target) {
     CK(cudaMemcpy2DAsync(c->arena + hs.o_tgt, (size_t)hs.ld * sizeof(float), target, (size_t)hs.L * sizeof(float),
                          (size_t)hs.L * sizeof(float), 2, k, c->stream));
+    // target spectrograms and their norms of this song only
     LaunchCtx x = make_ctx(c, nullptr);
-    const bool prof = c->profiling;
-    c->profiling = false;
-    loss_forward(c, x, 0, nullptr, nullptr, 0);
-    c->profiling = prof;
+    for (int r = 0; r < c->nres; ++r) {
+      const int2 rg = c->song_litems[song][r];
+      if (rg.y > 0) launch_loss_frames(x, c->d_songs, c->d_res, c->loss_items[r].d + rg.x, rg.y, 0, 8192);
+    }
+    launch_loss_finalize_mode(x, c->d_songs + song, 1, c->d_res, c->nres, c->d_alphas, 0, nullptr, nullptr, 0);
   }
   c->fwd_valid = false;
   CK(cudaGetLastError());
@@ -1304,12 +1338,7 @@ const char* mg_kernel_family_name(int32_t f) { return (f >= 0 && f < F_COUNT) ? 
 mg_status mg_get_kernel_times(mg_console* c, double* ms, int64_t* launches, int32_t n) {
   if (!c) return MG_ERR_INVALID;
   CK(cudaStreamSynchronize(c->stream));
-  for (auto& pr : c->pending) {
-    float t = 0.f;
-    cudaEventElapsedTime(&t, pr.second.first, pr.second.second);
-    c->fam_ms[pr.first] += t;
-    c->fam_n[pr.first] += 1;
-  }
+  for (auto& pr : c->pending) accumulate_pair(c, pr.first, pr.second.first, pr.second.second);
   c->pending.clear();
   if (!c->capturing && c->graph_pairs.empty()) c->ev_next = 0;
   for (int i = 0; i < n && i < F_COUNT; ++i) {
@@ -1319,8 +1348,24 @@ mg_status mg_get_kernel_times(mg_console* c, double* ms, int64_t* launches, int3
   return MG_OK;
 }
 
+mg_status mg_get_stage_times(mg_console* c, double* ms, int64_t* launches, int32_t n) {
+  if (!c) return MG_ERR_INVALID;
+  double tmp[F_COUNT];
+  mg_status s = mg_get_kernel_times(c, tmp, nullptr, F_COUNT);   // folds pending event pairs in
+  if (s != MG_OK) return s;
+  for (int i = 0; i < n && i < 10; ++i) {
+    if (ms) ms[i] = c->stage_ms[i];
+    if (launches) launches[i] = c->stage_n[i];
+  }
+  return MG_OK;
+}
+
 mg_status mg_reset_kernel_times(mg_console* c) {
   if (!c) return MG_ERR_INVALID;
+  for (int i = 0; i < 10; ++i) {
+    c->stage_ms[i] = 0;
+    c->stage_n[i] = 0;
+  }
   for (int i = 0; i < F_COUNT; ++i) {
     c->fam_ms[i] = 0;
     c->fam_n[i] = 0;
