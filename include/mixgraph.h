@@ -169,6 +169,25 @@ mg_status mg_get_stage_times(mg_console* c, double* ms, int64_t* launches, int32
  * du [2][L], 4 node statistics [16], 5 output adjoint dy [2][L].  host_out must hold exactly n = rows x columns floats. */
 mg_status mg_debug_read(const mg_console* c, int32_t proc, int32_t what, float* host_out, int64_t n);
 
+/* Equalizer forward that allocates nothing.  The paper has no counterpart: this entry point serves callers
+ * that cannot allocate device memory (code running under another framework's allocator or memory pool,
+ * plug-in hosts that forbid device allocations on their processing threads, work already being recorded on
+ * a stream).  It computes one equalizer processor of the console, y = w y_bar + (1 - w) u with
+ * y_bar = h_e * u (Eqs. 7-8) and w = sigmoid(q), using the same kernels as the console.
+ *   d_u:      device [2][L] stereo input (left row, then right row), FP32
+ *   d_y:      device [2][L] output (must not overlap d_u)
+ *   L:        1 <= L <= 127,001 samples (the 2^17-point FFT must hold the signal and the 2047-tap FIR);
+ *             larger L returns MG_ERR_UNSUPPORTED without touching the GPU
+ *   d_params: device [1025]: the 1024 log-magnitudes of Eq. (7), then the dry/wet logit q
+ * Scratch: one file-scope __device__ array of about 3.2 MB, held by every GPU that loads the library until the
+ * process exits.  Every buffer in it is fully written before it is read within a call, so nothing needs
+ * clearing; calls share the array, so calls that overlap on the GPU (on different streams, or on the same
+ * device from several threads without ordering) race and must not be issued.
+ * The first call on a device, made with that device current, sets the scratch up (symbol address and lookup
+ * tables) and synchronises the stream: make that first call before any stream capture.  Later calls are
+ * asynchronous on `stream`.  Returns MG_ERR_INVALID for null pointers and MG_ERR_CUDA if a CUDA call fails. */
+mg_status mg_eq_forward_noalloc(const float* d_u, float* d_y, int64_t L, const float* d_params, cudaStream_t stream);
+
 const char* mg_last_error(const mg_console* c);
 
 #ifdef __cplusplus
