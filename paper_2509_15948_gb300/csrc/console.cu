@@ -28,12 +28,12 @@ constexpr int kParamCount[NTYPES] = {1024, 4, 4, 1, 2, 880, 768};
 enum Family {
   F_GS_FWD, F_GS_BWD, F_SUM, F_DYN_FWD, F_DYN_BWD, F_EQ_FIR, F_DLY_FIR, F_REV_FIR, F_FIR_ADJ, F_COL_FWD, F_ROW_HZ,
   F_ROW_CONV, F_COL_OUT, F_COL_DYBAR, F_ROW_BWD2, F_COL_DU, F_COL_DH, F_LOSS_FWD, F_LOSS_BWD, F_LOSS_GATHER,
-  F_FINALIZE, F_ADAM, F_MISC, F_COUNT
+  F_FINALIZE, F_ADAM, F_MISC, F_EQ_OS, F_COUNT
 };
 const char* kFamilyNames[F_COUNT] = {
     "gs_fwd", "gs_bwd", "sum", "dyn_fwd", "dyn_bwd", "eq_fir", "dly_fir", "rev_fir", "fir_adj", "col_fwd", "row_hz",
     "row_conv", "col_out", "col_dybar", "row_bwd2", "col_du", "col_dh", "loss_fwd", "loss_bwd", "loss_gather",
-    "finalize", "adam", "misc"};
+    "finalize", "adam", "misc", "eq_os"};
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int ilog2_ceil(int64_t x) {
@@ -51,7 +51,7 @@ struct HostProc {
   int nfrows = 0, nbrows = 0;
   // arena offsets (bytes)
   size_t o_y = 0, o_stats = 0, o_fpart = 0, o_bpart = 0, o_taps = 0, o_dtaps = 0, o_aux = 0, o_carry = 0, o_rcarry = 0,
-         o_cagg = 0, o_nspec = 0;
+         o_cagg = 0, o_nspec = 0, o_hspec = 0, o_dhpart = 0;
   size_t scratch_bytes = 0;  // T1 + T2 + Hz
   size_t o_scratch = 0;      // offset inside the shared LTI scratch
 };
@@ -101,6 +101,7 @@ struct Stage {
   int level, type;
   ProcList procs;
   ItemList elem;                 // g, s, c, n (tile / chunk items)
+  ItemList osf, osb;             // e: overlap-save blocks of the forward and backward kernels
   std::vector<LtiGroup> groups;  // e, r, d
 };
 
@@ -273,9 +274,14 @@ void plan(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n)
           p.logN1 = (p.logN + 1) / 2;
           p.logN2 = p.logN / 2;
           p.colG = std::min(8, std::min(8192 >> p.logN2, 1 << p.logN1));
-          p.nfrows = (1 << p.logN1) / p.colG;
-          p.nbrows = p.nfrows;
-          p.scratch_bytes = (size_t)3 * ((size_t)1 << p.logN) * sizeof(float2);
+          if (t == T_E) {   // single-pass overlap-save in shared memory (no global FFT scratch)
+            p.nfrows = (p.L + kEqOsFwdBlock - 1) / kEqOsFwdBlock;
+            p.nbrows = (p.L + kEqOsBwdBlock - 1) / kEqOsBwdBlock;
+          } else {
+            p.nfrows = (1 << p.logN1) / p.colG;
+            p.nbrows = p.nfrows;
+            p.scratch_bytes = (size_t)3 * ((size_t)1 << p.logN) * sizeof(float2);
+          }
         } else if (t == T_C || t == T_N) {
           p.nchunks = (p.L + kDynChunk - 1) / kDynChunk;
           p.nbrows = p.nchunks;
@@ -451,6 +457,11 @@ void stage_forward(mg_console* c, const LaunchCtx& x, Stage& s) {
       run_procs(c, F_DYN_FWD, s.procs, [&](const int* p, int n) { launch_dyn_fwd_carry(x, p, n); });
       run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd_apply(x, it, n); });
       break;
+    case T_E:
+      run_procs(c, F_EQ_FIR, s.procs, [&](const int* p, int n) { launch_eq_fir(x, p, n); });
+      run_procs(c, F_EQ_FIR, s.procs, [&](const int* p, int n) { launch_eq_spec(x, p, n); });
+      run_items(c, F_EQ_OS, s.osf, [&](const Item* it, int n) { launch_eq_os_fwd(x, it, n); });
+      break;
     default:
       for (auto& g : s.groups) lti_forward(c, x, s.type, g);
   }
@@ -468,6 +479,11 @@ void stage_backward(mg_console* c, const LaunchCtx& x, Stage& s) {
       run_items(c, F_DYN_BWD, s.elem, [&](const Item* it, int n) { launch_dyn_bwd_agg(x, it, n); });
       run_procs(c, F_DYN_BWD, s.procs, [&](const int* p, int n) { launch_dyn_bwd_carry(x, p, n); });
       run_items(c, F_DYN_BWD, s.elem, [&](const Item* it, int n) { launch_dyn_bwd_apply(x, it, n); });
+      break;
+    case T_E:
+      run_items(c, F_EQ_OS, s.osb, [&](const Item* it, int n) { launch_eq_os_bwd(x, it, n); });
+      run_procs(c, F_FIR_ADJ, s.procs, [&](const int* p, int n) { launch_eq_dh_reduce(x, p, n); });
+      run_procs(c, F_FIR_ADJ, s.procs, [&](const int* p, int n) { launch_eq_fir_adj(x, p, n); });
       break;
     default:
       for (auto& g : s.groups) lti_backward(c, x, s.type, g);
@@ -626,8 +642,14 @@ mg_status build_tables(mg_console* c) {
       d.T1 = (float2*)(c->scratch + p.o_scratch);
       d.T2 = d.T1 + N;
       d.Hz = d.T2 + N;
+    }
+    if (p.type == T_E || p.type == T_R || p.type == T_D) {
       d.taps = (float*)A(p.o_taps);
       d.dtaps = (float*)A(p.o_dtaps);
+    }
+    if (p.type == T_E) {
+      d.hspec = (float*)A(p.o_hspec);
+      d.dhpart = (float*)A(p.o_dhpart);
     }
     d.aux = p.o_aux ? (float*)A(p.o_aux) : nullptr;
     d.carry = p.nchunks ? (float*)A(p.o_carry) : nullptr;
@@ -701,6 +723,17 @@ mg_status build_tables(mg_console* c) {
         }
         st.elem.beg.push_back((int)st.elem.h.size());
         if (upload_items(c, st.elem) || upload_procs(c, st.procs)) return MG_ERR_CUDA;
+      } else if (t == T_E) {
+        // equalizer: overlap-save blocks (forward and backward blockings differ)
+        for (int pi : st.procs.h) {
+          st.osf.beg.push_back((int)st.osf.h.size());
+          st.osb.beg.push_back((int)st.osb.h.size());
+          for (int i = 0; i < c->procs[pi].nfrows; ++i) st.osf.h.push_back(Item{pi, i});
+          for (int i = 0; i < c->procs[pi].nbrows; ++i) st.osb.h.push_back(Item{pi, i});
+        }
+        st.osf.beg.push_back((int)st.osf.h.size());
+        st.osb.beg.push_back((int)st.osb.h.size());
+        if (upload_items(c, st.osf) || upload_items(c, st.osb) || upload_procs(c, st.procs)) return MG_ERR_CUDA;
       } else {
         // LTI: groups under the workspace limit, each with its own scratch offsets
         size_t used = 0;
@@ -763,6 +796,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
   init_kernel_attributes();
   init_loss_attributes();
   init_fir_attributes();
+  init_eqos_attributes();
   const double fs = d->sample_rate;
   // ---- arena layout ----
   Bump b;
@@ -798,10 +832,14 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     p.o_stats = b.take(16 * sizeof(float));
     if (p.nfrows) p.o_fpart = b.take((size_t)p.nfrows * kNPart * sizeof(float));
     if (p.nbrows) p.o_bpart = b.take((size_t)p.nbrows * kNPart * sizeof(float));
-    if (p.scratch_bytes) {
+    if (p.type == T_E || p.type == T_R || p.type == T_D) {
       p.o_taps = b.take((size_t)2 * p.Nh * sizeof(float));
       p.o_dtaps = b.take((size_t)2 * p.Nh * sizeof(float));
       scratch_need = std::max(scratch_need, p.scratch_bytes);
+    }
+    if (p.type == T_E) {
+      p.o_hspec = b.take((size_t)kEqOsM * sizeof(float));
+      p.o_dhpart = b.take((size_t)p.nbrows * kEqTaps * sizeof(float));
     }
     if (p.type == T_D) p.o_aux = b.take((2 * kDlyTaps * kDlyFir + 2 * kDlyTaps) * sizeof(float));
     if (p.type == T_R) {
@@ -820,7 +858,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     const int64_t limit = d->workspace_limit_bytes > 0 ? d->workspace_limit_bytes : INT64_MAX;
     size_t worst = 0;
     for (int level = 0; level < 2; ++level)
-      for (int t : {T_E, T_R, T_D}) {
+      for (int t : {T_R, T_D}) {
         size_t used = 0;
         for (auto& p : c->procs) {
           if (p.level != level || p.type != t) continue;

@@ -25,6 +25,9 @@ constexpr int kRevFG = 16;                 // frames per reverb work item
 constexpr int kDynChunk = 4096;            // samples per envelope-scan work item (256 threads x 16)
 constexpr int kElemTile = 4096;            // samples per elementwise work item
 constexpr float kEnvEps = 1e-8f;           // G_u = ln(g + eps)
+constexpr int kEqOsM = 8192;               // overlap-save FFT size of the equalizer
+constexpr int kEqOsFwdBlock = kEqOsM - 2 * kEqHalf;        // 6146 outputs per forward block
+constexpr int kEqOsBwdBlock = kEqOsM - 4 * kEqHalf;        // 4100 outputs per backward block
 
 struct Item {
   int proc;
@@ -63,6 +66,9 @@ struct ProcDev {
   // reverb
   const float2* nspec;                     // [2][F][193] STFT of the fixed mid/side noise
   int nframes;                             // F
+  // equalizer (overlap-save)
+  float* hspec;                            // [8192] real spectrum of the FIR on the overlap-save grid
+  float* dhpart;                           // [backward blocks][2047] partial tap gradients
 };
 
 struct LossRes {                           // one STFT resolution of Eq. (21)
@@ -143,6 +149,11 @@ void launch_rev_noise_stft(const LaunchCtx&, const Item* items, int n, const flo
 void init_kernel_attributes();
 void init_loss_attributes();
 void init_fir_attributes();
+void init_eqos_attributes();
+void launch_eq_spec(const LaunchCtx&, const int* procs, int n);
+void launch_eq_os_fwd(const LaunchCtx&, const Item* items, int n);
+void launch_eq_os_bwd(const LaunchCtx&, const Item* items, int n);
+void launch_eq_dh_reduce(const LaunchCtx&, const int* procs, int n);
 void launch_col_fwd_audio(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_col_fwd_taps(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_row_fwd_hz(const LaunchCtx&, const Item* items, int n, int maxN1);
