@@ -72,6 +72,12 @@ typedef struct {
                                   (Sec. 3.4); required when reverbs are enabled; copied */
   int32_t noise_on_device;     /* 1: reverb_noise is a device pointer */
   int64_t workspace_limit_bytes;  /* bound on FFT scratch for one launch group; 0 = no bound */
+  int32_t retain_spectra;      /* reverb/delay FFT convolutions: 1 = every node keeps its filter spectrum, input
+                                  spectrum and wet signal from the forward for the backward (3 N complex values per
+                                  node, N the node's FFT size; the backward then runs 3 instead of 6 length-N FFTs);
+                                  -1 = the backward recomputes them in a shared scratch; 0 = automatic: keep when
+                                  the kept buffers fit in workspace_limit_bytes (if set) and in 80 % of the device
+                                  memory free after the console's other buffers */
 } mg_console_desc;
 
 /* Sizes of a console (layout only). */
@@ -85,6 +91,7 @@ typedef struct {
   double track_seconds;        /* sum over songs of K * L / fs */
   int64_t device_bytes;        /* device memory held by the console (0 from mg_plan) */
   int32_t launches_per_step;   /* kernel launches of forward_loss + backward + adam_step (0 from mg_plan) */
+  int32_t retains_spectra;     /* 1 when the reverb/delay spectra are kept between forward and backward */
 } mg_console_info;
 
 /* Host-only layout planning (no GPU needed): fills sizes for the given console. */

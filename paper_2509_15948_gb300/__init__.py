@@ -42,14 +42,14 @@ class ConsoleDesc(ctypes.Structure):
                 ("a_weighting", ctypes.c_int32), ("warmup_samples", ctypes.c_int64), ("alpha_lr", ctypes.c_float),
                 ("alpha_m", ctypes.c_float), ("alpha_s", ctypes.c_float), ("alpha_g", ctypes.c_float),
                 ("reverb_noise", ctypes.c_void_p), ("noise_on_device", ctypes.c_int32),
-                ("workspace_limit_bytes", ctypes.c_int64)]
+                ("workspace_limit_bytes", ctypes.c_int64), ("retain_spectra", ctypes.c_int32)]
 
 
 class ConsoleInfo(ctypes.Structure):
     _fields_ = [("n_songs", ctypes.c_int32), ("n_processors", ctypes.c_int32), ("n_proc_params", ctypes.c_int64),
                 ("n_params", ctypes.c_int64), ("n_reverbs", ctypes.c_int32), ("total_samples", ctypes.c_int64),
                 ("track_seconds", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("launches_per_step", ctypes.c_int32)]
+                ("launches_per_step", ctypes.c_int32), ("retains_spectra", ctypes.c_int32)]
 
 
 _lib = None
@@ -118,6 +118,7 @@ class ConsoleConfig:
     alpha_s: float = 0.25
     alpha_g: float = 1e-3
     workspace_limit_bytes: int = 0
+    retain_spectra: int = 0   # 1 keep, -1 recompute, 0 automatic (see mg_console_desc)
 
     def type_mask(self) -> int:
         return sum(1 << i for i, t in enumerate(TYPE_ORDER) if t in self.types)
@@ -146,6 +147,7 @@ def _desc(cfg: ConsoleConfig, noise_ptr: int = 0, noise_on_device: int = 0) -> C
     d.reverb_noise = noise_ptr
     d.noise_on_device = noise_on_device
     d.workspace_limit_bytes = cfg.workspace_limit_bytes
+    d.retain_spectra = cfg.retain_spectra
     return d
 
 

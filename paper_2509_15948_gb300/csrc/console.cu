@@ -161,6 +161,7 @@ struct mg_console {
   bool graph_profiled = false;
   int launches = 0;
   int launches_step = 0;
+  bool retain = false;           // reverb/delay nodes keep Hz, U and y_bar from the forward (own scratch each)
   // profiling
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_next = 0;
@@ -208,6 +209,7 @@ mg_status validate(mg_console* c, const mg_console_desc* d, const mg_song_desc* 
   }
   if (d->n_mels < 0 || d->n_mels > 512) return fail(c, MG_ERR_INVALID, "n_mels must be in [0, 512]");
   if (d->warmup_samples < 0) return fail(c, MG_ERR_INVALID, "negative warmup_samples");
+  if (d->retain_spectra < -1 || d->retain_spectra > 1) return fail(c, MG_ERR_INVALID, "retain_spectra must be -1, 0 or 1");
   for (int i = 0; i < n; ++i) {
     if (s[i].num_tracks < 1 || s[i].num_subgroups < 0) return fail(c, MG_ERR_INVALID, "song needs >= 1 track");
     if (s[i].num_samples < 1 || s[i].num_samples > (1 << 22) - 200000)
@@ -423,16 +425,25 @@ void lti_forward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
   run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
   run_items(c, F_ROW_HZ, g.rowhz, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowhz.maxv); });
   run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_audio(x, it, n, g.col.maxv); });
+  if (c->retain) {   // U stays in T1, y_bar in T2 (natural order) for the backward
+    run_items(c, F_ROW_CONV, g.rowpair, [&](const Item* it, int n) { launch_row_conv_fwd(x, it, n, g.rowpair.maxv, true); });
+    run_items(c, F_COL_OUT, g.col, [&](const Item* it, int n) { launch_col_inv_out_keep(x, it, n, g.col.maxv); });
+    return;
+  }
   run_items(c, F_ROW_CONV, g.rowpair, [&](const Item* it, int n) { launch_row_conv_fwd(x, it, n, g.rowpair.maxv, false); });
   run_items(c, F_COL_OUT, g.col, [&](const Item* it, int n) { launch_col_inv_out(x, it, n, g.col.maxv); });
 }
 
 void lti_backward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
-  run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
-  run_items(c, F_ROW_HZ, g.rowhz, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowhz.maxv); });
-  run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_audio(x, it, n, g.col.maxv); });
-  run_items(c, F_ROW_CONV, g.rowpair, [&](const Item* it, int n) { launch_row_conv_fwd(x, it, n, g.rowpair.maxv, true); });
-  run_items(c, F_COL_DYBAR, g.col, [&](const Item* it, int n) { launch_col_dybar(x, it, n, g.col.maxv); });
+  if (c->retain) {
+    run_items(c, F_COL_DYBAR, g.col, [&](const Item* it, int n) { launch_col_dybar_keep(x, it, n, g.col.maxv); });
+  } else {
+    run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
+    run_items(c, F_ROW_HZ, g.rowhz, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowhz.maxv); });
+    run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_audio(x, it, n, g.col.maxv); });
+    run_items(c, F_ROW_CONV, g.rowpair, [&](const Item* it, int n) { launch_row_conv_fwd(x, it, n, g.rowpair.maxv, true); });
+    run_items(c, F_COL_DYBAR, g.col, [&](const Item* it, int n) { launch_col_dybar(x, it, n, g.col.maxv); });
+  }
   run_items(c, F_ROW_BWD2, g.rowpair, [&](const Item* it, int n) { launch_row_bwd2(x, it, n, g.rowpair.maxv); });
   run_items(c, F_COL_DU, g.col, [&](const Item* it, int n) { launch_col_du(x, it, n, g.col.maxv); });
   run_items(c, F_COL_DH, g.col, [&](const Item* it, int n) { launch_col_dh(x, it, n, g.col.maxv); });
@@ -753,10 +764,12 @@ mg_status build_tables(mg_console* c) {
         };
         for (int pi : st.procs.h) {
           HostProc& p = c->procs[pi];
-          if (used > 0 && (int64_t)(used + p.scratch_bytes) > limit)
-            if (close() != MG_OK) return MG_ERR_CUDA;
-          p.o_scratch = used;
-          used += p.scratch_bytes;
+          if (!c->retain) {   // retained spectra: the offsets fixed at creation, one group per stage
+            if (used > 0 && (int64_t)(used + p.scratch_bytes) > limit)
+              if (close() != MG_OK) return MG_ERR_CUDA;
+            p.o_scratch = used;
+            used += p.scratch_bytes;
+          }
           ProcDev& d = c->hpd[pi];
           const size_t N = (size_t)1 << p.logN;
           d.T1 = (float2*)(c->scratch + p.o_scratch);
@@ -868,6 +881,30 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
         }
       }
     c->scratch_bytes = std::max(worst, scratch_need);
+    // retained spectra: every reverb/delay node gets its own T1 / T2 / Hz for the whole step
+    size_t keep = 0;
+    for (auto& p : c->procs)
+      if (p.type == T_R || p.type == T_D) keep += p.scratch_bytes;
+    bool retain = d->retain_spectra == 1;
+    if (d->retain_spectra == 0 && (int64_t)keep <= limit) {
+      retain = keep <= c->scratch_bytes;   // costs no memory beyond the shared scratch
+      if (!retain) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return MG_ERR_CUDA;
+        const size_t others = b.off + 4 * sizeof(float) * (size_t)c->nparams + ((size_t)256 << 20);
+        retain = free_b > others && (double)keep <= 0.8 * (double)(free_b - others);
+      }
+    }
+    c->retain = retain;
+    if (retain) {
+      size_t off = 0;
+      for (auto& p : c->procs)
+        if (p.type == T_R || p.type == T_D) {
+          p.o_scratch = off;
+          off += p.scratch_bytes;
+        }
+      c->scratch_bytes = std::max(keep, scratch_need);
+    }
   }
   c->arena_bytes = b.off;
   // ---- allocations ----
@@ -916,6 +953,12 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     std::vector<float2> dw(D);
     for (int q = 0; q < D; ++q) dw[q] = make_float2((float)std::cos(2 * PI * q / D), (float)std::sin(2 * PI * q / D));
     c->tab.tw = (const float2*)up_table(tw.data(), tw.size() * sizeof(float2));
+    std::vector<float2> twf(kTwN);
+    for (int j = 0; j < kTwN; ++j) {
+      const double a = 2 * PI * j / (double)(1 << kTwFineLog);
+      twf[j] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    c->tab.twf = (const float2*)up_table(twf.data(), twf.size() * sizeof(float2));
     c->tab.cos_eq = (const float*)up_table(ceq.data(), ceq.size() * sizeof(float));
     c->tab.cos_dl = (const float*)up_table(cdl.data(), cdl.size() * sizeof(float));
     c->tab.rev_win = (const float*)up_table(hwin.data(), hwin.size() * sizeof(float));
@@ -923,7 +966,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     c->tab.hann_eq = (const float*)up_table(heq.data(), heq.size() * sizeof(float));
     c->tab.hann_dl = (const float*)up_table(hdl.data(), hdl.size() * sizeof(float));
     c->tab.dly_w = (const float2*)up_table(dw.data(), dw.size() * sizeof(float2));
-    if (!c->tab.tw || !c->tab.dly_w) return fail(c, MG_ERR_OOM, "table allocation failed");
+    if (!c->tab.tw || !c->tab.twf || !c->tab.dly_w) return fail(c, MG_ERR_OOM, "table allocation failed");
   }
   // loss resolutions
   c->hres.assign(c->nres, LossRes{});
@@ -1115,6 +1158,7 @@ void fill_info(const mg_console* c, mg_console_info* o) {
   o->track_seconds = c->track_seconds;
   o->device_bytes = (int64_t)(c->arena_bytes + c->scratch_bytes + 4 * sizeof(float) * c->nparams);
   o->launches_per_step = c->launches_step;
+  o->retains_spectra = c->retain ? 1 : 0;
 }
 
 }  // namespace
@@ -1136,6 +1180,7 @@ mg_status mg_plan(const mg_console_desc* desc, const mg_song_desc* songs, int32_
   fill_info(&tmp, out);
   out->device_bytes = 0;
   out->launches_per_step = 0;
+  out->retains_spectra = 0;
   return MG_OK;
 }
 

@@ -9,7 +9,7 @@
 // Both channels travel as one complex signal z = left + i right; a stereo FIR (h_l, h_r) acts on the packed
 // spectrum as Y[k] = Z[k] A[k] + conj(Z[-k]) B[k] with A = (H_l + H_r)/2, B = (H_l - H_r)/2, where the
 // mirror bin -k sits in row N2 - k2.
-#include "mg_fft.cuh"
+#include "mg_fftp.cuh"
 
 namespace mg {
 
@@ -17,6 +17,11 @@ namespace {
 
 constexpr int kColThreads = 512;
 constexpr int kRowThreads = 256;
+// Shared-memory layouts (padded, see mg_fftp.cuh).  Column pass: column g, row r at sm[g * col_stride + pidx(r)],
+// with col_stride = 16 (mod 16) + 16 / G so that the G columns and 16 / G rows a half-warp touches fall in
+// distinct bank pairs.  Row pass: row slot s, position k1 at sm[s * pstride(N1) + pidx(k1)].
+constexpr int kColBuf = 8192 + 512 + 160;
+__host__ __device__ constexpr int col_stride(int N2, int G) { return ((N2 + (N2 >> 4) + 15) & ~15) + 16 / G; }
 
 __device__ __forceinline__ int mirror_pos(int k2, int k1, int N1) { return k2 == 0 ? ((N1 - k1) & (N1 - 1)) : (N1 - 1 - k1); }
 
@@ -43,10 +48,16 @@ __device__ __forceinline__ void fir_ab(float2 hz, float2 hzm, float2& A, float2&
   B = cscale(csub(hl, hr), 0.5f);
 }
 
-enum ColMode { COL_FWD_AUDIO = 0, COL_FWD_TAPS = 1, COL_INV_OUT = 2, COL_DYBAR = 3, COL_DU = 4, COL_DH = 5 };
+// COL_INV_OUT_KEEP / COL_DYBAR_KEEP: the retained-spectra variants.  The forward's inverse column pass reads the
+// product rows from T2 and also stores the wet signal y_bar in natural order over T2 (the positions the CTA read);
+// the backward's dL/dy_bar pass then loads y_bar from there instead of transforming the product again.
+enum ColMode {
+  COL_FWD_AUDIO = 0, COL_FWD_TAPS = 1, COL_INV_OUT = 2, COL_DYBAR = 3, COL_DU = 4, COL_DH = 5,
+  COL_INV_OUT_KEEP = 6, COL_DYBAR_KEEP = 7
+};
 
 template <int MODE>
-__global__ void __launch_bounds__(kColThreads) k_col(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   __shared__ float red[2 * 32];
   const Item it = items[blockIdx.x];
@@ -56,10 +67,15 @@ __global__ void __launch_bounds__(kColThreads) k_col(LaunchCtx c, const Item* __
   const int64_t N = (int64_t)1 << logN;
   const int c0 = it.idx * G;
   const int tot = N2 * G;
-  constexpr bool kInv = MODE == COL_INV_OUT || MODE == COL_DYBAR || MODE == COL_DU || MODE == COL_DH;
+  const int cs = col_stride(N2, G);
+  constexpr bool kInv = MODE == COL_INV_OUT || MODE == COL_DYBAR || MODE == COL_DU || MODE == COL_DH ||
+                        MODE == COL_INV_OUT_KEEP;
+  constexpr bool kOut = MODE == COL_INV_OUT || MODE == COL_INV_OUT_KEEP;
+  constexpr bool kDybar = MODE == COL_DYBAR || MODE == COL_DYBAR_KEEP;
 
   // ---- load ----
   float2* src = (MODE == COL_INV_OUT || MODE == COL_DH) ? P.T1 : P.T2;
+#pragma unroll 4
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     const int g = e & (G - 1), r = e >> logG;
     const int n1 = c0 + g;
@@ -73,31 +89,32 @@ __global__ void __launch_bounds__(kColThreads) k_col(LaunchCtx c, const Item* __
     } else {
       v = src[n];
     }
-    sm[e] = v;
+    sm[g * cs + pidx(r)] = v;
   }
   __syncthreads();
-  fft_smem<kInv, 4>(sm, logN2, G, G, 1, c.tab.tw);
+  if (MODE != COL_DYBAR_KEEP) fft_p<kInv>(sm, logN2, G, cs, c.tab.tw);
 
-  if (!kInv) {  // forward column pass: twiddle, store in place (row k2 = r)
+  if (!kInv && !kDybar) {  // forward column pass: twiddle, store in place (row k2 = r)
     float2* dst = MODE == COL_FWD_TAPS ? P.Hz : P.T1;
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
       const int g = e & (G - 1), k2 = e >> logG;
       const int n1 = c0 + g;
-      const float2 w = twiddle_pow2((unsigned)n1 * (unsigned)k2, logN, false);
-      dst[(int64_t)n1 + ((int64_t)k2 << logN1)] = cmul(sm[e], w);
+      const float2 w = twiddle_tab((unsigned)n1 * (unsigned)k2, logN, false, c.tab);
+      dst[(int64_t)n1 + ((int64_t)k2 << logN1)] = cmul(sm[g * cs + pidx(k2)], w);
     }
     return;
   }
 
   const float inv_n = ldexpf(1.f, -logN);
-  if (MODE == COL_INV_OUT) {
+  if (kOut) {
     const float w = dry_wet_w(c, P.qidx);
     float acc[2] = {0.f, 0.f};
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
       const int g = e & (G - 1), r = e >> logG;
       const int64_t n = (int64_t)(c0 + g) + ((int64_t)r << logN1);
       if (n < P.L) {
-        const float2 yb = cscale(sm[e], inv_n);
+        const float2 yb = cscale(sm[g * cs + pidx(r)], inv_n);
+        if (MODE == COL_INV_OUT_KEEP) P.T2[n] = yb;
         const float ul = P.u[n], ur = P.u[P.ld + n];
         P.y[n] = w * yb.x + (1.f - w) * ul;
         P.y[P.ld + n] = w * yb.y + (1.f - w) * ur;
@@ -114,7 +131,7 @@ __global__ void __launch_bounds__(kColThreads) k_col(LaunchCtx c, const Item* __
     }
     return;
   }
-  if (MODE == COL_DYBAR) {
+  if (kDybar) {
     // y_bar -> dL/dy_bar = w dy + c1 (y_bar_l + y_bar_r) on both channels; dw partial; then forward FFT
     const float w = dry_wet_w(c, P.qidx);
     const float c1 = P.stats[2];
@@ -124,24 +141,24 @@ __global__ void __launch_bounds__(kColThreads) k_col(LaunchCtx c, const Item* __
       const int64_t n = (int64_t)(c0 + g) + ((int64_t)r << logN1);
       float2 v = make_float2(0.f, 0.f);
       if (n < P.L) {
-        const float2 yb = cscale(sm[e], inv_n);
+        const float2 yb = MODE == COL_DYBAR_KEEP ? sm[g * cs + pidx(r)] : cscale(sm[g * cs + pidx(r)], inv_n);
         const float gl = P.dy[n], gr = P.dy[P.ld + n];
         const float ul = P.u[n], ur = P.u[P.ld + n];
         acc[0] += gl * (yb.x - ul) + gr * (yb.y - ur);
         const float gm = c1 * (yb.x + yb.y);
         v = make_float2(w * gl + gm, w * gr + gm);
       }
-      sm[e] = v;
+      sm[g * cs + pidx(r)] = v;
     }
     float out[1];
     block_sum<1>(acc, red, out);   // also acts as the barrier before the FFT
     if (threadIdx.x == 0) P.bpart[it.idx * kNPart + 0] = out[0];
-    fft_smem<false, 4>(sm, logN2, G, G, 1, c.tab.tw);
+    fft_p<false>(sm, logN2, G, cs, c.tab.tw);
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
       const int g = e & (G - 1), k2 = e >> logG;
       const int n1 = c0 + g;
-      const float2 tw = twiddle_pow2((unsigned)n1 * (unsigned)k2, logN, false);
-      P.T2[(int64_t)n1 + ((int64_t)k2 << logN1)] = cmul(sm[e], tw);
+      const float2 tw = twiddle_tab((unsigned)n1 * (unsigned)k2, logN, false, c.tab);
+      P.T2[(int64_t)n1 + ((int64_t)k2 << logN1)] = cmul(sm[g * cs + pidx(k2)], tw);
     }
     return;
   }
@@ -152,7 +169,7 @@ __global__ void __launch_bounds__(kColThreads) k_col(LaunchCtx c, const Item* __
       const int g = e & (G - 1), r = e >> logG;
       const int64_t n = (int64_t)(c0 + g) + ((int64_t)r << logN1);
       if (n < P.L) {
-        const float2 dw = cscale(sm[e], inv_n);
+        const float2 dw = cscale(sm[g * cs + pidx(r)], inv_n);
         const float um = c2 * (P.u[n] + P.u[P.ld + n]);
         P.du[n] = (1.f - w) * P.dy[n] + dw.x + um;
         P.du[P.ld + n] = (1.f - w) * P.dy[P.ld + n] + dw.y + um;
@@ -170,7 +187,7 @@ __global__ void __launch_bounds__(kColThreads) k_col(LaunchCtx c, const Item* __
       if (j >= 0 && j < P.Nh) {
         // dL/dh[t] = sum_n dL/dy_bar[n] u[n - t] is identically zero for lags t >= L: store the exact zero
         // instead of the FFT rounding residue (the delay's Eq. 19 direction takes sgn(0) = 0 there)
-        const float2 v = (j + P.n0 >= P.L) ? make_float2(0.f, 0.f) : cscale(sm[e], inv_n);
+        const float2 v = (j + P.n0 >= P.L) ? make_float2(0.f, 0.f) : cscale(sm[g * cs + pidx(r)], inv_n);
         P.dtaps[j] = v.x;
         P.dtaps[P.Nh + j] = v.y;
       }
@@ -179,85 +196,86 @@ __global__ void __launch_bounds__(kColThreads) k_col(LaunchCtx c, const Item* __
 }
 
 // Row pass of the filter spectrum: forward N1-point FFT of row k2 of Hz, in place.
-__global__ void __launch_bounds__(kRowThreads) k_row_fwd_hz(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kRowThreads, 4) k_row_fwd_hz(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const int logN1 = P.logN1, N1 = 1 << logN1;
   float2* row = P.Hz + ((int64_t)it.idx << logN1);
-  for (int e = threadIdx.x; e < N1; e += blockDim.x) sm[e] = row[e];
+  for (int e = threadIdx.x; e < N1; e += blockDim.x) sm[pidx(e)] = row[e];
   __syncthreads();
-  fft_smem<false, 2>(sm, logN1, 1, 1, N1, c.tab.tw);
-  for (int e = threadIdx.x; e < N1; e += blockDim.x) row[e] = sm[e];
+  fft_p<false>(sm, logN1, 1, pstride(N1), c.tab.tw);
+  for (int e = threadIdx.x; e < N1; e += blockDim.x) row[e] = sm[pidx(e)];
 }
 
 // Loads rows a and b (b may equal a) of src into smem slots 0/1 and runs their forward FFTs.
 __device__ __forceinline__ void load_rows_fft(float2* s, const float2* src, int a, int b, int logN1, const float2* tw) {
-  const int N1 = 1 << logN1;
+  const int N1 = 1 << logN1, rs = pstride(N1);
   const int nr = a == b ? 1 : 2;
   for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
     const int slot = e >> logN1, k1 = e & (N1 - 1);
-    s[e] = src[((int64_t)(slot ? b : a) << logN1) + k1];
+    s[slot * rs + pidx(k1)] = src[((int64_t)(slot ? b : a) << logN1) + k1];
   }
   __syncthreads();
-  fft_smem<false, 4>(s, logN1, nr, 1, N1, tw);
+  fft_p<false>(s, logN1, nr, rs, tw);
 }
 
 // Inverse row FFT of the slots in o, twiddle exp(+2 pi i n1 k2 / N), store rows a, b of dst.
-__device__ __forceinline__ void inv_rows_store(float2* o, float2* dst, int a, int b, int logN1, int logN, const float2* tw) {
-  const int N1 = 1 << logN1;
+__device__ __forceinline__ void inv_rows_store(float2* o, float2* dst, int a, int b, int logN1, int logN, const Tables& tab) {
+  const int N1 = 1 << logN1, rs = pstride(N1);
   const int nr = a == b ? 1 : 2;
   __syncthreads();
-  fft_smem<true, 4>(o, logN1, nr, 1, N1, tw);
+  fft_p<true>(o, logN1, nr, rs, tab.tw);
   for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
     const int slot = e >> logN1, n1 = e & (N1 - 1);
     const int k2 = slot ? b : a;
-    dst[((int64_t)k2 << logN1) + n1] = cmul(o[e], twiddle_pow2((unsigned)n1 * (unsigned)k2, logN, true));
+    dst[((int64_t)k2 << logN1) + n1] = cmul(o[slot * rs + pidx(n1)], twiddle_tab((unsigned)n1 * (unsigned)k2, logN, true, tab));
   }
 }
 
 // Forward convolution (and first backward step): spectrum of u in rows of T1; Y = Z A + conj(Z_-) B;
 // inverse row FFT to T1 (forward) or T2 (backward, where T1 keeps the spectrum of u for the FIR gradient).
 template <bool BWD>
-__global__ void __launch_bounds__(kRowThreads) k_row_conv(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kRowThreads, 4) k_row_conv(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const int logN1 = P.logN1, N1 = 1 << logN1, logN2 = P.logN2, N2 = 1 << logN2;
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
-  const int nr = a == b ? 1 : 2;
+  const int nr = a == b ? 1 : 2, rs = pstride(N1);
   float2* s = sm;
-  float2* o = sm + 2 * N1;
+  float2* o = sm + 2 * rs;
   load_rows_fft(s, P.T1, a, b, logN1, c.tab.tw);
   for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
     const int slot = e >> logN1, k1 = e & (N1 - 1);
     const int k2 = slot ? b : a, m2 = slot ? a : b;
     const int mslot = (a == b) ? 0 : (slot ^ 1);
     const int mk1 = mirror_pos(k2, k1, N1);
-    if (BWD) P.T1[((int64_t)k2 << logN1) + k1] = s[e];
+    const float2 z = s[slot * rs + pidx(k1)];
+    if (BWD) P.T1[((int64_t)k2 << logN1) + k1] = z;
     const float2 hz = P.Hz[((int64_t)k2 << logN1) + k1];
     const float2 hzm = P.Hz[((int64_t)m2 << logN1) + mk1];
     float2 A, B;
     fir_ab(hz, hzm, A, B);
-    o[e] = cadd(cmul(s[e], A), cmul(cconj(s[(mslot << logN1) + mk1]), B));
+    o[slot * rs + pidx(k1)] = cadd(cmul(z, A), cmul(cconj(s[mslot * rs + pidx(mk1)]), B));
   }
-  inv_rows_store(o, BWD ? P.T2 : P.T1, a, b, logN1, P.logN, c.tab.tw);
+  inv_rows_store(o, BWD ? P.T2 : P.T1, a, b, logN1, P.logN, c.tab);
 }
 
 // Second backward step.  Rows of T2 hold the column-transformed dL/dy_bar; T1 holds the spectrum of u.
 //   dU  = Dz conj(A) + conj(Dz_-) conj(B)                    (correlation with the FIR: adjoint of y = h * u)
 //   dH  = D_l conj(U_l) + i D_r conj(U_r)                      (dL/dh_c[j] = sum_n dL/dy_bar_c[n] u_c[n - j])
 // Inverse row FFTs: dU to T2, dH to T1.
-__global__ void __launch_bounds__(kRowThreads) k_row_bwd2(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kRowThreads, 4) k_row_bwd2(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const int logN1 = P.logN1, N1 = 1 << logN1, logN2 = P.logN2, N2 = 1 << logN2;
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
-  const int nr = a == b ? 1 : 2;
+  const int nr = a == b ? 1 : 2, rs = pstride(N1);
   float2* s = sm;
-  float2* o1 = sm + 2 * N1;
-  float2* o2 = sm + 4 * N1;
+  float2* o1 = sm + 2 * rs;
+  float2* o2 = sm + 4 * rs;
   load_rows_fft(s, P.T2, a, b, logN1, c.tab.tw);
   for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
     const int slot = e >> logN1, k1 = e & (N1 - 1);
@@ -267,8 +285,9 @@ __global__ void __launch_bounds__(kRowThreads) k_row_bwd2(LaunchCtx c, const Ite
     const int64_t ib = ((int64_t)k2 << logN1) + k1, im = ((int64_t)m2 << logN1) + mk1;
     float2 A, B;
     fir_ab(P.Hz[ib], P.Hz[im], A, B);
-    const float2 dz = s[e], dzm = s[(mslot << logN1) + mk1];
-    o1[e] = cadd(cmul(dz, cconj(A)), cmul(cconj(dzm), cconj(B)));
+    const int pe = slot * rs + pidx(k1);
+    const float2 dz = s[pe], dzm = s[mslot * rs + pidx(mk1)];
+    o1[pe] = cadd(cmul(dz, cconj(A)), cmul(cconj(dzm), cconj(B)));
     const float2 zu = P.T1[ib], zum = P.T1[im];
     const float2 ul = cscale(cadd(zu, cconj(zum)), 0.5f);
     const float2 du_ = csub(zu, cconj(zum));
@@ -277,34 +296,38 @@ __global__ void __launch_bounds__(kRowThreads) k_row_bwd2(LaunchCtx c, const Ite
     const float2 dd = csub(dz, cconj(dzm));
     const float2 dr = make_float2(0.5f * dd.y, -0.5f * dd.x);
     const float2 hl = cmulc(dl, ul), hr = cmulc(dr, ur);
-    o2[e] = make_float2(hl.x - hr.y, hl.y + hr.x);   // hl + i hr
+    o2[pe] = make_float2(hl.x - hr.y, hl.y + hr.x);   // hl + i hr
   }
   __syncthreads();
   // every thread has read its T1 entries; the inverse FFTs below overwrite T1 rows a, b only
-  inv_rows_store(o1, P.T2, a, b, logN1, P.logN, c.tab.tw);
-  inv_rows_store(o2, P.T1, a, b, logN1, P.logN, c.tab.tw);
+  inv_rows_store(o1, P.T2, a, b, logN1, P.logN, c.tab);
+  inv_rows_store(o2, P.T1, a, b, logN1, P.logN, c.tab);
 }
 
 template <int MODE>
 void launch_col(const LaunchCtx& c, const Item* items, int n, int maxN2G) {
   if (!n) return;
-  const size_t smem = (size_t)maxN2G * sizeof(float2);
+  (void)maxN2G;
+  const size_t smem = (size_t)kColBuf * sizeof(float2);
   k_col<MODE><<<n, kColThreads, smem, c.stream>>>(c, items);
 }
 
 }  // namespace
 
 void init_kernel_attributes() {
-  const int big = 8192 * (int)sizeof(float2);
+  const int big = kColBuf * (int)sizeof(float2);
   cudaFuncSetAttribute(k_col<COL_FWD_AUDIO>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_col<COL_FWD_TAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_col<COL_INV_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_col<COL_DYBAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_col<COL_DU>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_col<COL_DH>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_row_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 2048 * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_row_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 2048 * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_row_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * 2048 * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_col<COL_INV_OUT_KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_col<COL_DYBAR_KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_row_fwd_hz, cudaFuncAttributeMaxDynamicSharedMemorySize, pstride(4096) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * pstride(2048) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * pstride(2048) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * pstride(2048) * (int)sizeof(float2));
 }
 
 void launch_col_fwd_audio(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_FWD_AUDIO>(c, items, n, m); }
@@ -313,21 +336,23 @@ void launch_col_inv_out(const LaunchCtx& c, const Item* items, int n, int m) { l
 void launch_col_dybar(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_DYBAR>(c, items, n, m); }
 void launch_col_du(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_DU>(c, items, n, m); }
 void launch_col_dh(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_DH>(c, items, n, m); }
+void launch_col_inv_out_keep(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_INV_OUT_KEEP>(c, items, n, m); }
+void launch_col_dybar_keep(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_DYBAR_KEEP>(c, items, n, m); }
 
 void launch_row_fwd_hz(const LaunchCtx& c, const Item* items, int n, int maxN1) {
-  if (n) k_row_fwd_hz<<<n, kRowThreads, (size_t)maxN1 * sizeof(float2), c.stream>>>(c, items);
+  if (n) k_row_fwd_hz<<<n, kRowThreads, (size_t)pstride(maxN1) * sizeof(float2), c.stream>>>(c, items);
 }
 
 void launch_row_conv_fwd(const LaunchCtx& c, const Item* items, int n, int maxN1, bool bwd) {
   if (!n) return;
-  const size_t smem = (size_t)4 * maxN1 * sizeof(float2);
+  const size_t smem = (size_t)4 * pstride(maxN1) * sizeof(float2);
   if (bwd) k_row_conv<true><<<n, kRowThreads, smem, c.stream>>>(c, items);
   else k_row_conv<false><<<n, kRowThreads, smem, c.stream>>>(c, items);
 }
 
 void launch_row_bwd2(const LaunchCtx& c, const Item* items, int n, int maxN1) {
   if (!n) return;
-  const size_t smem = (size_t)6 * maxN1 * sizeof(float2);
+  const size_t smem = (size_t)6 * pstride(maxN1) * sizeof(float2);
   k_row_bwd2<<<n, kRowThreads, smem, c.stream>>>(c, items);
 }
 

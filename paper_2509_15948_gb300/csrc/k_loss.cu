@@ -8,7 +8,7 @@
 // Adjoint: the same frames are re-transformed, dL/dY_hat per band goes back to the bins through the
 // transposed Mel CSR, to the complex bins through |X|, to the packed Hermitian spectrum, and through one
 // inverse FFT to the windowed frame; a gather kernel overlap-adds the frames of all resolutions.
-#include "mg_fft.cuh"
+#include "mg_fftp.cuh"
 
 namespace mg {
 
@@ -16,10 +16,13 @@ namespace {
 constexpr int kLossThreads = 512;
 constexpr float kLogEps = 1e-5f;
 constexpr float kMagEps = 1e-8f;
+// frames of one item live in a padded layout: frame f, sample j at sm[f * pstride(n) + pidx(j)];
+// an item holds 8192 samples (8192 / n_fft <= 128 frames), so the buffer needs 8192 + 512 + 128 entries.
+constexpr int kFrameBuf = 8192 + 512 + 128;
 
 // channel magnitudes^2 of bin k (|X_L|^2, |X_R|^2, |X_M|^2, |X_S|^2) and the complex X_L, X_R
 __device__ __forceinline__ void bin_spectra(const float2* Z, int k, int n, float2& XL, float2& XR) {
-  const float2 a = Z[k], b = Z[(n - k) & (n - 1)];
+  const float2 a = Z[pidx(k)], b = Z[pidx((n - k) & (n - 1))];
   XL = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
   // (a - conj b) / 2i
   const float2 d = make_float2(a.x - b.x, a.y + b.y);
@@ -46,19 +49,19 @@ __device__ __forceinline__ float band_value(const LossRes& R, const float2* Z, i
 }
 
 __device__ __forceinline__ void load_frames(float2* sm, const float* x, int ld, int L, const LossRes& R, int t0, int nb) {
-  const int n = R.nfft;
+  const int n = R.nfft, bs = pstride(n);
   for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
     const int f = e >> R.log_nfft, j = e & (n - 1);
     const int s = (t0 + f) * R.hop + j;
     const float w = R.win[j];
-    sm[e] = (s < L) ? make_float2(x[s] * w, x[ld + s] * w) : make_float2(0.f, 0.f);
+    sm[f * bs + pidx(j)] = (s < L) ? make_float2(x[s] * w, x[ld + s] * w) : make_float2(0.f, 0.f);
   }
 }
 }  // namespace
 
 // item (song, res, first frame, frames); mode 0: write target spectrogram + partial sum Y^2 per set;
 // mode 1: partial sums of |dlog| and (Y - Yhat)^2 per set; mode 2: adjoint frames to dF.
-__global__ void __launch_bounds__(kLossThreads) k_loss_frames(LaunchCtx c, const SongDev* __restrict__ songs,
+__global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, const SongDev* __restrict__ songs,
                                                               const LossRes* __restrict__ resv,
                                                               const int4* __restrict__ items, int mode) {
   extern __shared__ float2 sm[];
@@ -66,17 +69,17 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_frames(LaunchCtx c, const
   const int4 it = items[blockIdx.x];
   const SongDev& S = songs[it.x];
   const LossRes& R = resv[it.y];
-  const int t0 = it.z, nb = it.w, n = R.nfft, nbands = R.nbands;
+  const int t0 = it.z, nb = it.w, n = R.nfft, nbands = R.nbands, bs = pstride(n);
   const float* x = mode == 0 ? S.target : S.mix;
   load_frames(sm, x, S.ld, S.L, R, t0, nb);
   __syncthreads();
-  fft_smem<false, 4>(sm, R.log_nfft, nb, 1, n, c.tab.tw);
+  fft_p<false>(sm, R.log_nfft, nb, bs, c.tab.tw);
   float* Yt = S.Y[it.y];
   if (mode < 2) {
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int e = threadIdx.x; e < nb * nbands * 4; e += blockDim.x) {
       const int f = e / (nbands * 4), r = e % (nbands * 4), b = r >> 2, ch = r & 3;
-      const float yh = band_value(R, sm + f * n, b, ch);
+      const float yh = band_value(R, sm + f * bs, b, ch);
       const int set = ch < 2 ? 0 : ch - 1;
       float* ydst = Yt + ((size_t)(t0 + f) * nbands + b) * 4 + ch;
       if (mode == 0) {
@@ -99,11 +102,11 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_frames(LaunchCtx c, const
     return;
   }
   // ---- adjoint ----
-  float* dY = reinterpret_cast<float*>(sm + nb * n);       // [nb][nbands][4]
+  float* dY = reinterpret_cast<float*>(sm + kFrameBuf);   // [nb][nbands][4]
   const float* coef = S.coef + it.y * 6;                    // per set: (alpha / count, alpha / (|Y - Yh| |Y|))
   for (int e = threadIdx.x; e < nb * nbands * 4; e += blockDim.x) {
     const int f = e / (nbands * 4), r = e % (nbands * 4), b = r >> 2, ch = r & 3;
-    const float yh = band_value(R, sm + f * n, b, ch);
+    const float yh = band_value(R, sm + f * bs, b, ch);
     const int set = ch < 2 ? 0 : ch - 1;
     const float y = Yt[((size_t)(t0 + f) * nbands + b) * 4 + ch];
     const float dl = logf(yh + kLogEps) - logf(y + kLogEps);
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_frames(LaunchCtx c, const
   const int half = n >> 1;
   for (int e = threadIdx.x; e < nb * (half + 1); e += blockDim.x) {
     const int f = e / (half + 1), k = e % (half + 1);
-    float2* Z = sm + f * n;
+    float2* Z = sm + f * bs;
     float2 XL, XR;
     bin_spectra(Z, k, n, XL, XR);
     const float* dYf = dY + (size_t)f * nbands * 4;
@@ -133,20 +136,20 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_frames(LaunchCtx c, const
       else { gl = cadd(gl, g); gr = csub(gr, g); }
     }
     if (k == 0 || k == half) {
-      Z[k] = make_float2(gl.x, gr.x);
+      Z[pidx(k)] = make_float2(gl.x, gr.x);
     } else {
       // G_L[k] = gl/2, G_L[n-k] = conj(gl)/2 (same for R); packed P = G_L + i G_R
-      Z[k] = make_float2(0.5f * (gl.x - gr.y), 0.5f * (gl.y + gr.x));
-      Z[n - k] = make_float2(0.5f * (gl.x + gr.y), 0.5f * (gr.x - gl.y));
+      Z[pidx(k)] = make_float2(0.5f * (gl.x - gr.y), 0.5f * (gl.y + gr.x));
+      Z[pidx(n - k)] = make_float2(0.5f * (gl.x + gr.y), 0.5f * (gr.x - gl.y));
     }
   }
   __syncthreads();
-  fft_smem<true, 4>(sm, R.log_nfft, nb, 1, n, c.tab.tw);
+  fft_p<true>(sm, R.log_nfft, nb, bs, c.tab.tw);
   float* dF = S.dF[it.y];
   for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
     const int f = e >> R.log_nfft, j = e & (n - 1);
     const float w = R.win[j];
-    reinterpret_cast<float2*>(dF)[(size_t)(t0 + f) * n + j] = cscale(sm[e], w);
+    reinterpret_cast<float2*>(dF)[(size_t)(t0 + f) * n + j] = cscale(sm[f * bs + pidx(j)], w);
   }
 }
 
@@ -179,7 +182,7 @@ void launch_loss_frames(const LaunchCtx& c, const SongDev* songs, const LossRes*
                         int mode, int maxfft) {
   if (!n) return;
   (void)maxfft;
-  const size_t smem = 8192 * sizeof(float2) + (mode == 2 ? (size_t)(4096 + 128) * 4 * sizeof(float) : 0);
+  const size_t smem = kFrameBuf * sizeof(float2) + (mode == 2 ? (size_t)(4096 + 128) * 4 * sizeof(float) : 0);
   k_loss_frames<<<n, kLossThreads, smem, c.stream>>>(c, songs, res, items, mode);
 }
 
@@ -190,7 +193,7 @@ void launch_loss_gather(const LaunchCtx& c, const SongDev* songs, const LossRes*
 
 void init_loss_attributes() {
   cudaFuncSetAttribute(k_loss_frames, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       8192 * sizeof(float2) + (4096 + 128) * 4 * sizeof(float));
+                       kFrameBuf * sizeof(float2) + (4096 + 128) * 4 * sizeof(float));
 }
 
 }  // namespace mg

@@ -5,8 +5,8 @@
 // stream where an allocation would synchronise the device.  mg_eq_forward_noalloc gives them one processor
 // of the console (the zero-phase FIR equalizer followed by the dry/wet blend) with no allocation at all: the
 // FIR taps, the FFT scratch, the node table and the lookup tables live in one file-scope __device__ array of
-// fixed size (about 3.2 MB) that every GPU which loads this library keeps until the process exits.  The same
-// kernels as the console's equalizer stage do the work.
+// fixed size (about 3.3 MB) that every GPU which loads this library keeps until the process exits.  The
+// console's four-step FFT convolution kernels (those of the reverb and delay stages) do the work.
 #include <algorithm>
 #include <mutex>
 
@@ -28,6 +28,7 @@ constexpr int64_t kNaMaxSamples = kNaN - kEqTaps - kEqHalf - 1;
 struct NaLayout {
   float2 fft[3 * kNaN];                      // T1, T2, Hz
   float2 tw[kTwN];
+  float2 twf[kTwN];                          // exp(-2 pi i j / 2^26): fine factor of the four-step twiddles
   float cos_eq[kEqTaps];
   float hann_eq[kEqTaps];
   float taps[2 * kEqTaps];
@@ -55,6 +56,8 @@ __global__ void k_na_tables() {
     double s, c;
     sincospi(2.0 * j / kTwN, &s, &c);
     S->tw[j] = make_float2((float)c, (float)-s);
+    sincospi(2.0 * j / (double)(1 << kTwFineLog), &s, &c);
+    S->twf[j] = make_float2((float)c, (float)-s);
   }
   for (int m = t; m < kEqTaps; m += gridDim.x * blockDim.x) {
     S->cos_eq[m] = (float)cospi(2.0 * m / kEqTaps);
@@ -151,6 +154,7 @@ extern "C" mg_status mg_eq_forward_noalloc(const float* d_u, float* d_y, int64_t
   x.alpha_g = 0.f;
   x.fs = 0.0;
   x.tab.tw = S->tw;
+  x.tab.twf = S->twf;
   x.tab.cos_eq = S->cos_eq;
   x.tab.hann_eq = S->hann_eq;
   launch_eq_fir(x, S->proc_list, 1);

@@ -26,6 +26,20 @@ __device__ __forceinline__ float2 twiddle_pow2(unsigned m, int logN, bool invers
   return make_float2(c, inverse ? s : -s);
 }
 
+// exp(-+2 pi i m / 2^logN), m < 2^logN <= 2^26, from the tables: the top 13 bits of m index the coarse table,
+// the rest the fine one, and the two entries are multiplied (about 1.5 ulp).
+__device__ __forceinline__ float2 twiddle_tab(unsigned m, int logN, bool inverse, const Tables& t) {
+  float2 w;
+  if (logN <= kTwLog) {
+    w = t.tw[m << (kTwLog - logN)];
+  } else {
+    const int lo = logN - kTwLog;
+    w = cmul(t.tw[m >> lo], t.twf[(m & ((1u << lo) - 1)) << (kTwFineLog - logN)]);
+  }
+  if (inverse) w.y = -w.y;
+  return w;
+}
+
 // In-place FFTs of size M = 2^logM over nb batches held in shared memory: element e of batch b sits at
 // d[b * bs + e * es].  Forward: X[k] = sum_n x[n] exp(-2 pi i nk/M); inverse: exp(+...), unscaled.
 // Each pass reads all operands into registers, synchronises, then writes, so the caller must

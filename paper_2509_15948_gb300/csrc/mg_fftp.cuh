@@ -1,0 +1,198 @@
+// Shared-memory Stockham FFT, radix 16 (plus one radix-8/4/2 pass for the remaining factor), on a padded
+// layout: element e of a transform sits at offset pidx(e) = e + e/16 inside its batch, which makes the
+// strided stores of every pass free of bank conflicts.  Used by the hot convolution and loss kernels.
+//
+// Stockham pass of radix R with p = product of the previous radices: butterfly i (k = i mod p) reads
+// x[i + r M/R], multiplies by w_{Rp}^{r k}, runs an R-point DFT in registers and writes the R results to
+// (i - k) R + k + q p.  Twiddles come from the 8192-entry table exp(-2 pi i j / 8192) (rounded once from
+// double): four loads per butterfly, the remaining powers formed as products.
+#pragma once
+#include "mg_fft.cuh"
+
+namespace mg {
+
+__device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
+// batch stride of a padded transform of size M (odd, to spread consecutive batches over the banks)
+__host__ __device__ constexpr int pstride(int M) { return M + (M >> 4) + 1; }
+
+namespace fftp {
+
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {  // a * (-i) forward, a * (+i) inverse
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  const float2 t = csub(a, b);
+  a = cadd(a, b);
+  b = t;
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  const float2 b0 = cadd(x0, x2), b1 = csub(x0, x2), b2 = cadd(x1, x3), b3 = mul_mi<INV>(csub(x1, x3));
+  x0 = cadd(b0, b2);
+  x2 = csub(b0, b2);
+  x1 = cadd(b1, b3);
+  x3 = csub(b1, b3);
+}
+
+__device__ __forceinline__ float2 w16(int m, bool inv) {
+  // exp(-+2 pi i m / 16) for the products n2 k1 of the 4 x 4 decomposition
+  constexpr float c8 = 0.92387953251128674f, s8 = 0.38268343236508978f, r2 = 0.70710678118654752f;
+  float2 w;
+  switch (m) {
+    case 1: w = make_float2(c8, -s8); break;
+    case 2: w = make_float2(r2, -r2); break;
+    case 3: w = make_float2(s8, -c8); break;
+    case 4: w = make_float2(0.f, -1.f); break;
+    case 6: w = make_float2(-r2, -r2); break;
+    default: w = make_float2(-c8, s8); break;  // m = 9
+  }
+  if (inv) w.y = -w.y;
+  return w;
+}
+
+// 16-point DFT in place: n = 4 n1 + n2, k = k1 + 4 k2.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&x)[16]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
+  // now x[4 k1 + n2] holds Y[n2][k1]; twiddle by w16^(n2 k1)
+#pragma unroll
+  for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) x[4 * k1 + n2] = cmul(x[4 * k1 + n2], w16(n2 * k1, INV));
+  // DFT over n2 for every k1 (contiguous group 4 k1 .. 4 k1 + 3) gives X[k1 + 4 k2] at index 4 k1 + k2
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+  // transpose 4 x 4: natural order X[k] at index k
+  float2 t[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = x[4 * k1 + k2];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) x[j] = t[j];
+}
+
+// 8-point DFT in place: n = 4 n1 + n2 (n1 < 2), k = k1 + 2 k2.
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&x)[8]) {
+  constexpr float r2 = 0.70710678118654752f;
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft2<INV>(x[n2], x[4 + n2]);
+  // x[4 k1 + n2] = Y[n2][k1]; twiddle k1 = 1 by w8^n2
+  const float2 w1 = make_float2(r2, INV ? r2 : -r2), w3 = make_float2(-r2, INV ? r2 : -r2);
+  x[5] = cmul(x[5], w1);
+  x[6] = mul_mi<INV>(x[6]);
+  x[7] = cmul(x[7], w3);
+  dft4<INV>(x[0], x[1], x[2], x[3]);
+  dft4<INV>(x[4], x[5], x[6], x[7]);
+  // X[k1 + 2 k2] at index 4 k1 + k2
+  float2 t[8];
+#pragma unroll
+  for (int k1 = 0; k1 < 2; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) t[k1 + 2 * k2] = x[4 * k1 + k2];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = t[j];
+}
+
+template <bool INV, int R>
+__device__ __forceinline__ void dftR(float2 (&x)[R]) {
+  if constexpr (R == 16) dft16<INV>(x);
+  else if constexpr (R == 8) dft8<INV>(x);
+  else if constexpr (R == 4) dft4<INV>(x[0], x[1], x[2], x[3]);
+  else dft2<INV>(x[0], x[1]);
+}
+
+// Multiplies x[r] by w^r (w = table entry m, conjugated for the inverse), r = 1..R-1.  Only the powers 1, 2, 4, 8
+// come from the table; the others are products of at most three of them (error a few ulp, no extra loads).
+template <bool INV, int R>
+__device__ __forceinline__ void twiddle(float2 (&x)[R], const float2* __restrict__ tw, int m) {
+  auto ld = [&](int r) {
+    float2 w = tw[r * m];
+    if (INV) w.y = -w.y;
+    return w;
+  };
+  const float2 w1 = ld(1);
+  x[1] = cmul(x[1], w1);
+  if constexpr (R >= 4) {
+    const float2 w2 = ld(2), w3 = cmul(w1, w2);
+    x[2] = cmul(x[2], w2);
+    x[3] = cmul(x[3], w3);
+    if constexpr (R >= 8) {
+      const float2 w4 = ld(4), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+      x[4] = cmul(x[4], w4);
+      x[5] = cmul(x[5], w5);
+      x[6] = cmul(x[6], w6);
+      x[7] = cmul(x[7], w7);
+      if constexpr (R >= 16) {
+        const float2 w8 = ld(8);
+        x[8] = cmul(x[8], w8);
+        x[9] = cmul(x[9], cmul(w1, w8));
+        x[10] = cmul(x[10], cmul(w2, w8));
+        x[11] = cmul(x[11], cmul(w3, w8));
+        x[12] = cmul(x[12], cmul(w4, w8));
+        x[13] = cmul(x[13], cmul(w5, w8));
+        x[14] = cmul(x[14], cmul(w6, w8));
+        x[15] = cmul(x[15], cmul(w7, w8));
+      }
+    }
+  }
+}
+
+template <bool INV, int R, int LOGR>
+__device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, int bs, int lp,
+                                     const float2* __restrict__ tw) {
+  constexpr int PER = 16 / R;
+  const int MR = 1 << (logM - LOGR), p = 1 << lp, total = nb << (logM - LOGR);
+  const int nth = blockDim.x, tid = threadIdx.x;
+  float2 v[PER][R];
+  int ob[PER];
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    const int it = tid + s * nth;
+    ob[s] = -1;
+    if (it < total) {
+      const int b = it >> (logM - LOGR), i = it & (MR - 1), k = i & (p - 1);
+      const float2* src = d + b * bs;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[s][r] = src[pidx(i + r * MR)];
+      if (p > 1) twiddle<INV, R>(v[s], tw, k << (kTwLog - lp - LOGR));
+      dftR<INV, R>(v[s]);
+      ob[s] = b * bs + (i - k) * R + k;   // + q p, padded at store
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    if (ob[s] >= 0) {
+      const int b = (tid + s * nth) >> (logM - LOGR);
+      const int e0 = ob[s] - b * bs;
+      float2* dst = d + b * bs;
+#pragma unroll
+      for (int q = 0; q < R; ++q) dst[pidx(e0 + q * p)] = v[s][q];
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace fftp
+
+// FFTs of size M = 2^logM (M <= 8192) over nb batches, padded layout (element e of batch b at
+// d[b * bs + pidx(e)]), in place.  Requires nb * M <= 16 * blockDim.x.  Forward: exp(-2 pi i nk/M); inverse:
+// exp(+...), unscaled.  The caller synchronises before the call; the call ends with a barrier.
+template <bool INV>
+__device__ void fft_p(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ tw) {
+  int lp = 0;
+  for (; logM - lp >= 4; lp += 4) fftp::pass<INV, 16, 4>(d, logM, nb, bs, lp, tw);
+  const int rem = logM - lp;
+  if (rem == 3) fftp::pass<INV, 8, 3>(d, logM, nb, bs, lp, tw);
+  else if (rem == 2) fftp::pass<INV, 4, 2>(d, logM, nb, bs, lp, tw);
+  else if (rem == 1) fftp::pass<INV, 2, 1>(d, logM, nb, bs, lp, tw);
+}
+
+}  // namespace mg

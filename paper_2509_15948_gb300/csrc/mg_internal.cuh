@@ -9,6 +9,7 @@ enum ProcType { T_E = 0, T_C = 1, T_N = 2, T_S = 3, T_G = 4, T_D = 5, T_R = 6, N
 
 constexpr int kTwLog = 13;                 // shared twiddle table exp(-2 pi i j / 8192)
 constexpr int kTwN = 1 << kTwLog;
+constexpr int kTwFineLog = 26;            // fine table exp(-2 pi i j / 2^26), j < 8192: twiddles of N <= 2^26
 constexpr int kNPart = 8;                  // partial sums per work item
 constexpr int kEqTaps = 2047;              // Sec. 3.3
 constexpr int kEqHalf = 1023;
@@ -103,6 +104,7 @@ struct SongDev {
 // ----------------------------------------------------------------------------------------------
 struct Tables {
   const float2* tw;                        // exp(-2 pi i j / 8192)
+  const float2* twf;                       // exp(-2 pi i j / 2^26), j < 8192 (fine factor of large-N twiddles)
   const float* cos_eq;                     // cos(2 pi m / 2047), m < 2047
   const float* cos_dl;                     // cos(2 pi m / 39), m < 39
   const float* rev_win;                    // periodic Hann 384
@@ -160,6 +162,8 @@ void launch_row_fwd_hz(const LaunchCtx&, const Item* items, int n, int maxN1);
 void launch_row_conv_fwd(const LaunchCtx&, const Item* items, int n, int maxN1, bool bwd_keep_u);
 void launch_col_inv_out(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_col_dybar(const LaunchCtx&, const Item* items, int n, int maxN2G);
+void launch_col_inv_out_keep(const LaunchCtx&, const Item* items, int n, int maxN2G);
+void launch_col_dybar_keep(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_row_bwd2(const LaunchCtx&, const Item* items, int n, int maxN1);
 void launch_col_du(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_col_dh(const LaunchCtx&, const Item* items, int n, int maxN2G);

@@ -112,6 +112,16 @@ def test_single_type_console(types):
     check(case)
 
 
+@pytest.mark.parametrize("retain", [1, -1])
+@pytest.mark.parametrize("types", ["r", "dg", "ecnsgdr"])
+def test_retained_and_recomputed_spectra(types, retain):
+    """Reverb / delay backward with the spectra kept from the forward (1) and recomputed in the shared
+    scratch (-1): both match the oracle."""
+    case = make_case([W.layout_plain(88200), W.SongLayout(3, 1, [0, -1, 0], 30011)], types=types, seed=3)
+    con, _, _ = check(case, retain_spectra=retain)
+    assert con.get_info()["retains_spectra"] == (1 if retain == 1 else 0)
+
+
 def test_full_console_plain_workload():
     """4 tracks x 2 s at 44.1 kHz, one subgroup of 2 tracks, every processor type."""
     case = make_case([W.layout_plain(88200)], seed=0)
