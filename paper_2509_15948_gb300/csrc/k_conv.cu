@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
 
   const float inv_n = ldexpf(1.f, -logN);
   if (kOut) {
-    const float w = dry_wet_w(c, P.qidx);
+    const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
     float acc[2] = {0.f, 0.f};
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
       const int g = e & (G - 1), r = e >> logG;
@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
         const float2 yb = cscale(sm[g * cs + pidx(r)], inv_n);
         if (MODE == COL_INV_OUT_KEEP) P.T2[n] = yb;
         const float ul = P.u[n], ur = P.u[P.ld + n];
-        P.y[n] = w * yb.x + (1.f - w) * ul;
-        P.y[P.ld + n] = w * yb.y + (1.f - w) * ur;
+        P.y[n] = w * yb.x + wd * ul;
+        P.y[P.ld + n] = w * yb.y + wd * ur;
         const float ym = yb.x + yb.y, um = ul + ur;
         acc[0] += ym * ym;
         acc[1] += um * um;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   }
   if (kDybar) {
     // y_bar -> dL/dy_bar = w dy + c1 (y_bar_l + y_bar_r) on both channels; dw partial; then forward FFT
-    const float w = dry_wet_w(c, P.qidx);
+    const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
     const float c1 = P.stats[2];
     float acc[1] = {0.f};
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
     return;
   }
   if (MODE == COL_DU) {
-    const float w = dry_wet_w(c, P.qidx);
+    const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
     const float c2 = P.stats[3];
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
       const int g = e & (G - 1), r = e >> logG;
@@ -171,8 +171,8 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
       if (n < P.L) {
         const float2 dw = cscale(sm[g * cs + pidx(r)], inv_n);
         const float um = c2 * (P.u[n] + P.u[P.ld + n]);
-        P.du[n] = (1.f - w) * P.dy[n] + dw.x + um;
-        P.du[P.ld + n] = (1.f - w) * P.dy[P.ld + n] + dw.y + um;
+        P.du[n] = wd * P.dy[n] + dw.x + um;
+        P.du[P.ld + n] = wd * P.dy[P.ld + n] + dw.y + um;
       }
     }
     return;

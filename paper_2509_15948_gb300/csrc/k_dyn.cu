@@ -16,7 +16,7 @@ constexpr int kPer = 16;   // samples per thread
 constexpr int kThreads = kDynChunk / kPer;
 
 struct DynParams {
-  float alpha, lna, T, W, R;
+  float alpha, beta, lna, T, W, R, Rm1;   // Rm1 = R - 1 = exp(p3)   // beta = 1 - alpha, evaluated as sigmoid(-p0) (no cancellation near 1)
   bool gate;
 };
 
@@ -24,25 +24,27 @@ __device__ __forceinline__ DynParams dyn_params(const ProcDev& P) {
   DynParams d;
   const float p0 = P.p[0];
   d.alpha = 1.f / (1.f + expf(-p0));
+  d.beta = 1.f / (1.f + expf(p0));
   d.lna = -log1pf(expf(-p0));          // ln sigmoid(p0)
   if (p0 < -20.f) d.lna = p0;          // log1p(exp(-p0)) = -p0 + log1p(exp(p0))
   d.T = P.p[1];
   d.W = expf(P.p[2]);
-  d.R = 1.f + expf(P.p[3]);
+  d.Rm1 = expf(P.p[3]);
+  d.R = 1.f + d.Rm1;
   d.gate = P.type == T_N;
   return d;
 }
 
 // Gain laws (Eqs. 13-14 compressor, Eq. 16 noisegate) with their partial derivatives.
 __device__ __forceinline__ float gain_law(const DynParams& d, float G, float& dG, float& dT, float& dW, float& dR) {
-  const float T = d.T, W = d.W, R = d.R;
+  const float T = d.T, W = d.W, R = d.R, Rm1 = d.Rm1;
   if (!d.gate) {
     if (G >= T + W) {
-      dG = 1.f / R; dT = 1.f - 1.f / R; dW = 0.f; dR = -(G - T) / (R * R);
+      dG = 1.f / R; dT = Rm1 / R; dW = 0.f; dR = -(G - T) / (R * R);
       return T + (G - T) / R;
     }
     if (G >= T - W) {
-      const float q = G - T + W, k = 1.f / R - 1.f;
+      const float q = G - T + W, k = -Rm1 / R;
       dG = 1.f + k * q / (2.f * W); dT = -k * q / (2.f * W);
       dW = k * (q / (2.f * W) - q * q / (4.f * W * W)); dR = -(q * q) / (4.f * W * R * R);
       return G + k * q * q / (4.f * W);
@@ -55,12 +57,12 @@ __device__ __forceinline__ float gain_law(const DynParams& d, float G, float& dG
     return G;
   }
   if (G >= T - W) {
-    const float q = G - T - W, k = 1.f - R;
+    const float q = G - T - W, k = -Rm1;
     dG = 1.f + k * q / (2.f * W); dT = -k * q / (2.f * W);
     dW = k * (-q / (2.f * W) - q * q / (4.f * W * W)); dR = -(q * q) / (4.f * W);
     return G + k * q * q / (4.f * W);
   }
-  dG = R; dT = 1.f - R; dW = 0.f; dR = G - T;
+  dG = R; dT = -Rm1; dW = 0.f; dR = G - T;
   return T + R * (G - T);
 }
 
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_dyn_fwd_agg(LaunchCtx c, const Ite
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const float m = l[j] + r[j];
-    s = d.alpha * s + (1.f - d.alpha) * (m * m);
+    s = d.alpha * s + d.beta * (m * m);
   }
   float v[1] = {s * expf((float)(kPer * (kThreads - 1 - (int)threadIdx.x)) * d.lna)};
   float out[1];
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_dyn_fwd_apply(LaunchCtx c, const I
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const DynParams d = dyn_params(P);
-  const float w = dry_wet_w(c, P.qidx);
+  const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
   float l[kPer], r[kPer];
   load16(P.u, P.ld, P.L, n0, l, r);
@@ -213,17 +215,17 @@ __global__ void __launch_bounds__(kThreads) k_dyn_fwd_apply(LaunchCtx c, const I
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const float m = l[j] + r[j];
-    s = d.alpha * s + (1.f - d.alpha) * (m * m);
+    s = d.alpha * s + d.beta * (m * m);
   }
   float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const float m = l[j] + r[j];
-    g = d.alpha * g + (1.f - d.alpha) * (m * m);
+    g = d.alpha * g + d.beta * (m * m);
     const float Gu = logf(g + kEnvEps);
     const float gain = expf(gain_law_v(d, Gu) - Gu);
-    l[j] = w * (gain * l[j]) + (1.f - w) * l[j];
-    r[j] = w * (gain * r[j]) + (1.f - w) * r[j];
+    l[j] = w * (gain * l[j]) + wd * l[j];
+    r[j] = w * (gain * r[j]) + wd * r[j];
   }
   store16(P.y, P.ld, P.L, n0, l, r);
 }
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_dyn_bwd_agg(LaunchCtx c, const Ite
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const DynParams d = dyn_params(P);
-  const float w = dry_wet_w(c, P.qidx);
+  const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
   float l[kPer], r[kPer], gl[kPer], gr[kPer];
   load16(P.u, P.ld, P.L, n0, l, r);
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_dyn_bwd_agg(LaunchCtx c, const Ite
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const float m = l[j] + r[j];
-    s = d.alpha * s + (1.f - d.alpha) * (m * m);
+    s = d.alpha * s + d.beta * (m * m);
   }
   float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
   float dg[kPer];
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) k_dyn_bwd_agg(LaunchCtx c, const Ite
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const float m = l[j] + r[j];
-    g = d.alpha * g + (1.f - d.alpha) * (m * m);
+    g = d.alpha * g + d.beta * (m * m);
     float gain;
     dg[j] = dyn_dg(d, w, g, l[j], r[j], gl[j], gr[j], gain, acc);
   }
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_dyn_bwd_apply(LaunchCtx c, const I
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const DynParams d = dyn_params(P);
-  const float w = dry_wet_w(c, P.qidx);
+  const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
   float l[kPer], r[kPer], gl[kPer], gr[kPer];
   load16(P.u, P.ld, P.L, n0, l, r);
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_dyn_bwd_apply(LaunchCtx c, const I
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const float m = l[j] + r[j];
-    s = d.alpha * s + (1.f - d.alpha) * (m * m);
+    s = d.alpha * s + d.beta * (m * m);
   }
   const float gin = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
   float gv[kPer], dg[kPer], gains[kPer];
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_dyn_bwd_apply(LaunchCtx c, const I
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const float m = l[j] + r[j];
-    g = d.alpha * g + (1.f - d.alpha) * (m * m);
+    g = d.alpha * g + d.beta * (m * m);
     gv[j] = g;
     dg[j] = dyn_dg(d, w, g, l[j], r[j], gl[j], gr[j], gains[j], acc);
   }
@@ -335,9 +337,9 @@ __global__ void __launch_bounds__(kThreads) k_dyn_bwd_apply(LaunchCtx c, const I
     const float x = m * m;
     const float gprev = j > 0 ? gv[j - 1] : gin;
     dalpha += lam * (gprev - x);
-    const float dx2m = (1.f - d.alpha) * lam * 2.f * m;
-    const float ol = (1.f - w) * gl[j] + gains[j] * (w * gl[j]) + dx2m;
-    const float orr = (1.f - w) * gr[j] + gains[j] * (w * gr[j]) + dx2m;
+    const float dx2m = d.beta * lam * 2.f * m;
+    const float ol = wd * gl[j] + gains[j] * (w * gl[j]) + dx2m;
+    const float orr = wd * gr[j] + gains[j] * (w * gr[j]) + dx2m;
     l[j] = ol;
     r[j] = orr;
   }

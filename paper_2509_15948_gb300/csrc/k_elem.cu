@@ -9,7 +9,7 @@ namespace mg {
 __global__ void __launch_bounds__(256) k_gs_fwd(LaunchCtx c, const Item* __restrict__ items) {
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
-  const float w = dry_wet_w(c, P.qidx);
+  const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const float4* ul = reinterpret_cast<const float4*>(P.u);
   const float4* ur = reinterpret_cast<const float4*>(P.u + P.ld);
   float4* yl = reinterpret_cast<float4*>(P.y);
@@ -21,10 +21,10 @@ __global__ void __launch_bounds__(256) k_gs_fwd(LaunchCtx c, const Item* __restr
     for (int v = v0 + threadIdx.x; v < vend; v += blockDim.x) {
       const float4 a = ul[v], b = ur[v];
       float4 oa, ob;
-      oa.x = w * (gl * a.x) + (1.f - w) * a.x; oa.y = w * (gl * a.y) + (1.f - w) * a.y;
-      oa.z = w * (gl * a.z) + (1.f - w) * a.z; oa.w = w * (gl * a.w) + (1.f - w) * a.w;
-      ob.x = w * (gr * b.x) + (1.f - w) * b.x; ob.y = w * (gr * b.y) + (1.f - w) * b.y;
-      ob.z = w * (gr * b.z) + (1.f - w) * b.z; ob.w = w * (gr * b.w) + (1.f - w) * b.w;
+      oa.x = w * (gl * a.x) + wd * a.x; oa.y = w * (gl * a.y) + wd * a.y;
+      oa.z = w * (gl * a.z) + wd * a.z; oa.w = w * (gl * a.w) + wd * a.w;
+      ob.x = w * (gr * b.x) + wd * b.x; ob.y = w * (gr * b.y) + wd * b.y;
+      ob.z = w * (gr * b.z) + wd * b.z; ob.w = w * (gr * b.w) + wd * b.w;
       yl[v] = oa;
       yr[v] = ob;
     }
@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(256) k_gs_fwd(LaunchCtx c, const Item* __restr
 #define MG_IMG(X)                                         \
   {                                                       \
     const float m = a.X + b.X, s = e * (a.X - b.X);       \
-    oa.X = w * ((m + s) * 0.5f) + (1.f - w) * a.X;        \
-    ob.X = w * ((m - s) * 0.5f) + (1.f - w) * b.X;        \
+    oa.X = w * ((m + s) * 0.5f) + wd * a.X;        \
+    ob.X = w * ((m - s) * 0.5f) + wd * b.X;        \
   }
       MG_IMG(x) MG_IMG(y) MG_IMG(z) MG_IMG(w)
 #undef MG_IMG
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_gs_bwd(LaunchCtx c, const Item* __restr
   __shared__ float red[2 * 32];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
-  const float w = dry_wet_w(c, P.qidx);
+  const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const float4* ul = reinterpret_cast<const float4*>(P.u);
   const float4* ur = reinterpret_cast<const float4*>(P.u + P.ld);
   const float4* gl4 = reinterpret_cast<const float4*>(P.dy);
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_gs_bwd(LaunchCtx c, const Item* __restr
   const int vend = min(v0 + kElemTile / 4, (P.L + 3) >> 2);
   float acc[2] = {0.f, 0.f};
   if (P.type == T_G) {
-    const float kl = (1.f - w) + w * expf(P.p[0]), kr = (1.f - w) + w * expf(P.p[1]);
+    const float kl = wd + w * expf(P.p[0]), kr = wd + w * expf(P.p[1]);
     for (int v = v0 + threadIdx.x; v < vend; v += blockDim.x) {
       const float4 a = ul[v], b = ur[v], ga = gl4[v], gb = gr4[v];
       acc[0] += ga.x * a.x + ga.y * a.y + ga.z * a.z + ga.w * a.w;
@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(256) k_gs_bwd(LaunchCtx c, const Item* __restr
   {                                                                  \
     const float bl = w * ga.X, br = w * gb.X;                        \
     const float sm = 0.5f * (bl + br), df = 0.5f * e * (bl - br);    \
-    oa.X = (1.f - w) * ga.X + sm + df;                               \
-    ob.X = (1.f - w) * gb.X + sm - df;                               \
+    oa.X = wd * ga.X + sm + df;                               \
+    ob.X = wd * gb.X + sm - df;                               \
     acc[0] += (a.X - b.X) * (ga.X - gb.X);                           \
   }
       MG_IMGB(x) MG_IMGB(y) MG_IMGB(z) MG_IMGB(w)

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kOsThreads, 2) k_eq_os_fwd(LaunchCtx c, const 
   for (int k = threadIdx.x; k < kOsM; k += blockDim.x) sm[pidx(k)] = cscale(sm[pidx(k)], P.hspec[k]);
   __syncthreads();
   fft_p<true>(sm, kOsLog, 1, kOsP, c.tab.tw);
-  const float w = dry_wet_w(c, P.qidx);
+  const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const float inv = 1.f / kOsM;
   float acc[2] = {0.f, 0.f};
   for (int t = threadIdx.x; t < B; t += blockDim.x) {
@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(kOsThreads, 2) k_eq_os_fwd(LaunchCtx c, const 
     if (s >= P.L) break;
     const float2 yb = cscale(sm[pidx(kEqHalf + t)], inv);
     const float ul = P.u[s], ur = P.u[P.ld + s];
-    P.y[s] = w * yb.x + (1.f - w) * ul;
-    P.y[P.ld + s] = w * yb.y + (1.f - w) * ur;
+    P.y[s] = w * yb.x + wd * ul;
+    P.y[P.ld + s] = w * yb.y + wd * ur;
     const float ym = yb.x + yb.y, um = ul + ur;
     acc[0] += ym * ym;
     acc[1] += um * um;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kOsThreads) k_eq_os_bwd(LaunchCtx c, const Ite
   for (int k = threadIdx.x; k < kOsM; k += blockDim.x) Bf[pidx(k)] = cscale(A[pidx(k)], P.hspec[k]);
   __syncthreads();
   fft_p<true>(Bf, kOsLog, 1, kOsP, c.tab.tw);
-  const float w = dry_wet_w(c, P.qidx);
+  const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const float c1 = P.stats[2], c2 = P.stats[3];
   const float inv = 1.f / kOsM;
   float acc[1] = {0.f};
@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(kOsThreads) k_eq_os_bwd(LaunchCtx c, const Ite
     if (s >= P.L) break;
     const float2 dw = cscale(Bf[pidx(H2 + t)], inv);
     const float um = c2 * (P.u[s] + P.u[P.ld + s]);
-    P.du[s] = (1.f - w) * P.dy[s] + dw.x + um;
-    P.du[P.ld + s] = (1.f - w) * P.dy[P.ld + s] + dw.y + um;
+    P.du[s] = wd * P.dy[s] + dw.x + um;
+    P.du[P.ld + s] = wd * P.dy[P.ld + s] + dw.y + um;
   }
   // lags n = -1023..1023 sit at circular positions n mod M; partial row of this block
   float* dst = P.dhpart + (size_t)it.idx * kEqTaps;

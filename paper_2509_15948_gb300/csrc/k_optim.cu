@@ -123,8 +123,8 @@ __global__ void k_grad_finalize(LaunchCtx c, const int* __restrict__ procs, int 
     }
     case T_C:
     case T_N: {
-      const float a = 1.f / (1.f + expf(-P.p[0]));
-      P.gp[0] = s[0] * a * (1.f - a);
+      const float a = 1.f / (1.f + expf(-P.p[0])), b = 1.f / (1.f + expf(P.p[0]));   // sigmoid(p0), 1 - sigmoid(p0)
+      P.gp[0] = s[0] * a * b;
       P.gp[1] = s[1];
       P.gp[2] = s[2] * expf(P.p[2]);
       P.gp[3] = s[3] * expf(P.p[3]);
@@ -134,7 +134,7 @@ __global__ void k_grad_finalize(LaunchCtx c, const int* __restrict__ procs, int 
     default:
       dw = s[0];   // LTI: dL/dw from the y_bar pass; FIR parameter gradients come from the adjoint kernels
   }
-  gq[P.qidx] = (dw + c.hyper[0]) * wr * (1.f - wr);
+  gq[P.qidx] = (dw + c.hyper[0]) * wr / (1.f + expf(c.q[P.qidx]));   // w (1 - w), 1 - w = sigmoid(-q)
 }
 
 __global__ void k_adam(const float* __restrict__ hyper, const int* __restrict__ step, float* __restrict__ p,

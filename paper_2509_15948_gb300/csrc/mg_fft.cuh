@@ -185,4 +185,11 @@ __device__ __forceinline__ float dry_wet_w(const LaunchCtx& c, int qidx) {
   return c.mask ? w * (float)c.mask[qidx] : w;
 }
 
+// The dry weight 1 - w, evaluated as sigmoid(-q) (1 where the mask is 0) so that it keeps full relative
+// precision when w is close to 1.
+__device__ __forceinline__ float dry_wet_d(const LaunchCtx& c, int qidx) {
+  if (c.mask && !c.mask[qidx]) return 1.f;
+  return 1.f / (1.f + expf(c.q[qidx]));
+}
+
 }  // namespace mg

@@ -8,7 +8,7 @@ import pytest
 import workloads as W
 from oracle import adam as OA
 from tests.cases import (make_case, gpu_console, rel_l2, grad_groups, LOSS_FIELDS, oracle_with_delay_taps,
-                         delay_slot_conditioning)
+                         delay_slot_conditioning, gain_term_magnitudes)
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +68,7 @@ def check_delay(case, og, gg, taps):
     return worst
 
 
-def check(case, alpha_p=1e-3, skip_losses=(), check_grads=True, **cfg):
+def check(case, alpha_p=1e-3, skip_losses=(), check_grads=True, grad_floor=False, **cfg):
     (ol, og, omix, taps), (gl, gg, gmix), con = run_both(case, alpha_p, **cfg)
     for s in range(len(omix)):
         assert rel_l2(gmix[s], omix[s]) <= MIX_TOL, ("mix", s, rel_l2(gmix[s], omix[s]))
@@ -96,9 +96,16 @@ def check(case, alpha_p=1e-3, skip_losses=(), check_grads=True, **cfg):
             err = abs(gl[s, j] - ol[s, j]) / max(abs(ol[s, j]), 1e-12)
             assert err <= tol, (name, s, gl[s, j], ol[s, j], err, tol)
     if check_grads:
+        floors = gain_term_magnitudes(case, alpha_p) if grad_floor else {}
         for name, idx in grad_groups(case).items():
             if name == "d":
                 check_delay(case, og, gg, taps)
+                continue
+            if name in floors:
+                # ||error|| <= 1e-3 ||grad|| + 1e-5 ||sum_n |terms| ||: the FP32 floor of a cancelling sum
+                err = np.linalg.norm(gg[idx] - og[idx])
+                bound = GRAD_TOL * np.linalg.norm(og[idx]) + MIX_TOL * np.linalg.norm(floors[name])
+                assert err <= bound, ("grad", name, err, bound, rel_l2(gg[idx], og[idx]))
                 continue
             e = rel_l2(gg[idx], og[idx])
             assert e <= GRAD_TOL, ("grad", name, e)
@@ -120,6 +127,19 @@ def test_retained_and_recomputed_spectra(types, retain):
     case = make_case([W.layout_plain(88200), W.SongLayout(3, 1, [0, -1, 0], 30011)], types=types, seed=3)
     con, _, _ = check(case, retain_spectra=retain)
     assert con.get_info()["retains_spectra"] == (1 if retain == 1 else 0)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_full_console_at_ground_truth_parameters(seed):
+    """The ground-truth graph's own parameters (slow envelopes with sigmoid(p0) near 1, delays with |z| near 1,
+    strong compression), dry/wet logits +-4: the regime the search runs in, where 1 - sigmoid must not be
+    formed by subtraction."""
+    case = make_case([W.layout_plain(88200)], seed=seed)
+    gt, keep = W.ground_truth(case.ptypes, (seed, 77))
+    params = gt.copy()
+    params[case.oracle.n_proc_params:] = np.where(keep == 1, 4.0, -4.0)
+    case.params = params
+    check(case, grad_floor=True)
 
 
 def test_full_console_plain_workload():
