@@ -1,0 +1,210 @@
+"""Mixing-graph search with dry/wet candidate sampling (Alg. 3, Sec. 6.1-6.3) on the CUDA console.
+
+Every song of a console runs its own search.  The songs advance in lockstep: one masked forward
+(mg_prune_scores with a single mask over all processors) evaluates the current trial of every song at once,
+because a song's audio loss L_a depends only on its own processors.  Training between rounds is the console's
+CUDA-graph step (forward, backward, Adam).
+
+Readings where the paper is silent:
+  * N_t is fixed when the round starts; the candidate count is k = max(1, floor(N_t r_t + 0.5)) capped at
+    |V_t| (the rounding of Alg. 3 can give 0, which would never end the round);
+  * the least-weight nodes are ordered by (w, processor index), w = sigmoid(q) in double precision from the
+    FP32 logits;
+  * SampleType draws from the remaining types kept in chain order e c n s g d r with the splitmix64
+    generator (Steele, Lea, Flood 2014): index = next() mod |T_c|; one generator per song, seeded with
+    song_seed(seed, song);
+  * a type whose node set V_t has become empty leaves T_c when it is drawn (the draw is consumed);
+  * a failed trial with k > 1 halves r_t, a failed trial with k = 1 removes the type;
+  * L_min is the unmasked L_a after the initial training and is only updated by accepted trials (Alg. 3);
+  * the sparsity weight alpha_p rises linearly from 0 to alpha_p_max over the first ramp_steps fine-tuning
+    steps (Sec. 6.3: 0 to 1e-4 over the first 4k of 6k steps) and stays there.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+TYPE_ORDER = "ecnsgdr"
+_M64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """splitmix64 (Steele, Lea, Flood, OOPSLA 2014): state += golden gamma, then two xor-shift-multiply
+    rounds and a final xor-shift."""
+
+    def __init__(self, seed: int):
+        self.s = seed & _M64
+
+    def next(self) -> int:
+        self.s = (self.s + 0x9E3779B97F4A7C15) & _M64
+        x = self.s
+        x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & _M64
+        return x ^ (x >> 31)
+
+
+def song_seed(seed: int, song: int) -> int:
+    """Seed of song `song`'s type sampler."""
+    return (seed * 0x100000001B3 + song + 1) & _M64
+
+
+def dry_wet_weights(q: np.ndarray) -> np.ndarray:
+    """w = sigmoid(q) in double precision (Sec. 3.1 dry/wet weights)."""
+    q = np.asarray(q, np.float64)
+    return 1.0 / (1.0 + np.exp(-q))
+
+
+@dataclasses.dataclass
+class Trial:
+    song: int
+    type: str
+    candidates: tuple          # processor indices (console-wide) switched off by the trial
+    la: float                  # L_a of the song with the trial mask
+    accepted: bool
+
+
+class _SongRound:
+    """State of one song's pruning round (Alg. 3, inner loop)."""
+
+    def __init__(self, procs: Sequence[int], types: Sequence[str], w: np.ndarray, l_min: float, rng: SplitMix64):
+        self.w = w
+        self.tc = [t for t in TYPE_ORDER if any(types[i] == t for i in procs)]
+        self.V = {t: [i for i in procs if types[i] == t] for t in self.tc}
+        self.N = {t: len(self.V[t]) for t in self.tc}
+        self.r = {t: 0.1 for t in self.tc}
+        self.removed: set = set()     # processors switched off by accepted trials
+        self.l_min = float(l_min)
+        self.rng = rng
+        self.pending: Optional[tuple] = None
+
+    def advance(self) -> bool:
+        """Draws the next trial; False when the round of this song is over."""
+        while self.tc:
+            t = self.tc[self.rng.next() % len(self.tc)]
+            if not self.V[t]:
+                self.tc.remove(t)
+                continue
+            k = min(max(1, int(np.floor(self.N[t] * self.r[t] + 0.5))), len(self.V[t]))
+            order = sorted(self.V[t], key=lambda i: (self.w[i], i))
+            self.pending = (t, tuple(order[:k]))
+            return True
+        self.pending = None
+        return False
+
+    def resolve(self, la: float, tau: float) -> Trial:
+        t, cand = self.pending
+        ok = la < self.l_min + tau
+        if ok:
+            self.l_min = min(self.l_min, la)
+            self.removed.update(cand)
+            drop = set(cand)
+            self.V[t] = [i for i in self.V[t] if i not in drop]
+        elif len(cand) > 1:
+            self.r[t] /= 2.0
+        else:
+            self.tc.remove(t)
+        self.pending = None
+        return t, cand, ok
+
+
+def dry_wet_round(con, l_min: Sequence[float], tau: float, rngs: Sequence[SplitMix64],
+                  w: Optional[np.ndarray] = None) -> tuple:
+    """One pruning round of Alg. 3 for every song of `con`, in lockstep.
+
+    Returns (keep mask [P] uint8 over all processors, updated L_min per song, list of Trial)."""
+    types = con.processor_types()
+    _, _, song_of = con.layout()
+    present = con.present()
+    if w is None:
+        w = dry_wet_weights(con.get_params().cpu().numpy()[con.n_proc_params:])
+    P = con.n_processors
+    songs = []
+    for s in range(con.n_songs):
+        procs = [i for i in range(P) if song_of[i] == s and present[i]]
+        songs.append(_SongRound(procs, types, w, l_min[s], rngs[s]))
+    trials: List[Trial] = []
+    active = [sr.advance() for sr in songs]
+    while any(active):
+        mask = np.ones(P, np.uint8)
+        for s, sr in enumerate(songs):
+            for i in sr.removed:
+                mask[i] = 0
+            if active[s]:
+                for i in sr.pending[1]:
+                    mask[i] = 0
+        la = con.prune_scores(mask[None, :])[0].cpu().numpy().astype(np.float64)
+        for s, sr in enumerate(songs):
+            if not active[s]:
+                continue
+            t, cand, ok = sr.resolve(float(la[s]), tau)
+            trials.append(Trial(s, t, cand, float(la[s]), ok))
+            active[s] = sr.advance()
+    keep = present.astype(np.uint8).copy()
+    for sr in songs:
+        for i in sr.removed:
+            keep[i] = 0
+    return keep, [sr.l_min for sr in songs], trials
+
+
+@dataclasses.dataclass
+class SearchResult:
+    present: np.ndarray            # processors left after the last round
+    l_min: List[float]             # per song
+    la_final: List[float]          # per song, unmasked L_a of the pruned graph after the last fine-tuning
+    pruning_ratio: List[float]     # per song: pruned processors / initial processors (Sec. 6.1)
+    trials: List[List[Trial]]      # per round
+    seconds: Dict[str, float]      # wall time of training, rounds and fine-tuning
+
+
+def alpha_p_at(step: int, ramp_steps: int, alpha_p_max: float) -> float:
+    """Sparsity weight after `step` fine-tuning steps (linear ramp, Sec. 6.3)."""
+    if ramp_steps <= 0:
+        return alpha_p_max
+    return alpha_p_max * min(1.0, step / ramp_steps)
+
+
+def search(con, n_iter: int, train_steps: int, finetune_steps: int, lr: float = 1e-2, tau: float = 0.01,
+           seed: int = 0, alpha_p_max: float = 1e-4, ramp_steps: Optional[int] = None) -> SearchResult:
+    """Alg. 3 on every song of `con`: train, L_min from the unmasked graph, then n_iter rounds of
+    {dry/wet pruning round, structural prune, fine-tuning}."""
+    import torch
+    if ramp_steps is None:
+        ramp_steps = (2 * n_iter * finetune_steps) // 3
+    _, _, song_of = con.layout()
+    present0 = con.present().copy()
+    init_count = [int(np.sum(present0[song_of == s])) for s in range(con.n_songs)]
+    rngs = [SplitMix64(song_seed(seed, s)) for s in range(con.n_songs)]
+    sync = lambda: torch.cuda.synchronize(con.device)
+    secs = {"train": 0.0, "rounds": 0.0, "finetune": 0.0}
+
+    t0 = time.perf_counter()
+    con.set_alpha_p(0.0)
+    for _ in range(train_steps):
+        con.train_step(lr)
+    ones = np.ones((1, con.n_processors), np.uint8)
+    l_min = con.prune_scores(ones)[0].cpu().numpy().astype(np.float64).tolist()
+    sync()
+    secs["train"] += time.perf_counter() - t0
+
+    all_trials, ft = [], 0
+    for _ in range(n_iter):
+        t0 = time.perf_counter()
+        keep, l_min, trials = dry_wet_round(con, l_min, tau, rngs)
+        con.prune(keep)
+        sync()
+        secs["rounds"] += time.perf_counter() - t0
+        all_trials.append(trials)
+        t0 = time.perf_counter()
+        for _ in range(finetune_steps):
+            con.set_alpha_p(alpha_p_at(ft, ramp_steps, alpha_p_max))
+            con.train_step(lr)
+            ft += 1
+        sync()
+        secs["finetune"] += time.perf_counter() - t0
+    la = con.prune_scores(ones)[0].cpu().numpy().astype(np.float64).tolist()
+    present = con.present().copy()
+    ratio = [1.0 - int(np.sum(present[song_of == s])) / max(1, init_count[s]) for s in range(con.n_songs)]
+    return SearchResult(present, l_min, la, ratio, all_trials, secs)

@@ -1,0 +1,112 @@
+"""Alg. 3 search on the CUDA console against the oracle (GPU).
+
+The round is replayed twice: (a) through the oracle's round logic with the GPU's own evaluations, which
+must give the identical trial sequence and pruned set; (b) trial by trial with the oracle's FP64 L_a at the
+same masks and parameters.  Alg. 3 decides on d = L_a(trial) - L_min < tau, a difference of two losses of
+nearly the same mix, so (b) holds d to the gradient bound (1e-3 relative, plus 1e-6 of L_a for rounding,
+plus the L_a floor below) and requires the same decision wherever |d - tau| exceeds twice that bound.  With no near-tie the oracle's own
+search takes the same decisions in the same order, so its pruned set is the GPU's.  L_a itself is held to
+the mix bound propagated through the loss: 1e-5 (times the channel conditioning) relative, plus the change
+of the oracle's L_a when its mix moves by white noise of relative L2 1e-5 (the log-spectral term of Eq. 21
+is sensitive on near-silent bins, so FP32 rounding of the mix shifts L_a by a nearly constant amount that
+cancels in d)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import loss as OL
+from oracle import search as OS
+from paper_2509_15948_gb300 import search as GS
+from tests.cases import make_case, gpu_console
+
+pytestmark = pytest.mark.gpu
+
+LA_TOL = 1e-5
+D_TOL = 1e-3
+
+
+def conditioning(mix, row):
+    """k_la of the parity tests: the per-set terms scale the mix's relative error by ||(l,r)|| / ||x||."""
+    lr = np.linalg.norm(mix)
+    kap = {"Llr": 1.0, "Lm": lr / max(np.linalg.norm(mix[0] + mix[1]), 1e-30),
+           "Ls": lr / max(np.linalg.norm(mix[0] - mix[1]), 1e-30)}
+    alphas = {"Llr": 0.5, "Lm": 0.25, "Ls": 0.25}
+    return max(1.0, sum(alphas[x] * row[i + 1] * kap[x] for i, x in enumerate(alphas)) / max(row[0], 1e-30))
+
+
+def test_dry_wet_round_matches_oracle():
+    tau = 0.01
+    # start near the ground-truth graph, so that the mix has the target's level and L_a the paper's scale
+    # (at the initial parameters the raw reverb magnitudes make the mix ~1e5 times louder than the target)
+    seed_case = 1
+    case = make_case([W.layout_plain(88200)], seed=seed_case)
+    gt, gt_keep = W.ground_truth(case.ptypes, (seed_case, 77))
+    npp = case.oracle.n_proc_params
+    start = gt.copy()
+    start[npp:] = np.where(gt_keep == 1, 4.0, -4.0)
+    con = gpu_console(case)
+    con.set_params(start)
+    for _ in range(5):
+        con.train_step(1e-2)
+    params = con.get_params().cpu().numpy()
+    P = con.n_processors
+    l_min0 = float(con.prune_scores(np.ones((1, P), np.uint8))[0, 0])
+    seed = GS.song_seed(3, 0)
+    keep, lm, trials = GS.dry_wet_round(con, [l_min0], tau, [GS.SplitMix64(seed)])
+    assert len(trials) >= 3
+
+    # (a) the oracle's round logic on the GPU's evaluations
+    w = GS.dry_wet_weights(params[con.n_proc_params:])
+    gpu_eval = lambda m: float(con.prune_scores(np.asarray(m, np.uint8)[None, :])[0, 0])
+    m, olm, trace = OS.dry_wet_round(w, con.processor_types(), np.ones(P, np.uint8), l_min0, tau, gpu_eval,
+                                     OS.SplitMix64(seed))
+    assert [(t.type, tuple(t.candidates), t.la, t.accepted) for t in trials] == \
+           [(t, tuple(c), la, ok) for (t, c, la, ok) in trace]
+    assert np.array_equal(keep, m) and lm[0] == olm
+
+    # (b) FP64 oracle losses at every trial mask
+    full, mixes = case.oracle.losses(params)
+    mix = torch.tensor(mixes[0], dtype=torch.float64)
+    tgt = torch.tensor(case.targets[0], dtype=torch.float64)
+    noise = torch.tensor(np.random.default_rng(0).standard_normal(mix.shape))
+    noise *= 1e-5 * mix.norm() / noise.norm()
+    floor = abs(float(OL.audio_loss(mix + noise, tgt, case.oracle.desc.loss)["a"]) - full[0, 0])
+    l_min_o, l_min_g = full[0, 0], l_min0
+    assert abs(l_min_g - l_min_o) <= LA_TOL * conditioning(mixes[0], full[0]) * abs(l_min_o) + floor
+    removed, near_ties = set(), 0
+    for t in trials:
+        mask = np.ones(P, np.uint8)
+        mask[list(removed | set(t.candidates))] = 0
+        row, mix_t = case.oracle.losses(params, mask=mask)
+        la_o = row[0, 0]
+        assert abs(t.la - la_o) <= LA_TOL * conditioning(mix_t[0], row[0]) * abs(la_o) + floor, (t, la_o, floor)
+        d_g, d_o = t.la - l_min_g, la_o - l_min_o
+        tol = D_TOL * abs(d_o) + 1e-6 * abs(la_o) + floor
+        assert abs(d_g - d_o) <= tol, (t, d_g, d_o, tol)
+        if abs(d_o - tau) <= 2 * tol:
+            near_ties += 1
+        else:
+            assert (d_o < tau) == t.accepted, (t, d_o)
+        if t.accepted:
+            l_min_o, l_min_g = min(l_min_o, la_o), min(l_min_g, t.la)
+            removed |= set(t.candidates)
+    print(f"trials {len(trials)}, pruned {int(np.sum(keep == 0))} of {P}, near ties {near_ties}, "
+          f"L_a floor {floor:.3g}")
+    assert near_ties == 0       # every decision is resolved: the pruned set is the oracle's
+
+
+def test_search_rounds_prune_and_fine_tune():
+    """Two rounds of Alg. 3 on a two-song batch: the pruned set is what the trials accepted, the pruned
+    console keeps training, and the final losses are finite."""
+    case = make_case([W.layout_plain(44100), W.SongLayout(3, 1, [0, -1, 0], 30011)], seed=3)
+    con = gpu_console(case)
+    con.set_params(case.params)
+    res = GS.search(con, n_iter=2, train_steps=10, finetune_steps=5, seed=1)
+    present = con.present()
+    accepted = {i for rnd in res.trials for t in rnd if t.accepted for i in t.candidates}
+    assert set(np.nonzero(present == 0)[0]) == accepted
+    assert all(np.isfinite(res.la_final)) and all(0.0 <= r <= 1.0 for r in res.pruning_ratio)
+    for rnd in res.trials:
+        for s in range(con.n_songs):
+            assert any(t.song == s for t in rnd)
