@@ -220,6 +220,50 @@ def build_console(layouts, rank, per_song_seed=0):
     return con, sources, mixes
 
 
+def serving_run(args, rank):
+    """Serving under a Poisson stream of search jobs (continuous batching, admission by footprint)."""
+    import torch
+    import paper_2509_15948_gb300 as M
+    from paper_2509_15948_gb300.serve import Job, Server, latency_summary
+    rng = np.random.default_rng(0x5E + rank)
+    layouts = W.layout_uneven_batch(args.serve_jobs, seed=40 + rank)
+    bank = source_bank(key=100 + rank)
+    sources = [song_sources_from_bank(bank, l, s) for s, l in enumerate(layouts)]
+    songs = [M.Song(l.num_tracks, l.num_subgroups, l.track_group, l.num_samples) for l in layouts]
+    types = [W.processor_types([l]) for l in layouts]
+    noises = [W.reverb_noise((rank, 11, j), sum(t == "r" for t in types[j])) for j in range(len(layouts))]
+    # targets: each job's ground-truth graph rendered by a console (outside the timed region)
+    targets = []
+    for j, l in enumerate(layouts):
+        zeros = [np.zeros((2, l.num_samples), np.float32)]
+        con = M.Console([songs[j]], [sources[j]], zeros, noises[j], M.ConsoleConfig(retain_spectra=-1))
+        gt, keep = W.ground_truth(types[j], (rank, 78, j))
+        gt[con.n_proc_params:] = 30.0
+        con.set_params(gt)
+        _, mixes = con.forward_loss(mask=keep, with_mix=True)
+        targets.append(mixes[0].cpu().numpy())
+        con.close()
+    torch.cuda.synchronize()
+    t_arr = np.cumsum(rng.exponential(1.0 / args.serve_rate, len(layouts))) if args.serve_rate > 0 else \
+        np.zeros(len(layouts))
+    t_arr -= t_arr[0]
+    jobs = [Job(j, songs[j], sources[j], targets[j], noises[j], init_params=W.init_params(types[j], (rank, 6, j)),
+                train_steps=args.serve_train_steps, n_iter=args.serve_rounds, finetune_steps=args.serve_finetune_steps,
+                seed=j, arrival=float(t_arr[j])) for j in range(len(layouts))]
+    budget = int(args.serve_budget_gb * (1 << 30))
+    srv = Server(budget, cfg=M.ConsoleConfig(retain_spectra=-1))
+    res = srv.run(jobs)
+    out = latency_summary(res)
+    out.update({"arrival_rate_jobs_per_s": args.serve_rate if args.serve_rate > 0 else "burst",
+                "budget_gb": args.serve_budget_gb, "peak_gb_admitted": srv.peak_in_use / (1 << 30),
+                "peak_concurrent_jobs": srv.peak_active,
+                "schedule": f"{args.serve_train_steps} Adam steps + {args.serve_rounds} x (dry/wet round, "
+                            f"{args.serve_finetune_steps} steps)",
+                "jobs_desc": "K~U{4..32}, S~U{1..8}, 5-30 s at 44.1 kHz, one song per job",
+                "mean_pruning_ratio": float(np.mean([r.pruning_ratio for r in res if r.error is None]))})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -230,6 +274,12 @@ def main():
     ap.add_argument("--per-node-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-baseline-steps", type=int, default=3)
+    ap.add_argument("--serve-jobs", type=int, default=16, help="search jobs of the serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate, jobs/s (0: burst)")
+    ap.add_argument("--serve-budget-gb", type=float, default=24.0)
+    ap.add_argument("--serve-train-steps", type=int, default=60)
+    ap.add_argument("--serve-rounds", type=int, default=3)
+    ap.add_argument("--serve-finetune-steps", type=int, default=20)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -359,6 +409,16 @@ def main():
         cpu = {"value": ts / tt, "unit": "track-s/s", "cores": torch.get_num_threads(), "kind": "oracle",
                "sample": desc + f", {args.cpu_baseline_steps} steps"}
 
+    serving = None
+    if args.serve_jobs > 0:
+        dev_bytes = info["device_bytes"]
+        con.close()
+        del con
+        torch.cuda.synchronize()
+        serving = serving_run(args, rank)
+    else:
+        dev_bytes = info["device_bytes"]
+
     if rank == 0:
         line = {"metric": metric, "value": value, "unit": "track-s/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -367,7 +427,7 @@ def main():
                 "clocks": clk, "per_node": per_node, "losses_finite": finite,
                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in stage.items()},
                 "kernel_families_ms_per_step": {k: v[0] / args.steps for k, v in fam.items() if v[1] > 0},
-                "device_bytes": info["device_bytes"]}
+                "device_bytes": dev_bytes, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -15,7 +15,11 @@
  *    stream reaches the call.
  *  - The library owns all device memory it allocates; the caller owns what it passes in.
  *  - No C++ exception crosses the ABI.  Failures return a status; mg_last_error(console) gives a message
- *    (valid until the next call on that console).
+ *    (valid until the next call on that console); mg_last_error(NULL) is per host thread.
+ *  - Threads: different consoles may be driven from different host threads at the same time (one thread
+ *    per console at a time).  Console creation, destruction, pruning and the capture of a console's
+ *    training-step graph are serialised inside the library; callers that share the device must not
+ *    synchronise the whole device (cudaDeviceSynchronize) while other threads' consoles may be capturing.
  *  - Processor order P ("canonical"): song -> chain (tracks 0..K-1, then subgroups 0..S-1) -> type in
  *    chain order e c n s g d r (enabled types only).  The flat parameter vector holds every processor's
  *    parameters in that order (g 2, s 1, e 1024, r 768, c 4, n 4, d 880; Sec. 3), followed by one
@@ -89,7 +93,9 @@ typedef struct {
   int32_t n_reverbs;
   int64_t total_samples;       /* sum of L over songs */
   double track_seconds;        /* sum over songs of K * L / fs */
-  int64_t device_bytes;        /* device memory held by the console (0 from mg_plan) */
+  int64_t device_bytes;        /* device memory held by the console; from mg_plan, the footprint a console with
+                                  this descriptor would allocate (retained spectra only when retain_spectra = 1,
+                                  else the shared scratch), used for admission by memory footprint */
   int32_t launches_per_step;   /* kernel launches of forward_loss + backward + adam_step (0 from mg_plan) */
   int32_t retains_spectra;     /* 1 when the reverb/delay spectra are kept between forward and backward */
 } mg_console_info;

@@ -209,7 +209,9 @@ class Console:
             noise_ptr = noise_t.data_ptr()
         arr, keep = _song_array(self.songs, [x.data_ptr() for x in src_t],
                                 [x.data_ptr() for x in tgt_t] if tgt_t else None, on_device=1)
-        torch.cuda.synchronize(dev)
+        # the copies above ran on the caller's stream; a stream (not device) synchronisation, so that a graph
+        # being captured by another console on another thread is not disturbed
+        torch.cuda.current_stream(dev).synchronize()
         h = ctypes.c_void_p()
         st = self.lib.mg_console_create(ctypes.byref(_desc(cfg, noise_ptr, 1)), arr, len(self.songs),
                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))

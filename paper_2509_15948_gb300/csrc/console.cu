@@ -107,6 +107,11 @@ struct Stage {
 
 }  // namespace
 
+// Graph capture of one console must not overlap another thread's device allocation or release (cudaFree may
+// synchronise the device, which invalidates a capture in progress): consoles driven from several host threads
+// serialise those three operations on this lock.
+std::mutex g_device_mutex;
+
 struct mg_console {
   mg_console_desc desc{};
   std::vector<HostSong> songs;
@@ -180,7 +185,7 @@ struct mg_console {
 
 namespace {
 
-std::string g_static_err;
+thread_local std::string g_static_err;   // errors of calls without a console (per host thread)
 
 mg_status fail(mg_console* c, mg_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -804,14 +809,9 @@ mg_status build_tables(mg_console* c) {
   return MG_OK;
 }
 
-mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
-  plan(c, d, s, n);
-  init_kernel_attributes();
-  init_loss_attributes();
-  init_fir_attributes();
-  init_eqos_attributes();
-  const double fs = d->sample_rate;
-  // ---- arena layout ----
+// Host-only sizing: arena offsets of every song, chain and processor buffer, and the two LTI scratch sizes
+// (one group's shared scratch, and the retained per-node spectra).  Returns the arena size in bytes.
+size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scratch, size_t* keep_scratch) {
   Bump b;
   for (auto& hs : c->songs) {
     const size_t st = (size_t)2 * hs.ld * sizeof(float);
@@ -866,36 +866,57 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
       p.o_cagg = b.take(p.nchunks * sizeof(float));
     }
   }
-  // LTI scratch: the largest stage group (the stage lists are built later; size for the worst case)
-  {
-    const int64_t limit = d->workspace_limit_bytes > 0 ? d->workspace_limit_bytes : INT64_MAX;
-    size_t worst = 0;
-    for (int level = 0; level < 2; ++level)
-      for (int t : {T_R, T_D}) {
-        size_t used = 0;
-        for (auto& p : c->procs) {
-          if (p.level != level || p.type != t) continue;
-          if (used > 0 && (int64_t)(used + p.scratch_bytes) > limit) used = 0;
-          used += p.scratch_bytes;
-          worst = std::max(worst, used);
-        }
+  const int64_t limit = d->workspace_limit_bytes > 0 ? d->workspace_limit_bytes : INT64_MAX;
+  size_t worst = 0;
+  for (int level = 0; level < 2; ++level)
+    for (int t : {T_R, T_D}) {
+      size_t used = 0;
+      for (auto& p : c->procs) {
+        if (p.level != level || p.type != t) continue;
+        if (used > 0 && (int64_t)(used + p.scratch_bytes) > limit) used = 0;
+        used += p.scratch_bytes;
+        worst = std::max(worst, used);
       }
-    c->scratch_bytes = std::max(worst, scratch_need);
+    }
+  size_t keep = 0;
+  for (auto& p : c->procs)
+    if (p.type == T_R || p.type == T_D) keep += p.scratch_bytes;
+  *shared_scratch = std::max(worst, scratch_need);
+  *keep_scratch = std::max(keep, scratch_need);
+  return b.off;
+}
+
+// Device bytes of a console with the given scratch choice: arena, LTI scratch, parameters, gradients and the
+// two Adam moments.
+size_t console_device_bytes(const mg_console* c, size_t arena, size_t scratch) {
+  return arena + scratch + 4 * sizeof(float) * (size_t)c->nparams;
+}
+
+mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
+  plan(c, d, s, n);
+  init_kernel_attributes();
+  init_loss_attributes();
+  init_fir_attributes();
+  init_eqos_attributes();
+  const double fs = d->sample_rate;
+  // ---- arena layout and LTI scratch ----
+  size_t shared_scratch = 0, keep_scratch = 0;
+  const size_t arena = layout_arena(c, d, &shared_scratch, &keep_scratch);
+  {
     // retained spectra: every reverb/delay node gets its own T1 / T2 / Hz for the whole step
-    size_t keep = 0;
-    for (auto& p : c->procs)
-      if (p.type == T_R || p.type == T_D) keep += p.scratch_bytes;
+    const int64_t limit = d->workspace_limit_bytes > 0 ? d->workspace_limit_bytes : INT64_MAX;
     bool retain = d->retain_spectra == 1;
-    if (d->retain_spectra == 0 && (int64_t)keep <= limit) {
-      retain = keep <= c->scratch_bytes;   // costs no memory beyond the shared scratch
+    if (d->retain_spectra == 0 && (int64_t)keep_scratch <= limit) {
+      retain = keep_scratch <= shared_scratch;   // costs no memory beyond the shared scratch
       if (!retain) {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return MG_ERR_CUDA;
-        const size_t others = b.off + 4 * sizeof(float) * (size_t)c->nparams + ((size_t)256 << 20);
-        retain = free_b > others && (double)keep <= 0.8 * (double)(free_b - others);
+        const size_t others = console_device_bytes(c, arena, 0) + ((size_t)256 << 20);
+        retain = free_b > others && (double)keep_scratch <= 0.8 * (double)(free_b - others);
       }
     }
     c->retain = retain;
+    c->scratch_bytes = shared_scratch;
     if (retain) {
       size_t off = 0;
       for (auto& p : c->procs)
@@ -903,10 +924,10 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
           p.o_scratch = off;
           off += p.scratch_bytes;
         }
-      c->scratch_bytes = std::max(keep, scratch_need);
+      c->scratch_bytes = keep_scratch;
     }
   }
-  c->arena_bytes = b.off;
+  c->arena_bytes = arena;
   // ---- allocations ----
   CK(cudaMalloc(&c->arena, c->arena_bytes));
   CK(cudaMemsetAsync(c->arena, 0, c->arena_bytes, c->stream));
@@ -1178,9 +1199,12 @@ mg_status mg_plan(const mg_console_desc* desc, const mg_song_desc* songs, int32_
   }
   plan(&tmp, desc, songs, n_songs);
   fill_info(&tmp, out);
-  out->device_bytes = 0;
+  size_t shared_scratch = 0, keep_scratch = 0;
+  const size_t arena = layout_arena(&tmp, desc, &shared_scratch, &keep_scratch);
+  const bool keep = desc->retain_spectra == 1;
+  out->device_bytes = (int64_t)console_device_bytes(&tmp, arena, keep ? keep_scratch : shared_scratch);
   out->launches_per_step = 0;
-  out->retains_spectra = 0;
+  out->retains_spectra = keep ? 1 : 0;
   return MG_OK;
 }
 
@@ -1192,10 +1216,16 @@ mg_status mg_console_create(const mg_console_desc* desc, const mg_song_desc* son
   if (!c) return fail(nullptr, MG_ERR_OOM, "host allocation failed");
   c->stream = stream;
   mg_status st = validate(c, desc, songs, n_songs);
-  if (st == MG_OK) st = create_impl(c, desc, songs, n_songs);
+  if (st == MG_OK) {
+    std::lock_guard<std::mutex> lock(g_device_mutex);
+    st = create_impl(c, desc, songs, n_songs);
+  }
   if (st != MG_OK) {
     g_static_err = c->err;
-    destroy_impl(c);
+    {
+      std::lock_guard<std::mutex> lock(g_device_mutex);
+      destroy_impl(c);
+    }
     delete c;
     return st;
   }
@@ -1206,7 +1236,10 @@ mg_status mg_console_create(const mg_console_desc* desc, const mg_song_desc* son
 mg_status mg_console_destroy(mg_console* c) {
   if (!c) return MG_ERR_INVALID;
   cudaStreamSynchronize(c->stream);
-  destroy_impl(c);
+  {
+    std::lock_guard<std::mutex> lock(g_device_mutex);
+    destroy_impl(c);
+  }
   delete c;
   return MG_OK;
 }
@@ -1331,6 +1364,7 @@ mg_status mg_train_step(mg_console* c, float lr, float beta1, float beta2, float
     c->graph_pairs.clear();
     c->ev_next = 0;
     cudaGraph_t g;
+    std::lock_guard<std::mutex> capture_lock(g_device_mutex);
     c->capturing = true;
     c->launches = 0;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -1359,6 +1393,7 @@ mg_status mg_train_step(mg_console* c, float lr, float beta1, float beta2, float
 mg_status mg_prune(mg_console* c, const uint8_t* h_keep) {
   if (!c || !h_keep) return fail(c, MG_ERR_INVALID, "null pointer");
   CK(cudaStreamSynchronize(c->stream));
+  std::lock_guard<std::mutex> lock(g_device_mutex);   // rebuilds device tables (allocation and release)
   for (int i = 0; i < c->P; ++i)
     if (!h_keep[i]) c->procs[i].present = 0;
   if (build_tables(c) != MG_OK) return MG_ERR_CUDA;

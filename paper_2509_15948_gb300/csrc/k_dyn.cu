@@ -202,7 +202,7 @@ __global__ void k_dyn_fwd_carry(LaunchCtx c, const int* __restrict__ procs, int 
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_dyn_fwd_apply(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kThreads, 4) k_dyn_fwd_apply(LaunchCtx c, const Item* __restrict__ items) {
   __shared__ float sm[16];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
@@ -250,7 +250,7 @@ __device__ __forceinline__ float dyn_dg(const DynParams& d, float w, float g, fl
   return dE * (dG - 1.f) / (g + kEnvEps);
 }
 
-__global__ void __launch_bounds__(kThreads) k_dyn_bwd_agg(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_agg(LaunchCtx c, const Item* __restrict__ items) {
   __shared__ float sm[32];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
@@ -298,7 +298,7 @@ __global__ void k_dyn_bwd_carry(LaunchCtx c, const int* __restrict__ procs, int 
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_dyn_bwd_apply(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_apply(LaunchCtx c, const Item* __restrict__ items) {
   __shared__ float sm[32 * 5];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];

@@ -170,14 +170,13 @@ def search(con, n_iter: int, train_steps: int, finetune_steps: int, lr: float = 
            seed: int = 0, alpha_p_max: float = 1e-4, ramp_steps: Optional[int] = None) -> SearchResult:
     """Alg. 3 on every song of `con`: train, L_min from the unmasked graph, then n_iter rounds of
     {dry/wet pruning round, structural prune, fine-tuning}."""
-    import torch
     if ramp_steps is None:
         ramp_steps = (2 * n_iter * finetune_steps) // 3
     _, _, song_of = con.layout()
     present0 = con.present().copy()
     init_count = [int(np.sum(present0[song_of == s])) for s in range(con.n_songs)]
     rngs = [SplitMix64(song_seed(seed, s)) for s in range(con.n_songs)]
-    sync = lambda: torch.cuda.synchronize(con.device)
+    sync = lambda: con.stream.synchronize()       # the console's stream only (other consoles may be capturing)
     secs = {"train": 0.0, "rounds": 0.0, "finetune": 0.0}
 
     t0 = time.perf_counter()
