@@ -94,7 +94,7 @@ struct ProcList {
 
 struct LtiGroup {
   ProcList procs;
-  ItemList col, rowhz, rowpair, firtaps, dlyadj, revfir;
+  ItemList col, rowpair, firtaps, dlyadj, revfir;
 };
 
 struct Stage {
@@ -428,7 +428,7 @@ void lti_forward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
   }
   if (type == T_R) run_items(c, F_REV_FIR, g.revfir, [&](const Item* it, int n) { launch_rev_fir(x, it, n); });
   run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
-  run_items(c, F_ROW_HZ, g.rowhz, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowhz.maxv); });
+  run_items(c, F_ROW_HZ, g.rowpair, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowpair.maxv); });
   run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_audio(x, it, n, g.col.maxv); });
   if (c->retain) {   // U stays in T1, y_bar in T2 (natural order) for the backward
     run_items(c, F_ROW_CONV, g.rowpair, [&](const Item* it, int n) { launch_row_conv_fwd(x, it, n, g.rowpair.maxv, true); });
@@ -444,7 +444,7 @@ void lti_backward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
     run_items(c, F_COL_DYBAR, g.col, [&](const Item* it, int n) { launch_col_dybar_keep(x, it, n, g.col.maxv); });
   } else {
     run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
-    run_items(c, F_ROW_HZ, g.rowhz, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowhz.maxv); });
+    run_items(c, F_ROW_HZ, g.rowpair, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowpair.maxv); });
     run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_audio(x, it, n, g.col.maxv); });
     run_items(c, F_ROW_CONV, g.rowpair, [&](const Item* it, int n) { launch_row_conv_fwd(x, it, n, g.rowpair.maxv, true); });
     run_items(c, F_COL_DYBAR, g.col, [&](const Item* it, int n) { launch_col_dybar(x, it, n, g.col.maxv); });
@@ -756,9 +756,9 @@ mg_status build_tables(mg_console* c) {
         LtiGroup g;
         auto close = [&]() -> mg_status {
           if (g.procs.h.empty()) return MG_OK;
-          for (ItemList* L : {&g.col, &g.rowhz, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
+          for (ItemList* L : {&g.col, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
             L->beg.push_back((int)L->h.size());
-          if (upload_procs(c, g.procs) || upload_items(c, g.col) || upload_items(c, g.rowhz) ||
+          if (upload_procs(c, g.procs) || upload_items(c, g.col) ||
               upload_items(c, g.rowpair) || upload_items(c, g.firtaps) || upload_items(c, g.dlyadj) ||
               upload_items(c, g.revfir))
             return MG_ERR_CUDA;
@@ -782,12 +782,10 @@ mg_status build_tables(mg_console* c) {
           d.Hz = d.T2 + N;
           g.procs.h.push_back(pi);
           const int N1 = 1 << p.logN1, N2 = 1 << p.logN2;
-          for (ItemList* L : {&g.col, &g.rowhz, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
+          for (ItemList* L : {&g.col, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
             L->beg.push_back((int)L->h.size());
           for (int i = 0; i < N1 / p.colG; ++i) g.col.h.push_back(Item{pi, i});
           g.col.maxv = std::max(g.col.maxv, N2 * p.colG);
-          for (int i = 0; i < N2; ++i) g.rowhz.h.push_back(Item{pi, i});
-          g.rowhz.maxv = std::max(g.rowhz.maxv, N1);
           for (int i = 0; i <= N2 / 2; ++i) g.rowpair.h.push_back(Item{pi, i});
           g.rowpair.maxv = std::max(g.rowpair.maxv, N1);
           if (t == T_D) {

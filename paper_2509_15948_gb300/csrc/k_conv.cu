@@ -9,6 +9,8 @@
 // Both channels travel as one complex signal z = left + i right; a stereo FIR (h_l, h_r) acts on the packed
 // spectrum as Y[k] = Z[k] A[k] + conj(Z[-k]) B[k] with A = (H_l + H_r)/2, B = (H_l - H_r)/2, where the
 // mirror bin -k sits in row N2 - k2.
+#include <algorithm>
+
 #include "mg_fftp.cuh"
 
 namespace mg {
@@ -16,7 +18,7 @@ namespace mg {
 namespace {
 
 constexpr int kColThreads = 512;
-constexpr int kRowThreads = 256;
+constexpr int kRowThreads = 256;   // largest row block: N1 = 2048 (logN <= 22)
 // Shared-memory layouts (padded, see mg_fftp.cuh).  Column pass: column g, row r at sm[g * col_stride + pidx(r)],
 // with col_stride = 16 (mod 16) + 16 / G so that the G columns and 16 / G rows a half-warp touches fall in
 // distinct bank pairs.  Row pass: row slot s, position k1 at sm[s * pstride(N1) + pidx(k1)].
@@ -195,17 +197,24 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   }
 }
 
-// Row pass of the filter spectrum: forward N1-point FFT of row k2 of Hz, in place.
+// Row pass of the filter spectrum: forward N1-point FFTs of rows a and b = N2 - a of Hz, in place.
 __global__ void __launch_bounds__(kRowThreads, 4) k_row_fwd_hz(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
-  const int logN1 = P.logN1, N1 = 1 << logN1;
-  float2* row = P.Hz + ((int64_t)it.idx << logN1);
-  for (int e = threadIdx.x; e < N1; e += blockDim.x) sm[pidx(e)] = row[e];
+  const int logN1 = P.logN1, N1 = 1 << logN1, N2 = 1 << P.logN2, rs = pstride(N1);
+  const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
+  const int nr = a == b ? 1 : 2;
+  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
+    const int slot = e >> logN1, k1 = e & (N1 - 1);
+    sm[slot * rs + pidx(k1)] = P.Hz[((int64_t)(slot ? b : a) << logN1) + k1];
+  }
   __syncthreads();
-  fft_p<false>(sm, logN1, 1, pstride(N1), c.tab.tw);
-  for (int e = threadIdx.x; e < N1; e += blockDim.x) row[e] = sm[pidx(e)];
+  fft_p<false>(sm, logN1, nr, rs, c.tab.tw);
+  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
+    const int slot = e >> logN1, k1 = e & (N1 - 1);
+    P.Hz[((int64_t)(slot ? b : a) << logN1) + k1] = sm[slot * rs + pidx(k1)];
+  }
 }
 
 // Loads rows a and b (b may equal a) of src into smem slots 0/1 and runs their forward FFTs.
@@ -233,75 +242,91 @@ __device__ __forceinline__ void inv_rows_store(float2* o, float2* dst, int a, in
   }
 }
 
-// Forward convolution (and first backward step): spectrum of u in rows of T1; Y = Z A + conj(Z_-) B;
-// inverse row FFT to T1 (forward) or T2 (backward, where T1 keeps the spectrum of u for the FIR gradient).
-template <bool BWD>
+// Every bin of rows a, b = N2 - a together with its mirror -k, once per pair: for a != b the partner of
+// (a, k1) is (b, N1 - 1 - k1); for a == b (rows 0 and N2/2) both bins lie in the same row and a pair is
+// visited from its smaller position (bins 0 and N1/2 of row 0 are their own mirrors).  f gets the two
+// shared-memory positions (slot layout of load_rows_fft) and the two global positions of the row-major grid.
+template <typename F>
+__device__ __forceinline__ void for_mirror_pairs(int a, int b, int logN1, F&& f) {
+  const int N1 = 1 << logN1;
+  const int qs = a == b ? 0 : pstride(N1);
+  for (int k1 = threadIdx.x; k1 < N1; k1 += blockDim.x) {
+    const int mk1 = mirror_pos(a, k1, N1);
+    if (a == b && mk1 < k1) continue;
+    f(pidx(k1), qs + pidx(mk1), ((int64_t)a << logN1) + k1, ((int64_t)b << logN1) + mk1);
+  }
+}
+
+// Forward convolution: spectrum Z of u (rows of T1 after the column pass), Y = Z A + conj(Z_-) B, inverse row
+// FFT.  KEEP = false: the result goes back to T1.  KEEP = true (retained spectra, and the recomputing
+// backward): T1 keeps Z for the FIR gradient and the result goes to T2.  The product is formed in place,
+// each thread owning a bin and its mirror.
+template <bool KEEP>
 __global__ void __launch_bounds__(kRowThreads, 4) k_row_conv(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
-  const int logN1 = P.logN1, N1 = 1 << logN1, logN2 = P.logN2, N2 = 1 << logN2;
+  const int logN1 = P.logN1, N2 = 1 << P.logN2;
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
-  const int nr = a == b ? 1 : 2, rs = pstride(N1);
   float2* s = sm;
-  float2* o = sm + 2 * rs;
   load_rows_fft(s, P.T1, a, b, logN1, c.tab.tw);
-  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >> logN1, k1 = e & (N1 - 1);
-    const int k2 = slot ? b : a, m2 = slot ? a : b;
-    const int mslot = (a == b) ? 0 : (slot ^ 1);
-    const int mk1 = mirror_pos(k2, k1, N1);
-    const float2 z = s[slot * rs + pidx(k1)];
-    if (BWD) P.T1[((int64_t)k2 << logN1) + k1] = z;
-    const float2 hz = P.Hz[((int64_t)k2 << logN1) + k1];
-    const float2 hzm = P.Hz[((int64_t)m2 << logN1) + mk1];
-    float2 A, B;
-    fir_ab(hz, hzm, A, B);
-    o[slot * rs + pidx(k1)] = cadd(cmul(z, A), cmul(cconj(s[mslot * rs + pidx(mk1)]), B));
-  }
-  inv_rows_store(o, BWD ? P.T2 : P.T1, a, b, logN1, P.logN, c.tab);
+  for_mirror_pairs(a, b, logN1, [&](int pP, int pQ, int64_t gP, int64_t gQ) {
+    const float2 zP = s[pP], zQ = s[pQ];
+    const float2 hP = P.Hz[gP], hQ = P.Hz[gQ];
+    float2 AP, BP, AQ, BQ;
+    fir_ab(hP, hQ, AP, BP);
+    fir_ab(hQ, hP, AQ, BQ);
+    if (KEEP) {
+      P.T1[gP] = zP;
+      P.T1[gQ] = zQ;
+    }
+    s[pP] = cadd(cmul(zP, AP), cmul(cconj(zQ), BP));
+    s[pQ] = cadd(cmul(zQ, AQ), cmul(cconj(zP), BQ));
+  });
+  inv_rows_store(s, KEEP ? P.T2 : P.T1, a, b, logN1, P.logN, c.tab);
 }
 
 // Second backward step.  Rows of T2 hold the column-transformed dL/dy_bar; T1 holds the spectrum of u.
 //   dU  = Dz conj(A) + conj(Dz_-) conj(B)                    (correlation with the FIR: adjoint of y = h * u)
 //   dH  = D_l conj(U_l) + i D_r conj(U_r)                      (dL/dh_c[j] = sum_n dL/dy_bar_c[n] u_c[n - j])
-// Inverse row FFTs: dU to T2, dH to T1.
+// dU is formed in place over the spectrum of dL/dy_bar, dH in a second pair of rows; inverse row FFTs: dU to
+// T2, dH to T1.
+__device__ __forceinline__ float2 fir_grad_bin(float2 dz, float2 dzm, float2 zu, float2 zum) {
+  const float2 ul = cscale(cadd(zu, cconj(zum)), 0.5f);
+  const float2 du_ = csub(zu, cconj(zum));
+  const float2 ur = make_float2(0.5f * du_.y, -0.5f * du_.x);
+  const float2 dl = cscale(cadd(dz, cconj(dzm)), 0.5f);
+  const float2 dd = csub(dz, cconj(dzm));
+  const float2 dr = make_float2(0.5f * dd.y, -0.5f * dd.x);
+  const float2 hl = cmulc(dl, ul), hr = cmulc(dr, ur);
+  return make_float2(hl.x - hr.y, hl.y + hr.x);   // hl + i hr
+}
+
 __global__ void __launch_bounds__(kRowThreads, 4) k_row_bwd2(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
-  const int logN1 = P.logN1, N1 = 1 << logN1, logN2 = P.logN2, N2 = 1 << logN2;
+  const int logN1 = P.logN1, N1 = 1 << logN1, N2 = 1 << P.logN2;
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
-  const int nr = a == b ? 1 : 2, rs = pstride(N1);
   float2* s = sm;
-  float2* o1 = sm + 2 * rs;
-  float2* o2 = sm + 4 * rs;
+  float2* o = sm + 2 * pstride(N1);
   load_rows_fft(s, P.T2, a, b, logN1, c.tab.tw);
-  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >> logN1, k1 = e & (N1 - 1);
-    const int k2 = slot ? b : a, m2 = slot ? a : b;
-    const int mslot = (a == b) ? 0 : (slot ^ 1);
-    const int mk1 = mirror_pos(k2, k1, N1);
-    const int64_t ib = ((int64_t)k2 << logN1) + k1, im = ((int64_t)m2 << logN1) + mk1;
-    float2 A, B;
-    fir_ab(P.Hz[ib], P.Hz[im], A, B);
-    const int pe = slot * rs + pidx(k1);
-    const float2 dz = s[pe], dzm = s[mslot * rs + pidx(mk1)];
-    o1[pe] = cadd(cmul(dz, cconj(A)), cmul(cconj(dzm), cconj(B)));
-    const float2 zu = P.T1[ib], zum = P.T1[im];
-    const float2 ul = cscale(cadd(zu, cconj(zum)), 0.5f);
-    const float2 du_ = csub(zu, cconj(zum));
-    const float2 ur = make_float2(0.5f * du_.y, -0.5f * du_.x);
-    const float2 dl = cscale(cadd(dz, cconj(dzm)), 0.5f);
-    const float2 dd = csub(dz, cconj(dzm));
-    const float2 dr = make_float2(0.5f * dd.y, -0.5f * dd.x);
-    const float2 hl = cmulc(dl, ul), hr = cmulc(dr, ur);
-    o2[pe] = make_float2(hl.x - hr.y, hl.y + hr.x);   // hl + i hr
-  }
-  __syncthreads();
-  // every thread has read its T1 entries; the inverse FFTs below overwrite T1 rows a, b only
-  inv_rows_store(o1, P.T2, a, b, logN1, P.logN, c.tab);
-  inv_rows_store(o2, P.T1, a, b, logN1, P.logN, c.tab);
+  for_mirror_pairs(a, b, logN1, [&](int pP, int pQ, int64_t gP, int64_t gQ) {
+    const float2 dzP = s[pP], dzQ = s[pQ];
+    const float2 hP = P.Hz[gP], hQ = P.Hz[gQ];
+    const float2 uP = P.T1[gP], uQ = P.T1[gQ];
+    float2 AP, BP, AQ, BQ;
+    fir_ab(hP, hQ, AP, BP);
+    fir_ab(hQ, hP, AQ, BQ);
+    s[pP] = cadd(cmul(dzP, cconj(AP)), cmul(cconj(dzQ), cconj(BP)));
+    s[pQ] = cadd(cmul(dzQ, cconj(AQ)), cmul(cconj(dzP), cconj(BQ)));
+    o[pP] = fir_grad_bin(dzP, dzQ, uP, uQ);
+    o[pQ] = fir_grad_bin(dzQ, dzP, uQ, uP);
+  });
+  // every thread has read its T1 entries before the barrier that opens the inverse FFTs; they overwrite T1
+  // rows a, b only
+  inv_rows_store(s, P.T2, a, b, logN1, P.logN, c.tab);
+  inv_rows_store(o, P.T1, a, b, logN1, P.logN, c.tab);
 }
 
 template <int MODE>
@@ -324,10 +349,10 @@ void init_kernel_attributes() {
   cudaFuncSetAttribute(k_col<COL_DH>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_col<COL_INV_OUT_KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_col<COL_DYBAR_KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_row_fwd_hz, cudaFuncAttributeMaxDynamicSharedMemorySize, pstride(4096) * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_row_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * pstride(2048) * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_row_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * pstride(2048) * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_row_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * pstride(2048) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_fwd_hz, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(2048) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(2048) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(2048) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * pstride(2048) * (int)sizeof(float2));
 }
 
 void launch_col_fwd_audio(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_FWD_AUDIO>(c, items, n, m); }
@@ -339,21 +364,25 @@ void launch_col_dh(const LaunchCtx& c, const Item* items, int n, int m) { launch
 void launch_col_inv_out_keep(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_INV_OUT_KEEP>(c, items, n, m); }
 void launch_col_dybar_keep(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_DYBAR_KEEP>(c, items, n, m); }
 
+// Row kernels run one thread per 8 elements of a row pair (2 N1 elements, fft_p's limit of 16 per thread with
+// radix-16 passes keeping every thread busy), so the block size follows the largest N1 of the launch.
+int row_threads(int maxN1) { return std::max(32, std::min(kRowThreads, maxN1 / 8)); }
+
 void launch_row_fwd_hz(const LaunchCtx& c, const Item* items, int n, int maxN1) {
-  if (n) k_row_fwd_hz<<<n, kRowThreads, (size_t)pstride(maxN1) * sizeof(float2), c.stream>>>(c, items);
+  if (n) k_row_fwd_hz<<<n, row_threads(maxN1), (size_t)2 * pstride(maxN1) * sizeof(float2), c.stream>>>(c, items);
 }
 
-void launch_row_conv_fwd(const LaunchCtx& c, const Item* items, int n, int maxN1, bool bwd) {
+void launch_row_conv_fwd(const LaunchCtx& c, const Item* items, int n, int maxN1, bool keep) {
   if (!n) return;
-  const size_t smem = (size_t)4 * pstride(maxN1) * sizeof(float2);
-  if (bwd) k_row_conv<true><<<n, kRowThreads, smem, c.stream>>>(c, items);
-  else k_row_conv<false><<<n, kRowThreads, smem, c.stream>>>(c, items);
+  const size_t smem = (size_t)2 * pstride(maxN1) * sizeof(float2);
+  if (keep) k_row_conv<true><<<n, row_threads(maxN1), smem, c.stream>>>(c, items);
+  else k_row_conv<false><<<n, row_threads(maxN1), smem, c.stream>>>(c, items);
 }
 
 void launch_row_bwd2(const LaunchCtx& c, const Item* items, int n, int maxN1) {
   if (!n) return;
-  const size_t smem = (size_t)6 * pstride(maxN1) * sizeof(float2);
-  k_row_bwd2<<<n, kRowThreads, smem, c.stream>>>(c, items);
+  const size_t smem = (size_t)4 * pstride(maxN1) * sizeof(float2);
+  k_row_bwd2<<<n, row_threads(maxN1), smem, c.stream>>>(c, items);
 }
 
 }  // namespace mg

@@ -38,7 +38,6 @@ struct NaLayout {
   ProcDev proc;
   int proc_list[4];
   Item col_items[kNaMaxCol];
-  Item row_items[kNaMaxRow];
   Item pair_items[kNaMaxRow / 2 + 1];
 };
 
@@ -98,7 +97,6 @@ __global__ void k_na_prep(const float* u, float* y, const float* params, int L, 
     S->proc_list[0] = 0;
   }
   for (int i = t; i < N1 / G; i += blockDim.x) S->col_items[i] = Item{0, i};
-  for (int i = t; i < N2; i += blockDim.x) S->row_items[i] = Item{0, i};
   for (int i = t; i <= N2 / 2; i += blockDim.x) S->pair_items[i] = Item{0, i};
 }
 
@@ -159,7 +157,7 @@ extern "C" mg_status mg_eq_forward_noalloc(const float* d_u, float* d_y, int64_t
   x.tab.hann_eq = S->hann_eq;
   launch_eq_fir(x, S->proc_list, 1);
   launch_col_fwd_taps(x, S->col_items, N1 / G, N2 * G);
-  launch_row_fwd_hz(x, S->row_items, N2, N1);
+  launch_row_fwd_hz(x, S->pair_items, N2 / 2 + 1, N1);
   launch_col_fwd_audio(x, S->col_items, N1 / G, N2 * G);
   launch_row_conv_fwd(x, S->pair_items, N2 / 2 + 1, N1, false);
   launch_col_inv_out(x, S->col_items, N1 / G, N2 * G);
