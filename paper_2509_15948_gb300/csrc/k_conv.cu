@@ -58,6 +58,13 @@ enum ColMode {
   COL_INV_OUT_KEEP = 6, COL_DYBAR_KEEP = 7
 };
 
+// A column tile is G adjacent columns of the N1 x N2 grid (N2 * G <= 8192 elements, 512 threads).  Because the
+// block size is a multiple of G, every thread stays on one column g and handles the rows r0 + s * RS
+// (RS = 512 / G, s < kSlots): the global positions of its elements step by RS * N1, its loads are independent
+// and issued eight at a time before the shared-memory stores, and the epilogues batch their side loads
+// (input u, upstream gradient dy) four slots at a time.
+constexpr int kSlots = 8192 / kColThreads;
+
 template <int MODE>
 __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
@@ -65,44 +72,59 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const int G = P.colG, logG = __ffs(G) - 1;
-  const int logN2 = P.logN2, N2 = 1 << logN2, logN1 = P.logN1, N1 = 1 << logN1, logN = P.logN;
+  const int logN2 = P.logN2, N2 = 1 << logN2, logN1 = P.logN1, logN = P.logN;
   const int64_t N = (int64_t)1 << logN;
-  const int c0 = it.idx * G;
-  const int tot = N2 * G;
   const int cs = col_stride(N2, G);
   constexpr bool kInv = MODE == COL_INV_OUT || MODE == COL_DYBAR || MODE == COL_DU || MODE == COL_DH ||
                         MODE == COL_INV_OUT_KEEP;
   constexpr bool kOut = MODE == COL_INV_OUT || MODE == COL_INV_OUT_KEEP;
   constexpr bool kDybar = MODE == COL_DYBAR || MODE == COL_DYBAR_KEEP;
 
-  // ---- load ----
-  float2* src = (MODE == COL_INV_OUT || MODE == COL_DH) ? P.T1 : P.T2;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int g = e & (G - 1), r = e >> logG;
-    const int n1 = c0 + g;
-    const int64_t n = (int64_t)n1 + ((int64_t)r << logN1);
-    float2 v;
-    if (MODE == COL_FWD_AUDIO) {
-      v = make_float2(0.f, 0.f);
-      if (n < P.L) v = make_float2(P.u[n], P.u[P.ld + n]);
-    } else if (MODE == COL_FWD_TAPS) {
-      v = tap_at(P, n, N);
-    } else {
-      v = src[n];
-    }
-    sm[g * cs + pidx(r)] = v;
-  }
-  __syncthreads();
-  if (MODE != COL_DYBAR_KEEP) fft_p<kInv>(sm, logN2, G, cs, c.tab.tw);
+  const int g = threadIdx.x & (G - 1), r0 = threadIdx.x >> logG;
+  const int RS = blockDim.x >> logG;
+  const int n1 = it.idx * G + g;
+  const int64_t nbase = (int64_t)n1 + ((int64_t)r0 << logN1);
+  const int64_t nstep = (int64_t)RS << logN1;
+  float2* col = sm + g * cs;
+  auto row_of = [&](int s) { return r0 + s * RS; };
+  auto live = [&](int s) { return row_of(s) < N2; };
+  auto pos = [&](int s) { return nbase + (int64_t)s * nstep; };
 
-  if (!kInv && !kDybar) {  // forward column pass: twiddle, store in place (row k2 = r)
+  // ---- load ----
+  if (MODE != COL_DYBAR_KEEP) {
+    const float2* src = (MODE == COL_INV_OUT || MODE == COL_DH) ? P.T1 : P.T2;
+#pragma unroll
+    for (int h = 0; h < kSlots; h += 8) {
+      float2 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        v[j] = make_float2(0.f, 0.f);
+        if (live(h + j)) {
+          const int64_t n = pos(h + j);
+          if (MODE == COL_FWD_AUDIO) {
+            if (n < P.L) v[j] = make_float2(P.u[n], P.u[P.ld + n]);
+          } else if (MODE == COL_FWD_TAPS) {
+            v[j] = tap_at(P, n, N);
+          } else {
+            v[j] = src[n];
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (live(h + j)) col[pidx(row_of(h + j))] = v[j];
+    }
+    __syncthreads();
+    fft_p<kInv>(sm, logN2, G, cs, c.tab.tw);
+  }
+
+  if (!kInv && !kDybar) {  // forward column pass: twiddle, store in place (row k2)
     float2* dst = MODE == COL_FWD_TAPS ? P.Hz : P.T1;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int g = e & (G - 1), k2 = e >> logG;
-      const int n1 = c0 + g;
-      const float2 w = twiddle_tab((unsigned)n1 * (unsigned)k2, logN, false, c.tab);
-      dst[(int64_t)n1 + ((int64_t)k2 << logN1)] = cmul(sm[g * cs + pidx(k2)], w);
+#pragma unroll 4
+    for (int s = 0; s < kSlots; ++s) {
+      if (!live(s)) continue;
+      const int k2 = row_of(s);
+      dst[pos(s)] = cmul(col[pidx(k2)], twiddle_tab((unsigned)n1 * (unsigned)k2, logN, false, c.tab));
     }
     return;
   }
@@ -111,16 +133,27 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   if (kOut) {
     const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
     float acc[2] = {0.f, 0.f};
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int g = e & (G - 1), r = e >> logG;
-      const int64_t n = (int64_t)(c0 + g) + ((int64_t)r << logN1);
-      if (n < P.L) {
-        const float2 yb = cscale(sm[g * cs + pidx(r)], inv_n);
+#pragma unroll 1
+    for (int h = 0; h < kSlots; h += 4) {
+      float ul[4], ur[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        ul[j] = ur[j] = 0.f;
+        if (live(h + j) && n < P.L) {
+          ul[j] = P.u[n];
+          ur[j] = P.u[P.ld + n];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        if (!live(h + j) || n >= P.L) continue;
+        const float2 yb = cscale(col[pidx(row_of(h + j))], inv_n);
         if (MODE == COL_INV_OUT_KEEP) P.T2[n] = yb;
-        const float ul = P.u[n], ur = P.u[P.ld + n];
-        P.y[n] = w * yb.x + wd * ul;
-        P.y[P.ld + n] = w * yb.y + wd * ur;
-        const float ym = yb.x + yb.y, um = ul + ur;
+        P.y[n] = w * yb.x + wd * ul[j];
+        P.y[P.ld + n] = w * yb.y + wd * ur[j];
+        const float ym = yb.x + yb.y, um = ul[j] + ur[j];
         acc[0] += ym * ym;
         acc[1] += um * um;
       }
@@ -134,62 +167,88 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
     return;
   }
   if (kDybar) {
-    // y_bar -> dL/dy_bar = w dy + c1 (y_bar_l + y_bar_r) on both channels; dw partial; then forward FFT
-    const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
+    // y_bar -> dL/dy_bar = w dy + c1 (y_bar_l + y_bar_r) on both channels; dw partial; then forward FFT.
+    // Retained spectra: y_bar is read in natural order from T2; otherwise it is the inverse column FFT above.
+    const float w = dry_wet_w(c, P.qidx);
     const float c1 = P.stats[2];
     float acc[1] = {0.f};
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int g = e & (G - 1), r = e >> logG;
-      const int64_t n = (int64_t)(c0 + g) + ((int64_t)r << logN1);
-      float2 v = make_float2(0.f, 0.f);
-      if (n < P.L) {
-        const float2 yb = MODE == COL_DYBAR_KEEP ? sm[g * cs + pidx(r)] : cscale(sm[g * cs + pidx(r)], inv_n);
-        const float gl = P.dy[n], gr = P.dy[P.ld + n];
-        const float ul = P.u[n], ur = P.u[P.ld + n];
-        acc[0] += gl * (yb.x - ul) + gr * (yb.y - ur);
-        const float gm = c1 * (yb.x + yb.y);
-        v = make_float2(w * gl + gm, w * gr + gm);
+#pragma unroll 1
+    for (int h = 0; h < kSlots; h += 4) {
+      float2 yb[4];
+      float gl[4], gr[4], ul[4], ur[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        yb[j] = make_float2(0.f, 0.f);
+        gl[j] = gr[j] = ul[j] = ur[j] = 0.f;
+        if (live(h + j) && n < P.L) {
+          yb[j] = MODE == COL_DYBAR_KEEP ? P.T2[n] : cscale(col[pidx(row_of(h + j))], inv_n);
+          gl[j] = P.dy[n];
+          gr[j] = P.dy[P.ld + n];
+          ul[j] = P.u[n];
+          ur[j] = P.u[P.ld + n];
+        }
       }
-      sm[g * cs + pidx(r)] = v;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!live(h + j)) continue;
+        acc[0] += gl[j] * (yb[j].x - ul[j]) + gr[j] * (yb[j].y - ur[j]);
+        const float gm = c1 * (yb[j].x + yb[j].y);
+        // rows past the signal are zero (gl = gr = 0 and y_bar = 0 there)
+        col[pidx(row_of(h + j))] = make_float2(w * gl[j] + gm, w * gr[j] + gm);
+      }
     }
     float out[1];
     block_sum<1>(acc, red, out);   // also acts as the barrier before the FFT
     if (threadIdx.x == 0) P.bpart[it.idx * kNPart + 0] = out[0];
     fft_p<false>(sm, logN2, G, cs, c.tab.tw);
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int g = e & (G - 1), k2 = e >> logG;
-      const int n1 = c0 + g;
-      const float2 tw = twiddle_tab((unsigned)n1 * (unsigned)k2, logN, false, c.tab);
-      P.T2[(int64_t)n1 + ((int64_t)k2 << logN1)] = cmul(sm[g * cs + pidx(k2)], tw);
+#pragma unroll 4
+    for (int s = 0; s < kSlots; ++s) {
+      if (!live(s)) continue;
+      const int k2 = row_of(s);
+      P.T2[pos(s)] = cmul(col[pidx(k2)], twiddle_tab((unsigned)n1 * (unsigned)k2, logN, false, c.tab));
     }
     return;
   }
   if (MODE == COL_DU) {
-    const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
+    const float wd = dry_wet_d(c, P.qidx);
     const float c2 = P.stats[3];
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int g = e & (G - 1), r = e >> logG;
-      const int64_t n = (int64_t)(c0 + g) + ((int64_t)r << logN1);
-      if (n < P.L) {
-        const float2 dw = cscale(sm[g * cs + pidx(r)], inv_n);
-        const float um = c2 * (P.u[n] + P.u[P.ld + n]);
-        P.du[n] = wd * P.dy[n] + dw.x + um;
-        P.du[P.ld + n] = wd * P.dy[P.ld + n] + dw.y + um;
+#pragma unroll 1
+    for (int h = 0; h < kSlots; h += 4) {
+      float gl[4], gr[4], um[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        gl[j] = gr[j] = um[j] = 0.f;
+        if (live(h + j) && n < P.L) {
+          gl[j] = P.dy[n];
+          gr[j] = P.dy[P.ld + n];
+          um[j] = c2 * (P.u[n] + P.u[P.ld + n]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        if (!live(h + j) || n >= P.L) continue;
+        const float2 dw = cscale(col[pidx(row_of(h + j))], inv_n);
+        P.du[n] = wd * gl[j] + dw.x + um[j];
+        P.du[P.ld + n] = wd * gr[j] + dw.y + um[j];
       }
     }
     return;
   }
   if (MODE == COL_DH) {
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int g = e & (G - 1), r = e >> logG;
-      const int64_t n = (int64_t)(c0 + g) + ((int64_t)r << logN1);
+#pragma unroll 4
+    for (int s = 0; s < kSlots; ++s) {
+      if (!live(s)) continue;
+      const int64_t n = pos(s);
       int64_t j = -1;
       if (n < (int64_t)P.n0 + P.Nh) j = n - P.n0;
       else if (n >= N + P.n0) j = n - N - P.n0;
       if (j >= 0 && j < P.Nh) {
         // dL/dh[t] = sum_n dL/dy_bar[n] u[n - t] is identically zero for lags t >= L: store the exact zero
         // instead of the FFT rounding residue (the delay's Eq. 19 direction takes sgn(0) = 0 there)
-        const float2 v = (j + P.n0 >= P.L) ? make_float2(0.f, 0.f) : cscale(sm[g * cs + pidx(r)], inv_n);
+        const float2 v = (j + P.n0 >= P.L) ? make_float2(0.f, 0.f) : cscale(col[pidx(row_of(s))], inv_n);
         P.dtaps[j] = v.x;
         P.dtaps[P.Nh + j] = v.y;
       }
