@@ -51,7 +51,7 @@ struct HostProc {
   int nfrows = 0, nbrows = 0;
   // arena offsets (bytes)
   size_t o_y = 0, o_stats = 0, o_fpart = 0, o_bpart = 0, o_taps = 0, o_dtaps = 0, o_aux = 0, o_carry = 0, o_rcarry = 0,
-         o_cagg = 0, o_nspec = 0, o_hspec = 0, o_dhpart = 0;
+         o_cagg = 0, o_nspec = 0, o_hspec = 0, o_ybar = 0, o_dhspec = 0;
   size_t scratch_bytes = 0;  // T1 + T2 + Hz
   size_t o_scratch = 0;      // offset inside the shared LTI scratch
 };
@@ -283,7 +283,7 @@ void plan(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n)
           p.colG = std::min(8, std::min(8192 >> p.logN2, 1 << p.logN1));
           if (t == T_E) {   // single-pass overlap-save in shared memory (no global FFT scratch)
             p.nfrows = (p.L + kEqOsFwdBlock - 1) / kEqOsFwdBlock;
-            p.nbrows = (p.L + kEqOsBwdBlock - 1) / kEqOsBwdBlock;
+            p.nbrows = (p.nfrows + kEqChunk - 1) / kEqChunk;   // backward items: chunks of forward blocks
           } else {
             p.nfrows = (1 << p.logN1) / p.colG;
             p.nbrows = p.nfrows;
@@ -665,7 +665,8 @@ mg_status build_tables(mg_console* c) {
     }
     if (p.type == T_E) {
       d.hspec = (float*)A(p.o_hspec);
-      d.dhpart = (float*)A(p.o_dhpart);
+      d.ybar = (float*)A(p.o_ybar);
+      d.dhspec = (float2*)A(p.o_dhspec);
     }
     d.aux = p.o_aux ? (float*)A(p.o_aux) : nullptr;
     d.carry = p.nchunks ? (float*)A(p.o_carry) : nullptr;
@@ -850,7 +851,8 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
     }
     if (p.type == T_E) {
       p.o_hspec = b.take((size_t)kEqOsM * sizeof(float));
-      p.o_dhpart = b.take((size_t)p.nbrows * kEqTaps * sizeof(float));
+      p.o_ybar = b.take((size_t)2 * p.ld * sizeof(float));
+      p.o_dhspec = b.take((size_t)p.nbrows * kEqOsM * sizeof(float2));
     }
     if (p.type == T_D) p.o_aux = b.take((2 * kDlyTaps * kDlyFir + 2 * kDlyTaps) * sizeof(float));
     if (p.type == T_R) {

@@ -28,7 +28,7 @@ constexpr int kElemTile = 4096;            // samples per elementwise work item
 constexpr float kEnvEps = 1e-8f;           // G_u = ln(g + eps)
 constexpr int kEqOsM = 8192;               // overlap-save FFT size of the equalizer
 constexpr int kEqOsFwdBlock = kEqOsM - 2 * kEqHalf;        // 6146 outputs per forward block
-constexpr int kEqOsBwdBlock = kEqOsM - 4 * kEqHalf;        // 4100 outputs per backward block
+constexpr int kEqChunk = 8;                 // equalizer backward: blocks per work item (spectra summed in registers)
 
 struct Item {
   int proc;
@@ -69,7 +69,8 @@ struct ProcDev {
   int nframes;                             // F
   // equalizer (overlap-save)
   float* hspec;                            // [8192] real spectrum of the FIR on the overlap-save grid
-  float* dhpart;                           // [backward blocks][2047] partial tap gradients
+  float* ybar;                             // [2][ld] wet signal kept by the forward for the backward
+  float2* dhspec;                          // [backward items][8192] summed spectra of the tap correlation
 };
 
 struct LossRes {                           // one STFT resolution of Eq. (21)
