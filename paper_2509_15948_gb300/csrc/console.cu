@@ -47,7 +47,7 @@ struct HostProc {
   int present = 1;
   int64_t poff;
   int L, ld;
-  int logN = 0, logN1 = 0, logN2 = 0, colG = 0, n0 = 0, Nh = 0, nchunks = 0, nframes = 0;
+  int logN = 0, logN1 = 0, logN2 = 0, f = 1, colG = 0, n0 = 0, Nh = 0, nchunks = 0, nframes = 0;
   int nfrows = 0, nbrows = 0;
   // arena offsets (bytes)
   size_t o_y = 0, o_stats = 0, o_fpart = 0, o_bpart = 0, o_taps = 0, o_dtaps = 0, o_aux = 0, o_carry = 0, o_rcarry = 0,
@@ -277,17 +277,29 @@ void plan(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n)
           if (t == T_E) { p.n0 = -kEqHalf; p.Nh = kEqTaps; }
           if (t == T_D) { p.n0 = -kDlyHalf; p.Nh = kDlyTaps * D + kDlyFir - 1; }
           if (t == T_R) { p.n0 = 0; p.Nh = revlen; p.nframes = (revlen - kRevFft) / kRevHop + 1; }
-          p.logN = std::max(12, ilog2_ceil((int64_t)p.L + p.Nh + std::abs(p.n0) + 1));
-          p.logN1 = (p.logN + 1) / 2;
-          p.logN2 = p.logN / 2;
+          // N = f 2^logN >= L + taps: the smaller of 2^k and 3 2^k'; rows N1 = f 2^logN1, columns N2 = 2^logN2
+          const int64_t need = (int64_t)p.L + p.Nh + std::abs(p.n0) + 1;
+          const int k2 = std::max(12, ilog2_ceil(need));
+          const int k3 = std::max(11, ilog2_ceil((need + 2) / 3));
+          if (t != T_E && ((int64_t)3 << k3) < ((int64_t)1 << k2)) {
+            p.f = 3;
+            p.logN = k3;
+            p.logN2 = std::min(10, (k3 + 1) / 2);
+            p.logN1 = k3 - p.logN2;
+          } else {
+            p.f = 1;
+            p.logN = k2;
+            p.logN1 = (k2 + 1) / 2;
+            p.logN2 = k2 / 2;
+          }
           p.colG = std::min(8, std::min(8192 >> p.logN2, 1 << p.logN1));
           if (t == T_E) {   // single-pass overlap-save in shared memory (no global FFT scratch)
             p.nfrows = (p.L + kEqOsFwdBlock - 1) / kEqOsFwdBlock;
             p.nbrows = (p.nfrows + kEqChunk - 1) / kEqChunk;   // backward items: chunks of forward blocks
           } else {
-            p.nfrows = (1 << p.logN1) / p.colG;
+            p.nfrows = (p.f << p.logN1) / p.colG;
             p.nbrows = p.nfrows;
-            p.scratch_bytes = (size_t)3 * ((size_t)1 << p.logN) * sizeof(float2);
+            p.scratch_bytes = (size_t)3 * ((size_t)p.f << p.logN) * sizeof(float2);
           }
         } else if (t == T_C || t == T_N) {
           p.nchunks = (p.L + kDynChunk - 1) / kDynChunk;
@@ -650,11 +662,16 @@ mg_status build_tables(mg_console* c) {
     d.logN = p.logN;
     d.logN1 = p.logN1;
     d.logN2 = p.logN2;
+    d.f = p.f;
+    for (int r = 0; r < 3; ++r) {   // exp(-2 pi i r / N), N = 3 2^logN (used when f = 3)
+      const double ang = -2.0 * 3.14159265358979323846 * r / (3.0 * std::ldexp(1.0, p.logN));
+      d.c3n[r] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
     d.colG = p.colG;
     d.n0 = p.n0;
     d.Nh = p.Nh;
     if (p.scratch_bytes) {
-      const size_t N = (size_t)1 << p.logN;
+      const size_t N = (size_t)p.f << p.logN;
       d.T1 = (float2*)(c->scratch + p.o_scratch);
       d.T2 = d.T1 + N;
       d.Hz = d.T2 + N;
@@ -777,12 +794,12 @@ mg_status build_tables(mg_console* c) {
             used += p.scratch_bytes;
           }
           ProcDev& d = c->hpd[pi];
-          const size_t N = (size_t)1 << p.logN;
+          const size_t N = (size_t)p.f << p.logN;
           d.T1 = (float2*)(c->scratch + p.o_scratch);
           d.T2 = d.T1 + N;
           d.Hz = d.T2 + N;
           g.procs.h.push_back(pi);
-          const int N1 = 1 << p.logN1, N2 = 1 << p.logN2;
+          const int N1 = p.f << p.logN1, N2 = 1 << p.logN2;
           for (ItemList* L : {&g.col, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
             L->beg.push_back((int)L->h.size());
           for (int i = 0; i < N1 / p.colG; ++i) g.col.h.push_back(Item{pi, i});
@@ -980,6 +997,13 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
       twf[j] = make_float2((float)std::cos(a), (float)-std::sin(a));
     }
     c->tab.twf = (const float2*)up_table(twf.data(), twf.size() * sizeof(float2));
+    std::vector<float2> c3((kTwLog + 1) * 3);
+    for (int a = 0; a <= kTwLog; ++a)
+      for (int r = 0; r < 3; ++r) {
+        const double ang = -2.0 * PI * r / (3.0 * std::ldexp(1.0, a));
+        c3[a * 3 + r] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+      }
+    c->tab.c3 = (const float2*)up_table(c3.data(), c3.size() * sizeof(float2));
     c->tab.cos_eq = (const float*)up_table(ceq.data(), ceq.size() * sizeof(float));
     c->tab.cos_dl = (const float*)up_table(cdl.data(), cdl.size() * sizeof(float));
     c->tab.rev_win = (const float*)up_table(hwin.data(), hwin.size() * sizeof(float));
@@ -987,7 +1011,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     c->tab.hann_eq = (const float*)up_table(heq.data(), heq.size() * sizeof(float));
     c->tab.hann_dl = (const float*)up_table(hdl.data(), hdl.size() * sizeof(float));
     c->tab.dly_w = (const float2*)up_table(dw.data(), dw.size() * sizeof(float2));
-    if (!c->tab.tw || !c->tab.twf || !c->tab.dly_w) return fail(c, MG_ERR_OOM, "table allocation failed");
+    if (!c->tab.tw || !c->tab.twf || !c->tab.c3 || !c->tab.dly_w) return fail(c, MG_ERR_OOM, "table allocation failed");
   }
   // loss resolutions
   c->hres.assign(c->nres, LossRes{});

@@ -1,6 +1,8 @@
-// FIR convolution of the LTI processors (equalizer Eq. 8, reverb Sec. 3.4, multitap delay Eq. 17) and its
-// adjoint, by one zero-padded FFT of size N = N1 * N2 >= L + |taps| per node (exact linear convolution),
-// evaluated with the four-step algorithm in two shared-memory passes:
+// FIR convolution of the LTI processors (reverb Sec. 3.4, multitap delay Eq. 17; the equalizer of Eq. 8 in the
+// allocation-free entry) and its adjoint, by one zero-padded FFT of size N = N1 * N2 >= L + |taps| per node
+// (exact linear convolution), N = f 2^k with f in {1, 3} (whichever is smaller: the odd factor cuts the
+// average padding from ~1.5x to ~1.2x), N1 = f 2^a rows, N2 = 2^b columns, evaluated with the four-step
+// algorithm in two shared-memory passes:
 //   column pass: N2-point FFTs over n2 of x[n1 + N1 n2] for a group of G adjacent n1, twiddle
 //                exp(-+2 pi i n1 k2 / N); stored in place, so row k2 holds A[n1][k2] contiguously;
 //   row pass:    N1-point FFTs of row k2 give X[k2 + N2 k1] at row k2, position k1 (transposed order).
@@ -18,14 +20,36 @@ namespace mg {
 namespace {
 
 constexpr int kColThreads = 512;
-constexpr int kRowThreads = 256;   // largest row block: N1 = 2048 (logN <= 22)
+constexpr int kRowThreads = 512;   // largest row block: N1 = 3072 (one thread per 8 elements of a row pair)
 // Shared-memory layouts (padded, see mg_fftp.cuh).  Column pass: column g, row r at sm[g * col_stride + pidx(r)],
 // with col_stride = 16 (mod 16) + 16 / G so that the G columns and 16 / G rows a half-warp touches fall in
 // distinct bank pairs.  Row pass: row slot s, position k1 at sm[s * pstride(N1) + pidx(k1)].
 constexpr int kColBuf = 8192 + 512 + 160;
+constexpr int kMaxRow = 3072;      // longest row N1 (3 x 1024)
 __host__ __device__ constexpr int col_stride(int N2, int G) { return ((N2 + (N2 >> 4) + 15) & ~15) + 16 / G; }
 
-__device__ __forceinline__ int mirror_pos(int k2, int k1, int N1) { return k2 == 0 ? ((N1 - k1) & (N1 - 1)) : (N1 - 1 - k1); }
+__device__ __forceinline__ int mirror_pos(int k2, int k1, int N1) { return k2 == 0 ? (k1 ? N1 - k1 : 0) : (N1 - 1 - k1); }
+
+__device__ __forceinline__ int rows_len(const ProcDev& P) { return P.f << P.logN1; }
+__device__ __forceinline__ int64_t fft_len(const ProcDev& P) { return (int64_t)P.f << P.logN; }
+
+// Transposition twiddle exp(-+2 pi i m / N), m < N: the power-of-two tables, times exp(-2 pi i (m mod 3) / N)
+// when N = 3 2^logN.
+__device__ __forceinline__ float2 twiddle_node(const ProcDev& P, unsigned m, bool inverse, const Tables& tab) {
+  if (P.f == 1) return twiddle_tab(m, P.logN, inverse, tab);
+  const unsigned q = m / 3u, r = m - 3u * q;
+  float2 w = twiddle_tab(q, P.logN, false, tab);
+  if (r) w = cmul(w, P.c3n[r]);
+  if (inverse) w.y = -w.y;
+  return w;
+}
+
+// Row FFTs (length N1 = f 2^logN1) of nb padded rows with batch stride bs.
+template <bool INV>
+__device__ __forceinline__ void row_fft(float2* d, const ProcDev& P, int nb, int bs, const Tables& tab) {
+  if (P.f == 1) fft_p<INV>(d, P.logN1, nb, bs, tab.tw);
+  else fft_p3<INV>(d, P.logN1, nb, bs, tab.tw, tab.c3);
+}
 
 // Tap value of the stereo FIR at circular position n (time n, or n - N for the negative taps).
 __device__ __forceinline__ float2 tap_at(const ProcDev& P, int64_t n, int64_t N) {
@@ -72,8 +96,8 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const int G = P.colG, logG = __ffs(G) - 1;
-  const int logN2 = P.logN2, N2 = 1 << logN2, logN1 = P.logN1, logN = P.logN;
-  const int64_t N = (int64_t)1 << logN;
+  const int logN2 = P.logN2, N2 = 1 << logN2, N1 = rows_len(P);
+  const int64_t N = fft_len(P);
   const int cs = col_stride(N2, G);
   constexpr bool kInv = MODE == COL_INV_OUT || MODE == COL_DYBAR || MODE == COL_DU || MODE == COL_DH ||
                         MODE == COL_INV_OUT_KEEP;
@@ -83,8 +107,8 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   const int g = threadIdx.x & (G - 1), r0 = threadIdx.x >> logG;
   const int RS = blockDim.x >> logG;
   const int n1 = it.idx * G + g;
-  const int64_t nbase = (int64_t)n1 + ((int64_t)r0 << logN1);
-  const int64_t nstep = (int64_t)RS << logN1;
+  const int64_t nbase = (int64_t)n1 + (int64_t)r0 * N1;
+  const int64_t nstep = (int64_t)RS * N1;
   float2* col = sm + g * cs;
   auto row_of = [&](int s) { return r0 + s * RS; };
   auto live = [&](int s) { return row_of(s) < N2; };
@@ -124,12 +148,12 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
     for (int s = 0; s < kSlots; ++s) {
       if (!live(s)) continue;
       const int k2 = row_of(s);
-      dst[pos(s)] = cmul(col[pidx(k2)], twiddle_tab((unsigned)n1 * (unsigned)k2, logN, false, c.tab));
+      dst[pos(s)] = cmul(col[pidx(k2)], twiddle_node(P, (unsigned)n1 * (unsigned)k2, false, c.tab));
     }
     return;
   }
 
-  const float inv_n = ldexpf(1.f, -logN);
+  const float inv_n = ldexpf(1.f, -P.logN) / (float)P.f;
   if (kOut) {
     const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
     float acc[2] = {0.f, 0.f};
@@ -206,7 +230,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
     for (int s = 0; s < kSlots; ++s) {
       if (!live(s)) continue;
       const int k2 = row_of(s);
-      P.T2[pos(s)] = cmul(col[pidx(k2)], twiddle_tab((unsigned)n1 * (unsigned)k2, logN, false, c.tab));
+      P.T2[pos(s)] = cmul(col[pidx(k2)], twiddle_node(P, (unsigned)n1 * (unsigned)k2, false, c.tab));
     }
     return;
   }
@@ -257,84 +281,106 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
 }
 
 // Row pass of the filter spectrum: forward N1-point FFTs of rows a and b = N2 - a of Hz, in place.
-__global__ void __launch_bounds__(kRowThreads, 4) k_row_fwd_hz(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kRowThreads, 2) k_row_fwd_hz(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
-  const int logN1 = P.logN1, N1 = 1 << logN1, N2 = 1 << P.logN2, rs = pstride(N1);
+  const int N1 = rows_len(P), N2 = 1 << P.logN2, rs = pstride(N1);
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
   const int nr = a == b ? 1 : 2;
   for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >> logN1, k1 = e & (N1 - 1);
-    sm[slot * rs + pidx(k1)] = P.Hz[((int64_t)(slot ? b : a) << logN1) + k1];
+    const int slot = e >= N1, k1 = e - slot * N1;
+    sm[slot * rs + pidx(k1)] = P.Hz[(int64_t)(slot ? b : a) * N1 + k1];
   }
   __syncthreads();
-  fft_p<false>(sm, logN1, nr, rs, c.tab.tw);
+  row_fft<false>(sm, P, nr, rs, c.tab);
   for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >> logN1, k1 = e & (N1 - 1);
-    P.Hz[((int64_t)(slot ? b : a) << logN1) + k1] = sm[slot * rs + pidx(k1)];
+    const int slot = e >= N1, k1 = e - slot * N1;
+    P.Hz[(int64_t)(slot ? b : a) * N1 + k1] = sm[slot * rs + pidx(k1)];
   }
 }
 
 // Loads rows a and b (b may equal a) of src into smem slots 0/1 and runs their forward FFTs.
-__device__ __forceinline__ void load_rows_fft(float2* s, const float2* src, int a, int b, int logN1, const float2* tw) {
-  const int N1 = 1 << logN1, rs = pstride(N1);
+__device__ __forceinline__ void load_rows_fft(float2* s, const float2* src, int a, int b, const ProcDev& P,
+                                              const Tables& tab) {
+  const int N1 = rows_len(P), rs = pstride(N1);
   const int nr = a == b ? 1 : 2;
+#pragma unroll 8
   for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >> logN1, k1 = e & (N1 - 1);
-    s[slot * rs + pidx(k1)] = src[((int64_t)(slot ? b : a) << logN1) + k1];
+    const int slot = e >= N1, k1 = e - slot * N1;
+    s[slot * rs + pidx(k1)] = src[(int64_t)(slot ? b : a) * N1 + k1];
   }
   __syncthreads();
-  fft_p<false>(s, logN1, nr, rs, tw);
+  row_fft<false>(s, P, nr, rs, tab);
 }
 
 // Inverse row FFT of the slots in o, twiddle exp(+2 pi i n1 k2 / N), store rows a, b of dst.
-__device__ __forceinline__ void inv_rows_store(float2* o, float2* dst, int a, int b, int logN1, int logN, const Tables& tab) {
-  const int N1 = 1 << logN1, rs = pstride(N1);
+__device__ __forceinline__ void inv_rows_store(float2* o, float2* dst, int a, int b, const ProcDev& P, const Tables& tab) {
+  const int N1 = rows_len(P), rs = pstride(N1);
   const int nr = a == b ? 1 : 2;
   __syncthreads();
-  fft_p<true>(o, logN1, nr, rs, tab.tw);
+  row_fft<true>(o, P, nr, rs, tab);
+#pragma unroll 4
   for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >> logN1, n1 = e & (N1 - 1);
+    const int slot = e >= N1, n1 = e - slot * N1;
     const int k2 = slot ? b : a;
-    dst[((int64_t)k2 << logN1) + n1] = cmul(o[slot * rs + pidx(n1)], twiddle_tab((unsigned)n1 * (unsigned)k2, logN, true, tab));
+    dst[(int64_t)k2 * N1 + n1] = cmul(o[slot * rs + pidx(n1)], twiddle_node(P, (unsigned)n1 * (unsigned)k2, true, tab));
   }
 }
 
 // Every bin of rows a, b = N2 - a together with its mirror -k, once per pair: for a != b the partner of
 // (a, k1) is (b, N1 - 1 - k1); for a == b (rows 0 and N2/2) both bins lie in the same row and a pair is
-// visited from its smaller position (bins 0 and N1/2 of row 0 are their own mirrors).  f gets the two
-// shared-memory positions (slot layout of load_rows_fft) and the two global positions of the row-major grid.
-template <typename F>
-__device__ __forceinline__ void for_mirror_pairs(int a, int b, int logN1, F&& f) {
-  const int N1 = 1 << logN1;
+// visited from its smaller position (bins 0 and N1/2 of row 0 are their own mirrors).  The pairs of a thread
+// are taken NB at a time: load(gP, gQ) fetches the global operands of all NB pairs first (independent loads in
+// flight together), then op(pP, pQ, gP, gQ, v) runs on each; pP, pQ are the shared-memory positions (slot
+// layout of load_rows_fft), gP, gQ the positions in the row-major grid.
+template <int NB, typename Ld, typename Op>
+__device__ __forceinline__ void for_mirror_pairs(int a, int b, int N1, Ld&& load, Op&& op) {
   const int qs = a == b ? 0 : pstride(N1);
-  for (int k1 = threadIdx.x; k1 < N1; k1 += blockDim.x) {
-    const int mk1 = mirror_pos(a, k1, N1);
-    if (a == b && mk1 < k1) continue;
-    f(pidx(k1), qs + pidx(mk1), ((int64_t)a << logN1) + k1, ((int64_t)b << logN1) + mk1);
+  using V = decltype(load(int64_t(0), int64_t(0)));
+  for (int k0 = threadIdx.x; k0 < N1; k0 += NB * blockDim.x) {
+    V v[NB];
+    int kk[NB], mk[NB];
+    bool ok[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      kk[j] = k0 + j * blockDim.x;
+      mk[j] = mirror_pos(a, kk[j], N1);
+      ok[j] = kk[j] < N1 && !(a == b && mk[j] < kk[j]);
+      if (ok[j]) v[j] = load((int64_t)a * N1 + kk[j], (int64_t)b * N1 + mk[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+      if (ok[j]) op(pidx(kk[j]), qs + pidx(mk[j]), (int64_t)a * N1 + kk[j], (int64_t)b * N1 + mk[j], v[j]);
   }
 }
+
+struct HzPair {
+  float2 hP, hQ;
+};
+struct HzUPair {
+  float2 hP, hQ, uP, uQ;
+};
 
 // Forward convolution: spectrum Z of u (rows of T1 after the column pass), Y = Z A + conj(Z_-) B, inverse row
 // FFT.  KEEP = false: the result goes back to T1.  KEEP = true (retained spectra, and the recomputing
 // backward): T1 keeps Z for the FIR gradient and the result goes to T2.  The product is formed in place,
 // each thread owning a bin and its mirror.
 template <bool KEEP>
-__global__ void __launch_bounds__(kRowThreads, 4) k_row_conv(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kRowThreads, 2) k_row_conv(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
-  const int logN1 = P.logN1, N2 = 1 << P.logN2;
+  const int N1 = rows_len(P), N2 = 1 << P.logN2;
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
   float2* s = sm;
-  load_rows_fft(s, P.T1, a, b, logN1, c.tab.tw);
-  for_mirror_pairs(a, b, logN1, [&](int pP, int pQ, int64_t gP, int64_t gQ) {
+  load_rows_fft(s, P.T1, a, b, P, c.tab);
+  for_mirror_pairs<4>(a, b, N1, [&](int64_t gP, int64_t gQ) { return HzPair{P.Hz[gP], P.Hz[gQ]}; },
+                      [&](int pP, int pQ, int64_t gP, int64_t gQ, const HzPair& v) {
     const float2 zP = s[pP], zQ = s[pQ];
-    const float2 hP = P.Hz[gP], hQ = P.Hz[gQ];
     float2 AP, BP, AQ, BQ;
-    fir_ab(hP, hQ, AP, BP);
-    fir_ab(hQ, hP, AQ, BQ);
+    fir_ab(v.hP, v.hQ, AP, BP);
+    fir_ab(v.hQ, v.hP, AQ, BQ);
     if (KEEP) {
       P.T1[gP] = zP;
       P.T1[gQ] = zQ;
@@ -342,7 +388,7 @@ __global__ void __launch_bounds__(kRowThreads, 4) k_row_conv(LaunchCtx c, const 
     s[pP] = cadd(cmul(zP, AP), cmul(cconj(zQ), BP));
     s[pQ] = cadd(cmul(zQ, AQ), cmul(cconj(zP), BQ));
   });
-  inv_rows_store(s, KEEP ? P.T2 : P.T1, a, b, logN1, P.logN, c.tab);
+  inv_rows_store(s, KEEP ? P.T2 : P.T1, a, b, P, c.tab);
 }
 
 // Second backward step.  Rows of T2 hold the column-transformed dL/dy_bar; T1 holds the spectrum of u.
@@ -361,31 +407,31 @@ __device__ __forceinline__ float2 fir_grad_bin(float2 dz, float2 dzm, float2 zu,
   return make_float2(hl.x - hr.y, hl.y + hr.x);   // hl + i hr
 }
 
-__global__ void __launch_bounds__(kRowThreads, 4) k_row_bwd2(LaunchCtx c, const Item* __restrict__ items) {
+__global__ void __launch_bounds__(kRowThreads, 2) k_row_bwd2(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
-  const int logN1 = P.logN1, N1 = 1 << logN1, N2 = 1 << P.logN2;
+  const int N1 = rows_len(P), N2 = 1 << P.logN2;
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
   float2* s = sm;
   float2* o = sm + 2 * pstride(N1);
-  load_rows_fft(s, P.T2, a, b, logN1, c.tab.tw);
-  for_mirror_pairs(a, b, logN1, [&](int pP, int pQ, int64_t gP, int64_t gQ) {
+  load_rows_fft(s, P.T2, a, b, P, c.tab);
+  for_mirror_pairs<4>(a, b, N1,
+                      [&](int64_t gP, int64_t gQ) { return HzUPair{P.Hz[gP], P.Hz[gQ], P.T1[gP], P.T1[gQ]}; },
+                      [&](int pP, int pQ, int64_t gP, int64_t gQ, const HzUPair& v) {
     const float2 dzP = s[pP], dzQ = s[pQ];
-    const float2 hP = P.Hz[gP], hQ = P.Hz[gQ];
-    const float2 uP = P.T1[gP], uQ = P.T1[gQ];
     float2 AP, BP, AQ, BQ;
-    fir_ab(hP, hQ, AP, BP);
-    fir_ab(hQ, hP, AQ, BQ);
+    fir_ab(v.hP, v.hQ, AP, BP);
+    fir_ab(v.hQ, v.hP, AQ, BQ);
     s[pP] = cadd(cmul(dzP, cconj(AP)), cmul(cconj(dzQ), cconj(BP)));
     s[pQ] = cadd(cmul(dzQ, cconj(AQ)), cmul(cconj(dzP), cconj(BQ)));
-    o[pP] = fir_grad_bin(dzP, dzQ, uP, uQ);
-    o[pQ] = fir_grad_bin(dzQ, dzP, uQ, uP);
+    o[pP] = fir_grad_bin(dzP, dzQ, v.uP, v.uQ);
+    o[pQ] = fir_grad_bin(dzQ, dzP, v.uQ, v.uP);
   });
   // every thread has read its T1 entries before the barrier that opens the inverse FFTs; they overwrite T1
   // rows a, b only
-  inv_rows_store(s, P.T2, a, b, logN1, P.logN, c.tab);
-  inv_rows_store(o, P.T1, a, b, logN1, P.logN, c.tab);
+  inv_rows_store(s, P.T2, a, b, P, c.tab);
+  inv_rows_store(o, P.T1, a, b, P, c.tab);
 }
 
 template <int MODE>
@@ -408,10 +454,10 @@ void init_kernel_attributes() {
   cudaFuncSetAttribute(k_col<COL_DH>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_col<COL_INV_OUT_KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   cudaFuncSetAttribute(k_col<COL_DYBAR_KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  cudaFuncSetAttribute(k_row_fwd_hz, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(2048) * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_row_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(2048) * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_row_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(2048) * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_row_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * pstride(2048) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_fwd_hz, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * pstride(kMaxRow) * (int)sizeof(float2));
 }
 
 void launch_col_fwd_audio(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_FWD_AUDIO>(c, items, n, m); }

@@ -86,6 +86,7 @@ __global__ void k_na_prep(const float* u, float* y, const float* params, int L, 
     d.logN = logN;
     d.logN1 = logN1;
     d.logN2 = logN2;
+    d.f = 1;
     d.colG = G;
     d.n0 = -kEqHalf;
     d.Nh = kEqTaps;

@@ -180,7 +180,143 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
   __syncthreads();
 }
 
+// ---- transforms of size M = 3 * 2^a (one radix-3 pass, then radix 16 / 8 / 4 / 2) ----
+
+// exp(-+2 pi i m / (3 * 2^a)), m < 3 * 2^a: the 2^a-point table entry of floor(m / 3) times
+// c3[a][m mod 3] = exp(-2 pi i (m mod 3) / (3 * 2^a)) (both rounded once from double).
+template <bool INV>
+__device__ __forceinline__ float2 tw3(unsigned m, int a, const float2* __restrict__ tw, const float2* __restrict__ c3) {
+  const unsigned q = m / 3u, r = m - 3u * q;
+  float2 w = tw[q << (kTwLog - a)];
+  if (r) w = cmul(w, c3[a * 3 + r]);
+  if (INV) w.y = -w.y;
+  return w;
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2& x0, float2& x1, float2& x2) {
+  constexpr float h = 0.86602540378443865f;   // sin(2 pi / 3)
+  const float2 s = cadd(x1, x2), d = csub(x1, x2);
+  const float2 m = make_float2(x0.x - 0.5f * s.x, x0.y - 0.5f * s.y);
+  // forward: X1 = m - i h d, X2 = m + i h d (inverse: signs of the i h d term swapped)
+  const float2 ihd = make_float2(-h * d.y, h * d.x);
+  x0 = cadd(x0, s);
+  x1 = INV ? cadd(m, ihd) : csub(m, ihd);
+  x2 = INV ? csub(m, ihd) : cadd(m, ihd);
+}
+
+// First pass (p = 1, no twiddles): butterfly i < 2^a reads x[i + r 2^a], writes 3 i + q.
+template <bool INV>
+__device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int bs) {
+  constexpr int PER = 6;                      // 16 elements per thread -> at most 16/3 butterflies
+  const int MR = 1 << a, total = nb << a, nth = blockDim.x, tid = threadIdx.x;
+  float2 v[PER][3];
+  int ob[PER];
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    const int it = tid + s * nth;
+    ob[s] = -1;
+    if (it < total) {
+      const int b = it >> a, i = it & (MR - 1);
+      const float2* src = d + b * bs;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) v[s][r] = src[pidx(i + r * MR)];
+      dft3<INV>(v[s][0], v[s][1], v[s][2]);
+      ob[s] = b * bs;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    if (ob[s] >= 0) {
+      const int i = (tid + s * nth) & (MR - 1);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) d[ob[s] + pidx(3 * i + q)] = v[s][q];
+    }
+  }
+  __syncthreads();
+}
+
+// Later passes: p = 3 * 2^lp2, radix R = 2^LOGR; butterfly i < M / R, k = i mod p, twiddle w_M^{r k M / (R p)}.
+template <bool INV, int R, int LOGR>
+__device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int bs, int lp2,
+                                      const float2* __restrict__ tw, const float2* __restrict__ c3) {
+  constexpr int PER = 16 / R;
+  const int MR = 3 << (a - LOGR), p = 3 << lp2, total = nb * MR;
+  const int nth = blockDim.x, tid = threadIdx.x;
+  float2 v[PER][R];
+  int ob[PER];
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    const int it = tid + s * nth;
+    ob[s] = -1;
+    if (it < total) {
+      const int b = it / MR, i = it - b * MR;
+      const int k = i - p * (i / p);
+      const float2* src = d + b * bs;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[s][r] = src[pidx(i + r * MR)];
+      const unsigned m1 = (unsigned)k << (a - lp2 - LOGR);
+      if (k) {
+        const float2 w1 = tw3<INV>(m1, a, tw, c3);
+        v[s][1] = cmul(v[s][1], w1);
+        if constexpr (R >= 4) {
+          const float2 w2 = tw3<INV>(2 * m1, a, tw, c3), w3 = cmul(w1, w2);
+          v[s][2] = cmul(v[s][2], w2);
+          v[s][3] = cmul(v[s][3], w3);
+          if constexpr (R >= 8) {
+            const float2 w4 = tw3<INV>(4 * m1, a, tw, c3);
+            const float2 w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+            v[s][4] = cmul(v[s][4], w4);
+            v[s][5] = cmul(v[s][5], w5);
+            v[s][6] = cmul(v[s][6], w6);
+            v[s][7] = cmul(v[s][7], w7);
+            if constexpr (R >= 16) {
+              const float2 w8 = tw3<INV>(8 * m1, a, tw, c3);
+              v[s][8] = cmul(v[s][8], w8);
+              v[s][9] = cmul(v[s][9], cmul(w1, w8));
+              v[s][10] = cmul(v[s][10], cmul(w2, w8));
+              v[s][11] = cmul(v[s][11], cmul(w3, w8));
+              v[s][12] = cmul(v[s][12], cmul(w4, w8));
+              v[s][13] = cmul(v[s][13], cmul(w5, w8));
+              v[s][14] = cmul(v[s][14], cmul(w6, w8));
+              v[s][15] = cmul(v[s][15], cmul(w7, w8));
+            }
+          }
+        }
+      }
+      dftR<INV, R>(v[s]);
+      ob[s] = b * bs + (i - k) * R + k;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < PER; ++s) {
+    if (ob[s] >= 0) {
+      const int b = (tid + s * nth) / MR;
+      const int e0 = ob[s] - b * bs;
+      float2* dst = d + b * bs;
+#pragma unroll
+      for (int q = 0; q < R; ++q) dst[pidx(e0 + q * p)] = v[s][q];
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace fftp
+
+// FFTs of size M = 3 * 2^a (a >= 1) over nb batches in the padded layout, in place; same contract as fft_p.
+template <bool INV>
+__device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const float2* __restrict__ tw,
+                       const float2* __restrict__ c3) {
+  fftp::pass3<INV>(d, a, nb, bs);
+  int lp2 = 0;
+  for (; a - lp2 >= 4; lp2 += 4) fftp::passm<INV, 16, 4>(d, a, nb, bs, lp2, tw, c3);
+  const int rem = a - lp2;
+  if (rem == 3) fftp::passm<INV, 8, 3>(d, a, nb, bs, lp2, tw, c3);
+  else if (rem == 2) fftp::passm<INV, 4, 2>(d, a, nb, bs, lp2, tw, c3);
+  else if (rem == 1) fftp::passm<INV, 2, 1>(d, a, nb, bs, lp2, tw, c3);
+}
 
 // FFTs of size M = 2^logM (M <= 8192) over nb batches, padded layout (element e of batch b at
 // d[b * bs + pidx(e)]), in place.  Requires nb * M <= 16 * blockDim.x.  Forward: exp(-2 pi i nk/M); inverse:

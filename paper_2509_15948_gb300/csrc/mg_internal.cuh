@@ -50,8 +50,11 @@ struct ProcDev {
   float* bpart;                            // backward partials [items][kNPart]
   int nfpart, nbpart;                      // number of partial rows written by the main pass
   float* stats;                            // [8]: 0 E_ybar_mid, 1 E_u_mid, 2 c1, 3 c2, 4.. backward sums
-  // LTI processors (e, r, d): four-step FFT convolution of size N = N1 * N2
+  // LTI processors (r, d): four-step FFT convolution of size N = N1 * N2 = f 2^logN, N1 = f 2^logN1 (rows),
+  // N2 = 2^logN2 (columns), f in {1, 3}
   int logN, logN1, logN2, colG;            // colG: columns per column-pass work item
+  int f;
+  float2 c3n[3];                           // exp(-2 pi i r / N), r < 3 (transposition twiddles when f = 3)
   int n0, Nh;                              // FIR: first tap time, number of taps
   float2* T1;
   float2* T2;
@@ -106,6 +109,7 @@ struct SongDev {
 struct Tables {
   const float2* tw;                        // exp(-2 pi i j / 8192)
   const float2* twf;                       // exp(-2 pi i j / 2^26), j < 8192 (fine factor of large-N twiddles)
+  const float2* c3;                        // [14][3] exp(-2 pi i r / (3 2^a)): twiddles of 3 2^a-point FFTs
   const float* cos_eq;                     // cos(2 pi m / 2047), m < 2047
   const float* cos_dl;                     // cos(2 pi m / 39), m < 39
   const float* rev_win;                    // periodic Hann 384

@@ -116,9 +116,43 @@ def oracle_with_delay_taps(case: Case, alpha_p: float):
     return losses, grads, mixes, taps
 
 
-def delay_slot_conditioning(case: Case, taps: dict, D: int = 4410):
+def delay_term_rms(case: Case, alpha_p: float = 1e-3, D: int = 4410, n0: int = -19) -> dict:
+    """Per delay processor and channel: rms over the tap lags of A[j] = sum_n |dL/dy_bar[n]| |u[n - j]|, the
+    magnitudes of the terms whose sum is dL/dh[j] (dL/dy_bar taken as w dL/dy from the oracle's intermediates).
+    Near an optimum dL/dh cancels strongly (A is 4-2000x its rms), and FP32 rounding of the upstream adjoint
+    bounds dL/dh's accuracy by a fraction of A rather than of dL/dh."""
+    import torch
+    params = torch.tensor(np.asarray(case.params, np.float64), requires_grad=True)
+    res = case.oracle.forward(params, alpha_p=alpha_p, keep_outputs=True)
+    for r in res:
+        for v in r["outputs"].values():
+            if isinstance(v, torch.Tensor) and v.requires_grad:
+                v.retain_grad()
+    sum(r["total"] for r in res).backward()
+    q = np.asarray(case.params, np.float64)[case.oracle.n_proc_params:]
+    out = {}
+    for p in case.oracle.procs:
+        if p.type != "d":
+            continue
+        o = res[p.song]["outputs"]
+        u = np.abs(o[p.index - 1].detach().numpy())
+        db = np.abs(o[p.index].grad.numpy()) / (1.0 + np.exp(-q[p.index]))
+        L = u.shape[1]
+        nh = 20 * D + 38                      # taps of Eq. (17): 20 slots of D plus the 39-tap FIR span
+        M = 1 << int(np.ceil(np.log2(2 * L + nh)))
+        lags = (np.arange(nh) + n0) % M
+        rms = np.zeros(2)
+        for ch in range(2):
+            c = np.fft.irfft(np.fft.rfft(db[ch], M) * np.conj(np.fft.rfft(u[ch], M)), M)
+            rms[ch] = np.sqrt(np.mean(c[lags] ** 2))
+        out[p.index] = rms
+    return out
+
+
+def delay_slot_conditioning(case: Case, taps: dict, D: int = 4410, term_rms: dict = None):
     """Per delay processor, channel and tap m: kappa = |g_m| / (rms(dL/dh) ||c_m|| ||s'||), the ratio of the
-    Eq. (19) inner product g_m to its Cauchy-Schwarz scale (how far g_m stands above cancellation)."""
+    Eq. (19) inner product g_m to its Cauchy-Schwarz scale (how far g_m stands above cancellation).  With
+    term_rms (delay_term_rms) the scale uses the rms of the summed term magnitudes instead of rms(dL/dh)."""
     from oracle import processors as OP
     out = {}
     for p in case.oracle.procs:
@@ -127,7 +161,7 @@ def delay_slot_conditioning(case: Case, taps: dict, D: int = 4410):
         dh, cvals = taps[p.index]
         kap = np.zeros((2, 20))
         for ch in range(2):
-            rms = np.sqrt(np.mean(dh[ch] ** 2))
+            rms = term_rms[p.index][ch] if term_rms is not None else np.sqrt(np.mean(dh[ch] ** 2))
             for m in range(20):
                 o = p.offset + (ch * 20 + m) * 22
                 z = complex(case.params[o], case.params[o + 1])
