@@ -69,3 +69,45 @@ def dry_wet_round(w: Sequence[float], types: Sequence[str], present: Sequence[in
             else:
                 tc.remove(t)
     return m, l_min, trace
+
+
+def brute_force_round(present: Sequence[int], l_min: float, tau: float, evaluate: Callable[[np.ndarray], float],
+                      rng: SplitMix64) -> Tuple[np.ndarray, float, List[tuple]]:
+    """One pruning round with brute-force candidate sampling (Sec. 6.2, first method): every processor of
+    the pool is tried alone, V_c = {v} with v drawn uniformly from the pool, until the pool is empty.
+    Readings: the pool holds the present processors in ascending index order and v = pool[next() mod |pool|];
+    a tried processor leaves the pool whether or not its trial succeeds (UpdatePool of Alg. 2).
+    Returns (m, updated L_min, trace of (processor, L_a, accepted))."""
+    P = len(present)
+    m = np.ones(P, np.uint8)
+    pool = [i for i in range(P) if present[i]]
+    trace = []
+    while pool:
+        v = pool[rng.next() % len(pool)]
+        cand = np.ones(P, np.uint8)
+        cand[v] = 0
+        la = float(evaluate(m * cand))
+        ok = la < l_min + tau
+        trace.append((v, la, ok))
+        if ok:
+            l_min = min(l_min, la)
+            m = m * cand
+        pool.remove(v)
+    return m, l_min, trace
+
+
+def uses_brute_force(iteration: int, every: int = 4) -> bool:
+    """Hybrid sampling (Sec. 6.2): brute force on every 4th pruning iteration (1-based), dry/wet otherwise."""
+    return iteration % every == 0
+
+
+def node_deltas(la_full: float, evaluate: Callable[[np.ndarray], float], present: Sequence[int]) -> np.ndarray:
+    """Delta_i = L_a(G minus v_i) - L_a(G) for every present processor (Sec. 7.2); NaN for absent ones."""
+    P = len(present)
+    out = np.full(P, np.nan)
+    for i in range(P):
+        if present[i]:
+            m = np.ones(P, np.uint8)
+            m[i] = 0
+            out[i] = float(evaluate(m)) - la_full
+    return out

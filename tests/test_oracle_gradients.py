@@ -110,3 +110,38 @@ def test_alg3_skips_absent_processors_and_types():
     m, _, trace = S.dry_wet_round(w, types, present, 1.0, 0.01, _scripted(np.zeros(5)), S.SplitMix64(11))
     tried = sorted(i for t in trace for i in t[1])
     assert tried == [0, 2, 3] and m[1] == 1 and m[4] == 1
+
+
+def test_brute_force_round_tries_every_processor_once_and_keeps_the_costly_ones():
+    # nodes 2 and 5 cost more than tau: never pruned; node 0 improves the match (L_min moves down); the rest
+    # are free.  The outcome does not depend on the draw order.
+    costs = np.zeros(8)
+    costs[2] = costs[5] = 0.02
+    costs[0] = -0.005
+    present = np.ones(8, int)
+    present[7] = 0
+    m, lmin, trace = S.brute_force_round(present, 1.0, 0.01, _scripted(costs), S.SplitMix64(5))
+    assert sorted(t[0] for t in trace) == [0, 1, 2, 3, 4, 5, 6]
+    assert list(np.where(m == 0)[0]) == [0, 1, 3, 4, 6] and m[7] == 1
+    assert lmin == pytest.approx(0.995)
+    assert all(ok == (t[0] not in (2, 5)) for t in trace for ok in [t[2]])
+
+
+def test_brute_force_round_order_decides_between_two_partial_costs():
+    # two nodes of cost 0.006 each: the first tried fits under tau, the second then does not
+    costs = np.zeros(4)
+    costs[1] = costs[3] = 0.006
+    m, _, trace = S.brute_force_round(np.ones(4, int), 1.0, 0.01, _scripted(costs), S.SplitMix64(9))
+    tried = [t[0] for t in trace if t[0] in (1, 3)]
+    assert m[tried[0]] == 0 and m[tried[1]] == 1
+    # the draw is pool[next() mod |pool|] over the pool in ascending order
+    g, pool = S.SplitMix64(9), [0, 1, 2, 3]
+    first = pool[g.next() % 4]
+    assert trace[0][0] == first
+
+
+def test_hybrid_schedule_and_node_deltas():
+    assert [S.uses_brute_force(n) for n in range(1, 13)] == [n % 4 == 0 for n in range(1, 13)]
+    costs = np.array([0.1, -0.2, 0.0, 0.3])
+    d = S.node_deltas(1.0, _scripted(costs), [1, 1, 0, 1])
+    assert np.allclose(d[[0, 1, 3]], costs[[0, 1, 3]]) and np.isnan(d[2])
