@@ -1,4 +1,5 @@
-"""Mixing-graph search with dry/wet candidate sampling (Alg. 3, Sec. 6.1-6.3) on the CUDA console.
+"""Mixing-graph search (Alg. 2 with brute-force sampling, Alg. 3 with dry/wet sampling, and the hybrid of the
+two; Sec. 6.1-6.3) on the CUDA console.
 
 Every song of a console runs its own search.  The songs advance in lockstep: one masked forward
 (mg_prune_scores with a single mask over all processors) evaluates the current trial of every song at once,
@@ -17,7 +18,9 @@ Readings where the paper is silent:
   * a failed trial with k > 1 halves r_t, a failed trial with k = 1 removes the type;
   * L_min is the unmasked L_a after the initial training and is only updated by accepted trials (Alg. 3);
   * the sparsity weight alpha_p rises linearly from 0 to alpha_p_max over the first ramp_steps fine-tuning
-    steps (Sec. 6.3: 0 to 1e-4 over the first 4k of 6k steps) and stays there.
+    steps (Sec. 6.3: 0 to 1e-4 over the first 4k of 6k steps) and stays there;
+  * brute force: the pool holds the song's present processors in ascending order, v = pool[next() mod |pool|],
+    and a tried processor leaves the pool whatever the outcome; hybrid: brute force on iterations 4, 8, ...
 """
 from __future__ import annotations
 
@@ -149,6 +152,99 @@ def dry_wet_round(con, l_min: Sequence[float], tau: float, rngs: Sequence[SplitM
     return keep, [sr.l_min for sr in songs], trials
 
 
+class _SongBrute:
+    """State of one song's brute-force round: every pool processor is tried alone (Sec. 6.2)."""
+
+    def __init__(self, procs: Sequence[int], l_min: float, rng: SplitMix64):
+        self.pool = sorted(procs)
+        self.removed: set = set()
+        self.l_min = float(l_min)
+        self.rng = rng
+        self.pending: Optional[int] = None
+
+    def advance(self) -> bool:
+        if not self.pool:
+            self.pending = None
+            return False
+        self.pending = self.pool[self.rng.next() % len(self.pool)]
+        return True
+
+    def resolve(self, la: float, tau: float):
+        v = self.pending
+        ok = la < self.l_min + tau
+        if ok:
+            self.l_min = min(self.l_min, la)
+            self.removed.add(v)
+        self.pool.remove(v)
+        self.pending = None
+        return v, ok
+
+
+def brute_force_round(con, l_min: Sequence[float], tau: float, rngs: Sequence[SplitMix64]) -> tuple:
+    """One pruning round with brute-force sampling for every song of `con`, in lockstep: each masked forward
+    tries one processor of every song whose pool is not empty.  Pool in ascending processor order,
+    v = pool[next() mod |pool|], a tried processor leaves the pool whatever the outcome.
+    Returns (keep mask [P], updated L_min per song, list of Trial)."""
+    types = con.processor_types()
+    _, _, song_of = con.layout()
+    present = con.present()
+    P = con.n_processors
+    songs = [_SongBrute([i for i in range(P) if song_of[i] == s and present[i]], l_min[s], rngs[s])
+             for s in range(con.n_songs)]
+    trials: List[Trial] = []
+    active = [sr.advance() for sr in songs]
+    while any(active):
+        mask = np.ones(P, np.uint8)
+        for s, sr in enumerate(songs):
+            for i in sr.removed:
+                mask[i] = 0
+            if active[s]:
+                mask[sr.pending] = 0
+        la = con.prune_scores(mask[None, :])[0].cpu().numpy().astype(np.float64)
+        for s, sr in enumerate(songs):
+            if not active[s]:
+                continue
+            v, ok = sr.resolve(float(la[s]), tau)
+            trials.append(Trial(s, types[v], (v,), float(la[s]), ok))
+            active[s] = sr.advance()
+    keep = present.astype(np.uint8).copy()
+    for sr in songs:
+        for i in sr.removed:
+            keep[i] = 0
+    return keep, [sr.l_min for sr in songs], trials
+
+
+def uses_brute_force(iteration: int, every: int = 4) -> bool:
+    """Hybrid sampling (Sec. 6.2): brute force on every 4th pruning iteration (1-based), dry/wet otherwise."""
+    return iteration % every == 0
+
+
+def node_deltas(con, max_masks: int = 64) -> np.ndarray:
+    """Delta_i = L_a(G minus v_i) - L_a(G) for every present processor (Sec. 7.2; NaN for absent ones).
+    Mask j switches off the j-th present processor of every song at once (a song's L_a depends only on its
+    own processors), and up to max_masks masks go to the GPU per prune_scores call."""
+    _, _, song_of = con.layout()
+    present = con.present()
+    P = con.n_processors
+    per_song = [[i for i in range(P) if song_of[i] == s and present[i]] for s in range(con.n_songs)]
+    n = max((len(v) for v in per_song), default=0)
+    base = con.prune_scores(np.ones((1, P), np.uint8))[0].cpu().numpy().astype(np.float64)
+    out = np.full(P, np.nan)
+    for j0 in range(0, n, max_masks):
+        js = range(j0, min(n, j0 + max_masks))
+        masks = np.ones((len(js), P), np.uint8)
+        for r, j in enumerate(js):
+            for v in per_song:
+                if j < len(v):
+                    masks[r, v[j]] = 0
+        la = con.prune_scores(masks).cpu().numpy().astype(np.float64)
+        for r, j in enumerate(js):
+            for s, v in enumerate(per_song):
+                if j < len(v):
+                    out[v[j]] = la[r, s] - base[s]
+    return out
+
+
 @dataclasses.dataclass
 class SearchResult:
     present: np.ndarray            # processors left after the last round
@@ -167,9 +263,14 @@ def alpha_p_at(step: int, ramp_steps: int, alpha_p_max: float) -> float:
 
 
 def search(con, n_iter: int, train_steps: int, finetune_steps: int, lr: float = 1e-2, tau: float = 0.01,
-           seed: int = 0, alpha_p_max: float = 1e-4, ramp_steps: Optional[int] = None) -> SearchResult:
-    """Alg. 3 on every song of `con`: train, L_min from the unmasked graph, then n_iter rounds of
-    {dry/wet pruning round, structural prune, fine-tuning}."""
+           seed: int = 0, alpha_p_max: float = 1e-4, ramp_steps: Optional[int] = None,
+           method: str = "dry_wet") -> SearchResult:
+    """Alg. 2 / Alg. 3 on every song of `con`: train, L_min from the unmasked graph, then n_iter rounds of
+    {pruning round, structural prune, fine-tuning}.  method: "dry_wet" (Alg. 3), "brute_force" (every
+    processor tried alone) or "hybrid" (brute force on every 4th round, dry/wet otherwise; the paper's
+    default)."""
+    if method not in ("dry_wet", "brute_force", "hybrid"):
+        raise ValueError(method)
     if ramp_steps is None:
         ramp_steps = (2 * n_iter * finetune_steps) // 3
     _, _, song_of = con.layout()
@@ -189,9 +290,10 @@ def search(con, n_iter: int, train_steps: int, finetune_steps: int, lr: float = 
     secs["train"] += time.perf_counter() - t0
 
     all_trials, ft = [], 0
-    for _ in range(n_iter):
+    for it in range(1, n_iter + 1):
         t0 = time.perf_counter()
-        keep, l_min, trials = dry_wet_round(con, l_min, tau, rngs)
+        brute = method == "brute_force" or (method == "hybrid" and uses_brute_force(it))
+        keep, l_min, trials = (brute_force_round if brute else dry_wet_round)(con, l_min, tau, rngs)
         con.prune(keep)
         sync()
         secs["rounds"] += time.perf_counter() - t0

@@ -96,13 +96,81 @@ def test_dry_wet_round_matches_oracle():
     assert near_ties == 0       # every decision is resolved: the pruned set is the oracle's
 
 
+def near_ground_truth_console(seed_case=1, steps=5):
+    case = make_case([W.layout_plain(88200)], seed=seed_case)
+    gt, gt_keep = W.ground_truth(case.ptypes, (seed_case, 77))
+    start = gt.copy()
+    start[case.oracle.n_proc_params:] = np.where(gt_keep == 1, 4.0, -4.0)
+    con = gpu_console(case)
+    con.set_params(start)
+    for _ in range(steps):
+        con.train_step(1e-2)
+    return case, con
+
+
+def la_floor(case, params):
+    full, mixes = case.oracle.losses(params)
+    mix = torch.tensor(mixes[0], dtype=torch.float64)
+    tgt = torch.tensor(case.targets[0], dtype=torch.float64)
+    noise = torch.tensor(np.random.default_rng(0).standard_normal(mix.shape))
+    noise *= 1e-5 * mix.norm() / noise.norm()
+    return full, abs(float(OL.audio_loss(mix + noise, tgt, case.oracle.desc.loss)["a"]) - full[0, 0])
+
+
+def test_brute_force_round_matches_oracle():
+    """Brute-force sampling (every processor tried alone): the same two replays as the dry/wet round."""
+    tau = 0.01
+    case, con = near_ground_truth_console()
+    params = con.get_params().cpu().numpy()
+    P = con.n_processors
+    l_min0 = float(con.prune_scores(np.ones((1, P), np.uint8))[0, 0])
+    seed = GS.song_seed(6, 0)
+    keep, lm, trials = GS.brute_force_round(con, [l_min0], tau, [GS.SplitMix64(seed)])
+    assert len(trials) == P
+    gpu_eval = lambda m: float(con.prune_scores(np.asarray(m, np.uint8)[None, :])[0, 0])
+    m, olm, trace = OS.brute_force_round(np.ones(P, np.uint8), l_min0, tau, gpu_eval, OS.SplitMix64(seed))
+    assert [(t.candidates[0], t.la, t.accepted) for t in trials] == trace
+    assert np.array_equal(keep, m) and lm[0] == olm
+    full, floor = la_floor(case, params)
+    l_min_o, l_min_g = full[0, 0], l_min0
+    removed, near_ties = set(), 0
+    for t in trials:
+        mask = np.ones(P, np.uint8)
+        mask[list(removed | set(t.candidates))] = 0
+        la_o = case.oracle.losses(params, mask=mask)[0][0, 0]
+        d_g, d_o = t.la - l_min_g, la_o - l_min_o
+        tol = D_TOL * abs(d_o) + 1e-6 * abs(la_o) + floor
+        assert abs(d_g - d_o) <= tol, (t, d_g, d_o, tol)
+        if abs(d_o - tau) <= 2 * tol:
+            near_ties += 1
+        else:
+            assert (d_o < tau) == t.accepted, (t, d_o)
+        if t.accepted:
+            l_min_o, l_min_g = min(l_min_o, la_o), min(l_min_g, t.la)
+            removed |= set(t.candidates)
+    print(f"brute force: pruned {int(np.sum(keep == 0))} of {P}, near ties {near_ties}")
+    assert near_ties == 0
+
+
+def test_node_deltas_match_oracle():
+    """Delta_i = L_a(G minus v_i) - L_a(G) (Sec. 7.2) for every processor, scored with batched masks."""
+    case, con = near_ground_truth_console()
+    params = con.get_params().cpu().numpy()
+    d = GS.node_deltas(con, max_masks=16)
+    full, floor = la_floor(case, params)
+    od = OS.node_deltas(full[0, 0], lambda m: case.oracle.losses(params, mask=m)[0][0, 0],
+                        np.ones(con.n_processors, np.uint8))
+    err = np.abs(d - od)
+    assert np.all(err <= D_TOL * np.abs(od) + 1e-6 * abs(full[0, 0]) + floor), (err.max(), np.abs(od).max())
+
+
 def test_search_rounds_prune_and_fine_tune():
-    """Two rounds of Alg. 3 on a two-song batch: the pruned set is what the trials accepted, the pruned
-    console keeps training, and the final losses are finite."""
+    """Four hybrid rounds on a two-song batch: the pruned set is what the trials accepted, the pruned console
+    keeps training, and the final losses are finite."""
     case = make_case([W.layout_plain(44100), W.SongLayout(3, 1, [0, -1, 0], 30011)], seed=3)
     con = gpu_console(case)
     con.set_params(case.params)
-    res = GS.search(con, n_iter=2, train_steps=10, finetune_steps=5, seed=1)
+    res = GS.search(con, n_iter=4, train_steps=10, finetune_steps=3, seed=1, method="hybrid")
     present = con.present()
     accepted = {i for rnd in res.trials for t in rnd if t.accepted for i in t.candidates}
     assert set(np.nonzero(present == 0)[0]) == accepted
@@ -110,3 +178,5 @@ def test_search_rounds_prune_and_fine_tune():
     for rnd in res.trials:
         for s in range(con.n_songs):
             assert any(t.song == s for t in rnd)
+    # hybrid: rounds 1-3 dry/wet (a round starts with k = round(0.1 N_t) candidates), round 4 brute force
+    assert all(len(t.candidates) == 1 for t in res.trials[3]) and len(res.trials[3]) >= 1

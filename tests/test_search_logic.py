@@ -115,3 +115,45 @@ def test_alpha_p_ramp():
     assert GS.alpha_p_at(0, 100, 1e-4) == 0.0
     assert GS.alpha_p_at(50, 100, 1e-4) == pytest.approx(5e-5)
     assert GS.alpha_p_at(400, 100, 1e-4) == 1e-4
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.01])
+def test_lockstep_brute_force_equals_per_song_oracle_rounds(tau):
+    con = FakeConsole([2, 1, 3], seed=5)
+    l_min = [float(np.float32(b)) for b in con.base]
+    rngs = [GS.SplitMix64(GS.song_seed(4, s)) for s in range(con.n_songs)]
+    keep, lm, trials = GS.brute_force_round(con, l_min, tau, rngs)
+    for s in range(con.n_songs):
+        idx = np.nonzero(con.song == s)[0]
+
+        def evaluate(local_mask):
+            full = np.ones(con.n_processors, np.uint8)
+            full[idx] = local_mask
+            return float(np.float32(con.la(full)[s]))
+
+        m, olm, trace = OS.brute_force_round(np.ones(len(idx), np.uint8), l_min[s], tau, evaluate,
+                                             OS.SplitMix64(GS.song_seed(4, s)))
+        mine = [(t.candidates[0], t.la, t.accepted) for t in trials if t.song == s]
+        assert mine == [(int(idx[v]), la, ok) for (v, la, ok) in trace]
+        assert np.array_equal(keep[idx], m) and lm[s] == olm
+
+
+def test_node_deltas_match_the_oracle_definition():
+    con = FakeConsole([2, 3], seed=8)
+    con._present[4] = 0
+    d = GS.node_deltas(con, max_masks=5)
+    for s in range(con.n_songs):
+        idx = np.nonzero(con.song == s)[0]
+        base = float(np.float32(con.la(np.ones(con.n_processors, np.uint8))[s]))
+
+        def evaluate(local_mask):
+            full = np.ones(con.n_processors, np.uint8)
+            full[idx] = local_mask
+            return float(np.float32(con.la(full)[s]))
+
+        od = OS.node_deltas(base, evaluate, con._present[idx])
+        assert np.allclose(d[idx], od, equal_nan=True, rtol=0, atol=1e-12)
+
+
+def test_hybrid_uses_brute_force_every_fourth_round():
+    assert [GS.uses_brute_force(n) for n in range(1, 9)] == [OS.uses_brute_force(n) for n in range(1, 9)]
