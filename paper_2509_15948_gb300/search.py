@@ -245,6 +245,36 @@ def node_deltas(con, max_masks: int = 64) -> np.ndarray:
     return out
 
 
+class CropFeeder:
+    """Random fixed-length segments (the training regime of Sec. 5.1: every step draws a 3.8 s segment; the
+    loss skips its first second through the console's warmup_samples).  Before each training step every
+    song's dry tracks and target in the crop-length console `con` are replaced by a crop of the full-length
+    audio, at an offset drawn with the song's splitmix64 generator: next() mod (L_full - crop + 1)."""
+
+    def __init__(self, con, sources, targets, seed: int = 0):
+        import torch
+        self.con = con
+        dev = con.device
+        as_dev = lambda x: (x if isinstance(x, torch.Tensor) else torch.as_tensor(np.asarray(x, np.float32))).to(
+            dev, torch.float32).contiguous()
+        self.src = [as_dev(x) for x in sources]
+        self.tgt = [as_dev(x) for x in targets]
+        self.crop = [song.num_samples for song in con.songs]
+        for s, (x, c) in enumerate(zip(self.src, self.crop)):
+            if x.shape[1] < c or self.tgt[s].shape[1] != x.shape[1]:
+                raise ValueError(f"song {s}: full-length audio shorter than the crop or target length mismatch")
+        self.rngs = [SplitMix64(song_seed(seed, 1000 + s)) for s in range(len(self.src))]
+        self.last: List[int] = []
+
+    def next(self) -> List[int]:
+        self.last = []
+        for s, (x, t, c) in enumerate(zip(self.src, self.tgt, self.crop)):
+            off = self.rngs[s].next() % (x.shape[1] - c + 1)
+            self.con.update_audio(s, x[:, off:off + c], t[:, off:off + c])
+            self.last.append(off)
+        return self.last
+
+
 @dataclasses.dataclass
 class SearchResult:
     present: np.ndarray            # processors left after the last round
@@ -264,13 +294,28 @@ def alpha_p_at(step: int, ramp_steps: int, alpha_p_max: float) -> float:
 
 def search(con, n_iter: int, train_steps: int, finetune_steps: int, lr: float = 1e-2, tau: float = 0.01,
            seed: int = 0, alpha_p_max: float = 1e-4, ramp_steps: Optional[int] = None,
-           method: str = "dry_wet") -> SearchResult:
+           method: str = "dry_wet", feeder: Optional[CropFeeder] = None, eval_con=None) -> SearchResult:
     """Alg. 2 / Alg. 3 on every song of `con`: train, L_min from the unmasked graph, then n_iter rounds of
     {pruning round, structural prune, fine-tuning}.  method: "dry_wet" (Alg. 3), "brute_force" (every
     processor tried alone) or "hybrid" (brute force on every 4th round, dry/wet otherwise; the paper's
-    default)."""
+    default).  With a CropFeeder every training step runs on fresh random crops; trials and L_min are then
+    evaluated by eval_con (the same songs at full length; parameters copied from `con` before every round,
+    both consoles pruned alike), or by `con` on its current crops when eval_con is None."""
     if method not in ("dry_wet", "brute_force", "hybrid"):
         raise ValueError(method)
+    ev = eval_con if eval_con is not None else con
+
+    def train(steps, alpha):
+        for _ in range(steps):
+            if feeder is not None:
+                feeder.next()
+            if alpha is not None:
+                con.set_alpha_p(alpha())
+            con.train_step(lr)
+
+    def sync_eval():
+        if eval_con is not None:
+            eval_con.set_params(con.get_params())
     if ramp_steps is None:
         ramp_steps = (2 * n_iter * finetune_steps) // 3
     _, _, song_of = con.layout()
@@ -282,30 +327,37 @@ def search(con, n_iter: int, train_steps: int, finetune_steps: int, lr: float = 
 
     t0 = time.perf_counter()
     con.set_alpha_p(0.0)
-    for _ in range(train_steps):
-        con.train_step(lr)
+    train(train_steps, None)
     ones = np.ones((1, con.n_processors), np.uint8)
-    l_min = con.prune_scores(ones)[0].cpu().numpy().astype(np.float64).tolist()
+    sync_eval()
+    l_min = ev.prune_scores(ones)[0].cpu().numpy().astype(np.float64).tolist()
     sync()
     secs["train"] += time.perf_counter() - t0
 
-    all_trials, ft = [], 0
+    all_trials, ft = [], [0]
+
+    def ramp():
+        a = alpha_p_at(ft[0], ramp_steps, alpha_p_max)
+        ft[0] += 1
+        return a
+
     for it in range(1, n_iter + 1):
         t0 = time.perf_counter()
+        sync_eval()
         brute = method == "brute_force" or (method == "hybrid" and uses_brute_force(it))
-        keep, l_min, trials = (brute_force_round if brute else dry_wet_round)(con, l_min, tau, rngs)
+        keep, l_min, trials = (brute_force_round if brute else dry_wet_round)(ev, l_min, tau, rngs)
         con.prune(keep)
+        if eval_con is not None:
+            eval_con.prune(keep)
         sync()
         secs["rounds"] += time.perf_counter() - t0
         all_trials.append(trials)
         t0 = time.perf_counter()
-        for _ in range(finetune_steps):
-            con.set_alpha_p(alpha_p_at(ft, ramp_steps, alpha_p_max))
-            con.train_step(lr)
-            ft += 1
+        train(finetune_steps, ramp)
         sync()
         secs["finetune"] += time.perf_counter() - t0
-    la = con.prune_scores(ones)[0].cpu().numpy().astype(np.float64).tolist()
+    sync_eval()
+    la = ev.prune_scores(ones)[0].cpu().numpy().astype(np.float64).tolist()
     present = con.present().copy()
     ratio = [1.0 - int(np.sum(present[song_of == s])) / max(1, init_count[s]) for s in range(con.n_songs)]
     return SearchResult(present, l_min, la, ratio, all_trials, secs)

@@ -180,3 +180,42 @@ def test_search_rounds_prune_and_fine_tune():
             assert any(t.song == s for t in rnd)
     # hybrid: rounds 1-3 dry/wet (a round starts with k = round(0.1 N_t) candidates), round 4 brute force
     assert all(len(t.candidates) == 1 for t in res.trials[3]) and len(res.trials[3]) >= 1
+
+
+def test_crop_feeder_equals_a_console_built_on_the_crop():
+    """The training regime of Sec. 5.1: a crop-length console fed a random segment computes exactly what a
+    console created on that segment computes (losses with a loss warm-up, mixes)."""
+    import paper_2509_15948_gb300 as M
+    case = make_case([W.layout_plain(88200)], seed=4)
+    crop = 44100 + 13
+    song = M.Song(4, 1, [0, 0, -1, -1], crop)
+    cfg = M.ConsoleConfig(warmup_samples=22050)
+    src, tgt = case.sources[0], case.targets[0]
+    con = M.Console([song], [src[:, :crop]], [tgt[:, :crop]], case.noise, cfg)
+    feeder = GS.CropFeeder(con, [src], [tgt], seed=3)
+    off = feeder.next()[0]
+    assert 0 <= off <= 88200 - crop
+    con.set_params(case.params)
+    l1, m1 = con.forward_loss(with_mix=True)
+    ref = M.Console([song], [src[:, off:off + crop]], [tgt[:, off:off + crop]], case.noise, cfg)
+    ref.set_params(case.params)
+    l2, m2 = ref.forward_loss(with_mix=True)
+    assert np.array_equal(l1.cpu().numpy(), l2.cpu().numpy())
+    assert np.array_equal(m1[0].cpu().numpy(), m2[0].cpu().numpy())
+    assert feeder.next()[0] != off or feeder.next()[0] != off     # offsets move
+
+
+def test_crop_trained_search_evaluated_on_full_songs():
+    import paper_2509_15948_gb300 as M
+    case = make_case([W.layout_plain(88200)], seed=5)
+    crop = 44100
+    cfg = M.ConsoleConfig(warmup_samples=11025)
+    src, tgt = case.sources[0], case.targets[0]
+    con = M.Console([M.Song(4, 1, [0, 0, -1, -1], crop)], [src[:, :crop]], [tgt[:, :crop]], case.noise, cfg)
+    full = gpu_console(case)
+    con.set_params(case.params)
+    res = GS.search(con, n_iter=2, train_steps=6, finetune_steps=3, seed=2,
+                    feeder=GS.CropFeeder(con, [src], [tgt], seed=2), eval_con=full)
+    assert np.array_equal(con.present(), full.present())
+    assert np.isfinite(res.la_final).all() and 0.0 <= res.pruning_ratio[0] <= 1.0
+    assert np.array_equal(con.get_params().cpu().numpy(), full.get_params().cpu().numpy())
