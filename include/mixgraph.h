@@ -192,7 +192,7 @@ mg_status mg_debug_read(const mg_console* c, int32_t proc, int32_t what, float* 
  *   L:        1 <= L <= 127,001 samples (the 2^17-point FFT must hold the signal and the 2047-tap FIR);
  *             larger L returns MG_ERR_UNSUPPORTED without touching the GPU
  *   d_params: device [1025]: the 1024 log-magnitudes of Eq. (7), then the dry/wet logit q
- * Scratch: one file-scope __device__ array of about 3.2 MB, held by every GPU that loads the library until the
+ * Scratch: one file-scope __device__ array of about 3.3 MB, held by every GPU that loads the library until the
  * process exits.  Every buffer in it is fully written before it is read within a call, so nothing needs
  * clearing; calls share the array, so calls that overlap on the GPU (on different streams, or on the same
  * device from several threads without ordering) race and must not be issued.
@@ -200,6 +200,32 @@ mg_status mg_debug_read(const mg_console* c, int32_t proc, int32_t what, float* 
  * tables) and synchronises the stream: make that first call before any stream capture.  Later calls are
  * asynchronous on `stream`.  Returns MG_ERR_INVALID for null pointers and MG_ERR_CUDA if a CUDA call fails. */
 mg_status mg_eq_forward_noalloc(const float* d_u, float* d_y, int64_t L, const float* d_params, cudaStream_t stream);
+
+/* ---- Batched-processing schedule of a general processing graph (Sec. 4, Alg. 1 lines 1-4; host only) ----
+ * A schedule is a sequence of node types; step n computes the maximal subset V_n of not yet computed nodes of
+ * its type whose predecessors are all computed, so the subsets partition the graph, are causal and
+ * homogeneous (Sec. 4.1).  Greedy: the type with the most computable nodes at each step, ties to the smaller
+ * type code (Sec. 4.2).  Beam: a layered search keeping the beam_width states with the most computed nodes per
+ * depth, stopping at the first depth that completes the graph (the shortest schedule when the beam holds
+ * every state of a depth).  No GPU is used. */
+enum { MG_SCHED_GREEDY = 0, MG_SCHED_BEAM = 1 };
+
+/* node_type [n_nodes]: any non-negative type codes; edges edge_src[i] -> edge_dst[i], no self loops.
+ * Outputs (caller-allocated, n_nodes entries each): step_type[0 .. *n_steps) the type sequence; node_step[v]
+ * the step computing node v; order[i] the node placed at position i (ScheduleBatchedProcessing and
+ * OptimizeNodeOrder: nodes sorted by step, then index, so every subset is one contiguous slice).
+ * MG_ERR_INVALID for bad arguments or a graph with a cycle. */
+mg_status mg_schedule_graph(const int32_t* node_type, int32_t n_nodes, const int32_t* edge_src,
+                            const int32_t* edge_dst, int32_t n_edges, int32_t method, int32_t beam_width,
+                            int32_t* step_type, int32_t* n_steps, int32_t* node_step, int32_t* order);
+
+/* GetReadWriteIndex for a schedule in the new order: step_begin [n_steps + 1] the store slices (positions
+ * step_begin[k] .. step_begin[k+1] are V_k); gather_begin [n_steps + 1] and gather_src / gather_dst [n_edges]
+ * the gather lists of every step (producer position -> consumer position, grouped by the consumer's step,
+ * then consumer, then producer; the aggregate of a consumer is the sum over its entries). */
+mg_status mg_schedule_io(const int32_t* node_step, const int32_t* order, int32_t n_nodes, int32_t n_steps,
+                         const int32_t* edge_src, const int32_t* edge_dst, int32_t n_edges, int32_t* step_begin,
+                         int32_t* gather_begin, int32_t* gather_src, int32_t* gather_dst);
 
 const char* mg_last_error(const mg_console* c);
 

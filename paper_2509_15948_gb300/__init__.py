@@ -66,6 +66,8 @@ def load_library(path: str = LIB_PATH):
     P, I32, I64, F32, U8P = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
     sig = {
         "mg_plan": [ctypes.POINTER(ConsoleDesc), ctypes.POINTER(SongDesc), I32, ctypes.POINTER(ConsoleInfo)],
+        "mg_schedule_graph": [P, I32, P, P, I32, I32, I32, P, P, P, P],
+        "mg_schedule_io": [P, P, I32, I32, P, P, I32, P, P, P, P],
         "mg_console_create": [ctypes.POINTER(ConsoleDesc), ctypes.POINTER(SongDesc), I32, P, ctypes.POINTER(P)],
         "mg_console_destroy": [P],
         "mg_console_get_info": [P, ctypes.POINTER(ConsoleInfo)],
@@ -165,6 +167,36 @@ def _song_array(songs: Sequence[Song], src_ptrs=None, tgt_ptrs=None, on_device=0
         arr[i].target = tgt_ptrs[i] if tgt_ptrs else None
         arr[i].on_device = on_device
     return arr, keep
+
+
+def schedule_graph(types: Sequence[int], edges: Sequence[tuple], method: str = "greedy", beam_width: int = 8) -> dict:
+    """Batched-processing schedule of a general graph (Sec. 4) through the C ABI (host only): the type sequence,
+    each node's step, the node order with contiguous subsets, and the per-step store slices and gather lists."""
+    lib = load_library()
+    n, m = len(types), len(edges)
+    t = np.ascontiguousarray(types, np.int32)
+    es = np.ascontiguousarray([e[0] for e in edges], np.int32)
+    ed = np.ascontiguousarray([e[1] for e in edges], np.int32)
+    step_type = np.zeros(max(1, n), np.int32)
+    node_step = np.zeros(max(1, n), np.int32)
+    order = np.zeros(max(1, n), np.int32)
+    nsteps = ctypes.c_int32()
+    meth = {"greedy": 0, "beam": 1}[method]
+    st = lib.mg_schedule_graph(t.ctypes.data, n, es.ctypes.data, ed.ctypes.data, m, meth, beam_width,
+                               step_type.ctypes.data, ctypes.byref(nsteps), node_step.ctypes.data, order.ctypes.data)
+    if st != MG_OK:
+        raise MgError(st, "mg_schedule_graph failed (bad arguments or a cycle)")
+    k = nsteps.value
+    step_begin = np.zeros(k + 1, np.int32)
+    gather_begin = np.zeros(k + 1, np.int32)
+    gsrc = np.zeros(max(1, m), np.int32)
+    gdst = np.zeros(max(1, m), np.int32)
+    st = lib.mg_schedule_io(node_step.ctypes.data, order.ctypes.data, n, k, es.ctypes.data, ed.ctypes.data, m,
+                            step_begin.ctypes.data, gather_begin.ctypes.data, gsrc.ctypes.data, gdst.ctypes.data)
+    if st != MG_OK:
+        raise MgError(st, "mg_schedule_io failed")
+    return {"steps": step_type[:k].tolist(), "node_step": node_step[:n], "order": order[:n],
+            "step_begin": step_begin, "gather_begin": gather_begin, "gather_src": gsrc[:m], "gather_dst": gdst[:m]}
 
 
 def plan(songs: Sequence[Song], cfg: ConsoleConfig = ConsoleConfig()) -> dict:
