@@ -201,6 +201,15 @@ mg_status mg_debug_read(const mg_console* c, int32_t proc, int32_t what, float* 
  * asynchronous on `stream`.  Returns MG_ERR_INVALID for null pointers and MG_ERR_CUDA if a CUDA call fails. */
 mg_status mg_eq_forward_noalloc(const float* d_u, float* d_y, int64_t L, const float* d_params, cudaStream_t stream);
 
+/* Evaluation metrics of every song's mix from the most recent forward (forward_loss, train_step or
+ * prune_scores) against its target (Sec. 5.3): d_out (device) [n_songs][6] = SI-SDR in dB over the stereo
+ * signal, then the MIR feature distances of Eq. (27), log10 of the mean squared feature difference over
+ * disjoint 8 s segments (a shorter song is one segment) for RMS (per channel), crest factor (per channel),
+ * stereo width ||l - r|| / ||l + r||, stereo imbalance (||l||^2 - ||r||^2) / (||l||^2 + ||r||^2) and the
+ * 24-band Zwicker Bark spectrum of the mid signal (Hann-windowed 8192-sample frames, mean power, dB);
+ * -inf where the features agree exactly.  FAD needs a pre-trained encoder and is not computed.  Stream-ordered. */
+mg_status mg_evaluate(mg_console* c, float* d_out);
+
 /* ---- Batched-processing schedule of a general processing graph (Sec. 4, Alg. 1 lines 1-4; host only) ----
  * A schedule is a sequence of node types; step n computes the maximal subset V_n of not yet computed nodes of
  * its type whose predecessors are all computed, so the subsets partition the graph, are causal and

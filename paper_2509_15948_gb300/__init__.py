@@ -67,6 +67,7 @@ def load_library(path: str = LIB_PATH):
     sig = {
         "mg_plan": [ctypes.POINTER(ConsoleDesc), ctypes.POINTER(SongDesc), I32, ctypes.POINTER(ConsoleInfo)],
         "mg_schedule_graph": [P, I32, P, P, I32, I32, I32, P, P, P, P],
+        "mg_evaluate": [P, P],
         "mg_schedule_io": [P, P, I32, I32, P, P, I32, P, P, P, P],
         "mg_console_create": [ctypes.POINTER(ConsoleDesc), ctypes.POINTER(SongDesc), I32, P, ctypes.POINTER(P)],
         "mg_console_destroy": [P],
@@ -394,6 +395,14 @@ class Console:
         s = np.ascontiguousarray(s, np.float32)
         t = np.ascontiguousarray(t, np.float32) if t is not None else None
         self._check(self.lib.mg_update_audio(self.h, song, s.ctypes.data, t.ctypes.data if t is not None else None, 0))
+
+    def evaluate(self):
+        """[n_songs, 6] on the device: SI-SDR (dB) and the MIR feature distances d_rms, d_cf, d_sw, d_si, d_bs
+        (Eq. 27) of the mix of the most recent forward against the target."""
+        out = self.torch.empty(self.n_songs, 6, dtype=self.torch.float32, device=self.device)
+        self._enter()
+        self._check(self.lib.mg_evaluate(self.h, out.data_ptr()))
+        return out
 
     def set_launch_mode(self, per_node: bool):
         self._check(self.lib.mg_set_launch_mode(self.h, int(per_node)))

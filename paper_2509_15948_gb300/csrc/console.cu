@@ -155,6 +155,15 @@ struct mg_console {
   ProcList all_lti_present;
   DevVec<int4> loss_items[3];
   ItemList gather_items;
+  // evaluation metrics (Sec. 5.3): (song, 8 s segment) items, per-song item ranges, Bark band bin ranges
+  std::vector<int2> ev_items;
+  std::vector<int> ev_begin, ev_lo, ev_hi;
+  int2* d_ev_items = nullptr;
+  int* d_ev_begin = nullptr;
+  int* d_ev_lo = nullptr;
+  int* d_ev_hi = nullptr;
+  double* d_ev_out = nullptr;
+  int ev_seg_len = 0;
   // state
   bool fwd_valid = false;
   bool per_node = false;
@@ -915,6 +924,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
   init_loss_attributes();
   init_fir_attributes();
   init_eqos_attributes();
+  init_eval_attributes();
   const double fs = d->sample_rate;
   // ---- arena layout and LTI scratch ----
   size_t shared_scratch = 0, keep_scratch = 0;
@@ -1115,6 +1125,42 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
   }
   c->gather_items.beg.push_back((int)c->gather_items.h.size());
   if (upload_items(c, c->gather_items) != MG_OK) return MG_ERR_CUDA;
+  // evaluation items: disjoint full 8 s segments (a shorter song is one segment); Zwicker band bin ranges of
+  // the 8192-point Bark frames
+  {
+    static const double edges[25] = {0, 100, 200, 300, 400, 510, 630, 770, 920, 1080, 1270, 1480, 1720, 2000, 2320,
+                                     2700, 3150, 3700, 4400, 5300, 6400, 7700, 9500, 12000, 15500};
+    c->ev_seg_len = (int)std::llround(8.0 * fs);
+    c->ev_items.clear();
+    c->ev_begin.clear();
+    for (size_t si = 0; si < c->songs.size(); ++si) {
+      c->ev_begin.push_back((int)c->ev_items.size());
+      const int L = c->songs[si].L;
+      const int nseg = L < c->ev_seg_len ? 1 : L / c->ev_seg_len;
+      for (int k = 0; k < nseg; ++k) c->ev_items.push_back(make_int2((int)si, k));
+    }
+    c->ev_begin.push_back((int)c->ev_items.size());
+    c->ev_lo.assign(24, 0);
+    c->ev_hi.assign(24, 0);
+    for (int b = 0; b < 24; ++b) {
+      // bins k = 0 .. 4096 with edges[b] <= k fs / 8192 < edges[b + 1]
+      int lo = 4097, hi = 0;
+      for (int k = 0; k <= 4096; ++k) {
+        const double f = k * fs / 8192.0;
+        if (f >= edges[b] && f < edges[b + 1]) {
+          lo = std::min(lo, k);
+          hi = std::max(hi, k + 1);
+        }
+      }
+      c->ev_lo[b] = lo > 4096 ? 0 : lo;
+      c->ev_hi[b] = hi;
+    }
+    if (upload(c, c->ev_items, &c->d_ev_items) || upload(c, c->ev_begin, &c->d_ev_begin) ||
+        upload(c, c->ev_lo, &c->d_ev_lo) || upload(c, c->ev_hi, &c->d_ev_hi))
+      return MG_ERR_CUDA;
+    CK(cudaMalloc(&c->d_ev_out, std::max<size_t>(1, c->ev_items.size()) * 66 * sizeof(double)));
+    c->small_allocs.push_back(c->d_ev_out);
+  }
   // ---- audio ----
   {
     float* tmp = nullptr;
@@ -1433,6 +1479,14 @@ mg_status mg_prune(mg_console* c, const uint8_t* h_keep) {
 mg_status mg_get_present(const mg_console* c, uint8_t* h_present) {
   if (!c || !h_present) return MG_ERR_INVALID;
   for (int i = 0; i < c->P; ++i) h_present[i] = (uint8_t)c->procs[i].present;
+  return MG_OK;
+}
+
+mg_status mg_evaluate(mg_console* c, float* d_out) {
+  if (!c || !d_out) return fail(c, MG_ERR_INVALID, "null pointer");
+  launch_eval(c->stream, c->d_songs, (int)c->songs.size(), c->d_ev_items, (int)c->ev_items.size(), c->d_ev_begin,
+              c->ev_seg_len, c->d_ev_lo, c->d_ev_hi, c->d_ev_out, d_out, c->tab.tw);
+  CK(cudaGetLastError());
   return MG_OK;
 }
 

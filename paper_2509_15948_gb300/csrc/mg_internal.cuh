@@ -167,6 +167,10 @@ void launch_row_fwd_hz(const LaunchCtx&, const Item* items, int n, int maxN1);
 void launch_row_conv_fwd(const LaunchCtx&, const Item* items, int n, int maxN1, bool bwd_keep_u);
 void launch_col_inv_out(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_col_dybar(const LaunchCtx&, const Item* items, int n, int maxN2G);
+void launch_eval(cudaStream_t st, const SongDev* songs, int n_songs, const int2* items, int n_items,
+                 const int* item_begin, int seg_len, const int* band_lo, const int* band_hi, double* seg_out,
+                 float* out_song, const float2* tw);
+void init_eval_attributes();
 void launch_col_inv_out_keep(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_col_dybar_keep(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_row_bwd2(const LaunchCtx&, const Item* items, int n, int maxN1);
