@@ -81,3 +81,28 @@ def mir_distances(est: np.ndarray, ref: np.ndarray, fs: float) -> Dict[str, floa
             acc[k] = acc.get(k, 0.0) + float(np.sum((fa[k] - fb[k]) ** 2))
             cnt[k] = cnt.get(k, 0) + fa[k].size
     return {k: float(np.log10(acc[k] / cnt[k])) if acc[k] > 0 else -np.inf for k in acc}
+
+
+def classification_metrics(truth, pred, types, type_order: str = "ecnsgdr") -> Dict[str, Dict[str, float]]:
+    """Consistency check (Sec. 7.3): processors present in the pruned graph G (truth) against those present
+    after re-running the search on G's own mix (pred), one binary decision per (input or subgroup chain, type).
+    Per type and micro-averaged (key "mu") accuracy, precision, recall and F1; positive = present.  A metric with
+    a zero denominator is reported as 1.0 when its numerator is zero as well (nothing to get wrong)."""
+    truth = np.asarray(truth, bool)
+    pred = np.asarray(pred, bool)
+    types = np.asarray(list(types))
+
+    def stats(sel):
+        t, p = truth[sel], pred[sel]
+        tp = int(np.sum(t & p))
+        fp = int(np.sum(~t & p))
+        fn = int(np.sum(t & ~p))
+        tn = int(np.sum(~t & ~p))
+        div = lambda a, b: a / b if b else 1.0
+        prec, rec = div(tp, tp + fp), div(tp, tp + fn)
+        f1 = div(2 * prec * rec, prec + rec) if (tp + fp and tp + fn) else div(2 * tp, 2 * tp + fp + fn)
+        return {"accuracy": div(tp + tn, tp + tn + fp + fn), "precision": prec, "recall": rec, "f1": f1}
+
+    out = {t: stats(types == t) for t in type_order if np.any(types == t)}
+    out["mu"] = stats(np.ones(truth.shape, bool))
+    return out

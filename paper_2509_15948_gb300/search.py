@@ -361,3 +361,44 @@ def search(con, n_iter: int, train_steps: int, finetune_steps: int, lr: float = 
     present = con.present().copy()
     ratio = [1.0 - int(np.sum(present[song_of == s])) / max(1, init_count[s]) for s in range(con.n_songs)]
     return SearchResult(present, l_min, la, ratio, all_trials, secs)
+
+
+def presence_scores(truth: np.ndarray, pred: np.ndarray, types: Sequence[str]) -> Dict[str, Dict[str, float]]:
+    """Binary classification of processor presence (one decision per chain and type): accuracy, precision,
+    recall and F1 per type and micro-averaged ("mu"); positive = present; a ratio with nothing in its
+    denominator counts as 1.0."""
+    truth = np.asarray(truth).astype(bool)
+    pred = np.asarray(pred).astype(bool)
+    ty = np.array(list(types))
+
+    def one(sel):
+        counts = {}
+        for name, a, b in (("tp", True, True), ("fp", False, True), ("fn", True, False), ("tn", False, False)):
+            counts[name] = int(np.count_nonzero((truth[sel] == a) & (pred[sel] == b)))
+        tp, fp, fn, tn = counts["tp"], counts["fp"], counts["fn"], counts["tn"]
+        ratio = lambda n, d: n / d if d > 0 else 1.0
+        precision, recall = ratio(tp, tp + fp), ratio(tp, tp + fn)
+        if tp + fp > 0 and tp + fn > 0:
+            f1 = ratio(2.0 * precision * recall, precision + recall)
+        else:
+            f1 = ratio(2.0 * tp, 2.0 * tp + fp + fn)
+        return {"accuracy": ratio(tp + tn, tp + tn + fp + fn), "precision": precision, "recall": recall, "f1": f1}
+
+    out = {t: one(ty == t) for t in TYPE_ORDER if np.any(ty == t)}
+    out["mu"] = one(np.ones(len(ty), bool))
+    return out
+
+
+def consistency_check(con, make_console, init_params, n_iter: int, train_steps: int, finetune_steps: int,
+                      **search_kw) -> Dict[str, Dict[str, float]]:
+    """Consistency analysis (Sec. 7.3): the pruned graph of `con` (after its search) is taken as a synthetic
+    ground truth; its own mixes become the targets of a fresh console (make_console(targets) builds it over the
+    same songs), the search is run again from init_params, and the two processor sets are compared per type."""
+    _, mixes = con.forward_loss(with_mix=True)
+    con2 = make_console([m.detach().clone() for m in mixes])
+    try:
+        con2.set_params(init_params)
+        search(con2, n_iter, train_steps, finetune_steps, **search_kw)
+        return presence_scores(con.present(), con2.present(), con.processor_types())
+    finally:
+        con2.close()

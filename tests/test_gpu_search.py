@@ -219,3 +219,16 @@ def test_crop_trained_search_evaluated_on_full_songs():
     assert np.array_equal(con.present(), full.present())
     assert np.isfinite(res.la_final).all() and 0.0 <= res.pruning_ratio[0] <= 1.0
     assert np.array_equal(con.get_params().cpu().numpy(), full.get_params().cpu().numpy())
+
+
+def test_consistency_check_runs_the_protocol():
+    """Sec. 7.3: re-running the search on the pruned graph's own mix recovers most of its processor set."""
+    import paper_2509_15948_gb300 as M
+    case, con = near_ground_truth_console(seed_case=1, steps=0)
+    GS.search(con, n_iter=1, train_steps=5, finetune_steps=3, seed=1)
+    songs = [M.Song(l.num_tracks, l.num_subgroups, l.track_group, l.num_samples) for l in case.layouts]
+    make = lambda targets: M.Console(songs, case.sources, targets, case.noise, M.ConsoleConfig())
+    scores = GS.consistency_check(con, make, con.get_params().cpu().numpy(), n_iter=1, train_steps=5,
+                                  finetune_steps=3, seed=1)
+    assert set(scores) >= {"mu"} and all(0.0 <= v <= 1.0 for d in scores.values() for v in d.values())
+    print("consistency", {k: round(v["f1"], 3) for k, v in scores.items()})

@@ -44,3 +44,19 @@ def test_mir_distances_equal_inputs_and_segmenting():
     assert d2["cf"] == -np.inf and d2["si"] == -np.inf and d2["sw"] == -np.inf
     r = [OM.features(sg, FS)["rms"] for sg in OM.segments(y, FS)]
     assert d2["rms"] == pytest.approx(np.log10(np.mean(np.concatenate(r) ** 2)))
+
+
+def test_classification_metrics_hand_counts():
+    types = list("eeeegg")
+    truth = [1, 1, 0, 0, 1, 0]
+    pred = [1, 0, 1, 0, 1, 1]
+    m = OM.classification_metrics(truth, pred, types)
+    # e: tp 1, fn 1, fp 1, tn 1 -> accuracy 0.5, precision 0.5, recall 0.5, f1 0.5
+    assert m["e"] == {"accuracy": 0.5, "precision": 0.5, "recall": 0.5, "f1": 0.5}
+    # g: tp 1, fp 1 -> accuracy 0.5, precision 0.5, recall 1, f1 2/3
+    assert m["g"]["precision"] == 0.5 and m["g"]["recall"] == 1.0 and m["g"]["f1"] == pytest.approx(2 / 3)
+    # micro: tp 2, fp 2, fn 1, tn 1
+    assert m["mu"]["accuracy"] == pytest.approx(3 / 6) and m["mu"]["precision"] == 0.5
+    assert m["mu"]["recall"] == pytest.approx(2 / 3) and m["mu"]["f1"] == pytest.approx(2 * 0.5 * (2 / 3) / (0.5 + 2 / 3))
+    perfect = OM.classification_metrics(truth, truth, types)
+    assert all(v == 1.0 for d in perfect.values() for v in d.values())

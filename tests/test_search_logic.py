@@ -157,3 +157,14 @@ def test_node_deltas_match_the_oracle_definition():
 
 def test_hybrid_uses_brute_force_every_fourth_round():
     assert [GS.uses_brute_force(n) for n in range(1, 9)] == [OS.uses_brute_force(n) for n in range(1, 9)]
+
+
+def test_presence_scores_equal_the_oracle_definition():
+    from oracle import metrics as OMet
+    rng = np.random.default_rng(2)
+    types = [t for t in "ecnsgdr" for _ in range(9)]
+    for _ in range(10):
+        truth = rng.random(len(types)) < 0.5
+        pred = rng.random(len(types)) < 0.5
+        assert GS.presence_scores(truth, pred, types) == OMet.classification_metrics(truth, pred, types)
+    assert GS.presence_scores(truth, truth, types)["mu"]["f1"] == 1.0
