@@ -204,7 +204,9 @@ def build_console(layouts, rank, per_song_seed=0):
     types = W.processor_types(layouts)
     noise = W.reverb_noise((rank, 9), sum(t == "r" for t in types))
     zeros = [np.zeros((2, l.num_samples), np.float32) for l in layouts]
-    con = M.Console(songs, sources, zeros, noise, M.ConsoleConfig())
+    t0 = time.perf_counter()
+    con = M.Console(songs, sources, zeros, noise, M.ConsoleConfig(autotune=1))
+    create_s = time.perf_counter() - t0
     # ground-truth targets rendered by the console itself (seeded graph keeping ~1/3 of the processors)
     gt, keep = W.ground_truth(types, (rank, 77))
     gtp = gt.copy()
@@ -217,6 +219,7 @@ def build_console(layouts, rank, per_song_seed=0):
     con.set_params(W.init_params(types, (rank, 5)))
     con.set_alpha_p(1e-4)
     torch.cuda.synchronize()
+    con.create_seconds = create_s
     return con, sources, mixes
 
 
@@ -347,6 +350,13 @@ def main():
     con, sources, mixes = build_console(layouts, rank)
     info = con.get_info()
     track_seconds = info["track_seconds"]
+    create_s = round(con.create_seconds, 2)
+    # autotuned four-step splits: "N = f 2^k -> N1 = f 2^a" with the number of nodes using each
+    fft_splits = {}
+    for f, logn, logn1 in con.fft_sizes():
+        if f:
+            key = f"{f}*2^{logn} -> N1 {f}*2^{logn1}"
+            fft_splits[key] = fft_splits.get(key, 0) + 1
     tot_bytes, type_bytes = model_bytes(layouts)
 
     for _ in range(args.warmup):
@@ -468,7 +478,8 @@ def main():
                 "clocks": clk, "per_node": per_node, "losses_finite": finite,
                 "stages_ms_per_step": {k: v[0] / args.steps for k, v in stage.items()},
                 "kernel_families_ms_per_step": {k: v[0] / args.steps for k, v in fam.items() if v[1] > 0},
-                "device_bytes": dev_bytes, "long_song": long_song, "serving": serving}
+                "device_bytes": dev_bytes, "fft_splits": fft_splits, "console_create_s": create_s,
+                "long_song": long_song, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

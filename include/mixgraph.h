@@ -82,6 +82,10 @@ typedef struct {
                                   -1 = the backward recomputes them in a shared scratch; 0 = automatic: keep when
                                   the kept buffers fit in workspace_limit_bytes (if set) and in 80 % of the device
                                   memory free after the console's other buffers */
+  int32_t autotune;            /* 1: at creation, time the reverb/delay FFT convolution passes of one node per FFT
+                                  size under the candidate row/column splits (N = N1 N2) and keep the fastest for
+                                  all nodes of that size (the split changes rounding, not the result beyond it);
+                                  0: the default split */
 } mg_console_desc;
 
 /* Sizes of a console (layout only). */
@@ -110,6 +114,10 @@ mg_status mg_console_create(const mg_console_desc* desc, const mg_song_desc* son
                             cudaStream_t stream, mg_console** out);
 mg_status mg_console_destroy(mg_console* c);
 mg_status mg_console_get_info(const mg_console* c, mg_console_info* out);
+
+/* FFT convolution size of every processor: N = f * 2^log_n, rows N1 = f * 2^log_n1 (0 for processors without
+ * a four-step convolution); any pointer may be NULL. */
+mg_status mg_processor_fft(const mg_console* c, int32_t* f, int32_t* log_n, int32_t* log_n1);
 
 /* Canonical layout: types[P] (index into "ecnsgdr"), param_offset[P], song[P]; any pointer may be NULL. */
 mg_status mg_processor_layout(const mg_console* c, int32_t* types, int64_t* param_offset, int32_t* song);

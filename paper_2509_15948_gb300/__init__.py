@@ -42,7 +42,8 @@ class ConsoleDesc(ctypes.Structure):
                 ("a_weighting", ctypes.c_int32), ("warmup_samples", ctypes.c_int64), ("alpha_lr", ctypes.c_float),
                 ("alpha_m", ctypes.c_float), ("alpha_s", ctypes.c_float), ("alpha_g", ctypes.c_float),
                 ("reverb_noise", ctypes.c_void_p), ("noise_on_device", ctypes.c_int32),
-                ("workspace_limit_bytes", ctypes.c_int64), ("retain_spectra", ctypes.c_int32)]
+                ("workspace_limit_bytes", ctypes.c_int64), ("retain_spectra", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
 
 
 class ConsoleInfo(ctypes.Structure):
@@ -68,6 +69,7 @@ def load_library(path: str = LIB_PATH):
         "mg_plan": [ctypes.POINTER(ConsoleDesc), ctypes.POINTER(SongDesc), I32, ctypes.POINTER(ConsoleInfo)],
         "mg_schedule_graph": [P, I32, P, P, I32, I32, I32, P, P, P, P],
         "mg_evaluate": [P, P],
+        "mg_processor_fft": [P, P, P, P],
         "mg_schedule_io": [P, P, I32, I32, P, P, I32, P, P, P, P],
         "mg_console_create": [ctypes.POINTER(ConsoleDesc), ctypes.POINTER(SongDesc), I32, P, ctypes.POINTER(P)],
         "mg_console_destroy": [P],
@@ -122,6 +124,7 @@ class ConsoleConfig:
     alpha_g: float = 1e-3
     workspace_limit_bytes: int = 0
     retain_spectra: int = 0   # 1 keep, -1 recompute, 0 automatic (see mg_console_desc)
+    autotune: int = 0         # 1: time the FFT convolution splits at creation and keep the fastest
 
     def type_mask(self) -> int:
         return sum(1 << i for i, t in enumerate(TYPE_ORDER) if t in self.types)
@@ -151,6 +154,7 @@ def _desc(cfg: ConsoleConfig, noise_ptr: int = 0, noise_on_device: int = 0) -> C
     d.noise_on_device = noise_on_device
     d.workspace_limit_bytes = cfg.workspace_limit_bytes
     d.retain_spectra = cfg.retain_spectra
+    d.autotune = cfg.autotune
     return d
 
 
@@ -292,6 +296,12 @@ class Console:
         song = np.zeros(self.n_processors, np.int32)
         self._check(self.lib.mg_processor_layout(self.h, types.ctypes.data, offs.ctypes.data, song.ctypes.data))
         return types, offs, song
+
+    def fft_sizes(self) -> np.ndarray:
+        """[P, 3]: f, log2 of N / f and log2 of N1 / f of every processor's FFT convolution (zeros elsewhere)."""
+        out = np.zeros((3, self.n_processors), np.int32)
+        self._check(self.lib.mg_processor_fft(self.h, out[0].ctypes.data, out[1].ctypes.data, out[2].ctypes.data))
+        return out.T.copy()
 
     def processor_types(self) -> List[str]:
         return [TYPE_ORDER[t] for t in self.layout()[0]]

@@ -7,6 +7,7 @@
 // aggregate / store with index_select and scatter: node outputs are written once into their own slice of
 // one device arena, and every node reads its input slice in place.  The backward pass walks the string in
 // reverse.  Per-node reductions use fixed-order partial sums so results do not depend on batch composition.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -49,6 +50,8 @@ struct HostProc {
   int L, ld;
   int logN = 0, logN1 = 0, logN2 = 0, f = 1, colG = 0, n0 = 0, Nh = 0, nchunks = 0, nframes = 0;
   int nfrows = 0, nbrows = 0;
+  int nfcap = 0;                 // partial-sum rows allocated (the largest column-item count of the candidate splits)
+  std::vector<int> splits;       // candidate row exponents logN1 of the FFT convolution (autotuner)
   // arena offsets (bytes)
   size_t o_y = 0, o_stats = 0, o_fpart = 0, o_bpart = 0, o_taps = 0, o_dtaps = 0, o_aux = 0, o_carry = 0, o_rcarry = 0,
          o_cagg = 0, o_nspec = 0, o_hspec = 0, o_ybar = 0, o_dhspec = 0;
@@ -211,6 +214,21 @@ mg_status fail(mg_console* c, mg_status s, const std::string& msg) {
 // ------------------------------------------------------------------------------------------------
 // planning (host only)
 // ------------------------------------------------------------------------------------------------
+// Four-step split of N = f 2^logN into rows N1 = f 2^logN1 and columns N2 = 2^logN2; a split is valid when the
+// rows fit the row kernels (N1 <= 2048, or 3072 with the factor 3), a column tile holds at least one column
+// (N2 <= 8192) and both factors are at least 8 (16 for the rows, one radix-16 pass).
+bool split_ok(int f, int logN, int logN1) {
+  const int logN2 = logN - logN1;
+  return logN1 >= 4 && logN2 >= 3 && logN2 <= 13 && (f << logN1) <= (f == 1 ? 2048 : 3072);
+}
+void apply_split(HostProc& p, int logN1) {
+  p.logN1 = logN1;
+  p.logN2 = p.logN - logN1;
+  p.colG = std::min(8, std::min(8192 >> p.logN2, 1 << p.logN1));
+  p.nfrows = (p.f << p.logN1) / p.colG;
+  p.nbrows = p.nfrows;
+}
+
 mg_status validate(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
   if (!d || !s || n <= 0) return fail(c, MG_ERR_INVALID, "null descriptor or no songs");
   if (!(d->sample_rate > 1000.0 && d->sample_rate < 1e6)) return fail(c, MG_ERR_INVALID, "sample_rate out of range");
@@ -309,6 +327,17 @@ void plan(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n)
             p.nfrows = (p.f << p.logN1) / p.colG;
             p.nbrows = p.nfrows;
             p.scratch_bytes = (size_t)3 * ((size_t)p.f << p.logN) * sizeof(float2);
+            // autotuner candidates: the default split and its neighbours; partial sums sized for all of them
+            p.splits.clear();
+            p.nfcap = p.nfrows;
+            for (int dl = -2; dl <= 2; ++dl) {
+              const int l1 = p.logN1 + dl;
+              if (!split_ok(p.f, p.logN, l1)) continue;
+              HostProc q = p;
+              apply_split(q, l1);
+              p.splits.push_back(l1);
+              p.nfcap = std::max(p.nfcap, q.nfrows);
+            }
           }
         } else if (t == T_C || t == T_N) {
           p.nchunks = (p.L + kDynChunk - 1) / kDynChunk;
@@ -868,8 +897,8 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
   for (auto& p : c->procs) {
     p.o_y = b.take((size_t)2 * p.ld * sizeof(float));
     p.o_stats = b.take(16 * sizeof(float));
-    if (p.nfrows) p.o_fpart = b.take((size_t)p.nfrows * kNPart * sizeof(float));
-    if (p.nbrows) p.o_bpart = b.take((size_t)p.nbrows * kNPart * sizeof(float));
+    if (p.nfrows) p.o_fpart = b.take((size_t)std::max(p.nfrows, p.nfcap) * kNPart * sizeof(float));
+    if (p.nbrows) p.o_bpart = b.take((size_t)std::max(p.nbrows, p.nfcap) * kNPart * sizeof(float));
     if (p.type == T_E || p.type == T_R || p.type == T_D) {
       p.o_taps = b.take((size_t)2 * p.Nh * sizeof(float));
       p.o_dtaps = b.take((size_t)2 * p.Nh * sizeof(float));
@@ -916,6 +945,108 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
 // two Adam moments.
 size_t console_device_bytes(const mg_console* c, size_t arena, size_t scratch) {
   return arena + scratch + 4 * sizeof(float) * (size_t)c->nparams;
+}
+
+// Autotuner of the FFT convolution split: for every size class (f, logN) of the reverb / delay nodes, one node
+// of the class runs its forward and backward passes (filter spectrum, input spectrum, product, inverse, dL/dy_bar,
+// backward rows, du, dL/dh) under each candidate split; the fastest (minimum of three timed repetitions after
+// one warm-up) is applied to the whole class.  The buffers hold whatever the console holds at that point; the
+// passes do the same work for any values.
+mg_status autotune_splits(mg_console* c) {
+  std::vector<std::pair<int, int>> classes;
+  std::vector<int> rep_of;
+  for (int pi = 0; pi < c->P; ++pi) {
+    const HostProc& p = c->procs[pi];
+    if ((p.type != T_R && p.type != T_D) || p.splits.size() < 2) continue;
+    const auto key = std::make_pair(p.f, p.logN);
+    if (std::find(classes.begin(), classes.end(), key) == classes.end()) {
+      classes.push_back(key);
+      rep_of.push_back(pi);
+    }
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  LaunchCtx x = make_ctx(c, nullptr);
+  for (size_t k = 0; k < classes.size(); ++k) {
+    const int pi = rep_of[k];
+    HostProc& p = c->procs[pi];
+    const HostProc saved = p;
+    int best = p.logN1;
+    float best_ms = 1e30f;
+    for (int l1 : saved.splits) {
+      apply_split(p, l1);
+      ProcDev& dv = c->hpd[pi];
+      dv.logN1 = p.logN1;
+      dv.logN2 = p.logN2;
+      dv.colG = p.colG;
+      dv.nfpart = p.nfrows;
+      dv.nbpart = p.nbrows;
+      ProcDev* dptr = c->d_procs + pi;
+      CK(cudaMemcpyAsync(dptr, &dv, sizeof(ProcDev), cudaMemcpyHostToDevice, c->stream));
+      ItemList col, pair;
+      for (int i = 0; i < p.nfrows; ++i) col.h.push_back(Item{pi, i});
+      for (int i = 0; i <= (1 << p.logN2) / 2; ++i) pair.h.push_back(Item{pi, i});
+      if (upload_items(c, col) || upload_items(c, pair)) return MG_ERR_CUDA;
+      const int n2g = (1 << p.logN2) * p.colG, n1 = p.f << p.logN1, nc = (int)col.h.size(), np_ = (int)pair.h.size();
+      auto passes = [&] {
+        launch_col_fwd_taps(x, col.d, nc, n2g);
+        launch_row_fwd_hz(x, pair.d, np_, n1);
+        launch_col_fwd_audio(x, col.d, nc, n2g);
+        launch_row_conv_fwd(x, pair.d, np_, n1, c->retain);
+        if (c->retain) launch_col_inv_out_keep(x, col.d, nc, n2g);
+        else launch_col_inv_out(x, col.d, nc, n2g);
+        if (c->retain) {
+          launch_col_dybar_keep(x, col.d, nc, n2g);
+        } else {
+          launch_col_fwd_taps(x, col.d, nc, n2g);
+          launch_row_fwd_hz(x, pair.d, np_, n1);
+          launch_col_fwd_audio(x, col.d, nc, n2g);
+          launch_row_conv_fwd(x, pair.d, np_, n1, true);
+          launch_col_dybar(x, col.d, nc, n2g);
+        }
+        launch_row_bwd2(x, pair.d, np_, n1);
+        launch_col_du(x, col.d, nc, n2g);
+        launch_col_dh(x, col.d, nc, n2g);
+      };
+      passes();
+      float ms = 1e30f;
+      for (int r = 0; r < 3; ++r) {
+        CK(cudaEventRecord(e0, c->stream));
+        passes();
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        ms = std::min(ms, t);
+      }
+      CK(cudaGetLastError());
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = l1;
+      }
+    }
+    p = saved;
+    for (HostProc& q : c->procs)
+      if ((q.type == T_R || q.type == T_D) && q.f == classes[k].first && q.logN == classes[k].second) apply_split(q, best);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the arena is untouched (partial sums sized for every candidate); the node table and work lists follow the
+  // chosen splits
+  for (int pi = 0; pi < c->P; ++pi) {
+    const HostProc& p = c->procs[pi];
+    if (p.type != T_R && p.type != T_D) continue;
+    ProcDev& dv = c->hpd[pi];
+    dv.logN1 = p.logN1;
+    dv.logN2 = p.logN2;
+    dv.colG = p.colG;
+    dv.nfpart = p.nfrows;
+    dv.nbpart = p.nbrows;
+  }
+  if (build_tables(c) != MG_OK) return MG_ERR_CUDA;
+  CK(cudaStreamSynchronize(c->stream));
+  return MG_OK;
 }
 
 mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
@@ -1208,6 +1339,8 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     CK(cudaStreamSynchronize(c->stream));
     cudaFree(nz);
   }
+  // ---- FFT split autotuner ----
+  if (d->autotune && autotune_splits(c) != MG_OK) return MG_ERR_CUDA;
   // ---- target spectrograms ----
   {
     LaunchCtx x = make_ctx(c, nullptr);
@@ -1317,6 +1450,18 @@ mg_status mg_console_destroy(mg_console* c) {
 mg_status mg_console_get_info(const mg_console* c, mg_console_info* out) {
   if (!c || !out) return MG_ERR_INVALID;
   fill_info(c, out);
+  return MG_OK;
+}
+
+mg_status mg_processor_fft(const mg_console* c, int32_t* f, int32_t* log_n, int32_t* log_n1) {
+  if (!c) return MG_ERR_INVALID;
+  for (int i = 0; i < c->P; ++i) {
+    const HostProc& p = c->procs[i];
+    const bool four = p.type == T_R || p.type == T_D;
+    if (f) f[i] = four ? p.f : 0;
+    if (log_n) log_n[i] = four ? p.logN : 0;
+    if (log_n1) log_n1[i] = four ? p.logN1 : 0;
+  }
   return MG_OK;
 }
 

@@ -143,6 +143,20 @@ def test_full_console_at_ground_truth_parameters(seed):
     check(case, grad_floor=True)
 
 
+def test_autotuned_splits_keep_parity():
+    """The FFT split autotuner picks a valid row/column split per FFT size; results stay within the bounds."""
+    lays = [W.layout_plain(88200), W.SongLayout(3, 1, [0, -1, 0], 30011)]
+    case = make_case(lays, seed=3)
+    con, _, _ = check(case, autotune=1)
+    sz = con.fft_sizes()
+    types = con.processor_types()
+    for (f, logn, logn1), t in zip(sz, types):
+        if t in "rd":
+            assert f in (1, 3) and 4 <= logn1 and logn - logn1 >= 3 and (f << logn1) <= (2048 if f == 1 else 3072)
+        else:
+            assert f == 0
+
+
 def test_full_console_plain_workload():
     """4 tracks x 2 s at 44.1 kHz, one subgroup of 2 tracks, every processor type."""
     case = make_case([W.layout_plain(88200)], seed=0)
