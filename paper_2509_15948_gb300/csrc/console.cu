@@ -70,7 +70,7 @@ struct HostSong {
   int K, S, L, ld;
   std::vector<int> group;
   int nframes[3] = {0, 0, 0}, first[3] = {0, 0, 0}, litems[3] = {0, 0, 0}, lcap = 0;
-  size_t o_mix = 0, o_dmix = 0, o_tgt = 0, o_Y[3] = {0, 0, 0}, o_dF[3] = {0, 0, 0}, o_lpart = 0, o_coef = 0,
+  size_t o_mix = 0, o_dmix = 0, o_tgt = 0, o_Y[3] = {0, 0, 0}, o_Yh[3] = {0, 0, 0}, o_dF[3] = {0, 0, 0}, o_lpart = 0, o_coef = 0,
          o_ynorm = 0;
   std::vector<int> tracks_chain, groups_chain;
   int pbeg = 0, pend = 0;
@@ -579,7 +579,7 @@ void loss_forward(mg_console* c, const LaunchCtx& x, int mode, float* out_losses
     auto& L = c->loss_items[r];
     if (!L.h.empty())
       run(c, F_LOSS_FWD, [&] {   // frame kernel: 0 target spectrogram, 1 loss partials (losses and trials)
-        launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), mode == 0 ? 0 : 1, 8192);
+        launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), mode == 0 ? 0 : (mode == 1 ? 3 : 1), 8192);
       });
   }
   if (mode != 0) run_procs(c, F_FINALIZE, c->all_lti_present, [&](const int* p, int n) { launch_node_stats(x, p, n, 1); });
@@ -881,6 +881,7 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
       hs.lcap = std::max(hs.lcap, hs.litems[r]);
       const int nbands = d->n_mels > 0 ? d->n_mels : nf / 2 + 1;
       hs.o_Y[r] = b.take((size_t)std::max(1, hs.nframes[r]) * nbands * 4 * sizeof(float));
+      hs.o_Yh[r] = b.take((size_t)std::max(1, hs.nframes[r]) * nbands * 4 * sizeof(float));
       hs.o_dF[r] = b.take((size_t)std::max(1, hs.nframes[r]) * nf * sizeof(float2));
     }
     hs.o_lpart = b.take((size_t)3 * std::max(1, hs.lcap) * 6 * sizeof(float));
@@ -1219,6 +1220,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
       sd.first_frame[r] = hs.first[r];
       sd.litems[r] = r < c->nres ? hs.litems[r] : 0;
       sd.Y[r] = r < c->nres ? (float*)(c->arena + hs.o_Y[r]) : nullptr;
+      sd.Yh[r] = r < c->nres ? (float*)(c->arena + hs.o_Yh[r]) : nullptr;
       sd.dF[r] = r < c->nres ? (float*)(c->arena + hs.o_dF[r]) : nullptr;
     }
     sd.lcap = std::max(1, hs.lcap);

@@ -121,9 +121,7 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_eq_os_bwd(LaunchCtx c, const 
       C[pidx(j)] = dblk;
     }
     __syncthreads();
-    fft_p<false>(A, kOsLog, 1, kOsP, c.tab.tw);
-    fft_p<false>(Bf, kOsLog, 1, kOsP, c.tab.tw);
-    fft_p<false>(C, kOsLog, 1, kOsP, c.tab.tw);
+    fft_p<false, 3>(A, kOsLog, 3, kOsP, c.tab.tw);   // A, Bf, C: three batches in one set of passes
 #pragma unroll 4
     for (int t = 0; t < kBins; ++t) {
       const int k = threadIdx.x + t * kOsThreads, e = pidx(k);

@@ -60,7 +60,9 @@ __device__ __forceinline__ void load_frames(float2* sm, const float* x, int ld, 
 }  // namespace
 
 // item (song, res, first frame, frames); mode 0: write target spectrogram + partial sum Y^2 per set;
-// mode 1: partial sums of |dlog| and (Y - Yhat)^2 per set; mode 2: adjoint frames to dF.
+// mode 1: partial sums of |dlog| and (Y - Yhat)^2 per set; mode 3: mode 1 that also keeps the frame spectra
+// (in dF, which the adjoint overwrites frame by frame) and the band values Yhat (training forward);
+// mode 2: adjoint frames to dF from the kept spectra and band values.
 __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, const SongDev* __restrict__ songs,
                                                               const LossRes* __restrict__ resv,
                                                               const int4* __restrict__ items, int mode) {
@@ -71,17 +73,34 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
   const LossRes& R = resv[it.y];
   const int t0 = it.z, nb = it.w, n = R.nfft, nbands = R.nbands, bs = pstride(n);
   const float* x = mode == 0 ? S.target : S.mix;
-  load_frames(sm, x, S.ld, S.L, R, t0, nb);
-  __syncthreads();
-  fft_p<false>(sm, R.log_nfft, nb, bs, c.tab.tw);
+  float2* Zk = reinterpret_cast<float2*>(S.dF[it.y]);     // frame spectra kept between mode 3 and mode 2
+  if (mode == 2) {
+    for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
+      const int f = e >> R.log_nfft, j = e & (n - 1);
+      sm[f * bs + pidx(j)] = Zk[(size_t)(t0 + f) * n + j];
+    }
+    __syncthreads();
+  } else {
+    load_frames(sm, x, S.ld, S.L, R, t0, nb);
+    __syncthreads();
+    fft_p<false>(sm, R.log_nfft, nb, bs, c.tab.tw);
+    if (mode == 3)
+      for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
+        const int f = e >> R.log_nfft, j = e & (n - 1);
+        Zk[(size_t)(t0 + f) * n + j] = sm[f * bs + pidx(j)];
+      }
+  }
   float* Yt = S.Y[it.y];
-  if (mode < 2) {
+  float* Yk = S.Yh[it.y];
+  if (mode != 2) {
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int e = threadIdx.x; e < nb * nbands * 4; e += blockDim.x) {
       const int f = e / (nbands * 4), r = e % (nbands * 4), b = r >> 2, ch = r & 3;
       const float yh = band_value(R, sm + f * bs, b, ch);
       const int set = ch < 2 ? 0 : ch - 1;
-      float* ydst = Yt + ((size_t)(t0 + f) * nbands + b) * 4 + ch;
+      const size_t yi = ((size_t)(t0 + f) * nbands + b) * 4 + ch;
+      float* ydst = Yt + yi;
+      if (mode == 3) Yk[yi] = yh;
       if (mode == 0) {
         *ydst = yh;
         acc[set] += yh * yh;
@@ -106,9 +125,10 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
   const float* coef = S.coef + it.y * 6;                    // per set: (alpha / count, alpha / (|Y - Yh| |Y|))
   for (int e = threadIdx.x; e < nb * nbands * 4; e += blockDim.x) {
     const int f = e / (nbands * 4), r = e % (nbands * 4), b = r >> 2, ch = r & 3;
-    const float yh = band_value(R, sm + f * bs, b, ch);
+    const size_t yi = ((size_t)(t0 + f) * nbands + b) * 4 + ch;
+    const float yh = Yk[yi];
     const int set = ch < 2 ? 0 : ch - 1;
-    const float y = Yt[((size_t)(t0 + f) * nbands + b) * 4 + ch];
+    const float y = Yt[yi];
     const float dl = logf(yh + kLogEps) - logf(y + kLogEps);
     const float sg = dl > 0.f ? 1.f : (dl < 0.f ? -1.f : 0.f);
     dY[e] = coef[2 * set] * sg / (yh + kLogEps) + coef[2 * set + 1] * (yh - y);

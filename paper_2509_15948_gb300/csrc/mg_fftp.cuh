@@ -144,10 +144,10 @@ __device__ __forceinline__ void twiddle(float2 (&x)[R], const float2* __restrict
   }
 }
 
-template <bool INV, int R, int LOGR>
+template <bool INV, int R, int LOGR, int SLOTS = 1>
 __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, int bs, int lp,
                                      const float2* __restrict__ tw) {
-  constexpr int PER = 16 / R;
+  constexpr int PER = SLOTS * 16 / R;
   const int MR = 1 << (logM - LOGR), p = 1 << lp, total = nb << (logM - LOGR);
   const int nth = blockDim.x, tid = threadIdx.x;
   float2 v[PER][R];
@@ -319,16 +319,17 @@ __device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const floa
 }
 
 // FFTs of size M = 2^logM (M <= 8192) over nb batches, padded layout (element e of batch b at
-// d[b * bs + pidx(e)]), in place.  Requires nb * M <= 16 * blockDim.x.  Forward: exp(-2 pi i nk/M); inverse:
-// exp(+...), unscaled.  The caller synchronises before the call; the call ends with a barrier.
-template <bool INV>
+// d[b * bs + pidx(e)]), in place.  Requires nb * M <= 16 * SLOTS * blockDim.x (SLOTS x 16 elements per thread
+// and pass).  Forward: exp(-2 pi i nk/M); inverse: exp(+...), unscaled.  The caller synchronises before the
+// call; the call ends with a barrier.
+template <bool INV, int SLOTS = 1>
 __device__ void fft_p(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ tw) {
   int lp = 0;
-  for (; logM - lp >= 4; lp += 4) fftp::pass<INV, 16, 4>(d, logM, nb, bs, lp, tw);
+  for (; logM - lp >= 4; lp += 4) fftp::pass<INV, 16, 4, SLOTS>(d, logM, nb, bs, lp, tw);
   const int rem = logM - lp;
-  if (rem == 3) fftp::pass<INV, 8, 3>(d, logM, nb, bs, lp, tw);
-  else if (rem == 2) fftp::pass<INV, 4, 2>(d, logM, nb, bs, lp, tw);
-  else if (rem == 1) fftp::pass<INV, 2, 1>(d, logM, nb, bs, lp, tw);
+  if (rem == 3) fftp::pass<INV, 8, 3, SLOTS>(d, logM, nb, bs, lp, tw);
+  else if (rem == 2) fftp::pass<INV, 4, 2, SLOTS>(d, logM, nb, bs, lp, tw);
+  else if (rem == 1) fftp::pass<INV, 2, 1, SLOTS>(d, logM, nb, bs, lp, tw);
 }
 
 }  // namespace mg

@@ -94,6 +94,7 @@ struct SongDev {
   float* dmix;                             // [2][ld]
   const float* target;
   float* Y[3];                             // target spectrograms [frames][nbands][4] (L, R, M, S)
+  float* Yh[3];                            // spectrograms of the mix kept by the training forward, same layout
   float* dF[3];                            // backward per-frame gradients [frames][nfft] (packed complex)
   float* lpart;                            // loss partials [3][lcap][6]
   int litems[3];                           // items per resolution
