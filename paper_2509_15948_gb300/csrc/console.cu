@@ -18,6 +18,7 @@
 
 #include "../../include/mixgraph.h"
 #include "mg_internal.cuh"
+#include "mg_fftp.cuh"
 
 using namespace mg;
 
@@ -1146,6 +1147,20 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
         c3[a * 3 + r] = make_float2((float)std::cos(ang), (float)std::sin(ang));
       }
     c->tab.c3 = (const float2*)up_table(c3.data(), c3.size() * sizeof(float2));
+    std::vector<float2> ptw(kPtwCount), ptw3(kPtw3Count);
+    for (int e = 0; e < kPtwCount; ++e) ptw[e] = tw[ptw_source(e)];
+    for (int a = 1; a <= kPtw3MaxA; ++a)
+      for (int lp2 = 0; lp2 < a; lp2 += 4) {
+        const int logr = std::min(4, a - lp2), p = 3 << lp2;
+        for (int r = 0; r < logr; ++r)
+          for (int k = 0; k < p; ++k) {
+            const int64_t m = ((int64_t)k << r) << (a - lp2 - logr);
+            const double ang = -2.0 * PI * (double)m / (3.0 * std::ldexp(1.0, a));
+            ptw3[ptw3_base(a, lp2) + r * p + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+          }
+      }
+    c->tab.ptw = (const float2*)up_table(ptw.data(), ptw.size() * sizeof(float2));
+    c->tab.ptw3 = (const float2*)up_table(ptw3.data(), ptw3.size() * sizeof(float2));
     c->tab.cos_eq = (const float*)up_table(ceq.data(), ceq.size() * sizeof(float));
     c->tab.cos_dl = (const float*)up_table(cdl.data(), cdl.size() * sizeof(float));
     c->tab.rev_win = (const float*)up_table(hwin.data(), hwin.size() * sizeof(float));
@@ -1153,7 +1168,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     c->tab.hann_eq = (const float*)up_table(heq.data(), heq.size() * sizeof(float));
     c->tab.hann_dl = (const float*)up_table(hdl.data(), hdl.size() * sizeof(float));
     c->tab.dly_w = (const float2*)up_table(dw.data(), dw.size() * sizeof(float2));
-    if (!c->tab.tw || !c->tab.twf || !c->tab.c3 || !c->tab.dly_w) return fail(c, MG_ERR_OOM, "table allocation failed");
+    if (!c->tab.tw || !c->tab.twf || !c->tab.c3 || !c->tab.ptw || !c->tab.ptw3 || !c->tab.dly_w) return fail(c, MG_ERR_OOM, "table allocation failed");
   }
   // loss resolutions
   c->hres.assign(c->nres, LossRes{});
@@ -1632,7 +1647,7 @@ mg_status mg_get_present(const mg_console* c, uint8_t* h_present) {
 mg_status mg_evaluate(mg_console* c, float* d_out) {
   if (!c || !d_out) return fail(c, MG_ERR_INVALID, "null pointer");
   launch_eval(c->stream, c->d_songs, (int)c->songs.size(), c->d_ev_items, (int)c->ev_items.size(), c->d_ev_begin,
-              c->ev_seg_len, c->d_ev_lo, c->d_ev_hi, c->d_ev_out, d_out, c->tab.tw);
+              c->ev_seg_len, c->d_ev_lo, c->d_ev_hi, c->d_ev_out, d_out, c->tab.ptw);
   CK(cudaGetLastError());
   return MG_OK;
 }

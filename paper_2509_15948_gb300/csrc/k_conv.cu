@@ -47,8 +47,8 @@ __device__ __forceinline__ float2 twiddle_node(const ProcDev& P, unsigned m, boo
 // Row FFTs (length N1 = f 2^logN1) of nb padded rows with batch stride bs.
 template <bool INV>
 __device__ __forceinline__ void row_fft(float2* d, const ProcDev& P, int nb, int bs, const Tables& tab) {
-  if (P.f == 1) fft_p<INV>(d, P.logN1, nb, bs, tab.tw);
-  else fft_p3<INV>(d, P.logN1, nb, bs, tab.tw, tab.c3);
+  if (P.f == 1) fft_p<INV>(d, P.logN1, nb, bs, tab.ptw);
+  else fft_p3<INV>(d, P.logN1, nb, bs, tab.ptw3);
 }
 
 // Tap value of the stereo FIR at circular position n (time n, or n - N for the negative taps).
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
         if (live(h + j)) col[pidx(row_of(h + j))] = v[j];
     }
     __syncthreads();
-    fft_p<kInv>(sm, logN2, G, cs, c.tab.tw);
+    fft_p<kInv>(sm, logN2, G, cs, c.tab.ptw);
   }
 
   if (!kInv && !kDybar) {  // forward column pass: twiddle, store in place (row k2)
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
     float out[1];
     block_sum<1>(acc, red, out);   // also acts as the barrier before the FFT
     if (threadIdx.x == 0) P.bpart[it.idx * kNPart + 0] = out[0];
-    fft_p<false>(sm, logN2, G, cs, c.tab.tw);
+    fft_p<false>(sm, logN2, G, cs, c.tab.ptw);
 #pragma unroll 4
     for (int s = 0; s < kSlots; ++s) {
       if (!live(s)) continue;

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kOsThreads) k_eq_spec(LaunchCtx c, const int* 
     sm[pidx(j)] = make_float2(v, 0.f);
   }
   __syncthreads();
-  fft_p<false>(sm, kOsLog, 1, kOsP, c.tab.tw);
+  fft_p<false>(sm, kOsLog, 1, kOsP, c.tab.ptw);
   for (int k = threadIdx.x; k < kOsM; k += blockDim.x) P.hspec[k] = sm[pidx(k)].x;
 }
 
@@ -50,10 +50,10 @@ __global__ void __launch_bounds__(kOsThreads, 2) k_eq_os_fwd(LaunchCtx c, const 
     sm[pidx(j)] = (s >= 0 && s < P.L) ? make_float2(P.u[s], P.u[P.ld + s]) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft_p<false>(sm, kOsLog, 1, kOsP, c.tab.tw);
+  fft_p<false>(sm, kOsLog, 1, kOsP, c.tab.ptw);
   for (int k = threadIdx.x; k < kOsM; k += blockDim.x) sm[pidx(k)] = cscale(sm[pidx(k)], P.hspec[k]);
   __syncthreads();
-  fft_p<true>(sm, kOsLog, 1, kOsP, c.tab.tw);
+  fft_p<true>(sm, kOsLog, 1, kOsP, c.tab.ptw);
   const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const float inv = 1.f / kOsM;
   float acc[2] = {0.f, 0.f};
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_eq_os_bwd(LaunchCtx c, const 
       C[pidx(j)] = dblk;
     }
     __syncthreads();
-    fft_p<false, 3>(A, kOsLog, 3, kOsP, c.tab.tw);   // A, Bf, C: three batches in one set of passes
+    fft_p<false, 3>(A, kOsLog, 3, kOsP, c.tab.ptw);   // A, Bf, C: three batches in one set of passes
 #pragma unroll 4
     for (int t = 0; t < kBins; ++t) {
       const int k = threadIdx.x + t * kOsThreads, e = pidx(k);
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kOsThreads, 1) k_eq_os_bwd(LaunchCtx c, const 
       dst[k] = blk == b0 ? prod : cadd(dst[k], prod);
     }
     __syncthreads();
-    fft_p<true>(Bf, kOsLog, 1, kOsP, c.tab.tw);
+    fft_p<true>(Bf, kOsLog, 1, kOsP, c.tab.ptw);
 #pragma unroll 2
     for (int t = threadIdx.x; t < B; t += blockDim.x) {
       const int s = s0 + t;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kOsThreads) k_eq_dh_reduce(LaunchCtx c, const 
     sm[pidx(k)] = s;
   }
   __syncthreads();
-  fft_p<true>(sm, kOsLog, 1, kOsP, c.tab.tw);
+  fft_p<true>(sm, kOsLog, 1, kOsP, c.tab.ptw);
   const float inv = 1.f / kOsM;
   for (int j = threadIdx.x; j < kEqTaps; j += blockDim.x) {
     P.dtaps[j] = sm[pidx((j - kEqHalf) & (kOsM - 1))].x * inv;

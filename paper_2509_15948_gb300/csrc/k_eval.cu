@@ -53,7 +53,7 @@ __device__ __forceinline__ float warp_max(float v) {
 __global__ void __launch_bounds__(kEvThreads) k_eval_seg(const SongDev* __restrict__ songs, const int2* __restrict__ items,
                                                          int seg_len, const int* __restrict__ band_lo,
                                                          const int* __restrict__ band_hi, double* __restrict__ out,
-                                                         const float2* __restrict__ tw) {
+                                                         const float2* __restrict__ ptw) {
   extern __shared__ float2 sm[];
   __shared__ double red[16 * 16];
   __shared__ float mred[2][16];
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kEvThreads) k_eval_seg(const SongDev* __restri
         sm[pidx(j)] = make_float2(a, b);
       }
       __syncthreads();
-      fft_p<false>(sm, kBarkLog, 1, rs, tw);
+      fft_p<false>(sm, kBarkLog, 1, rs, ptw);
       for (int b = 0; b < kBands; ++b) {
         double p = 0.0;
         for (int k = band_lo[b] + (int)threadIdx.x; k < band_hi[b]; k += blockDim.x) {
@@ -216,10 +216,10 @@ __global__ void k_eval_finalize(const int* __restrict__ item_begin,
 
 void launch_eval(cudaStream_t st, const SongDev* songs, int n_songs, const int2* items, int n_items,
                  const int* item_begin, int seg_len, const int* band_lo, const int* band_hi, double* seg_out,
-                 float* out_song, const float2* tw) {
+                 float* out_song, const float2* ptw) {
   if (!n_items) return;
   k_eval_seg<<<n_items, kEvThreads, pstride(kBarkFrame) * sizeof(float2), st>>>(songs, items, seg_len, band_lo,
-                                                                                  band_hi, seg_out, tw);
+                                                                                  band_hi, seg_out, ptw);
   k_eval_finalize<<<n_songs, 32, 0, st>>>(item_begin, seg_out, out_song);
 }
 

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
   } else {
     load_frames(sm, x, S.ld, S.L, R, t0, nb);
     __syncthreads();
-    fft_p<false>(sm, R.log_nfft, nb, bs, c.tab.tw);
+    fft_p<false>(sm, R.log_nfft, nb, bs, c.tab.ptw);
     if (mode == 3)
       for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
         const int f = e >> R.log_nfft, j = e & (n - 1);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
     }
   }
   __syncthreads();
-  fft_p<true>(sm, R.log_nfft, nb, bs, c.tab.tw);
+  fft_p<true>(sm, R.log_nfft, nb, bs, c.tab.ptw);
   float* dF = S.dF[it.y];
   for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
     const int f = e >> R.log_nfft, j = e & (n - 1);

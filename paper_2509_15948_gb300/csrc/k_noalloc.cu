@@ -11,7 +11,7 @@
 #include <mutex>
 
 #include "../../include/mixgraph.h"
-#include "mg_fft.cuh"
+#include "mg_fftp.cuh"
 
 namespace mg {
 namespace {
@@ -29,6 +29,7 @@ struct NaLayout {
   float2 fft[3 * kNaN];                      // T1, T2, Hz
   float2 tw[kTwN];
   float2 twf[kTwN];                          // exp(-2 pi i j / 2^26): fine factor of the four-step twiddles
+  float2 ptw[kPtwCount];                     // pass twiddles of the row and column FFTs
   float cos_eq[kEqTaps];
   float hann_eq[kEqTaps];
   float taps[2 * kEqTaps];
@@ -57,6 +58,11 @@ __global__ void k_na_tables() {
     S->tw[j] = make_float2((float)c, (float)-s);
     sincospi(2.0 * j / (double)(1 << kTwFineLog), &s, &c);
     S->twf[j] = make_float2((float)c, (float)-s);
+  }
+  for (int e = t; e < kPtwCount; e += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * ptw_source(e) / kTwN, &s, &c);
+    S->ptw[e] = make_float2((float)c, (float)-s);
   }
   for (int m = t; m < kEqTaps; m += gridDim.x * blockDim.x) {
     S->cos_eq[m] = (float)cospi(2.0 * m / kEqTaps);
@@ -154,6 +160,7 @@ extern "C" mg_status mg_eq_forward_noalloc(const float* d_u, float* d_y, int64_t
   x.fs = 0.0;
   x.tab.tw = S->tw;
   x.tab.twf = S->twf;
+  x.tab.ptw = S->ptw;
   x.tab.cos_eq = S->cos_eq;
   x.tab.hann_eq = S->hann_eq;
   launch_eq_fir(x, S->proc_list, 1);

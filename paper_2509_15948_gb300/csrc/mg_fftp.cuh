@@ -4,8 +4,9 @@
 //
 // Stockham pass of radix R with p = product of the previous radices: butterfly i (k = i mod p) reads
 // x[i + r M/R], multiplies by w_{Rp}^{r k}, runs an R-point DFT in registers and writes the R results to
-// (i - k) R + k + q p.  Twiddles come from the 8192-entry table exp(-2 pi i j / 8192) (rounded once from
-// double): four loads per butterfly, the remaining powers formed as products.
+// (i - k) R + k + q p.  The powers w^1, w^2, w^4, w^8 of a butterfly come from a pass twiddle table laid out
+// per pass as rows of p consecutive k, so that the loads of a warp (consecutive k) are coalesced; the other
+// powers are products.
 #pragma once
 #include "mg_fft.cuh"
 
@@ -14,6 +15,34 @@ namespace mg {
 __device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
 // batch stride of a padded transform of size M (odd, to spread consecutive batches over the banks)
 __host__ __device__ constexpr int pstride(int M) { return M + (M >> 4) + 1; }
+
+// Pass twiddle table of the power-of-two transforms (M <= 8192).  The pass with p = 2^lp (lp = 4, 8, 12) and
+// radix R = 2^logr owns logr rows of p entries; row j, entry k is w^(2^j k), w = exp(-2 pi i / (R p)), which is
+// entry (2^j k) 2^(13 - lp - logr) of the 8192-point table exp(-2 pi i j / 8192).
+constexpr int kPtwCount = 6816;
+__host__ __device__ constexpr int ptw_base(int lp, int logr) {
+  return (lp == 4 ? 0 : (lp == 8 ? 160 : 2720)) + (1 << lp) * (logr * (logr - 1) / 2);
+}
+// index into the 8192-point table of entry e of the pass twiddle table
+__host__ __device__ inline int ptw_source(int e) {
+  int lp = 4, start = 0;
+  if (e >= 2720) { lp = 12; start = 2720; }
+  else if (e >= 160) { lp = 8; start = 160; }
+  const int p = 1 << lp, row = (e - start) / p, k = (e - start) % p;
+  const int logr = row < 1 ? 1 : (row < 3 ? 2 : (row < 6 ? 3 : 4));
+  const int j = row - logr * (logr - 1) / 2;
+  return ((1 << j) * k) << (13 - lp - logr);
+}
+
+// Pass twiddle table of the transforms of size M = 3 * 2^a (1 <= a <= kPtw3MaxA).  Region a starts at
+// 12 (2^a - 2); in it, the twiddled pass number j (p = 3 * 16^j, radix 16 except the last) starts at
+// 12 (16^j - 1) / 15 and owns logr rows of p entries: row r, entry k is exp(-2 pi i m / M),
+// m = (2^r k) 2^(a - 4 j - logr).
+constexpr int kPtw3MaxA = 10;
+constexpr int kPtw3Count = 12 * ((2 << kPtw3MaxA) - 2);
+__host__ __device__ constexpr int ptw3_base(int a, int lp2) {
+  return 12 * ((1 << a) - 2) + 12 * (((1 << lp2) - 1) / 15);
+}
 
 namespace fftp {
 
@@ -108,29 +137,30 @@ __device__ __forceinline__ void dftR(float2 (&x)[R]) {
   else dft2<INV>(x[0], x[1]);
 }
 
-// Multiplies x[r] by w^r (w = table entry m, conjugated for the inverse), r = 1..R-1.  Only the powers 1, 2, 4, 8
-// come from the table; the others are products of at most three of them (error a few ulp, no extra loads).
+// Multiplies x[r] by w^r, r = 1..R-1, for the butterfly whose twiddle row entries start at t (row stride p,
+// conjugated for the inverse).  Only w^1, w^2, w^4, w^8 are loaded; the others are products of at most three of
+// them (error a few ulp, no extra loads).
 template <bool INV, int R>
-__device__ __forceinline__ void twiddle(float2 (&x)[R], const float2* __restrict__ tw, int m) {
-  auto ld = [&](int r) {
-    float2 w = tw[r * m];
+__device__ __forceinline__ void twiddle(float2 (&x)[R], const float2* __restrict__ t, int p) {
+  auto ld = [&](int j) {
+    float2 w = t[j * p];
     if (INV) w.y = -w.y;
     return w;
   };
-  const float2 w1 = ld(1);
+  const float2 w1 = ld(0);
   x[1] = cmul(x[1], w1);
   if constexpr (R >= 4) {
-    const float2 w2 = ld(2), w3 = cmul(w1, w2);
+    const float2 w2 = ld(1), w3 = cmul(w1, w2);
     x[2] = cmul(x[2], w2);
     x[3] = cmul(x[3], w3);
     if constexpr (R >= 8) {
-      const float2 w4 = ld(4), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+      const float2 w4 = ld(2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
       x[4] = cmul(x[4], w4);
       x[5] = cmul(x[5], w5);
       x[6] = cmul(x[6], w6);
       x[7] = cmul(x[7], w7);
       if constexpr (R >= 16) {
-        const float2 w8 = ld(8);
+        const float2 w8 = ld(3);
         x[8] = cmul(x[8], w8);
         x[9] = cmul(x[9], cmul(w1, w8));
         x[10] = cmul(x[10], cmul(w2, w8));
@@ -146,7 +176,7 @@ __device__ __forceinline__ void twiddle(float2 (&x)[R], const float2* __restrict
 
 template <bool INV, int R, int LOGR, int SLOTS = 1>
 __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, int bs, int lp,
-                                     const float2* __restrict__ tw) {
+                                     const float2* __restrict__ ptw) {
   constexpr int PER = SLOTS * 16 / R;
   const int MR = 1 << (logM - LOGR), p = 1 << lp, total = nb << (logM - LOGR);
   const int nth = blockDim.x, tid = threadIdx.x;
@@ -161,7 +191,7 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
       const float2* src = d + b * bs;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[s][r] = src[pidx(i + r * MR)];
-      if (p > 1) twiddle<INV, R>(v[s], tw, k << (kTwLog - lp - LOGR));
+      if (p > 1) twiddle<INV, R>(v[s], ptw + ptw_base(lp, LOGR) + k, p);
       dftR<INV, R>(v[s]);
       ob[s] = b * bs + (i - k) * R + k;   // + q p, padded at store
     }
@@ -181,17 +211,6 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
 }
 
 // ---- transforms of size M = 3 * 2^a (one radix-3 pass, then radix 16 / 8 / 4 / 2) ----
-
-// exp(-+2 pi i m / (3 * 2^a)), m < 3 * 2^a: the 2^a-point table entry of floor(m / 3) times
-// c3[a][m mod 3] = exp(-2 pi i (m mod 3) / (3 * 2^a)) (both rounded once from double).
-template <bool INV>
-__device__ __forceinline__ float2 tw3(unsigned m, int a, const float2* __restrict__ tw, const float2* __restrict__ c3) {
-  const unsigned q = m / 3u, r = m - 3u * q;
-  float2 w = tw[q << (kTwLog - a)];
-  if (r) w = cmul(w, c3[a * 3 + r]);
-  if (INV) w.y = -w.y;
-  return w;
-}
 
 template <bool INV>
 __device__ __forceinline__ void dft3(float2& x0, float2& x1, float2& x2) {
@@ -240,7 +259,7 @@ __device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int
 // Later passes: p = 3 * 2^lp2, radix R = 2^LOGR; butterfly i < M / R, k = i mod p, twiddle w_M^{r k M / (R p)}.
 template <bool INV, int R, int LOGR>
 __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int bs, int lp2,
-                                      const float2* __restrict__ tw, const float2* __restrict__ c3) {
+                                      const float2* __restrict__ ptw3) {
   constexpr int PER = 16 / R;
   const int MR = 3 << (a - LOGR), p = 3 << lp2, total = nb * MR;
   const int nth = blockDim.x, tid = threadIdx.x;
@@ -256,35 +275,7 @@ __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int
       const float2* src = d + b * bs;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[s][r] = src[pidx(i + r * MR)];
-      const unsigned m1 = (unsigned)k << (a - lp2 - LOGR);
-      if (k) {
-        const float2 w1 = tw3<INV>(m1, a, tw, c3);
-        v[s][1] = cmul(v[s][1], w1);
-        if constexpr (R >= 4) {
-          const float2 w2 = tw3<INV>(2 * m1, a, tw, c3), w3 = cmul(w1, w2);
-          v[s][2] = cmul(v[s][2], w2);
-          v[s][3] = cmul(v[s][3], w3);
-          if constexpr (R >= 8) {
-            const float2 w4 = tw3<INV>(4 * m1, a, tw, c3);
-            const float2 w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
-            v[s][4] = cmul(v[s][4], w4);
-            v[s][5] = cmul(v[s][5], w5);
-            v[s][6] = cmul(v[s][6], w6);
-            v[s][7] = cmul(v[s][7], w7);
-            if constexpr (R >= 16) {
-              const float2 w8 = tw3<INV>(8 * m1, a, tw, c3);
-              v[s][8] = cmul(v[s][8], w8);
-              v[s][9] = cmul(v[s][9], cmul(w1, w8));
-              v[s][10] = cmul(v[s][10], cmul(w2, w8));
-              v[s][11] = cmul(v[s][11], cmul(w3, w8));
-              v[s][12] = cmul(v[s][12], cmul(w4, w8));
-              v[s][13] = cmul(v[s][13], cmul(w5, w8));
-              v[s][14] = cmul(v[s][14], cmul(w6, w8));
-              v[s][15] = cmul(v[s][15], cmul(w7, w8));
-            }
-          }
-        }
-      }
+      if (k) twiddle<INV, R>(v[s], ptw3 + ptw3_base(a, lp2) + k, p);
       dftR<INV, R>(v[s]);
       ob[s] = b * bs + (i - k) * R + k;
     }
@@ -307,15 +298,14 @@ __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int
 
 // FFTs of size M = 3 * 2^a (a >= 1) over nb batches in the padded layout, in place; same contract as fft_p.
 template <bool INV>
-__device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const float2* __restrict__ tw,
-                       const float2* __restrict__ c3) {
+__device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const float2* __restrict__ ptw3) {
   fftp::pass3<INV>(d, a, nb, bs);
   int lp2 = 0;
-  for (; a - lp2 >= 4; lp2 += 4) fftp::passm<INV, 16, 4>(d, a, nb, bs, lp2, tw, c3);
+  for (; a - lp2 >= 4; lp2 += 4) fftp::passm<INV, 16, 4>(d, a, nb, bs, lp2, ptw3);
   const int rem = a - lp2;
-  if (rem == 3) fftp::passm<INV, 8, 3>(d, a, nb, bs, lp2, tw, c3);
-  else if (rem == 2) fftp::passm<INV, 4, 2>(d, a, nb, bs, lp2, tw, c3);
-  else if (rem == 1) fftp::passm<INV, 2, 1>(d, a, nb, bs, lp2, tw, c3);
+  if (rem == 3) fftp::passm<INV, 8, 3>(d, a, nb, bs, lp2, ptw3);
+  else if (rem == 2) fftp::passm<INV, 4, 2>(d, a, nb, bs, lp2, ptw3);
+  else if (rem == 1) fftp::passm<INV, 2, 1>(d, a, nb, bs, lp2, ptw3);
 }
 
 // FFTs of size M = 2^logM (M <= 8192) over nb batches, padded layout (element e of batch b at
@@ -323,13 +313,13 @@ __device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const floa
 // and pass).  Forward: exp(-2 pi i nk/M); inverse: exp(+...), unscaled.  The caller synchronises before the
 // call; the call ends with a barrier.
 template <bool INV, int SLOTS = 1>
-__device__ void fft_p(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ tw) {
+__device__ void fft_p(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ ptw) {
   int lp = 0;
-  for (; logM - lp >= 4; lp += 4) fftp::pass<INV, 16, 4, SLOTS>(d, logM, nb, bs, lp, tw);
+  for (; logM - lp >= 4; lp += 4) fftp::pass<INV, 16, 4, SLOTS>(d, logM, nb, bs, lp, ptw);
   const int rem = logM - lp;
-  if (rem == 3) fftp::pass<INV, 8, 3, SLOTS>(d, logM, nb, bs, lp, tw);
-  else if (rem == 2) fftp::pass<INV, 4, 2, SLOTS>(d, logM, nb, bs, lp, tw);
-  else if (rem == 1) fftp::pass<INV, 2, 1, SLOTS>(d, logM, nb, bs, lp, tw);
+  if (rem == 3) fftp::pass<INV, 8, 3, SLOTS>(d, logM, nb, bs, lp, ptw);
+  else if (rem == 2) fftp::pass<INV, 4, 2, SLOTS>(d, logM, nb, bs, lp, ptw);
+  else if (rem == 1) fftp::pass<INV, 2, 1, SLOTS>(d, logM, nb, bs, lp, ptw);
 }
 
 }  // namespace mg

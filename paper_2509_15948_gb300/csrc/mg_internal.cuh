@@ -111,6 +111,8 @@ struct Tables {
   const float2* tw;                        // exp(-2 pi i j / 8192)
   const float2* twf;                       // exp(-2 pi i j / 2^26), j < 8192 (fine factor of large-N twiddles)
   const float2* c3;                        // [14][3] exp(-2 pi i r / (3 2^a)): twiddles of 3 2^a-point FFTs
+  const float2* ptw;                       // pass twiddles of the 2^a-point FFTs (layout of ptw_base)
+  const float2* ptw3;                      // pass twiddles of the 3 2^a-point FFTs (layout of ptw3_base)
   const float* cos_eq;                     // cos(2 pi m / 2047), m < 2047
   const float* cos_dl;                     // cos(2 pi m / 39), m < 39
   const float* rev_win;                    // periodic Hann 384
@@ -170,7 +172,7 @@ void launch_col_inv_out(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_col_dybar(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_eval(cudaStream_t st, const SongDev* songs, int n_songs, const int2* items, int n_items,
                  const int* item_begin, int seg_len, const int* band_lo, const int* band_hi, double* seg_out,
-                 float* out_song, const float2* tw);
+                 float* out_song, const float2* ptw);
 void init_eval_attributes();
 void launch_col_inv_out_keep(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_col_dybar_keep(const LaunchCtx&, const Item* items, int n, int maxN2G);
