@@ -93,6 +93,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   __shared__ float red[2 * 32];
+  __shared__ float2 tws[kSlots * 8];   // W(n1 RS s) of the block's columns, [s][g]
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const int G = P.colG, logG = __ffs(G) - 1;
@@ -113,6 +114,21 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   auto row_of = [&](int s) { return r0 + s * RS; };
   auto live = [&](int s) { return row_of(s) < N2; };
   auto pos = [&](int s) { return nbase + (int64_t)s * nstep; };
+
+  // Forward passes end with the transposition twiddle W(n1 k2), W = exp(-2 pi i / N); for k2 = r0 + s RS it
+  // is W(n1 r0) W(n1 RS s): the first factor is the thread's own, the second comes from a per-block table.
+  constexpr bool kTwid = !(MODE == COL_INV_OUT || MODE == COL_DU || MODE == COL_DH || MODE == COL_INV_OUT_KEEP);
+  float2 w_r0 = make_float2(1.f, 0.f);
+  if (kTwid) {
+    if (r0 < N2) w_r0 = twiddle_node(P, (unsigned)n1 * (unsigned)r0, false, c.tab);
+    if ((int)threadIdx.x < kSlots * G) {   // visible after the barriers of the load and the FFT
+      const int ts = threadIdx.x >> logG, tg = threadIdx.x & (G - 1);
+      const unsigned step = (unsigned)(RS * ts);
+      tws[threadIdx.x] = step < (unsigned)N2 ? twiddle_node(P, (unsigned)(it.idx * G + tg) * step, false, c.tab)
+                                              : make_float2(1.f, 0.f);
+    }
+  }
+  auto tw_at = [&](int s) { return cmul(w_r0, tws[s * G + g]); };
 
   // ---- load ----
   if (MODE != COL_DYBAR_KEEP) {
@@ -147,8 +163,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
 #pragma unroll 4
     for (int s = 0; s < kSlots; ++s) {
       if (!live(s)) continue;
-      const int k2 = row_of(s);
-      dst[pos(s)] = cmul(col[pidx(k2)], twiddle_node(P, (unsigned)n1 * (unsigned)k2, false, c.tab));
+      dst[pos(s)] = cmul(col[pidx(row_of(s))], tw_at(s));
     }
     return;
   }
@@ -229,8 +244,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
 #pragma unroll 4
     for (int s = 0; s < kSlots; ++s) {
       if (!live(s)) continue;
-      const int k2 = row_of(s);
-      P.T2[pos(s)] = cmul(col[pidx(k2)], twiddle_node(P, (unsigned)n1 * (unsigned)k2, false, c.tab));
+      P.T2[pos(s)] = cmul(col[pidx(row_of(s))], tw_at(s));
     }
     return;
   }
@@ -314,9 +328,25 @@ __device__ __forceinline__ void load_rows_fft(float2* s, const float2* src, int 
   row_fft<false>(s, P, nr, rs, tab);
 }
 
-// Inverse row FFT of the slots in o, twiddle exp(+2 pi i n1 k2 / N), store rows a, b of dst.
-__device__ __forceinline__ void inv_rows_store(float2* o, float2* dst, int a, int b, const ProcDev& P, const Tables& tab) {
-  const int N1 = rows_len(P), rs = pstride(N1);
+// Transposition twiddles of rows a and b, W(n1 k2) = lo[n1 mod T] hi[n1 / T] (W = exp(-2 pi i / N), T = 64 or
+// the largest power of two dividing N1 when smaller, N1 / T <= 48), both factors from the accurate table:
+// per row slot kRowTwT lo entries, then the hi entries.  Visible after the caller's next barrier.
+constexpr int kRowTwT = 64, kRowTwS = 128;
+__device__ __forceinline__ void row_tw_init(float2* tt, const ProcDev& P, int a, int b, const Tables& tab) {
+  const int N1 = rows_len(P), logT = min(6, __ffs(N1) - 1), T = 1 << logT, H = N1 >> logT;
+  for (int e = threadIdx.x; e < 2 * (T + H); e += blockDim.x) {
+    const int slot = e >= T + H, j = e - slot * (T + H);
+    const unsigned k2 = slot ? b : a;
+    const unsigned m = j < T ? (unsigned)j * k2 : (unsigned)((j - T) << logT) * k2;
+    tt[slot * kRowTwS + (j < T ? j : kRowTwT + j - T)] = twiddle_node(P, m, false, tab);
+  }
+}
+
+// Inverse row FFT of the slots in o, twiddle exp(+2 pi i n1 k2 / N) (the conjugate of the tt entries), store
+// rows a, b of dst.
+__device__ __forceinline__ void inv_rows_store(float2* o, float2* dst, int a, int b, const ProcDev& P,
+                                               const Tables& tab, const float2* tt) {
+  const int N1 = rows_len(P), rs = pstride(N1), logT = min(6, __ffs(N1) - 1);
   const int nr = a == b ? 1 : 2;
   __syncthreads();
   row_fft<true>(o, P, nr, rs, tab);
@@ -324,7 +354,9 @@ __device__ __forceinline__ void inv_rows_store(float2* o, float2* dst, int a, in
   for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
     const int slot = e >= N1, n1 = e - slot * N1;
     const int k2 = slot ? b : a;
-    dst[(int64_t)k2 * N1 + n1] = cmul(o[slot * rs + pidx(n1)], twiddle_node(P, (unsigned)n1 * (unsigned)k2, true, tab));
+    const float2* t = tt + slot * kRowTwS;
+    const float2 w = cmul(t[n1 & ((1 << logT) - 1)], t[kRowTwT + (n1 >> logT)]);
+    dst[(int64_t)k2 * N1 + n1] = cmul(o[slot * rs + pidx(n1)], cconj(w));
   }
 }
 
@@ -373,6 +405,8 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_conv(LaunchCtx c, const 
   const ProcDev& P = c.procs[it.proc];
   const int N1 = rows_len(P), N2 = 1 << P.logN2;
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
+  __shared__ float2 tt[2 * kRowTwS];
+  row_tw_init(tt, P, a, b, c.tab);
   float2* s = sm;
   load_rows_fft(s, P.T1, a, b, P, c.tab);
   for_mirror_pairs<4>(a, b, N1, [&](int64_t gP, int64_t gQ) { return HzPair{P.Hz[gP], P.Hz[gQ]}; },
@@ -388,7 +422,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_conv(LaunchCtx c, const 
     s[pP] = cadd(cmul(zP, AP), cmul(cconj(zQ), BP));
     s[pQ] = cadd(cmul(zQ, AQ), cmul(cconj(zP), BQ));
   });
-  inv_rows_store(s, KEEP ? P.T2 : P.T1, a, b, P, c.tab);
+  inv_rows_store(s, KEEP ? P.T2 : P.T1, a, b, P, c.tab, tt);
 }
 
 // Second backward step.  Rows of T2 hold the column-transformed dL/dy_bar; T1 holds the spectrum of u.
@@ -415,6 +449,8 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_bwd2(LaunchCtx c, const 
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
   float2* s = sm;
   float2* o = sm + 2 * pstride(N1);
+  __shared__ float2 tt[2 * kRowTwS];
+  row_tw_init(tt, P, a, b, c.tab);
   load_rows_fft(s, P.T2, a, b, P, c.tab);
   for_mirror_pairs<4>(a, b, N1,
                       [&](int64_t gP, int64_t gQ) { return HzUPair{P.Hz[gP], P.Hz[gQ], P.T1[gP], P.T1[gQ]}; },
@@ -430,8 +466,8 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_bwd2(LaunchCtx c, const 
   });
   // every thread has read its T1 entries before the barrier that opens the inverse FFTs; they overwrite T1
   // rows a, b only
-  inv_rows_store(s, P.T2, a, b, P, c.tab);
-  inv_rows_store(o, P.T1, a, b, P, c.tab);
+  inv_rows_store(s, P.T2, a, b, P, c.tab, tt);
+  inv_rows_store(o, P.T1, a, b, P, c.tab, tt);
 }
 
 template <int MODE>
