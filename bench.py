@@ -35,9 +35,10 @@ STREAM_BYTES_PER_SAMPLE = 8  # one stereo FP32 sample
 # ------------------------------------------------------------------------------------------------
 # workloads
 # ------------------------------------------------------------------------------------------------
-def workload_layouts(name: str, rank: int = 0):
+def workload_layouts(name: str, rank: int = 0, songs: int = 64):
     if name == "uneven":
-        return W.layout_uneven_batch(64, seed=2 + 1000 * rank), "uneven batch: 64 songs, K~U{4..32}, S~U{1..8}, 5-30 s"
+        return (W.layout_uneven_batch(songs, seed=2 + 1000 * rank),
+                f"uneven batch: {songs} songs, K~U{{4..32}}, S~U{{1..8}}, 5-30 s")
     if name == "search":
         return [W.layout_single_search()], "single search song: 16 tracks x 10 s, 4 subgroups"
     if name == "plain":
@@ -313,6 +314,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uneven", choices=["uneven", "search", "plain"])
+    ap.add_argument("--songs", type=int, default=64, help="songs of the uneven batch (smaller: profiling cases)")
+    ap.add_argument("--profiler-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--per-node-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-baseline-steps", type=int, default=3)
@@ -329,7 +333,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     metric = "console fwd+bwd track-s/s batched vs per-node GPU; search-job p50/p99 latency"
-    layouts, wdesc = workload_layouts(args.workload, rank)
+    layouts, wdesc = workload_layouts(args.workload, rank, args.songs)
     config = {"workload": wdesc, "songs": len(layouts), "tracks": sum(l.num_tracks for l in layouts),
               "subgroups": sum(l.num_subgroups for l in layouts),
               "seconds": round(sum(l.num_samples for l in layouts) / FS, 2), "sample_rate": FS,
@@ -376,11 +380,15 @@ def main():
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    if args.profiler_range:
+        torch.cuda.profiler.start()
     ev0.record(con.stream)
     for _ in range(args.steps):
         losses = con.train_step(lr=1e-2)
     ev1.record(con.stream)
     torch.cuda.synchronize()
+    if args.profiler_range:
+        torch.cuda.profiler.stop()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()

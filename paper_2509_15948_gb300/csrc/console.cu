@@ -55,7 +55,7 @@ struct HostProc {
   std::vector<int> splits;       // candidate row exponents logN1 of the FFT convolution (autotuner)
   // arena offsets (bytes)
   size_t o_y = 0, o_stats = 0, o_fpart = 0, o_bpart = 0, o_taps = 0, o_dtaps = 0, o_aux = 0, o_carry = 0, o_rcarry = 0,
-         o_cagg = 0, o_nspec = 0, o_hspec = 0, o_ybar = 0, o_dhspec = 0;
+         o_cagg = 0, o_nspec = 0, o_hspec = 0, o_ybar = 0, o_dhspec = 0, o_eqg = 0;
   size_t scratch_bytes = 0;  // T1 + T2 + Hz
   size_t o_scratch = 0;      // offset inside the shared LTI scratch
 };
@@ -549,6 +549,7 @@ void stage_backward(mg_console* c, const LaunchCtx& x, Stage& s) {
       break;
     case T_E:
       run_items(c, F_EQ_OS, s.osb, [&](const Item* it, int n) { launch_eq_os_bwd(x, it, n); });
+      run_items(c, F_EQ_OS, s.osf, [&](const Item* it, int n) { launch_eq_os_du(x, it, n); });
       run_procs(c, F_FIR_ADJ, s.procs, [&](const int* p, int n) { launch_eq_dh_reduce(x, p, n); });
       run_procs(c, F_FIR_ADJ, s.procs, [&](const int* p, int n) { launch_eq_fir_adj(x, p, n); });
       break;
@@ -723,6 +724,7 @@ mg_status build_tables(mg_console* c) {
       d.hspec = (float*)A(p.o_hspec);
       d.ybar = (float*)A(p.o_ybar);
       d.dhspec = (float2*)A(p.o_dhspec);
+      d.eqg = (float2*)A(p.o_eqg);
     }
     d.aux = p.o_aux ? (float*)A(p.o_aux) : nullptr;
     d.carry = p.nchunks ? (float*)A(p.o_carry) : nullptr;
@@ -910,6 +912,7 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
       p.o_hspec = b.take((size_t)kEqOsM * sizeof(float));
       p.o_ybar = b.take((size_t)2 * p.ld * sizeof(float));
       p.o_dhspec = b.take((size_t)p.nbrows * kEqOsM * sizeof(float2));
+      p.o_eqg = b.take((size_t)p.nfrows * kEqOsM * sizeof(float2));
     }
     if (p.type == T_D) p.o_aux = b.take((2 * kDlyTaps * kDlyFir + 2 * kDlyTaps) * sizeof(float));
     if (p.type == T_R) {

@@ -3,12 +3,16 @@
 // computed by one CTA from its input segment [s0 - 1023, s0 + B + 1023) without any global FFT scratch:
 //   forward:  segment -> FFT -> x H -> IFFT -> B valid outputs, fused with the dry/wet blend and the L_g
 //             energies; the wet signal y_bar is kept for the backward;
-//   backward: a work item walks kEqChunk consecutive blocks.  Per block: U = FFT(u segment),
-//             D = FFT(dL/dy_bar on the segment), Dblk = FFT(dL/dy_bar on the block only), with
-//             dL/dy_bar = w dy + c1 y_bar_mid from the kept y_bar; du = IFFT(D H) on the block (h is even, so
-//             the correlation adjoint is the same convolution); Dblk conj(U) is summed over the item's blocks
-//             in the item's own row of a global buffer.  A per-node kernel adds the items' spectra in a fixed order and
-//             runs one inverse FFT whose real part at lags -1023..1023 is dL/dh summed over both channels.
+//   backward: a work item walks kEqChunk consecutive blocks.  Per block: D = FFT(dL/dy_bar on the segment)
+//             with dL/dy_bar = w dy + c1 y_bar_mid from the kept y_bar, Ub = FFT(u on the block only); D H is
+//             stored, and a second kernel forms du = IFFT(D H) on the block (h is even, so the correlation
+//             adjoint is the same convolution).
+//             dL/dh[j] = sum_n dL/dy_bar[n] u[n - j] = sum_m u[m] dL/dy_bar[m + j] is split over the blocks by the
+//             input position m: a block contributes IFFT(D conj(Ub)) at lags |j| <= 1023 (m + j stays inside the
+//             segment, no wrap-around), so the segment spectrum D serves both gradients.  D conj(Ub) is summed
+//             over the item's blocks in the item's own row of a global buffer; a per-node kernel adds the items'
+//             spectra in a fixed order and runs one inverse FFT whose real part at lags -1023..1023 is dL/dh
+//             summed over both channels.
 // H is real (h real and even); both channels travel packed as one complex signal.
 #include "mg_fftp.cuh"
 
@@ -18,6 +22,7 @@ namespace {
 constexpr int kOsLog = 13;
 constexpr int kOsM = 1 << kOsLog;
 constexpr int kOsThreads = 512;
+constexpr int kOsBwdThreads = 1024;
 constexpr int kOsP = pstride(kOsM);   // padded buffer stride
 }  // namespace
 
@@ -78,73 +83,88 @@ __global__ void __launch_bounds__(kOsThreads, 2) k_eq_os_fwd(LaunchCtx c, const 
   }
 }
 
-// item = (node, chunk): blocks chunk * kEqChunk ... of B = 6146 samples.  Three padded 8192-point buffers in
-// shared memory (204 KB, one CTA per SM).  The running sum of the correlation spectra stays in the item's row of
-// dhspec (each thread owns the same bins in every block, so the read-modify-write is race-free and ordered).
-__global__ void __launch_bounds__(kOsThreads, 1) k_eq_os_bwd(LaunchCtx c, const Item* __restrict__ items) {
+// item = (node, chunk): blocks chunk * kEqChunk ... of B = 6146 samples.  Two padded 8192-point buffers in
+// shared memory (139 KB) and 1024 threads; both forward transforms run as one batch, 16 elements per thread.
+// Per block the spectrum D H is stored for k_eq_os_du, and the running sum of the correlation spectra stays in
+// the item's row of dhspec (each thread owns the same bins in every block, so the read-modify-write is
+// race-free and ordered).  The inverse transform lives in its own kernel: in this loop, next to the forward
+// transforms, its index arithmetic would be hoisted into registers that spill.
+__global__ void __launch_bounds__(kOsBwdThreads, 1) k_eq_os_bwd(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   __shared__ float red[32];
-  float2* A = sm;                 // spectrum of the u segment
-  float2* Bf = sm + kOsP;         // dL/dy_bar on the segment, then du
-  float2* C = sm + 2 * kOsP;      // dL/dy_bar on the block
+  float2* D = sm;                 // dL/dy_bar on the segment, then its spectrum
+  float2* Ub = sm + kOsP;         // u on the block only, then its spectrum
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   constexpr int B = kOsM - 2 * kEqHalf;   // 6146
-  constexpr int kBins = kOsM / kOsThreads;
+  constexpr int kBins = kOsM / kOsBwdThreads;
   float2* dst = P.dhspec + (size_t)it.idx * kOsM;
-  const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
-  const float c1 = P.stats[2], c2 = P.stats[3];
-  const float inv = 1.f / kOsM;
+  const float w = dry_wet_w(c, P.qidx);
+  const float c1 = P.stats[2];
   float dwacc[1] = {0.f};
   const int nblk = (P.L + B - 1) / B;
   const int b0 = it.idx * kEqChunk, b1 = min(nblk, b0 + kEqChunk);
   for (int blk = b0; blk < b1; ++blk) {
-    const int s0 = blk * B, seg = s0 - kEqHalf;
+    const int seg = blk * B - kEqHalf;
 #pragma unroll 2
     for (int j = threadIdx.x; j < kOsM; j += blockDim.x) {
       const int s = seg + j;
-      float2 a = make_float2(0.f, 0.f), d = a, dblk = a;
+      float2 d = make_float2(0.f, 0.f), ub = d;
       if (s >= 0 && s < P.L) {
-        const float ul = P.u[s], ur = P.u[P.ld + s];
         const float yl = P.ybar[s], yr = P.ybar[P.ld + s];
         const float gl = P.dy[s], gr = P.dy[P.ld + s];
         const float gm = c1 * (yl + yr);
-        a = make_float2(ul, ur);
         d = make_float2(w * gl + gm, w * gr + gm);
         if (j >= kEqHalf && j < kEqHalf + B) {
-          dblk = d;
+          const float ul = P.u[s], ur = P.u[P.ld + s];
+          ub = make_float2(ul, ur);
           dwacc[0] += gl * (yl - ul) + gr * (yr - ur);
         }
       }
-      A[pidx(j)] = a;
-      Bf[pidx(j)] = d;
-      C[pidx(j)] = dblk;
+      D[pidx(j)] = d;
+      Ub[pidx(j)] = ub;
     }
     __syncthreads();
-    fft_p<false, 3>(A, kOsLog, 3, kOsP, c.tab.ptw);   // A, Bf, C: three batches in one set of passes
+    fft_p<false>(D, kOsLog, 2, kOsP, c.tab.ptw);   // D and Ub: one batch of two
+    float2* g = P.eqg + (size_t)blk * kOsM;
 #pragma unroll 4
     for (int t = 0; t < kBins; ++t) {
-      const int k = threadIdx.x + t * kOsThreads, e = pidx(k);
-      Bf[e] = cscale(Bf[e], P.hspec[k]);
-      const float2 prod = cmulc(C[e], A[e]);
+      const int k = threadIdx.x + t * kOsBwdThreads, e = pidx(k);
+      const float2 dk = D[e];
+      const float2 prod = cmulc(dk, Ub[e]);
       dst[k] = blk == b0 ? prod : cadd(dst[k], prod);
-    }
-    __syncthreads();
-    fft_p<true>(Bf, kOsLog, 1, kOsP, c.tab.ptw);
-#pragma unroll 2
-    for (int t = threadIdx.x; t < B; t += blockDim.x) {
-      const int s = s0 + t;
-      if (s >= P.L) break;
-      const float2 dw = cscale(Bf[pidx(kEqHalf + t)], inv);
-      const float um = c2 * (P.u[s] + P.u[P.ld + s]);
-      P.du[s] = wd * P.dy[s] + dw.x + um;
-      P.du[P.ld + s] = wd * P.dy[P.ld + s] + dw.y + um;
+      g[k] = cscale(dk, P.hspec[k]);
     }
     __syncthreads();   // the next block overwrites the buffers
   }
   float out[1];
   block_sum<1>(dwacc, red, out);
   if (threadIdx.x == 0) P.bpart[it.idx * kNPart] = out[0];
+}
+
+// item = (node, block): du on [s0, s0 + 6146) = IFFT(D H) on the block (h even: the adjoint of the
+// convolution is the same convolution) plus the dry path and the loudness-gain term.
+__global__ void __launch_bounds__(kOsThreads, 2) k_eq_os_du(LaunchCtx c, const Item* __restrict__ items) {
+  extern __shared__ float2 sm[];
+  const Item it = items[blockIdx.x];
+  const ProcDev& P = c.procs[it.proc];
+  constexpr int B = kOsM - 2 * kEqHalf;
+  const int s0 = it.idx * B;
+  const float2* g = P.eqg + (size_t)it.idx * kOsM;
+#pragma unroll 4
+  for (int k = threadIdx.x; k < kOsM; k += blockDim.x) sm[pidx(k)] = g[k];
+  __syncthreads();
+  fft_p<true>(sm, kOsLog, 1, kOsP, c.tab.ptw);
+  const float wd = dry_wet_d(c, P.qidx), c2 = P.stats[3];
+  const float inv = 1.f / kOsM;
+  for (int t = threadIdx.x; t < B; t += blockDim.x) {
+    const int s = s0 + t;
+    if (s >= P.L) break;
+    const float2 dw = cscale(sm[pidx(kEqHalf + t)], inv);
+    const float um = c2 * (P.u[s] + P.u[P.ld + s]);
+    P.du[s] = wd * P.dy[s] + dw.x + um;
+    P.du[P.ld + s] = wd * P.dy[P.ld + s] + dw.y + um;
+  }
 }
 
 // dL/dh (both channels summed into row 0, row 1 zero): the items' correlation spectra added in a fixed
@@ -173,7 +193,10 @@ void launch_eq_os_fwd(const LaunchCtx& c, const Item* items, int n) {
   if (n) k_eq_os_fwd<<<n, kOsThreads, kOsP * sizeof(float2), c.stream>>>(c, items);
 }
 void launch_eq_os_bwd(const LaunchCtx& c, const Item* items, int n) {
-  if (n) k_eq_os_bwd<<<n, kOsThreads, 3 * kOsP * sizeof(float2), c.stream>>>(c, items);
+  if (n) k_eq_os_bwd<<<n, kOsBwdThreads, 2 * kOsP * sizeof(float2), c.stream>>>(c, items);
+}
+void launch_eq_os_du(const LaunchCtx& c, const Item* items, int n) {
+  if (n) k_eq_os_du<<<n, kOsThreads, kOsP * sizeof(float2), c.stream>>>(c, items);
 }
 void launch_eq_dh_reduce(const LaunchCtx& c, const int* procs, int n) {
   if (n) k_eq_dh_reduce<<<n, kOsThreads, kOsP * sizeof(float2), c.stream>>>(c, procs);
@@ -181,7 +204,8 @@ void launch_eq_dh_reduce(const LaunchCtx& c, const int* procs, int n) {
 void init_eqos_attributes() {
   cudaFuncSetAttribute(k_eq_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, kOsP * (int)sizeof(float2));
   cudaFuncSetAttribute(k_eq_os_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kOsP * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_eq_os_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * kOsP * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_eq_os_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kOsP * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_eq_os_du, cudaFuncAttributeMaxDynamicSharedMemorySize, kOsP * (int)sizeof(float2));
   cudaFuncSetAttribute(k_eq_dh_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, kOsP * (int)sizeof(float2));
 }
 

@@ -74,6 +74,7 @@ struct ProcDev {
   float* hspec;                            // [8192] real spectrum of the FIR on the overlap-save grid
   float* ybar;                             // [2][ld] wet signal kept by the forward for the backward
   float2* dhspec;                          // [backward items][8192] summed spectra of the tap correlation
+  float2* eqg;                             // [forward blocks][8192] spectra D H of the equalizer backward
 };
 
 struct LossRes {                           // one STFT resolution of Eq. (21)
@@ -163,6 +164,7 @@ void init_eqos_attributes();
 void launch_eq_spec(const LaunchCtx&, const int* procs, int n);
 void launch_eq_os_fwd(const LaunchCtx&, const Item* items, int n);
 void launch_eq_os_bwd(const LaunchCtx&, const Item* items, int n);
+void launch_eq_os_du(const LaunchCtx&, const Item* items, int n);
 void launch_eq_dh_reduce(const LaunchCtx&, const int* procs, int n);
 void launch_col_fwd_audio(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_col_fwd_taps(const LaunchCtx&, const Item* items, int n, int maxN2G);
