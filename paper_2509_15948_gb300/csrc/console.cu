@@ -915,6 +915,7 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
       p.o_eqg = b.take((size_t)p.nfrows * kEqOsM * sizeof(float2));
     }
     if (p.type == T_D) p.o_aux = b.take((2 * kDlyTaps * kDlyFir + 2 * kDlyTaps) * sizeof(float));
+    if (p.type == T_C || p.type == T_N) p.o_aux = b.take((size_t)p.ld * sizeof(float));   // dL/dg per sample
     if (p.type == T_R) {
       const int ng = (p.nframes + kRevFG - 1) / kRevFG;
       p.o_aux = b.take((size_t)2 * ng * kRevBins * 2 * sizeof(float));

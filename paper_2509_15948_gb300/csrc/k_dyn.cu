@@ -5,7 +5,9 @@
 //   pass 3 (apply): every chunk rescans from its carried state with a warp-shuffle scan of the
 //                   per-thread states (decay alpha^16 per thread), then applies the gain law
 //                   (Eqs. 13-16) and Eq. (15), fused with the dry/wet blend.
-// The adjoint runs the same structure in reverse: lambda[n] = dL/dg[n] + alpha lambda[n+1].
+// The adjoint runs the same structure in reverse: lambda[n] = dL/dg[n] + alpha lambda[n+1].  Its first pass
+// also does all the per-sample work that does not depend on lambda (the gain law, its partials, dL/dg and
+// the lambda-free part of du, kept in global memory), so the third pass is only the two recursions.
 #include "mg_fft.cuh"
 
 namespace mg {
@@ -17,6 +19,7 @@ constexpr int kThreads = kDynChunk / kPer;
 
 struct DynParams {
   float alpha, beta, lna, T, W, R, Rm1;   // Rm1 = R - 1 = exp(p3)   // beta = 1 - alpha, evaluated as sigmoid(-p0) (no cancellation near 1)
+  float invR, invR2, inv2W, inv4W;        // 1/R, 1/R^2, 1/(2W), 1/(4W): the gain laws multiply instead of dividing
   bool gate;
 };
 
@@ -31,23 +34,27 @@ __device__ __forceinline__ DynParams dyn_params(const ProcDev& P) {
   d.W = expf(P.p[2]);
   d.Rm1 = expf(P.p[3]);
   d.R = 1.f + d.Rm1;
+  d.invR = 1.f / d.R;
+  d.invR2 = d.invR * d.invR;
+  d.inv2W = 0.5f / d.W;
+  d.inv4W = 0.25f / d.W;
   d.gate = P.type == T_N;
   return d;
 }
 
-// Gain laws (Eqs. 13-14 compressor, Eq. 16 noisegate) with their partial derivatives.
+// Gain laws (Eqs. 13-14 compressor, Eq. 16 noisegate) with their partial derivatives; t = q / (2W) in the knees.
 __device__ __forceinline__ float gain_law(const DynParams& d, float G, float& dG, float& dT, float& dW, float& dR) {
   const float T = d.T, W = d.W, R = d.R, Rm1 = d.Rm1;
   if (!d.gate) {
     if (G >= T + W) {
-      dG = 1.f / R; dT = Rm1 / R; dW = 0.f; dR = -(G - T) / (R * R);
-      return T + (G - T) / R;
+      dG = d.invR; dT = Rm1 * d.invR; dW = 0.f; dR = -(G - T) * d.invR2;
+      return T + (G - T) * d.invR;
     }
     if (G >= T - W) {
-      const float q = G - T + W, k = -Rm1 / R;
-      dG = 1.f + k * q / (2.f * W); dT = -k * q / (2.f * W);
-      dW = k * (q / (2.f * W) - q * q / (4.f * W * W)); dR = -(q * q) / (4.f * W * R * R);
-      return G + k * q * q / (4.f * W);
+      const float q = G - T + W, k = -Rm1 * d.invR, t = q * d.inv2W, qq = q * q * d.inv4W;
+      dG = 1.f + k * t; dT = -k * t;
+      dW = k * (t - t * t); dR = -qq * d.invR2;
+      return G + k * qq;
     }
     dG = 1.f; dT = 0.f; dW = 0.f; dR = 0.f;
     return G;
@@ -57,10 +64,10 @@ __device__ __forceinline__ float gain_law(const DynParams& d, float G, float& dG
     return G;
   }
   if (G >= T - W) {
-    const float q = G - T - W, k = -Rm1;
-    dG = 1.f + k * q / (2.f * W); dT = -k * q / (2.f * W);
-    dW = k * (-q / (2.f * W) - q * q / (4.f * W * W)); dR = -(q * q) / (4.f * W);
-    return G + k * q * q / (4.f * W);
+    const float q = G - T - W, k = -Rm1, t = q * d.inv2W, qq = q * q * d.inv4W;
+    dG = 1.f + k * t; dT = -k * t;
+    dW = k * (-t - t * t); dR = -qq;
+    return G + k * qq;
   }
   dG = R; dT = -Rm1; dW = 0.f; dR = G - T;
   return T + R * (G - T);
@@ -94,6 +101,25 @@ __device__ __forceinline__ void store16(float* base, int ld, int L, int n0, cons
       *reinterpret_cast<float4*>(base + n) = make_float4(l[4 * j], l[4 * j + 1], l[4 * j + 2], l[4 * j + 3]);
       *reinterpret_cast<float4*>(base + ld + n) = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
     }
+  }
+}
+
+// The same for a mono buffer of L samples.
+__device__ __forceinline__ void load16m(const float* base, int L, int n0, float (&v)[kPer]) {
+#pragma unroll
+  for (int j = 0; j < kPer / 4; ++j) {
+    const int n = n0 + 4 * j;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n < L) a = *reinterpret_cast<const float4*>(base + n);
+    v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
+  }
+}
+
+__device__ __forceinline__ void store16m(float* base, int L, int n0, const float (&v)[kPer]) {
+#pragma unroll
+  for (int j = 0; j < kPer / 4; ++j) {
+    const int n = n0 + 4 * j;
+    if (n < L) *reinterpret_cast<float4*>(base + n) = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
   }
 }
 
@@ -247,11 +273,14 @@ __device__ __forceinline__ float dyn_dg(const DynParams& d, float w, float g, fl
   acc.dW += dE * dW;
   acc.dR += dE * dR;
   acc.dw += gl * (gain * ul - ul) + gr * (gain * ur - ur);
-  return dE * (dG - 1.f) / (g + kEnvEps);
+  return dE * (dG - 1.f) * __frcp_rn(g + kEnvEps);
 }
 
+// Backward, pass 1: everything that does not depend on lambda.  Per sample dL/dg (to aux) and the part of du
+// without the envelope term, w.r.t. both channels (to du); per chunk the zero-start lambda aggregate and the
+// partials of dL/dT, dL/dW, dL/dR and dL/dw.
 __global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_agg(LaunchCtx c, const Item* __restrict__ items) {
-  __shared__ float sm[32];
+  __shared__ float sm[32 * 5];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const DynParams d = dyn_params(P);
@@ -275,14 +304,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_agg(LaunchCtx c, const 
     g = d.alpha * g + d.beta * (m * m);
     float gain;
     dg[j] = dyn_dg(d, w, g, l[j], r[j], gl[j], gr[j], gain, acc);
+    l[j] = wd * gl[j] + gain * (w * gl[j]);
+    r[j] = wd * gr[j] + gain * (w * gr[j]);
   }
+  store16(P.du, P.ld, P.L, n0, l, r);
+  store16m(P.aux, P.L, n0, dg);
   float lam = 0.f;
 #pragma unroll
   for (int j = kPer - 1; j >= 0; --j) lam = dg[j] + d.alpha * lam;
-  float v[1] = {lam * expf((float)(kPer * threadIdx.x) * d.lna)};
-  float out[1];
-  block_sum<1>(v, sm, out);
-  if (threadIdx.x == 0) P.chunkagg[it.idx] = out[0];
+  float v[5] = {lam * expf((float)(kPer * threadIdx.x) * d.lna), acc.dT, acc.dW, acc.dR, acc.dw};
+  float out[5];
+  block_sum<5>(v, sm, out);
+  if (threadIdx.x == 0) {
+    P.chunkagg[it.idx] = out[0];
+    float* bp = P.bpart + (size_t)it.idx * kNPart;
+#pragma unroll
+    for (int j = 1; j < 5; ++j) bp[j] = out[j];
+  }
 }
 
 __global__ void k_dyn_bwd_carry(LaunchCtx c, const int* __restrict__ procs, int n) {
@@ -298,32 +336,32 @@ __global__ void k_dyn_bwd_carry(LaunchCtx c, const int* __restrict__ procs, int 
   }
 }
 
+// Backward, pass 3: lambda[n] = dL/dg[n] + alpha lambda[n+1] from the chunk's carried state, then
+// du += 2 beta lambda m on both channels and the partial of dL/dalpha = sum lambda[n] (g[n-1] - x[n]).
 __global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_apply(LaunchCtx c, const Item* __restrict__ items) {
-  __shared__ float sm[32 * 5];
+  __shared__ float sm[32];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const DynParams d = dyn_params(P);
-  const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
-  float l[kPer], r[kPer], gl[kPer], gr[kPer];
+  float l[kPer], r[kPer], dg[kPer];
   load16(P.u, P.ld, P.L, n0, l, r);
-  load16(P.dy, P.ld, P.L, n0, gl, gr);
+  load16m(P.aux, P.L, n0, dg);
+  float m[kPer];
   float s = 0.f;
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
-    const float m = l[j] + r[j];
-    s = d.alpha * s + d.beta * (m * m);
+    m[j] = l[j] + r[j];
+    s = d.alpha * s + d.beta * (m[j] * m[j]);
   }
-  const float gin = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
-  float gv[kPer], dg[kPer], gains[kPer];
-  DynAdj acc = {0.f, 0.f, 0.f, 0.f};
-  float g = gin;
+  load16(P.du, P.ld, P.L, n0, l, r);
+  float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
+  float ex[kPer];
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
-    const float m = l[j] + r[j];
-    g = d.alpha * g + d.beta * (m * m);
-    gv[j] = g;
-    dg[j] = dyn_dg(d, w, g, l[j], r[j], gl[j], gr[j], gains[j], acc);
+    const float x = m[j] * m[j];
+    ex[j] = g - x;
+    g = d.alpha * g + d.beta * x;
   }
   float rl = 0.f;
 #pragma unroll
@@ -333,25 +371,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_apply(LaunchCtx c, cons
 #pragma unroll
   for (int j = kPer - 1; j >= 0; --j) {
     lam = dg[j] + d.alpha * lam;
-    const float m = l[j] + r[j];
-    const float x = m * m;
-    const float gprev = j > 0 ? gv[j - 1] : gin;
-    dalpha += lam * (gprev - x);
-    const float dx2m = d.beta * lam * 2.f * m;
-    const float ol = wd * gl[j] + gains[j] * (w * gl[j]) + dx2m;
-    const float orr = wd * gr[j] + gains[j] * (w * gr[j]) + dx2m;
-    l[j] = ol;
-    r[j] = orr;
+    dalpha += lam * ex[j];
+    const float dx2m = d.beta * lam * 2.f * m[j];
+    l[j] += dx2m;
+    r[j] += dx2m;
   }
   store16(P.du, P.ld, P.L, n0, l, r);
-  float v[5] = {dalpha, acc.dT, acc.dW, acc.dR, acc.dw};
-  float out[5];
-  block_sum<5>(v, sm, out);
-  if (threadIdx.x == 0) {
-    float* bp = P.bpart + (size_t)it.idx * kNPart;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) bp[j] = out[j];
-  }
+  float v[1] = {dalpha};
+  float out[1];
+  block_sum<1>(v, sm, out);
+  if (threadIdx.x == 0) P.bpart[(size_t)it.idx * kNPart] = out[0];
 }
 
 void launch_dyn_fwd_agg(const LaunchCtx& c, const Item* items, int n) {

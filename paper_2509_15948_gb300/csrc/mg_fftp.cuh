@@ -256,6 +256,9 @@ __device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int
   __syncthreads();
 }
 
+// floor(x / 3) for 0 <= x < 2^31 (multiply by the rounded-up 2^33 / 3, exact over that range)
+__device__ __forceinline__ int div3(int x) { return (int)(__umulhi((unsigned)x, 0xAAAAAAABu) >> 1); }
+
 // Later passes: p = 3 * 2^lp2, radix R = 2^LOGR; butterfly i < M / R, k = i mod p, twiddle w_M^{r k M / (R p)}.
 template <bool INV, int R, int LOGR>
 __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int bs, int lp2,
@@ -270,8 +273,8 @@ __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int
     const int it = tid + s * nth;
     ob[s] = -1;
     if (it < total) {
-      const int b = it / MR, i = it - b * MR;
-      const int k = i - p * (i / p);
+      const int b = div3(it >> (a - LOGR)), i = it - b * MR;   // it / MR, MR = 3 * 2^(a - LOGR)
+      const int k = i - p * div3(i >> lp2);                       // i mod p, p = 3 * 2^lp2
       const float2* src = d + b * bs;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[s][r] = src[pidx(i + r * MR)];
@@ -284,7 +287,7 @@ __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
     if (ob[s] >= 0) {
-      const int b = (tid + s * nth) / MR;
+      const int b = div3((tid + s * nth) >> (a - LOGR));
       const int e0 = ob[s] - b * bs;
       float2* dst = d + b * bs;
 #pragma unroll

@@ -61,7 +61,8 @@ struct ProcDev {
   float2* Hz;
   float* taps;                             // [2][Nh]
   float* dtaps;                            // [2][Nh]
-  float* aux;                              // type scratch (delay: c_m and d_m; reverb: adjoint partials)
+  float* aux;                              // type scratch (delay: c_m and d_m; reverb: adjoint partials;
+                                           // compressor, noisegate: dL/dg per sample)
   // envelope scans (c, n)
   float* carry;                            // [nchunks] forward state entering each chunk
   float* rcarry;                           // [nchunks] reverse state entering each chunk from the right
