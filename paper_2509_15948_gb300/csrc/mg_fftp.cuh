@@ -174,12 +174,16 @@ __device__ __forceinline__ void twiddle(float2 (&x)[R], const float2* __restrict
   }
 }
 
-template <bool INV, int R, int LOGR, int SLOTS = 1>
+// AL (transforms of at least 256 points): the load stride M/R and the store stride p are multiples of 16, or
+// p = 1 with R = 16 and 16-aligned outputs, so every padded address is a base plus a multiple of a per-pass
+// padded stride; otherwise each address is padded on its own.
+template <bool INV, int R, int LOGR, int SLOTS, bool AL>
 __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, int bs, int lp,
                                      const float2* __restrict__ ptw) {
   constexpr int PER = SLOTS * 16 / R;
   const int MR = 1 << (logM - LOGR), p = 1 << lp, total = nb << (logM - LOGR);
   const int nth = blockDim.x, tid = threadIdx.x;
+  const int lstr = MR + (MR >> 4), sstr = p == 1 ? 1 : p + (p >> 4);
   float2 v[PER][R];
   int ob[PER];
 #pragma unroll
@@ -188,23 +192,36 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
     ob[s] = -1;
     if (it < total) {
       const int b = it >> (logM - LOGR), i = it & (MR - 1), k = i & (p - 1);
-      const float2* src = d + b * bs;
+      if (AL) {
+        const float2* src = d + b * bs + pidx(i);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[s][r] = src[pidx(i + r * MR)];
+        for (int r = 0; r < R; ++r) v[s][r] = src[r * lstr];
+      } else {
+        const float2* src = d + b * bs;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[s][r] = src[pidx(i + r * MR)];
+      }
       if (p > 1) twiddle<INV, R>(v[s], ptw + ptw_base(lp, LOGR) + k, p);
       dftR<INV, R>(v[s]);
-      ob[s] = b * bs + (i - k) * R + k;   // + q p, padded at store
+      const int e0 = (i - k) * R + k;   // + q p
+      ob[s] = b * bs + (AL ? pidx(e0) : e0);
     }
   }
   __syncthreads();
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
     if (ob[s] >= 0) {
-      const int b = (tid + s * nth) >> (logM - LOGR);
-      const int e0 = ob[s] - b * bs;
-      float2* dst = d + b * bs;
+      if (AL) {
+        float2* dst = d + ob[s];
 #pragma unroll
-      for (int q = 0; q < R; ++q) dst[pidx(e0 + q * p)] = v[s][q];
+        for (int q = 0; q < R; ++q) dst[q * sstr] = v[s][q];
+      } else {
+        const int b = (tid + s * nth) >> (logM - LOGR);
+        const int e0 = ob[s] - b * bs;
+        float2* dst = d + b * bs;
+#pragma unroll
+        for (int q = 0; q < R; ++q) dst[pidx(e0 + q * p)] = v[s][q];
+      }
     }
   }
   __syncthreads();
@@ -315,14 +332,23 @@ __device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const floa
 // d[b * bs + pidx(e)]), in place.  Requires nb * M <= 16 * SLOTS * blockDim.x (SLOTS x 16 elements per thread
 // and pass).  Forward: exp(-2 pi i nk/M); inverse: exp(+...), unscaled.  The caller synchronises before the
 // call; the call ends with a barrier.
+namespace fftp {
+template <bool INV, int SLOTS, bool AL>
+__device__ __forceinline__ void fft_p_impl(float2* __restrict__ d, int logM, int nb, int bs,
+                                           const float2* __restrict__ ptw) {
+  int lp = 0;
+  for (; logM - lp >= 4; lp += 4) pass<INV, 16, 4, SLOTS, AL>(d, logM, nb, bs, lp, ptw);
+  const int rem = logM - lp;
+  if (rem == 3) pass<INV, 8, 3, SLOTS, AL>(d, logM, nb, bs, lp, ptw);
+  else if (rem == 2) pass<INV, 4, 2, SLOTS, AL>(d, logM, nb, bs, lp, ptw);
+  else if (rem == 1) pass<INV, 2, 1, SLOTS, AL>(d, logM, nb, bs, lp, ptw);
+}
+}  // namespace fftp
+
 template <bool INV, int SLOTS = 1>
 __device__ void fft_p(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ ptw) {
-  int lp = 0;
-  for (; logM - lp >= 4; lp += 4) fftp::pass<INV, 16, 4, SLOTS>(d, logM, nb, bs, lp, ptw);
-  const int rem = logM - lp;
-  if (rem == 3) fftp::pass<INV, 8, 3, SLOTS>(d, logM, nb, bs, lp, ptw);
-  else if (rem == 2) fftp::pass<INV, 4, 2, SLOTS>(d, logM, nb, bs, lp, ptw);
-  else if (rem == 1) fftp::pass<INV, 2, 1, SLOTS>(d, logM, nb, bs, lp, ptw);
+  if (logM >= 8) fftp::fft_p_impl<INV, SLOTS, true>(d, logM, nb, bs, ptw);
+  else fftp::fft_p_impl<INV, SLOTS, false>(d, logM, nb, bs, ptw);
 }
 
 }  // namespace mg
