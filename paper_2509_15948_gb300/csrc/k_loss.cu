@@ -36,16 +36,25 @@ __device__ __forceinline__ float2 chan(int c, float2 XL, float2 XR) {
   return csub(XL, XR);
 }
 
-__device__ __forceinline__ float band_value(const LossRes& R, const float2* Z, int b, int c) {
-  float s = 0.f;
-  for (int e = R.band_beg[b]; e < R.band_beg[b + 1]; ++e) {
-    const int k = R.band_bin[e];
-    float2 XL, XR;
-    bin_spectra(Z, k, R.nfft, XL, XR);
+// After the magnitude pass a frame holds, for bin k in [0, n/2], the weighted magnitudes
+// sqrt(A_k^2 |X_c|^2 + 1e-8) of channels 0, 1 at slot pidx(k) and of channels 2, 3 at mag_slot2(k): the
+// mirror slot pidx(n - k), or for the self-mirrored bins 0 and n/2 two padding slots no element uses
+// (pidx(n) = the last slot of the padded frame, and slot 16).
+__device__ __forceinline__ int mag_slot2(int k, int n) {
+  return k == 0 ? pidx(n) : (k == (n >> 1) ? 16 : pidx(n - k));
+}
+
+__device__ __forceinline__ float4 bin_mags(const LossRes& R, const float2* Z, int k) {
+  float2 XL, XR;
+  bin_spectra(Z, k, R.nfft, XL, XR);
+  const float a = R.aw2[k];
+  float m[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
     const float2 X = chan(c, XL, XR);
-    s = fmaf(R.band_w[e], sqrtf(R.aw2[k] * (X.x * X.x + X.y * X.y) + kMagEps), s);
+    m[c] = sqrtf(a * (X.x * X.x + X.y * X.y) + kMagEps);
   }
-  return s;
+  return make_float4(m[0], m[1], m[2], m[3]);
 }
 
 __device__ __forceinline__ void load_frames(float2* sm, const float* x, int ld, int L, const LossRes& R, int t0, int nb) {
@@ -93,10 +102,37 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
   float* Yt = S.Y[it.y];
   float* Yk = S.Yh[it.y];
   if (mode != 2) {
+    // magnitudes of the four channels per bin, in place (each thread owns the pair k, n - k; the thread of
+    // k = 0 also takes k = n/2)
+    const int half = n >> 1, lh = R.log_nfft - 1;
+    __syncthreads();   // mode 3: every thread has copied its part of the spectrum out
+    for (int e = threadIdx.x; e < nb << lh; e += blockDim.x) {
+      const int f = e >> lh, k = e & (half - 1);
+      float2* Z = sm + f * bs;
+      if (k == 0) {
+        const float4 m0 = bin_mags(R, Z, 0), mh = bin_mags(R, Z, half);
+        Z[pidx(0)] = make_float2(m0.x, m0.y);
+        Z[mag_slot2(0, n)] = make_float2(m0.z, m0.w);
+        Z[pidx(half)] = make_float2(mh.x, mh.y);
+        Z[mag_slot2(half, n)] = make_float2(mh.z, mh.w);
+      } else {
+        const float4 m = bin_mags(R, Z, k);
+        Z[pidx(k)] = make_float2(m.x, m.y);
+        Z[pidx(n - k)] = make_float2(m.z, m.w);
+      }
+    }
+    __syncthreads();
+    // band values from the magnitudes, one thread per (frame, band, channel)
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int e = threadIdx.x; e < nb * nbands * 4; e += blockDim.x) {
-      const int f = e / (nbands * 4), r = e % (nbands * 4), b = r >> 2, ch = r & 3;
-      const float yh = band_value(R, sm + f * bs, b, ch);
+      const int f = e / (nbands * 4), r = e - f * (nbands * 4), b = r >> 2, ch = r & 3;
+      const float* Zf = reinterpret_cast<const float*>(sm + f * bs);
+      float yh = 0.f;
+      for (int q = R.band_beg[b]; q < R.band_beg[b + 1]; ++q) {
+        const int k = R.band_bin[q];
+        const int slot = ch < 2 ? pidx(k) : mag_slot2(k, n);
+        yh = fmaf(R.band_w[q], Zf[2 * slot + (ch & 1)], yh);
+      }
       const int set = ch < 2 ? 0 : ch - 1;
       const size_t yi = ((size_t)(t0 + f) * nbands + b) * 4 + ch;
       float* ydst = Yt + yi;
