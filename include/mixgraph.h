@@ -67,7 +67,9 @@ typedef struct {
   int32_t n_resolutions;       /* 1..3 STFT resolutions of Eq. (21) */
   int32_t n_fft[3];            /* FFT sizes, powers of two in [64, 8192] (e.g. 512, 2048, 8192) */
   int32_t hop_div;             /* hop = n_fft / hop_div (4 in Sec. 5.1) */
-  int32_t n_mels;              /* Mel bands (96 in Sec. 5.1); 0 = linear-frequency bins */
+  int32_t n_mels;              /* Mel bands (96 in Sec. 5.1); 0 = linear-frequency bins.  Per resolution,
+                                  bands (n_fft / 2 + 1 when linear) x 8192 / n_fft x 4 must be at most 40192
+                                  (the loss adjoint's per-item buffer), else MG_ERR_INVALID */
   int32_t a_weighting;         /* 1 = A-weighting before the STFT (Sec. 5.1) */
   int64_t warmup_samples;      /* frames starting before this sample are left out of the loss */
   float alpha_lr, alpha_m, alpha_s;  /* Eq. (20) weights (0.5, 0.25, 0.25) */

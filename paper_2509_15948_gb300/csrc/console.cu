@@ -148,6 +148,7 @@ struct mg_console {
   std::vector<ProcDev> hpd;
   std::vector<SongDev> hsd;
   std::vector<LossRes> hres;
+  int loss_max_dy = 0;            // floats of the loss adjoint's per-item band gradients (largest resolution)
   std::vector<Stage> stages;      // forward order
   // sums
   DevVec<float*> sum_out;
@@ -241,6 +242,11 @@ mg_status validate(mg_console* c, const mg_console_desc* d, const mg_song_desc* 
     if (d->hop_div < 1 || nf % d->hop_div) return fail(c, MG_ERR_INVALID, "hop_div must divide n_fft");
   }
   if (d->n_mels < 0 || d->n_mels > 512) return fail(c, MG_ERR_INVALID, "n_mels must be in [0, 512]");
+  for (int r = 0; r < d->n_resolutions; ++r) {
+    const int nf = d->n_fft[r], bands = d->n_mels > 0 ? d->n_mels : nf / 2 + 1;
+    if ((8192 / nf) * bands * 4 > kLossMaxDy)
+      return fail(c, MG_ERR_INVALID, "bands x frames per loss work item exceed shared memory (fewer n_mels or a larger n_fft)");
+  }
   if (d->warmup_samples < 0) return fail(c, MG_ERR_INVALID, "negative warmup_samples");
   if (d->retain_spectra < -1 || d->retain_spectra > 1) return fail(c, MG_ERR_INVALID, "retain_spectra must be -1, 0 or 1");
   for (int i = 0; i < n; ++i) {
@@ -581,7 +587,7 @@ void loss_forward(mg_console* c, const LaunchCtx& x, int mode, float* out_losses
     auto& L = c->loss_items[r];
     if (!L.h.empty())
       run(c, F_LOSS_FWD, [&] {   // frame kernel: 0 target spectrogram, 1 loss partials (losses and trials)
-        launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), mode == 0 ? 0 : (mode == 1 ? 3 : 1), 8192);
+        launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), mode == 0 ? 0 : (mode == 1 ? 3 : 1), c->loss_max_dy);
       });
   }
   if (mode != 0) run_procs(c, F_FINALIZE, c->all_lti_present, [&](const int* p, int n) { launch_node_stats(x, p, n, 1); });
@@ -597,7 +603,7 @@ void backward_pass(mg_console* c, const LaunchCtx& x) {
     for (int r = 0; r < c->nres; ++r) {
       auto& L = c->loss_items[r];
       if (!L.h.empty())
-        run(c, F_LOSS_BWD, [&] { launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), 2, 8192); });
+        run(c, F_LOSS_BWD, [&] { launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), 2, c->loss_max_dy); });
     }
     run_items(c, F_LOSS_GATHER, c->gather_items,
               [&](const Item* it, int n) { launch_loss_gather(x, c->d_songs, c->d_res, c->nres, it, n); });
@@ -1224,6 +1230,8 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     R.bin_band = (const int*)up_table(kband.data(), kband.size() * sizeof(int));
     R.bin_w = (const float*)up_table(kw.data(), kw.size() * sizeof(float));
   }
+  c->loss_max_dy = 0;   // at most kLossMaxDy (validated with the description)
+  for (const LossRes& R : c->hres) c->loss_max_dy = std::max(c->loss_max_dy, (8192 / R.nfft) * R.nbands * 4);
   if (upload(c, c->hres, &c->d_res) != MG_OK) return MG_ERR_CUDA;
   // songs on device
   c->hsd.assign(c->songs.size(), SongDev{});
@@ -1673,7 +1681,7 @@ mg_status mg_update_audio(mg_console* c, int32_t song, const float* sources, con
     LaunchCtx x = make_ctx(c, nullptr);
     for (int r = 0; r < c->nres; ++r) {
       const int2 rg = c->song_litems[song][r];
-      if (rg.y > 0) launch_loss_frames(x, c->d_songs, c->d_res, c->loss_items[r].d + rg.x, rg.y, 0, 8192);
+      if (rg.y > 0) launch_loss_frames(x, c->d_songs, c->d_res, c->loss_items[r].d + rg.x, rg.y, 0, c->loss_max_dy);
     }
     launch_loss_finalize_mode(x, c->d_songs + song, 1, c->d_res, c->nres, c->d_alphas, 0, nullptr, nullptr, 0);
   }

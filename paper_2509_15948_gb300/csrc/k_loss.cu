@@ -18,7 +18,7 @@ constexpr float kLogEps = 1e-5f;
 constexpr float kMagEps = 1e-8f;
 // frames of one item live in a padded layout: frame f, sample j at sm[f * pstride(n) + pidx(j)];
 // an item holds 8192 samples (8192 / n_fft <= 128 frames), so the buffer needs 8192 + 512 + 128 entries.
-constexpr int kFrameBuf = 8192 + 512 + 128;
+constexpr int kFrameBuf = kLossFrameBuf;
 
 // channel magnitudes^2 of bin k (|X_L|^2, |X_R|^2, |X_M|^2, |X_S|^2) and the complex X_L, X_R
 __device__ __forceinline__ void bin_spectra(const float2* Z, int k, int n, float2& XL, float2& XR) {
@@ -235,10 +235,9 @@ __global__ void __launch_bounds__(256) k_loss_gather(const SongDev* __restrict__
 }
 
 void launch_loss_frames(const LaunchCtx& c, const SongDev* songs, const LossRes* res, const int4* items, int n,
-                        int mode, int maxfft) {
+                        int mode, int max_dy) {
   if (!n) return;
-  (void)maxfft;
-  const size_t smem = kFrameBuf * sizeof(float2) + (mode == 2 ? (size_t)(4096 + 128) * 4 * sizeof(float) : 0);
+  const size_t smem = kFrameBuf * sizeof(float2) + (mode == 2 ? (size_t)max_dy * sizeof(float) : 0);
   k_loss_frames<<<n, kLossThreads, smem, c.stream>>>(c, songs, res, items, mode);
 }
 
@@ -249,7 +248,7 @@ void launch_loss_gather(const LaunchCtx& c, const SongDev* songs, const LossRes*
 
 void init_loss_attributes() {
   cudaFuncSetAttribute(k_loss_frames, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kFrameBuf * sizeof(float2) + (4096 + 128) * 4 * sizeof(float));
+                       kFrameBuf * sizeof(float2) + kLossMaxDy * sizeof(float));
 }
 
 }  // namespace mg

@@ -26,6 +26,10 @@ constexpr int kRevFG = 16;                 // frames per reverb work item
 constexpr int kDynChunk = 4096;            // samples per envelope-scan work item (256 threads x 16)
 constexpr int kElemTile = 4096;            // samples per elementwise work item
 constexpr float kEnvEps = 1e-8f;           // G_u = ln(g + eps)
+constexpr int kLossFrameBuf = 8192 + 512 + 128;   // padded frames of one loss work item (float2)
+// floats of the loss adjoint's band gradients that fit next to the frames in the 227 KB of shared memory a
+// CTA may hold (1 KB left for the kernel's static shared memory)
+constexpr int kLossMaxDy = (227 * 1024 - 1024 - kLossFrameBuf * 8) / 4;
 constexpr int kEqOsM = 8192;               // overlap-save FFT size of the equalizer
 constexpr int kEqOsFwdBlock = kEqOsM - 2 * kEqHalf;        // 6146 outputs per forward block
 constexpr int kEqChunk = 8;                 // equalizer backward: blocks per work item (spectra summed in registers)
@@ -184,8 +188,9 @@ void launch_col_du(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_col_dh(const LaunchCtx&, const Item* items, int n, int maxN2G);
 // reductions, loss, optimiser
 void launch_node_stats(const LaunchCtx&, const int* procs, int n, int fwd);
+// max_dy: floats of the adjoint's band-gradient buffer, max over resolutions of (8192 / n_fft) bands 4
 void launch_loss_frames(const LaunchCtx&, const SongDev* songs, const LossRes* res, const int4* items, int n,
-                        int mode, int maxfft);
+                        int mode, int max_dy);
 void launch_loss_finalize_mode(const LaunchCtx&, const SongDev* songs, int nsongs, const LossRes* res, int nres,
                                const float* alphas, int mode, float* out_losses, float* out_la, int la_stride);
 void launch_loss_gather(const LaunchCtx&, const SongDev* songs, const LossRes* res, int nres, const Item* items,

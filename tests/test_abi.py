@@ -52,6 +52,11 @@ def test_plan_type_mask_and_validation():
         M.plan([M.Song(2, 1, [0, 3], 1000)])            # subgroup index out of range
     with pytest.raises(M.MgError):
         M.plan(s, M.ConsoleConfig(n_fft=(500,)))         # FFT size not a power of two
+    # the loss adjoint keeps bands x 4 channels of every frame of a work item (8192 samples) in shared
+    # memory: 512 Mel bands over 128 frames of 64 points do not fit, 96 bands do
+    with pytest.raises(M.MgError):
+        M.plan(s, M.ConsoleConfig(n_fft=(64,), n_mels=512))
+    assert M.plan(s, M.ConsoleConfig(n_fft=(512,), n_mels=96))["n_processors"] > 0
 
 
 def test_console_needs_a_gpu_and_fails_loudly():
