@@ -133,6 +133,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Algorithmic bytes per complex point of a node's four-step FFT grid (N = f 2^k points) moved by one launch of
+# the row kernels of the reverb/delay convolution with retained spectra (reads and writes of the N-point
+# arrays T1, T2, Hz): k_row_bwd2 reads the dL/dy_bar spectrum, Hz and the input spectrum and writes dU and dH;
+# k_row_conv reads the input spectrum and Hz and writes the kept spectrum and the product; k_row_fwd_hz
+# transforms Hz in place.
+KERNEL_BYTES_PER_POINT = {"row_bwd2": 40, "row_conv": 32, "row_hz": 16}
+# ncu DRAM bytes (read + write) per grid point of k_row_bwd2, from the one-song capture summarised in
+# profiles/, valid while the kernel's sources hash to KERNEL_SRC_SHA1 (otherwise the traffic is reported null)
+ROW_BWD2_DRAM_BYTES_PER_POINT = 32.6
+KERNEL_SRC_SHA1 = "b0f6005fd0bb6d732eb1f403403a2acf56ed011c"
+KERNEL_SRCS = ("k_conv.cu", "mg_fftp.cuh", "mg_fft.cuh", "mg_internal.cuh")
+
+
+def kernel_src_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for name in KERNEL_SRCS:
+        with open(os.path.join(ROOT, "paper_2509_15948_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -404,18 +426,41 @@ def main():
     value = world * track_seconds / (ms_per_step / 1e3)
     finite = bool(torch.isfinite(losses).all().item())
 
-    # roofline of the dominant stage: algorithmic bytes (5 streams per node, fwd+bwd) / its device time
+    # roofline of the dominant kernel (largest device time per step): its algorithmic bytes per launch over its
+    # CUDA-event time per launch (events on the console stream around each launch of the family); also the
+    # dominant stage against the byte model of 5 streams per node, and the whole step
     peak, peak_kind = measured_peaks()
     proc_stages = {k: v for k, v in stage.items() if k in "ecnsgdr"}
     dom = max(proc_stages, key=lambda k: proc_stages[k][0])
     dom_ms_per_step = proc_stages[dom][0] / args.steps
     dom_bytes = type_bytes[dom]
-    achieved = dom_bytes / (dom_ms_per_step / 1e3) / 1e9
+    stage_achieved = dom_bytes / (dom_ms_per_step / 1e3) / 1e9
     step_achieved = tot_bytes / (ms_per_step / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"stage '{dom}' (all its fwd+bwd kernels)", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{peak_kind} hbm_gbs",
-                "step": {"achieved": step_achieved, "frac": step_achieved / peak, "model_bytes": tot_bytes}}
+    stage_roof = {"stage": dom, "achieved": stage_achieved, "frac": stage_achieved / peak, "model_bytes": dom_bytes,
+                  "ms_per_step": dom_ms_per_step}
+    fam_step = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in fam.items() if v[1] > 0}
+    dom_k = max(fam_step, key=lambda k: fam_step[k][0])
+    ptypes = con.processor_types()
+    grid_points = sum(int(f) << int(logn) for (f, logn, _), t in zip(con.fft_sizes(), ptypes) if f and t in "dr")
+    if dom_k in KERNEL_BYTES_PER_POINT and grid_points:
+        launches = fam_step[dom_k][1]
+        ms_launch = fam_step[dom_k][0] / launches
+        bytes_launch = KERNEL_BYTES_PER_POINT[dom_k] * grid_points / launches
+        achieved = bytes_launch / (ms_launch / 1e3) / 1e9
+        traffic = None
+        if dom_k == "row_bwd2" and ROW_BWD2_DRAM_BYTES_PER_POINT and KERNEL_SRC_SHA1 == kernel_src_sha1():
+            traffic = ROW_BWD2_DRAM_BYTES_PER_POINT * grid_points / launches
+        roofline = {"bound": "hbm", "kernel": f"k_{dom_k}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic, "bytes_per_launch": bytes_launch,
+                    "ms_per_launch": ms_launch, "launches_per_step": launches,
+                    "byte_model": f"{KERNEL_BYTES_PER_POINT[dom_k]} B per complex grid point, {grid_points} points",
+                    "peak_source": f"{peak_kind} hbm_gbs (copy burst)"}
+    else:
+        roofline = {"bound": "hbm", "kernel": f"stage '{dom}' (all its fwd+bwd kernels)", "achieved": stage_achieved,
+                    "peak": peak, "unit": "GB/s", "frac": stage_achieved / peak, "traffic": None,
+                    "peak_source": f"{peak_kind} hbm_gbs (copy burst)"}
+    roofline["stage"] = stage_roof
+    roofline["step"] = {"achieved": step_achieved, "frac": step_achieved / peak, "model_bytes": tot_bytes}
 
     # ---------------- one launch per node (same kernels, one-by-one processing) ----------------
     per_node = None
