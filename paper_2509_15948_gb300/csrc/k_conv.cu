@@ -428,8 +428,10 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_conv(LaunchCtx c, const 
 // Second backward step.  Rows of T2 hold the column-transformed dL/dy_bar; T1 holds the spectrum of u.
 //   dU  = Dz conj(A) + conj(Dz_-) conj(B)                    (correlation with the FIR: adjoint of y = h * u)
 //   dH  = D_l conj(U_l) + i D_r conj(U_r)                      (dL/dh_c[j] = sum_n dL/dy_bar_c[n] u_c[n - j])
-// dU is formed in place over the spectrum of dL/dy_bar, dH in a second pair of rows; inverse row FFTs: dU to
-// T2, dH to T1.
+// dU is formed in place over the spectrum of dL/dy_bar; dH goes to global memory over the input spectrum in
+// T1 (each grid position belongs to one pair of one thread, which has read its U there before), so the block
+// holds two rows of shared memory instead of four.  Inverse row FFTs: dU to T2, then dH (reloaded from T1,
+// still in L2) to T1.
 __device__ __forceinline__ float2 fir_grad_bin(float2 dz, float2 dzm, float2 zu, float2 zum) {
   const float2 ul = cscale(cadd(zu, cconj(zum)), 0.5f);
   const float2 du_ = csub(zu, cconj(zum));
@@ -448,7 +450,6 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_bwd2(LaunchCtx c, const 
   const int N1 = rows_len(P), N2 = 1 << P.logN2;
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
   float2* s = sm;
-  float2* o = sm + 2 * pstride(N1);
   __shared__ float2 tt[2 * kRowTwS];
   row_tw_init(tt, P, a, b, c.tab);
   load_rows_fft(s, P.T2, a, b, P, c.tab);
@@ -461,13 +462,18 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_bwd2(LaunchCtx c, const 
     fir_ab(v.hQ, v.hP, AQ, BQ);
     s[pP] = cadd(cmul(dzP, cconj(AP)), cmul(cconj(dzQ), cconj(BP)));
     s[pQ] = cadd(cmul(dzQ, cconj(AQ)), cmul(cconj(dzP), cconj(BQ)));
-    o[pP] = fir_grad_bin(dzP, dzQ, v.uP, v.uQ);
-    o[pQ] = fir_grad_bin(dzQ, dzP, v.uQ, v.uP);
+    P.T1[gP] = fir_grad_bin(dzP, dzQ, v.uP, v.uQ);
+    P.T1[gQ] = fir_grad_bin(dzQ, dzP, v.uQ, v.uP);
   });
-  // every thread has read its T1 entries before the barrier that opens the inverse FFTs; they overwrite T1
-  // rows a, b only
   inv_rows_store(s, P.T2, a, b, P, c.tab, tt);
-  inv_rows_store(o, P.T1, a, b, P, c.tab, tt);
+  __syncthreads();   // the dH rows written to T1 are visible to the whole block, and s is free again
+  const int nr = a == b ? 1 : 2, rs = pstride(N1);
+#pragma unroll 8
+  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
+    const int slot = e >= N1, k1 = e - slot * N1;
+    s[slot * rs + pidx(k1)] = P.T1[(int64_t)(slot ? b : a) * N1 + k1];
+  }
+  inv_rows_store(s, P.T1, a, b, P, c.tab, tt);
 }
 
 template <int MODE>
@@ -493,7 +499,7 @@ void init_kernel_attributes() {
   cudaFuncSetAttribute(k_row_fwd_hz, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));
   cudaFuncSetAttribute(k_row_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));
   cudaFuncSetAttribute(k_row_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_row_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * pstride(kMaxRow) * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_row_bwd2, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));
 }
 
 void launch_col_fwd_audio(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_FWD_AUDIO>(c, items, n, m); }
@@ -522,7 +528,7 @@ void launch_row_conv_fwd(const LaunchCtx& c, const Item* items, int n, int maxN1
 
 void launch_row_bwd2(const LaunchCtx& c, const Item* items, int n, int maxN1) {
   if (!n) return;
-  const size_t smem = (size_t)4 * pstride(maxN1) * sizeof(float2);
+  const size_t smem = (size_t)2 * pstride(maxN1) * sizeof(float2);
   k_row_bwd2<<<n, row_threads(maxN1), smem, c.stream>>>(c, items);
 }
 
