@@ -317,8 +317,27 @@ __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int
 }  // namespace fftp
 
 // FFTs of size M = 3 * 2^a (a >= 1) over nb batches in the padded layout, in place; same contract as fft_p.
+namespace fftp {
+template <bool INV, int A>
+__device__ __forceinline__ void fft_p3_fixed(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw3) {
+  pass3<INV>(d, A, nb, bs);
+#pragma unroll
+  for (int lp2 = 0; lp2 + 4 <= A; lp2 += 4) passm<INV, 16, 4>(d, A, nb, bs, lp2, ptw3);
+  constexpr int rem = A % 4, lp2 = A - rem;
+  if constexpr (rem == 3) passm<INV, 8, 3>(d, A, nb, bs, lp2, ptw3);
+  else if constexpr (rem == 2) passm<INV, 4, 2>(d, A, nb, bs, lp2, ptw3);
+  else if constexpr (rem == 1) passm<INV, 2, 1>(d, A, nb, bs, lp2, ptw3);
+}
+}  // namespace fftp
+
 template <bool INV>
 __device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const float2* __restrict__ ptw3) {
+  switch (a) {
+    case 10: fftp::fft_p3_fixed<INV, 10>(d, nb, bs, ptw3); return;
+    case 9: fftp::fft_p3_fixed<INV, 9>(d, nb, bs, ptw3); return;
+    case 8: fftp::fft_p3_fixed<INV, 8>(d, nb, bs, ptw3); return;
+    default: break;
+  }
   fftp::pass3<INV>(d, a, nb, bs);
   int lp2 = 0;
   for (; a - lp2 >= 4; lp2 += 4) fftp::passm<INV, 16, 4>(d, a, nb, bs, lp2, ptw3);
@@ -345,8 +364,32 @@ __device__ __forceinline__ void fft_p_impl(float2* __restrict__ d, int logM, int
 }
 }  // namespace fftp
 
+namespace fftp {
+// The same passes for a size known at compile time: with logM and every pass offset literal, the strides,
+// masks, shifts and table bases of the inlined passes fold into immediates.
+template <bool INV, int SLOTS, int LOGM>
+__device__ __forceinline__ void fft_p_fixed(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw) {
+  constexpr bool AL = LOGM >= 8;
+#pragma unroll
+  for (int lp = 0; lp + 4 <= LOGM; lp += 4) pass<INV, 16, 4, SLOTS, AL>(d, LOGM, nb, bs, lp, ptw);
+  constexpr int rem = LOGM % 4, lp = LOGM - rem;
+  if constexpr (rem == 3) pass<INV, 8, 3, SLOTS, AL>(d, LOGM, nb, bs, lp, ptw);
+  else if constexpr (rem == 2) pass<INV, 4, 2, SLOTS, AL>(d, LOGM, nb, bs, lp, ptw);
+  else if constexpr (rem == 1) pass<INV, 2, 1, SLOTS, AL>(d, LOGM, nb, bs, lp, ptw);
+}
+}  // namespace fftp
+
 template <bool INV, int SLOTS = 1>
 __device__ void fft_p(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ ptw) {
+  switch (logM) {   // the sizes of the console's transforms run with compile-time strides
+    case 13: fftp::fft_p_fixed<INV, SLOTS, 13>(d, nb, bs, ptw); return;
+    case 12: fftp::fft_p_fixed<INV, SLOTS, 12>(d, nb, bs, ptw); return;
+    case 11: fftp::fft_p_fixed<INV, SLOTS, 11>(d, nb, bs, ptw); return;
+    case 10: fftp::fft_p_fixed<INV, SLOTS, 10>(d, nb, bs, ptw); return;
+    case 9: fftp::fft_p_fixed<INV, SLOTS, 9>(d, nb, bs, ptw); return;
+    case 8: fftp::fft_p_fixed<INV, SLOTS, 8>(d, nb, bs, ptw); return;
+    default: break;
+  }
   if (logM >= 8) fftp::fft_p_impl<INV, SLOTS, true>(d, logM, nb, bs, ptw);
   else fftp::fft_p_impl<INV, SLOTS, false>(d, logM, nb, bs, ptw);
 }
