@@ -1,0 +1,259 @@
+// Column passes of the four-step FFT convolution (see k_conv_common.cuh).
+#include "k_conv_common.cuh"
+
+namespace mg {
+
+namespace {
+
+// COL_INV_OUT_KEEP / COL_DYBAR_KEEP: the retained-spectra variants.  The forward's inverse column pass reads the
+// product rows from T2 and also stores the wet signal y_bar in natural order over T2 (the positions the CTA read);
+// the backward's dL/dy_bar pass then loads y_bar from there instead of transforming the product again.
+enum ColMode {
+  COL_FWD_AUDIO = 0, COL_FWD_TAPS = 1, COL_INV_OUT = 2, COL_DYBAR = 3, COL_DU = 4, COL_DH = 5,
+  COL_INV_OUT_KEEP = 6, COL_DYBAR_KEEP = 7
+};
+
+// A column tile is G adjacent columns of the N1 x N2 grid (N2 * G <= 8192 elements, 512 threads).  Because the
+// block size is a multiple of G, every thread stays on one column g and handles the rows r0 + s * RS
+// (RS = 512 / G, s < kSlots): the global positions of its elements step by RS * N1, its loads are independent
+// and issued eight at a time before the shared-memory stores, and the epilogues batch their side loads
+// (input u, upstream gradient dy) four slots at a time.
+constexpr int kSlots = 8192 / kColThreads;
+
+template <int MODE>
+__global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item* __restrict__ items) {
+  extern __shared__ float2 sm[];
+  __shared__ float red[2 * 32];
+  __shared__ float2 tws[kSlots * 8];   // W(n1 RS s) of the block's columns, [s][g]
+  const Item it = items[blockIdx.x];
+  const ProcDev& P = c.procs[it.proc];
+  const int G = P.colG, logG = __ffs(G) - 1;
+  const int logN2 = P.logN2, N2 = 1 << logN2, N1 = rows_len(P);
+  const int64_t N = fft_len(P);
+  const int cs = col_stride(N2, G);
+  constexpr bool kInv = MODE == COL_INV_OUT || MODE == COL_DYBAR || MODE == COL_DU || MODE == COL_DH ||
+                        MODE == COL_INV_OUT_KEEP;
+  constexpr bool kOut = MODE == COL_INV_OUT || MODE == COL_INV_OUT_KEEP;
+  constexpr bool kDybar = MODE == COL_DYBAR || MODE == COL_DYBAR_KEEP;
+
+  const int g = threadIdx.x & (G - 1), r0 = threadIdx.x >> logG;
+  const int RS = blockDim.x >> logG;
+  const int n1 = it.idx * G + g;
+  const int64_t nbase = (int64_t)n1 + (int64_t)r0 * N1;
+  const int64_t nstep = (int64_t)RS * N1;
+  float2* col = sm + g * cs;
+  auto row_of = [&](int s) { return r0 + s * RS; };
+  auto live = [&](int s) { return row_of(s) < N2; };
+  auto pos = [&](int s) { return nbase + (int64_t)s * nstep; };
+
+  // Forward passes end with the transposition twiddle W(n1 k2), W = exp(-2 pi i / N); for k2 = r0 + s RS it
+  // is W(n1 r0) W(n1 RS s): the first factor is the thread's own, the second comes from a per-block table.
+  constexpr bool kTwid = !(MODE == COL_INV_OUT || MODE == COL_DU || MODE == COL_DH || MODE == COL_INV_OUT_KEEP);
+  float2 w_r0 = make_float2(1.f, 0.f);
+  if (kTwid) {
+    if (r0 < N2) w_r0 = twiddle_node(P, (unsigned)n1 * (unsigned)r0, false, c.tab);
+    if ((int)threadIdx.x < kSlots * G) {   // visible after the barriers of the load and the FFT
+      const int ts = threadIdx.x >> logG, tg = threadIdx.x & (G - 1);
+      const unsigned step = (unsigned)(RS * ts);
+      tws[threadIdx.x] = step < (unsigned)N2 ? twiddle_node(P, (unsigned)(it.idx * G + tg) * step, false, c.tab)
+                                              : make_float2(1.f, 0.f);
+    }
+  }
+  auto tw_at = [&](int s) { return cmul(w_r0, tws[s * G + g]); };
+
+  // ---- load ----
+  if (MODE != COL_DYBAR_KEEP) {
+    const float2* src = (MODE == COL_INV_OUT || MODE == COL_DH) ? P.T1 : P.T2;
+#pragma unroll
+    for (int h = 0; h < kSlots; h += 8) {
+      float2 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        v[j] = make_float2(0.f, 0.f);
+        if (live(h + j)) {
+          const int64_t n = pos(h + j);
+          if (MODE == COL_FWD_AUDIO) {
+            if (n < P.L) v[j] = make_float2(P.u[n], P.u[P.ld + n]);
+          } else if (MODE == COL_FWD_TAPS) {
+            v[j] = tap_at(P, n, N);
+          } else {
+            v[j] = src[n];
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (live(h + j)) col[pidx(row_of(h + j))] = v[j];
+    }
+    __syncthreads();
+    fft_p<kInv>(sm, logN2, G, cs, c.tab.ptw);
+  }
+
+  if (!kInv && !kDybar) {  // forward column pass: twiddle, store in place (row k2)
+    float2* dst = MODE == COL_FWD_TAPS ? P.Hz : P.T1;
+#pragma unroll 4
+    for (int s = 0; s < kSlots; ++s) {
+      if (!live(s)) continue;
+      dst[pos(s)] = cmul(col[pidx(row_of(s))], tw_at(s));
+    }
+    return;
+  }
+
+  const float inv_n = ldexpf(1.f, -P.logN) / (float)P.f;
+  if (kOut) {
+    const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
+    float acc[2] = {0.f, 0.f};
+#pragma unroll 1
+    for (int h = 0; h < kSlots; h += 4) {
+      float ul[4], ur[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        ul[j] = ur[j] = 0.f;
+        if (live(h + j) && n < P.L) {
+          ul[j] = P.u[n];
+          ur[j] = P.u[P.ld + n];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        if (!live(h + j) || n >= P.L) continue;
+        const float2 yb = cscale(col[pidx(row_of(h + j))], inv_n);
+        if (MODE == COL_INV_OUT_KEEP) P.T2[n] = yb;
+        P.y[n] = w * yb.x + wd * ul[j];
+        P.y[P.ld + n] = w * yb.y + wd * ur[j];
+        const float ym = yb.x + yb.y, um = ul[j] + ur[j];
+        acc[0] += ym * ym;
+        acc[1] += um * um;
+      }
+    }
+    float out[2];
+    block_sum<2>(acc, red, out);
+    if (threadIdx.x == 0) {
+      P.fpart[it.idx * kNPart + 0] = out[0];
+      P.fpart[it.idx * kNPart + 1] = out[1];
+    }
+    return;
+  }
+  if (kDybar) {
+    // y_bar -> dL/dy_bar = w dy + c1 (y_bar_l + y_bar_r) on both channels; dw partial; then forward FFT.
+    // Retained spectra: y_bar is read in natural order from T2; otherwise it is the inverse column FFT above.
+    const float w = dry_wet_w(c, P.qidx);
+    const float c1 = P.stats[2];
+    float acc[1] = {0.f};
+#pragma unroll 1
+    for (int h = 0; h < kSlots; h += 4) {
+      float2 yb[4];
+      float gl[4], gr[4], ul[4], ur[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        yb[j] = make_float2(0.f, 0.f);
+        gl[j] = gr[j] = ul[j] = ur[j] = 0.f;
+        if (live(h + j) && n < P.L) {
+          yb[j] = MODE == COL_DYBAR_KEEP ? P.T2[n] : cscale(col[pidx(row_of(h + j))], inv_n);
+          gl[j] = P.dy[n];
+          gr[j] = P.dy[P.ld + n];
+          ul[j] = P.u[n];
+          ur[j] = P.u[P.ld + n];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!live(h + j)) continue;
+        acc[0] += gl[j] * (yb[j].x - ul[j]) + gr[j] * (yb[j].y - ur[j]);
+        const float gm = c1 * (yb[j].x + yb[j].y);
+        // rows past the signal are zero (gl = gr = 0 and y_bar = 0 there)
+        col[pidx(row_of(h + j))] = make_float2(w * gl[j] + gm, w * gr[j] + gm);
+      }
+    }
+    float out[1];
+    block_sum<1>(acc, red, out);   // also acts as the barrier before the FFT
+    if (threadIdx.x == 0) P.bpart[it.idx * kNPart + 0] = out[0];
+    fft_p<false>(sm, logN2, G, cs, c.tab.ptw);
+#pragma unroll 4
+    for (int s = 0; s < kSlots; ++s) {
+      if (!live(s)) continue;
+      P.T2[pos(s)] = cmul(col[pidx(row_of(s))], tw_at(s));
+    }
+    return;
+  }
+  if (MODE == COL_DU) {
+    const float wd = dry_wet_d(c, P.qidx);
+    const float c2 = P.stats[3];
+#pragma unroll 1
+    for (int h = 0; h < kSlots; h += 4) {
+      float gl[4], gr[4], um[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        gl[j] = gr[j] = um[j] = 0.f;
+        if (live(h + j) && n < P.L) {
+          gl[j] = P.dy[n];
+          gr[j] = P.dy[P.ld + n];
+          um[j] = c2 * (P.u[n] + P.u[P.ld + n]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = pos(h + j);
+        if (!live(h + j) || n >= P.L) continue;
+        const float2 dw = cscale(col[pidx(row_of(h + j))], inv_n);
+        P.du[n] = wd * gl[j] + dw.x + um[j];
+        P.du[P.ld + n] = wd * gr[j] + dw.y + um[j];
+      }
+    }
+    return;
+  }
+  if (MODE == COL_DH) {
+#pragma unroll 4
+    for (int s = 0; s < kSlots; ++s) {
+      if (!live(s)) continue;
+      const int64_t n = pos(s);
+      int64_t j = -1;
+      if (n < (int64_t)P.n0 + P.Nh) j = n - P.n0;
+      else if (n >= N + P.n0) j = n - N - P.n0;
+      if (j >= 0 && j < P.Nh) {
+        // dL/dh[t] = sum_n dL/dy_bar[n] u[n - t] is identically zero for lags t >= L: store the exact zero
+        // instead of the FFT rounding residue (the delay's Eq. 19 direction takes sgn(0) = 0 there)
+        const float2 v = (j + P.n0 >= P.L) ? make_float2(0.f, 0.f) : cscale(col[pidx(row_of(s))], inv_n);
+        P.dtaps[j] = v.x;
+        P.dtaps[P.Nh + j] = v.y;
+      }
+    }
+  }
+}
+
+template <int MODE>
+void launch_col(const LaunchCtx& c, const Item* items, int n, int maxN2G) {
+  if (!n) return;
+  (void)maxN2G;
+  const size_t smem = (size_t)kColBuf * sizeof(float2);
+  k_col<MODE><<<n, kColThreads, smem, c.stream>>>(c, items);
+}
+
+}  // namespace
+
+void init_col_attributes() {
+  const int big = kColBuf * (int)sizeof(float2);
+  cudaFuncSetAttribute(k_col<COL_FWD_AUDIO>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_col<COL_FWD_TAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_col<COL_INV_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_col<COL_DYBAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_col<COL_DU>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_col<COL_DH>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_col<COL_INV_OUT_KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  cudaFuncSetAttribute(k_col<COL_DYBAR_KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+void launch_col_fwd_audio(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_FWD_AUDIO>(c, items, n, m); }
+void launch_col_fwd_taps(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_FWD_TAPS>(c, items, n, m); }
+void launch_col_inv_out(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_INV_OUT>(c, items, n, m); }
+void launch_col_dybar(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_DYBAR>(c, items, n, m); }
+void launch_col_du(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_DU>(c, items, n, m); }
+void launch_col_dh(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_DH>(c, items, n, m); }
+void launch_col_inv_out_keep(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_INV_OUT_KEEP>(c, items, n, m); }
+void launch_col_dybar_keep(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_DYBAR_KEEP>(c, items, n, m); }
+
+}  // namespace mg

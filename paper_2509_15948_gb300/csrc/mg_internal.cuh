@@ -162,6 +162,8 @@ void launch_rev_fir(const LaunchCtx&, const Item* items, int n);
 void launch_rev_adj(const LaunchCtx&, const Item* items, int n);
 void launch_rev_adj_fin(const LaunchCtx&, const int* procs, int n);
 void launch_rev_noise_stft(const LaunchCtx&, const Item* items, int n, const float* noise, int noise_len);
+void init_col_attributes();      // column passes of the four-step convolution (called by the last)
+void init_row_bwd_attributes();  // backward row pass (called by the next)
 void init_kernel_attributes();
 void init_loss_attributes();
 void init_fir_attributes();
