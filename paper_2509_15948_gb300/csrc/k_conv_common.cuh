@@ -45,11 +45,13 @@ __device__ __forceinline__ float2 twiddle_node(const ProcDev& P, unsigned m, boo
   return w;
 }
 
-// Row FFTs (length N1 = f 2^logN1) of nb padded rows with batch stride bs.
-template <bool INV>
-__device__ __forceinline__ void row_fft(float2* d, const ProcDev& P, int nb, int bs, const Tables& tab) {
-  if (P.f == 1) fft_p<INV>(d, P.logN1, nb, bs, tab.ptw);
-  else fft_p3<INV>(d, P.logN1, nb, bs, tab.ptw3);
+// Row FFTs (length N1 = f 2^logN1) of nb padded rows with batch stride bs; inputs through ld(slot, k1) and
+// outputs through st(slot, k1, v) when those are functors (see fft_p_io).
+template <bool INV, class LD = fftp::SmemIO, class ST = fftp::SmemIO>
+__device__ __forceinline__ void row_fft(float2* d, const ProcDev& P, int nb, int bs, const Tables& tab, LD ld = LD(),
+                                        ST st = ST()) {
+  if (P.f == 1) fft_p_io<INV, 1>(d, P.logN1, nb, bs, tab.ptw, ld, st);
+  else fft_p3_io<INV>(d, P.logN1, nb, bs, tab.ptw3, ld, st);
 }
 
 // Tap value of the stereo FIR at circular position n (time n, or n - N for the negative taps).
@@ -75,18 +77,15 @@ __device__ __forceinline__ void fir_ab(float2 hz, float2 hzm, float2& A, float2&
   B = cscale(csub(hl, hr), 0.5f);
 }
 
-// Loads rows a and b (b may equal a) of src into smem slots 0/1 and runs their forward FFTs.
+// Forward FFTs of rows a and b (b may equal a) of src into smem slots 0/1; the first pass reads the rows from
+// global memory directly.  The buffer must be free when the call starts.
 __device__ __forceinline__ void load_rows_fft(float2* s, const float2* src, int a, int b, const ProcDev& P,
                                               const Tables& tab) {
   const int N1 = rows_len(P), rs = pstride(N1);
   const int nr = a == b ? 1 : 2;
-#pragma unroll 8
-  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >= N1, k1 = e - slot * N1;
-    s[slot * rs + pidx(k1)] = src[(int64_t)(slot ? b : a) * N1 + k1];
-  }
-  __syncthreads();
-  row_fft<false>(s, P, nr, rs, tab);
+  const float2* ra = src + (int64_t)a * N1;
+  const float2* rb = src + (int64_t)b * N1;
+  row_fft<false>(s, P, nr, rs, tab, [=](int slot, int k1) { return (slot ? rb : ra)[k1]; });
 }
 
 // Transposition twiddles of rows a and b, W(n1 k2) = lo[n1 mod T] hi[n1 / T] (W = exp(-2 pi i / N), T = 64 or
@@ -103,22 +102,22 @@ __device__ __forceinline__ void row_tw_init(float2* tt, const ProcDev& P, int a,
   }
 }
 
-// Inverse row FFT of the slots in o, twiddle exp(+2 pi i n1 k2 / N) (the conjugate of the tt entries), store
-// rows a, b of dst.
+// Inverse row FFT of the slots in o (or, with ld a functor, of rows read through it), twiddle
+// exp(+2 pi i n1 k2 / N) (the conjugate of the tt entries), rows a, b stored to dst by the last pass.  Opens with
+// a barrier and ends without one.
+template <class LD = fftp::SmemIO>
 __device__ __forceinline__ void inv_rows_store(float2* o, float2* dst, int a, int b, const ProcDev& P,
-                                               const Tables& tab, const float2* tt) {
+                                               const Tables& tab, const float2* tt, LD ld = LD()) {
   const int N1 = rows_len(P), rs = pstride(N1), logT = min(6, __ffs(N1) - 1);
   const int nr = a == b ? 1 : 2;
+  float2* da = dst + (int64_t)a * N1;
+  float2* db = dst + (int64_t)b * N1;
   __syncthreads();
-  row_fft<true>(o, P, nr, rs, tab);
-#pragma unroll 4
-  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >= N1, n1 = e - slot * N1;
-    const int k2 = slot ? b : a;
+  row_fft<true>(o, P, nr, rs, tab, ld, [=](int slot, int n1, float2 v) {
     const float2* t = tt + slot * kRowTwS;
     const float2 w = cmul(t[n1 & ((1 << logT) - 1)], t[kRowTwT + (n1 >> logT)]);
-    dst[(int64_t)k2 * N1 + n1] = cmul(o[slot * rs + pidx(n1)], cconj(w));
-  }
+    (slot ? db : da)[n1] = cmul(v, cconj(w));
+  });
 }
 
 // Every bin of rows a, b = N2 - a together with its mirror -k, once per pair: for a != b the partner of

@@ -13,16 +13,12 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_fwd_hz(LaunchCtx c, cons
   const int N1 = rows_len(P), N2 = 1 << P.logN2, rs = pstride(N1);
   const int a = it.idx, b = (N2 - it.idx) & (N2 - 1);
   const int nr = a == b ? 1 : 2;
-  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >= N1, k1 = e - slot * N1;
-    sm[slot * rs + pidx(k1)] = P.Hz[(int64_t)(slot ? b : a) * N1 + k1];
-  }
-  __syncthreads();
-  row_fft<false>(sm, P, nr, rs, c.tab);
-  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >= N1, k1 = e - slot * N1;
-    P.Hz[(int64_t)(slot ? b : a) * N1 + k1] = sm[slot * rs + pidx(k1)];
-  }
+  float2* ha = P.Hz + (int64_t)a * N1;
+  float2* hb = P.Hz + (int64_t)b * N1;
+  // global in, global out: the first pass reads the rows, the last writes them (the passes between hold
+  // barriers, so every read precedes every write)
+  row_fft<false>(sm, P, nr, rs, c.tab, [=](int slot, int k1) { return (slot ? hb : ha)[k1]; },
+                 [=](int slot, int k1, float2 v) { (slot ? hb : ha)[k1] = v; });
 }
 
 // Forward convolution: spectrum Z of u (rows of T1 after the column pass), Y = Z A + conj(Z_-) B, inverse row

@@ -46,14 +46,11 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_bwd2(LaunchCtx c, const 
     P.T1[gQ] = fir_grad_bin(dzQ, dzP, v.uQ, v.uP);
   });
   inv_rows_store(s, P.T2, a, b, P, c.tab, tt);
-  __syncthreads();   // the dH rows written to T1 are visible to the whole block, and s is free again
-  const int nr = a == b ? 1 : 2, rs = pstride(N1);
-#pragma unroll 8
-  for (int e = threadIdx.x; e < nr * N1; e += blockDim.x) {
-    const int slot = e >= N1, k1 = e - slot * N1;
-    s[slot * rs + pidx(k1)] = P.T1[(int64_t)(slot ? b : a) * N1 + k1];
-  }
-  inv_rows_store(s, P.T1, a, b, P, c.tab, tt);
+  // the dH rows written to T1 become visible to the whole block at the barrier that opens the second inverse
+  // transform, which reads them back from T1 in its first pass
+  const float2* ta = P.T1 + (int64_t)a * N1;
+  const float2* tb = P.T1 + (int64_t)b * N1;
+  inv_rows_store(s, P.T1, a, b, P, c.tab, tt, [=](int slot, int k1) { return (slot ? tb : ta)[k1]; });
 }
 
 }  // namespace

@@ -8,6 +8,8 @@
 // per pass as rows of p consecutive k, so that the loads of a warp (consecutive k) are coalesced; the other
 // powers are products.
 #pragma once
+#include <type_traits>
+
 #include "mg_fft.cuh"
 
 namespace mg {
@@ -45,6 +47,14 @@ __host__ __device__ constexpr int ptw3_base(int a, int lp2) {
 }
 
 namespace fftp {
+
+// Where a pass takes its inputs or puts its outputs: SmemIO is the shared buffer itself; any other type is a
+// functor, ld(batch, element) -> float2 for the first pass of a transform and st(batch, element, value) for the
+// last, so a transform can read from and write to global memory directly (the element is the natural input
+// position, resp. the natural output bin).
+struct SmemIO {};
+template <class T>
+constexpr bool is_io = !std::is_same<T, SmemIO>::value;
 
 template <bool INV>
 __device__ __forceinline__ float2 mul_mi(float2 a) {  // a * (-i) forward, a * (+i) inverse
@@ -177,9 +187,9 @@ __device__ __forceinline__ void twiddle(float2 (&x)[R], const float2* __restrict
 // AL (transforms of at least 256 points): the load stride M/R and the store stride p are multiples of 16, or
 // p = 1 with R = 16 and 16-aligned outputs, so every padded address is a base plus a multiple of a per-pass
 // padded stride; otherwise each address is padded on its own.
-template <bool INV, int R, int LOGR, int SLOTS, bool AL>
+template <bool INV, int R, int LOGR, int SLOTS, bool AL, class LD = SmemIO, class ST = SmemIO>
 __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, int bs, int lp,
-                                     const float2* __restrict__ ptw) {
+                                     const float2* __restrict__ ptw, LD ld = LD(), ST st = ST()) {
   constexpr int PER = SLOTS * 16 / R;
   const int MR = 1 << (logM - LOGR), p = 1 << lp, total = nb << (logM - LOGR);
   const int nth = blockDim.x, tid = threadIdx.x;
@@ -192,7 +202,10 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
     ob[s] = -1;
     if (it < total) {
       const int b = it >> (logM - LOGR), i = it & (MR - 1), k = i & (p - 1);
-      if (AL) {
+      if constexpr (is_io<LD>) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[s][r] = ld(b, i + r * MR);
+      } else if (AL) {
         const float2* src = d + b * bs + pidx(i);
 #pragma unroll
         for (int r = 0; r < R; ++r) v[s][r] = src[r * lstr];
@@ -204,14 +217,20 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
       if (p > 1) twiddle<INV, R>(v[s], ptw + ptw_base(lp, LOGR) + k, p);
       dftR<INV, R>(v[s]);
       const int e0 = (i - k) * R + k;   // + q p
-      ob[s] = b * bs + (AL ? pidx(e0) : e0);
+      ob[s] = is_io<ST> ? e0 : b * bs + (AL ? pidx(e0) : e0);
     }
   }
-  __syncthreads();
+  // in place over the shared buffer, every read of the pass precedes every write; a pass that reads global
+  // memory or writes it has no such hazard (the caller makes the buffer free before a transform starts)
+  if constexpr (!is_io<LD> && !is_io<ST>) __syncthreads();
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
     if (ob[s] >= 0) {
-      if (AL) {
+      if constexpr (is_io<ST>) {
+        const int b = (tid + s * nth) >> (logM - LOGR);
+#pragma unroll
+        for (int q = 0; q < R; ++q) st(b, ob[s] + q * p, v[s][q]);
+      } else if (AL) {
         float2* dst = d + ob[s];
 #pragma unroll
         for (int q = 0; q < R; ++q) dst[q * sstr] = v[s][q];
@@ -224,7 +243,7 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
       }
     }
   }
-  __syncthreads();
+  if constexpr (!is_io<ST>) __syncthreads();
 }
 
 // ---- transforms of size M = 3 * 2^a (one radix-3 pass, then radix 16 / 8 / 4 / 2) ----
@@ -242,8 +261,8 @@ __device__ __forceinline__ void dft3(float2& x0, float2& x1, float2& x2) {
 }
 
 // First pass (p = 1, no twiddles): butterfly i < 2^a reads x[i + r 2^a], writes 3 i + q.
-template <bool INV>
-__device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int bs) {
+template <bool INV, class LD = SmemIO>
+__device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int bs, LD ld = LD()) {
   constexpr int PER = 6;                      // 16 elements per thread -> at most 16/3 butterflies
   const int MR = 1 << a, total = nb << a, nth = blockDim.x, tid = threadIdx.x;
   float2 v[PER][3];
@@ -254,14 +273,19 @@ __device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int
     ob[s] = -1;
     if (it < total) {
       const int b = it >> a, i = it & (MR - 1);
-      const float2* src = d + b * bs;
+      if constexpr (is_io<LD>) {
 #pragma unroll
-      for (int r = 0; r < 3; ++r) v[s][r] = src[pidx(i + r * MR)];
+        for (int r = 0; r < 3; ++r) v[s][r] = ld(b, i + r * MR);
+      } else {
+        const float2* src = d + b * bs;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) v[s][r] = src[pidx(i + r * MR)];
+      }
       dft3<INV>(v[s][0], v[s][1], v[s][2]);
       ob[s] = b * bs;
     }
   }
-  __syncthreads();
+  if constexpr (!is_io<LD>) __syncthreads();
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
     if (ob[s] >= 0) {
@@ -277,9 +301,9 @@ __device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int
 __device__ __forceinline__ int div3(int x) { return (int)(__umulhi((unsigned)x, 0xAAAAAAABu) >> 1); }
 
 // Later passes: p = 3 * 2^lp2, radix R = 2^LOGR; butterfly i < M / R, k = i mod p, twiddle w_M^{r k M / (R p)}.
-template <bool INV, int R, int LOGR>
+template <bool INV, int R, int LOGR, class ST = SmemIO>
 __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int bs, int lp2,
-                                      const float2* __restrict__ ptw3) {
+                                      const float2* __restrict__ ptw3, ST st = ST()) {
   constexpr int PER = 16 / R;
   const int MR = 3 << (a - LOGR), p = 3 << lp2, total = nb * MR;
   const int nth = blockDim.x, tid = threadIdx.x;
@@ -300,51 +324,103 @@ __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int
       ob[s] = b * bs + (i - k) * R + k;
     }
   }
-  __syncthreads();
+  if constexpr (!is_io<ST>) __syncthreads();
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
     if (ob[s] >= 0) {
       const int b = div3((tid + s * nth) >> (a - LOGR));
       const int e0 = ob[s] - b * bs;
-      float2* dst = d + b * bs;
+      if constexpr (is_io<ST>) {
 #pragma unroll
-      for (int q = 0; q < R; ++q) dst[pidx(e0 + q * p)] = v[s][q];
+        for (int q = 0; q < R; ++q) st(b, e0 + q * p, v[s][q]);
+      } else {
+        float2* dst = d + b * bs;
+#pragma unroll
+        for (int q = 0; q < R; ++q) dst[pidx(e0 + q * p)] = v[s][q];
+      }
     }
   }
-  __syncthreads();
+  if constexpr (!is_io<ST>) __syncthreads();
 }
 
 }  // namespace fftp
 
 // FFTs of size M = 3 * 2^a (a >= 1) over nb batches in the padded layout, in place; same contract as fft_p.
 namespace fftp {
-template <bool INV, int A>
-__device__ __forceinline__ void fft_p3_fixed(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw3) {
-  pass3<INV>(d, A, nb, bs);
-#pragma unroll
-  for (int lp2 = 0; lp2 + 4 <= A; lp2 += 4) passm<INV, 16, 4>(d, A, nb, bs, lp2, ptw3);
-  constexpr int rem = A % 4, lp2 = A - rem;
-  if constexpr (rem == 3) passm<INV, 8, 3>(d, A, nb, bs, lp2, ptw3);
-  else if constexpr (rem == 2) passm<INV, 4, 2>(d, A, nb, bs, lp2, ptw3);
-  else if constexpr (rem == 1) passm<INV, 2, 1>(d, A, nb, bs, lp2, ptw3);
+// passm from p = 3 * 2^LP2 on, the last one writing through st
+template <bool INV, int A, int LP2, class ST>
+__device__ __forceinline__ void fft_p3_from(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw3,
+                                            ST st) {
+  constexpr int left = A - LP2;
+  if constexpr (left > 4) {
+    passm<INV, 16, 4>(d, A, nb, bs, LP2, ptw3);
+    fft_p3_from<INV, A, LP2 + 4, ST>(d, nb, bs, ptw3, st);
+  } else {
+    passm<INV, 1 << left, left, ST>(d, A, nb, bs, LP2, ptw3, st);
+  }
+}
+
+template <bool INV, int A, class LD, class ST>
+__device__ __forceinline__ void fft_p3_fixed(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw3,
+                                             LD ld, ST st) {
+  pass3<INV, LD>(d, A, nb, bs, ld);
+  fft_p3_from<INV, A, 0, ST>(d, nb, bs, ptw3, st);
+}
+
+template <bool INV>
+__device__ __forceinline__ void fft_p3_generic(float2* __restrict__ d, int a, int nb, int bs,
+                                               const float2* __restrict__ ptw3) {
+  pass3<INV>(d, a, nb, bs);
+  int lp2 = 0;
+  for (; a - lp2 >= 4; lp2 += 4) passm<INV, 16, 4>(d, a, nb, bs, lp2, ptw3);
+  const int rem = a - lp2;
+  if (rem == 3) passm<INV, 8, 3>(d, a, nb, bs, lp2, ptw3);
+  else if (rem == 2) passm<INV, 4, 2>(d, a, nb, bs, lp2, ptw3);
+  else if (rem == 1) passm<INV, 2, 1>(d, a, nb, bs, lp2, ptw3);
+}
+
+// Transforms of a size without a compile-time variant: the functors run as a staging loop before / after.
+template <bool INV, class LD>
+__device__ __forceinline__ void stage_in(float2* __restrict__ d, int M, int nb, int bs, LD ld) {
+  if constexpr (is_io<LD>) {
+    for (int e = threadIdx.x; e < nb * M; e += blockDim.x) {
+      const int b = e / M, j = e - b * M;
+      d[b * bs + pidx(j)] = ld(b, j);
+    }
+    __syncthreads();
+  }
+}
+template <bool INV, class ST>
+__device__ __forceinline__ void stage_out(const float2* __restrict__ d, int M, int nb, int bs, ST st) {
+  if constexpr (is_io<ST>) {
+    for (int e = threadIdx.x; e < nb * M; e += blockDim.x) {
+      const int b = e / M, j = e - b * M;
+      st(b, j, d[b * bs + pidx(j)]);
+    }
+  }
 }
 }  // namespace fftp
 
-template <bool INV>
-__device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const float2* __restrict__ ptw3) {
+// FFTs of size M = 3 * 2^a as fft_p3, with the inputs taken through ld and the outputs put through st (the
+// fftp::SmemIO defaults keep them in the buffer).  With st a functor the call ends without a barrier.
+template <bool INV, class LD = fftp::SmemIO, class ST = fftp::SmemIO>
+__device__ void fft_p3_io(float2* __restrict__ d, int a, int nb, int bs, const float2* __restrict__ ptw3, LD ld = LD(),
+                          ST st = ST()) {
   switch (a) {
-    case 10: fftp::fft_p3_fixed<INV, 10>(d, nb, bs, ptw3); return;
-    case 9: fftp::fft_p3_fixed<INV, 9>(d, nb, bs, ptw3); return;
-    case 8: fftp::fft_p3_fixed<INV, 8>(d, nb, bs, ptw3); return;
+    case 10: fftp::fft_p3_fixed<INV, 10>(d, nb, bs, ptw3, ld, st); return;
+    case 9: fftp::fft_p3_fixed<INV, 9>(d, nb, bs, ptw3, ld, st); return;
+    case 8: fftp::fft_p3_fixed<INV, 8>(d, nb, bs, ptw3, ld, st); return;
     default: break;
   }
-  fftp::pass3<INV>(d, a, nb, bs);
-  int lp2 = 0;
-  for (; a - lp2 >= 4; lp2 += 4) fftp::passm<INV, 16, 4>(d, a, nb, bs, lp2, ptw3);
-  const int rem = a - lp2;
-  if (rem == 3) fftp::passm<INV, 8, 3>(d, a, nb, bs, lp2, ptw3);
-  else if (rem == 2) fftp::passm<INV, 4, 2>(d, a, nb, bs, lp2, ptw3);
-  else if (rem == 1) fftp::passm<INV, 2, 1>(d, a, nb, bs, lp2, ptw3);
+  fftp::stage_in<INV>(d, 3 << a, nb, bs, ld);
+  fftp::fft_p3_generic<INV>(d, a, nb, bs, ptw3);
+  fftp::stage_out<INV>(d, 3 << a, nb, bs, st);
+}
+
+// FFTs of size M = 3 * 2^a (a >= 1) over nb batches in the padded layout, in place; same contract as fft_p.
+template <bool INV>
+__device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const float2* __restrict__ ptw3) {
+  fft_p3_io<INV>(d, a, nb, bs, ptw3);
 }
 
 // FFTs of size M = 2^logM (M <= 8192) over nb batches, padded layout (element e of batch b at
@@ -366,32 +442,54 @@ __device__ __forceinline__ void fft_p_impl(float2* __restrict__ d, int logM, int
 
 namespace fftp {
 // The same passes for a size known at compile time: with logM and every pass offset literal, the strides,
-// masks, shifts and table bases of the inlined passes fold into immediates.
-template <bool INV, int SLOTS, int LOGM>
-__device__ __forceinline__ void fft_p_fixed(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw) {
+// masks, shifts and twiddle-table bases of the inlined passes fold into immediates.  The first pass reads
+// through ld, the last writes through st.
+template <bool FIRST, class LD>
+__device__ __forceinline__ auto first_ld(LD ld) {
+  if constexpr (FIRST) return ld;
+  else return SmemIO();
+}
+
+template <bool INV, int SLOTS, int LOGM, int LP, class LD, class ST>
+__device__ __forceinline__ void fft_p_from(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw,
+                                           LD ld, ST st) {
   constexpr bool AL = LOGM >= 8;
-#pragma unroll
-  for (int lp = 0; lp + 4 <= LOGM; lp += 4) pass<INV, 16, 4, SLOTS, AL>(d, LOGM, nb, bs, lp, ptw);
-  constexpr int rem = LOGM % 4, lp = LOGM - rem;
-  if constexpr (rem == 3) pass<INV, 8, 3, SLOTS, AL>(d, LOGM, nb, bs, lp, ptw);
-  else if constexpr (rem == 2) pass<INV, 4, 2, SLOTS, AL>(d, LOGM, nb, bs, lp, ptw);
-  else if constexpr (rem == 1) pass<INV, 2, 1, SLOTS, AL>(d, LOGM, nb, bs, lp, ptw);
+  constexpr int left = LOGM - LP;
+  const auto l = first_ld<LP == 0>(ld);
+  using L = std::remove_const_t<decltype(l)>;
+  if constexpr (left > 4) {
+    pass<INV, 16, 4, SLOTS, AL, L, SmemIO>(d, LOGM, nb, bs, LP, ptw, l, SmemIO());
+    fft_p_from<INV, SLOTS, LOGM, LP + 4, LD, ST>(d, nb, bs, ptw, ld, st);
+  } else {
+    pass<INV, 1 << left, left, SLOTS, AL, L, ST>(d, LOGM, nb, bs, LP, ptw, l, st);
+  }
 }
 }  // namespace fftp
 
-template <bool INV, int SLOTS = 1>
-__device__ void fft_p(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ ptw) {
+// FFTs of size 2^logM as fft_p, with the inputs taken through ld and the outputs put through st (the
+// fftp::SmemIO defaults keep them in the buffer).  With st a functor the call ends without a barrier; with ld
+// a functor the caller must not be using the buffer any more when the call starts.
+template <bool INV, int SLOTS = 1, class LD = fftp::SmemIO, class ST = fftp::SmemIO>
+__device__ void fft_p_io(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ ptw,
+                         LD ld = LD(), ST st = ST()) {
   switch (logM) {   // the sizes of the console's transforms run with compile-time strides
-    case 13: fftp::fft_p_fixed<INV, SLOTS, 13>(d, nb, bs, ptw); return;
-    case 12: fftp::fft_p_fixed<INV, SLOTS, 12>(d, nb, bs, ptw); return;
-    case 11: fftp::fft_p_fixed<INV, SLOTS, 11>(d, nb, bs, ptw); return;
-    case 10: fftp::fft_p_fixed<INV, SLOTS, 10>(d, nb, bs, ptw); return;
-    case 9: fftp::fft_p_fixed<INV, SLOTS, 9>(d, nb, bs, ptw); return;
-    case 8: fftp::fft_p_fixed<INV, SLOTS, 8>(d, nb, bs, ptw); return;
+    case 13: fftp::fft_p_from<INV, SLOTS, 13, 0>(d, nb, bs, ptw, ld, st); return;
+    case 12: fftp::fft_p_from<INV, SLOTS, 12, 0>(d, nb, bs, ptw, ld, st); return;
+    case 11: fftp::fft_p_from<INV, SLOTS, 11, 0>(d, nb, bs, ptw, ld, st); return;
+    case 10: fftp::fft_p_from<INV, SLOTS, 10, 0>(d, nb, bs, ptw, ld, st); return;
+    case 9: fftp::fft_p_from<INV, SLOTS, 9, 0>(d, nb, bs, ptw, ld, st); return;
+    case 8: fftp::fft_p_from<INV, SLOTS, 8, 0>(d, nb, bs, ptw, ld, st); return;
     default: break;
   }
+  fftp::stage_in<INV>(d, 1 << logM, nb, bs, ld);
   if (logM >= 8) fftp::fft_p_impl<INV, SLOTS, true>(d, logM, nb, bs, ptw);
   else fftp::fft_p_impl<INV, SLOTS, false>(d, logM, nb, bs, ptw);
+  fftp::stage_out<INV>(d, 1 << logM, nb, bs, st);
+}
+
+template <bool INV, int SLOTS = 1>
+__device__ void fft_p(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ ptw) {
+  fft_p_io<INV, SLOTS>(d, logM, nb, bs, ptw);
 }
 
 }  // namespace mg
