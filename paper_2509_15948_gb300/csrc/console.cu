@@ -30,12 +30,12 @@ constexpr int kParamCount[NTYPES] = {1024, 4, 4, 1, 2, 880, 768};
 enum Family {
   F_GS_FWD, F_GS_BWD, F_SUM, F_DYN_FWD, F_DYN_BWD, F_EQ_FIR, F_DLY_FIR, F_REV_FIR, F_FIR_ADJ, F_COL_FWD, F_ROW_HZ,
   F_ROW_CONV, F_COL_OUT, F_COL_DYBAR, F_ROW_BWD2, F_COL_DU, F_COL_DH, F_LOSS_FWD, F_LOSS_BWD, F_LOSS_GATHER,
-  F_FINALIZE, F_ADAM, F_MISC, F_EQ_OS, F_COUNT
+  F_FINALIZE, F_ADAM, F_MISC, F_EQ_OS_FWD, F_EQ_OS_BWD, F_EQ_OS_DU, F_COUNT
 };
 const char* kFamilyNames[F_COUNT] = {
     "gs_fwd", "gs_bwd", "sum", "dyn_fwd", "dyn_bwd", "eq_fir", "dly_fir", "rev_fir", "fir_adj", "col_fwd", "row_hz",
     "row_conv", "col_out", "col_dybar", "row_bwd2", "col_du", "col_dh", "loss_fwd", "loss_bwd", "loss_gather",
-    "finalize", "adam", "misc", "eq_os"};
+    "finalize", "adam", "misc", "eq_os_fwd", "eq_os_bwd", "eq_os_du"};
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int ilog2_ceil(int64_t x) {
@@ -533,7 +533,7 @@ void stage_forward(mg_console* c, const LaunchCtx& x, Stage& s) {
     case T_E:
       run_procs(c, F_EQ_FIR, s.procs, [&](const int* p, int n) { launch_eq_fir(x, p, n); });
       run_procs(c, F_EQ_FIR, s.procs, [&](const int* p, int n) { launch_eq_spec(x, p, n); });
-      run_items(c, F_EQ_OS, s.osf, [&](const Item* it, int n) { launch_eq_os_fwd(x, it, n); });
+      run_items(c, F_EQ_OS_FWD, s.osf, [&](const Item* it, int n) { launch_eq_os_fwd(x, it, n); });
       break;
     default:
       for (auto& g : s.groups) lti_forward(c, x, s.type, g);
@@ -554,8 +554,8 @@ void stage_backward(mg_console* c, const LaunchCtx& x, Stage& s) {
       run_items(c, F_DYN_BWD, s.elem, [&](const Item* it, int n) { launch_dyn_bwd_apply(x, it, n); });
       break;
     case T_E:
-      run_items(c, F_EQ_OS, s.osb, [&](const Item* it, int n) { launch_eq_os_bwd(x, it, n); });
-      run_items(c, F_EQ_OS, s.osf, [&](const Item* it, int n) { launch_eq_os_du(x, it, n); });
+      run_items(c, F_EQ_OS_BWD, s.osb, [&](const Item* it, int n) { launch_eq_os_bwd(x, it, n); });
+      run_items(c, F_EQ_OS_DU, s.osf, [&](const Item* it, int n) { launch_eq_os_du(x, it, n); });
       run_procs(c, F_FIR_ADJ, s.procs, [&](const int* p, int n) { launch_eq_dh_reduce(x, p, n); });
       run_procs(c, F_FIR_ADJ, s.procs, [&](const int* p, int n) { launch_eq_fir_adj(x, p, n); });
       break;

@@ -49,32 +49,34 @@ __global__ void __launch_bounds__(kOsThreads, 2) k_eq_os_fwd(LaunchCtx c, const 
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   constexpr int B = kOsM - 2 * kEqHalf;
-  const int s0 = it.idx * B;
-  for (int j = threadIdx.x; j < kOsM; j += blockDim.x) {
-    const int s = s0 - kEqHalf + j;
-    sm[pidx(j)] = (s >= 0 && s < P.L) ? make_float2(P.u[s], P.u[P.ld + s]) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_p<false>(sm, kOsLog, 1, kOsP, c.tab.ptw);
+  const int s0 = it.idx * B, seg = s0 - kEqHalf, L = P.L, ld = P.ld;
+  const float* u = P.u;
+  // the segment goes straight from global memory into the first pass of the transform
+  fft_p_io<false>(sm, kOsLog, 1, kOsP, c.tab.ptw, [=](int, int j) {
+    const int s = seg + j;
+    return (s >= 0 && s < L) ? make_float2(u[s], u[ld + s]) : make_float2(0.f, 0.f);
+  });
   for (int k = threadIdx.x; k < kOsM; k += blockDim.x) sm[pidx(k)] = cscale(sm[pidx(k)], P.hspec[k]);
   __syncthreads();
-  fft_p<true>(sm, kOsLog, 1, kOsP, c.tab.ptw);
   const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const float inv = 1.f / kOsM;
   float acc[2] = {0.f, 0.f};
-  for (int t = threadIdx.x; t < B; t += blockDim.x) {
-    const int s = s0 + t;
-    if (s >= P.L) break;
-    const float2 yb = cscale(sm[pidx(kEqHalf + t)], inv);
-    P.ybar[s] = yb.x;
-    P.ybar[P.ld + s] = yb.y;
-    const float ul = P.u[s], ur = P.u[P.ld + s];
-    P.y[s] = w * yb.x + wd * ul;
-    P.y[P.ld + s] = w * yb.y + wd * ur;
+  float* ybar = P.ybar;
+  float* y = P.y;
+  // the last pass of the inverse writes the B valid outputs, blended with the dry signal
+  fft_p_io<true>(sm, kOsLog, 1, kOsP, c.tab.ptw, fftp::SmemIO(), [&](int, int j, float2 v) {
+    const int t = j - kEqHalf, s = s0 + t;
+    if (t < 0 || t >= B || s >= L) return;
+    const float2 yb = cscale(v, inv);
+    ybar[s] = yb.x;
+    ybar[ld + s] = yb.y;
+    const float ul = u[s], ur = u[ld + s];
+    y[s] = w * yb.x + wd * ul;
+    y[ld + s] = w * yb.y + wd * ur;
     const float ym = yb.x + yb.y, um = ul + ur;
     acc[0] += ym * ym;
     acc[1] += um * um;
-  }
+  });
   float out[2];
   block_sum<2>(acc, red, out);
   if (threadIdx.x == 0) {
@@ -104,28 +106,23 @@ __global__ void __launch_bounds__(kOsBwdThreads, 1) k_eq_os_bwd(LaunchCtx c, con
   float dwacc[1] = {0.f};
   const int nblk = (P.L + B - 1) / B;
   const int b0 = it.idx * kEqChunk, b1 = min(nblk, b0 + kEqChunk);
+  const int L = P.L, ld = P.ld;
+  const float *u = P.u, *ybar = P.ybar, *dy = P.dy;
   for (int blk = b0; blk < b1; ++blk) {
     const int seg = blk * B - kEqHalf;
-#pragma unroll 2
-    for (int j = threadIdx.x; j < kOsM; j += blockDim.x) {
+    // D and Ub as one batch of two, their inputs formed in the first pass: batch 0 is dL/dy_bar on the segment
+    // (which also accumulates the block's dL/dw), batch 1 the input on the block only
+    fft_p_io<false>(D, kOsLog, 2, kOsP, c.tab.ptw, [&](int bt, int j) {
       const int s = seg + j;
-      float2 d = make_float2(0.f, 0.f), ub = d;
-      if (s >= 0 && s < P.L) {
-        const float yl = P.ybar[s], yr = P.ybar[P.ld + s];
-        const float gl = P.dy[s], gr = P.dy[P.ld + s];
-        const float gm = c1 * (yl + yr);
-        d = make_float2(w * gl + gm, w * gr + gm);
-        if (j >= kEqHalf && j < kEqHalf + B) {
-          const float ul = P.u[s], ur = P.u[P.ld + s];
-          ub = make_float2(ul, ur);
-          dwacc[0] += gl * (yl - ul) + gr * (yr - ur);
-        }
-      }
-      D[pidx(j)] = d;
-      Ub[pidx(j)] = ub;
-    }
-    __syncthreads();
-    fft_p<false>(D, kOsLog, 2, kOsP, c.tab.ptw);   // D and Ub: one batch of two
+      const bool in_blk = j >= kEqHalf && j < kEqHalf + B;
+      if (s < 0 || s >= L || (bt && !in_blk)) return make_float2(0.f, 0.f);
+      if (bt) return make_float2(u[s], u[ld + s]);
+      const float yl = ybar[s], yr = ybar[ld + s];
+      const float gl = dy[s], gr = dy[ld + s];
+      const float gm = c1 * (yl + yr);
+      if (in_blk) dwacc[0] += gl * (yl - u[s]) + gr * (yr - u[ld + s]);
+      return make_float2(w * gl + gm, w * gr + gm);
+    });
     float2* g = P.eqg + (size_t)blk * kOsM;
 #pragma unroll 4
     for (int t = 0; t < kBins; ++t) {

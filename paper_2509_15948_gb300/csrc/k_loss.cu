@@ -56,16 +56,6 @@ __device__ __forceinline__ float4 bin_mags(const LossRes& R, const float2* Z, in
   }
   return make_float4(m[0], m[1], m[2], m[3]);
 }
-
-__device__ __forceinline__ void load_frames(float2* sm, const float* x, int ld, int L, const LossRes& R, int t0, int nb) {
-  const int n = R.nfft, bs = pstride(n);
-  for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
-    const int f = e >> R.log_nfft, j = e & (n - 1);
-    const int s = (t0 + f) * R.hop + j;
-    const float w = R.win[j];
-    sm[f * bs + pidx(j)] = (s < L) ? make_float2(x[s] * w, x[ld + s] * w) : make_float2(0.f, 0.f);
-  }
-}
 }  // namespace
 
 // item (song, res, first frame, frames); mode 0: write target spectrogram + partial sum Y^2 per set;
@@ -90,9 +80,14 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
     }
     __syncthreads();
   } else {
-    load_frames(sm, x, S.ld, S.L, R, t0, nb);
-    __syncthreads();
-    fft_p<false>(sm, R.log_nfft, nb, bs, c.tab.ptw);
+    // the windowed frames go straight from global memory into the first pass of the transform
+    const int L = S.L, ld = S.ld, hop = R.hop;
+    const float* win = R.win;
+    fft_p_io<false>(sm, R.log_nfft, nb, bs, c.tab.ptw, [=](int f, int j) {
+      const int s = (t0 + f) * hop + j;
+      const float w = win[j];
+      return s < L ? make_float2(x[s] * w, x[ld + s] * w) : make_float2(0.f, 0.f);
+    });
     if (mode == 3)
       for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
         const int f = e >> R.log_nfft, j = e & (n - 1);
@@ -200,13 +195,11 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
     }
   }
   __syncthreads();
-  fft_p<true>(sm, R.log_nfft, nb, bs, c.tab.ptw);
-  float* dF = S.dF[it.y];
-  for (int e = threadIdx.x; e < nb * n; e += blockDim.x) {
-    const int f = e >> R.log_nfft, j = e & (n - 1);
-    const float w = R.win[j];
-    reinterpret_cast<float2*>(dF)[(size_t)(t0 + f) * n + j] = cscale(sm[f * bs + pidx(j)], w);
-  }
+  // the last pass of the inverse writes the windowed frame gradients
+  float2* dF = reinterpret_cast<float2*>(S.dF[it.y]) + (size_t)t0 * n;
+  const float* win = R.win;
+  fft_p_io<true>(sm, R.log_nfft, nb, bs, c.tab.ptw, fftp::SmemIO(),
+                 [=](int f, int j, float2 v) { dF[(size_t)f * n + j] = cscale(v, win[j]); });
 }
 
 // dmix[c][s] = sum over resolutions and covering frames of dF (overlap-add, fixed order)
