@@ -20,19 +20,30 @@ enum ColMode {
 // (input u, upstream gradient dy) four slots at a time.
 constexpr int kSlots = 8192 / kColThreads;
 
+// Transposition twiddles of the tile's columns, W(n1 k2) = lo[k2 mod 64] hi[k2 / 64] (W = exp(-2 pi i / N),
+// N2 / 64 <= 32 hi entries), both factors from the accurate table; column gg at ctw + gg * kColTwS.  Visible
+// after the caller's next barrier.
+constexpr int kColTwS = 96;
+__device__ __forceinline__ void col_tw_init(float2* ctw, const ProcDev& P, int n1b, int G, int N2, const Tables& tab) {
+  for (int e = threadIdx.x; e < G * kColTwS; e += blockDim.x) {
+    const int gg = e / kColTwS, j = e - gg * kColTwS;
+    const unsigned n1 = (unsigned)(n1b + gg);
+    const unsigned k2 = j < 64 ? (unsigned)j : (unsigned)(j - 64) << 6;   // the lo power, or the hi power
+    ctw[e] = k2 < (unsigned)N2 ? twiddle_node(P, n1 * k2, false, tab) : make_float2(1.f, 0.f);
+  }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   __shared__ float red[2 * 32];
-  __shared__ float2 tws[kSlots * 8];   // W(n1 RS s) of the block's columns, [s][g]
+  __shared__ float2 ctw[8 * kColTwS];
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const int G = P.colG, logG = __ffs(G) - 1;
   const int logN2 = P.logN2, N2 = 1 << logN2, N1 = rows_len(P);
   const int64_t N = fft_len(P);
   const int cs = col_stride(N2, G);
-  constexpr bool kInv = MODE == COL_INV_OUT || MODE == COL_DYBAR || MODE == COL_DU || MODE == COL_DH ||
-                        MODE == COL_INV_OUT_KEEP;
   constexpr bool kOut = MODE == COL_INV_OUT || MODE == COL_INV_OUT_KEEP;
   constexpr bool kDybar = MODE == COL_DYBAR || MODE == COL_DYBAR_KEEP;
 
@@ -46,57 +57,35 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   auto live = [&](int s) { return row_of(s) < N2; };
   auto pos = [&](int s) { return nbase + (int64_t)s * nstep; };
 
-  // Forward passes end with the transposition twiddle W(n1 k2), W = exp(-2 pi i / N); for k2 = r0 + s RS it
-  // is W(n1 r0) W(n1 RS s): the first factor is the thread's own, the second comes from a per-block table.
+  // The column transforms run with the batch-fastest thread order (eight adjacent columns of one row per
+  // quarter warp), so their first pass reads, and a forward transform's last pass writes, global memory
+  // directly.  Forward transforms end with the transposition twiddle W(n1 k2), W = exp(-2 pi i / N).
   constexpr bool kTwid = !(MODE == COL_INV_OUT || MODE == COL_DU || MODE == COL_DH || MODE == COL_INV_OUT_KEEP);
-  float2 w_r0 = make_float2(1.f, 0.f);
-  if (kTwid) {
-    if (r0 < N2) w_r0 = twiddle_node(P, (unsigned)n1 * (unsigned)r0, false, c.tab);
-    if ((int)threadIdx.x < kSlots * G) {   // visible after the barriers of the load and the FFT
-      const int ts = threadIdx.x >> logG, tg = threadIdx.x & (G - 1);
-      const unsigned step = (unsigned)(RS * ts);
-      tws[threadIdx.x] = step < (unsigned)N2 ? twiddle_node(P, (unsigned)(it.idx * G + tg) * step, false, c.tab)
-                                              : make_float2(1.f, 0.f);
-    }
-  }
-  auto tw_at = [&](int s) { return cmul(w_r0, tws[s * G + g]); };
+  const int n1b = it.idx * G;
+  if (kTwid) col_tw_init(ctw, P, n1b, G, N2, c.tab);
+  auto tw_store = [&](float2* dst) {
+    return [&, dst](int gg, int k2, float2 v) {
+      const float2* t = ctw + gg * kColTwS;
+      dst[n1b + gg + (int64_t)N1 * k2] = cmul(v, cmul(t[k2 & 63], t[64 + (k2 >> 6)]));
+    };
+  };
 
-  // ---- load ----
+  if (MODE == COL_FWD_AUDIO || MODE == COL_FWD_TAPS) {   // forward pass of the input or the taps, in place
+    const float* u = P.u;
+    const int L = P.L, ld = P.ld;
+    fft_p_io<false, 1, true>(sm, logN2, G, cs, c.tab.ptw, [&](int gg, int n2) {
+      const int64_t n = n1b + gg + (int64_t)N1 * n2;
+      if (MODE == COL_FWD_AUDIO) return n < L ? make_float2(u[n], u[ld + n]) : make_float2(0.f, 0.f);
+      return tap_at(P, n, N);
+    }, tw_store(MODE == COL_FWD_TAPS ? P.Hz : P.T1));
+    return;
+  }
+
+  // ---- load: the inverse transform reads the rows of T1 / T2 in its first pass ----
   if (MODE != COL_DYBAR_KEEP) {
     const float2* src = (MODE == COL_INV_OUT || MODE == COL_DH) ? P.T1 : P.T2;
-#pragma unroll
-    for (int h = 0; h < kSlots; h += 8) {
-      float2 v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        v[j] = make_float2(0.f, 0.f);
-        if (live(h + j)) {
-          const int64_t n = pos(h + j);
-          if (MODE == COL_FWD_AUDIO) {
-            if (n < P.L) v[j] = make_float2(P.u[n], P.u[P.ld + n]);
-          } else if (MODE == COL_FWD_TAPS) {
-            v[j] = tap_at(P, n, N);
-          } else {
-            v[j] = src[n];
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (live(h + j)) col[pidx(row_of(h + j))] = v[j];
-    }
-    __syncthreads();
-    fft_p<kInv>(sm, logN2, G, cs, c.tab.ptw);
-  }
-
-  if (!kInv && !kDybar) {  // forward column pass: twiddle, store in place (row k2)
-    float2* dst = MODE == COL_FWD_TAPS ? P.Hz : P.T1;
-#pragma unroll 4
-    for (int s = 0; s < kSlots; ++s) {
-      if (!live(s)) continue;
-      dst[pos(s)] = cmul(col[pidx(row_of(s))], tw_at(s));
-    }
-    return;
+    fft_p_io<true, 1, true>(sm, logN2, G, cs, c.tab.ptw,
+                            [&](int gg, int n2) { return src[n1b + gg + (int64_t)N1 * n2]; });
   }
 
   const float inv_n = ldexpf(1.f, -P.logN) / (float)P.f;
@@ -171,12 +160,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
     float out[1];
     block_sum<1>(acc, red, out);   // also acts as the barrier before the FFT
     if (threadIdx.x == 0) P.bpart[it.idx * kNPart + 0] = out[0];
-    fft_p<false>(sm, logN2, G, cs, c.tab.ptw);
-#pragma unroll 4
-    for (int s = 0; s < kSlots; ++s) {
-      if (!live(s)) continue;
-      P.T2[pos(s)] = cmul(col[pidx(row_of(s))], tw_at(s));
-    }
+    fft_p_io<false, 1, true>(sm, logN2, G, cs, c.tab.ptw, fftp::SmemIO(), tw_store(P.T2));
     return;
   }
   if (MODE == COL_DU) {

@@ -186,14 +186,18 @@ __device__ __forceinline__ void twiddle(float2 (&x)[R], const float2* __restrict
 
 // AL (transforms of at least 256 points): the load stride M/R and the store stride p are multiples of 16, or
 // p = 1 with R = 16 and 16-aligned outputs, so every padded address is a base plus a multiple of a per-pass
-// padded stride; otherwise each address is padded on its own.
-template <bool INV, int R, int LOGR, int SLOTS, bool AL, class LD = SmemIO, class ST = SmemIO>
+// padded stride; otherwise each address is padded on its own.  BF (nb a power of two): consecutive threads take
+// consecutive batches of one butterfly index instead of consecutive butterflies of one batch, so that loads and
+// stores through ld / st of batches that sit side by side in global memory (adjacent columns) coalesce.
+template <bool INV, int R, int LOGR, int SLOTS, bool AL, bool BF = false, class LD = SmemIO, class ST = SmemIO>
 __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, int bs, int lp,
                                      const float2* __restrict__ ptw, LD ld = LD(), ST st = ST()) {
   constexpr int PER = SLOTS * 16 / R;
   const int MR = 1 << (logM - LOGR), p = 1 << lp, total = nb << (logM - LOGR);
   const int nth = blockDim.x, tid = threadIdx.x;
   const int lstr = MR + (MR >> 4), sstr = p == 1 ? 1 : p + (p >> 4);
+  const int lognb = BF ? __ffs(nb) - 1 : 0;
+  auto batch_of = [&](int it) { return BF ? (it & (nb - 1)) : it >> (logM - LOGR); };
   float2 v[PER][R];
   int ob[PER];
 #pragma unroll
@@ -201,7 +205,7 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
     const int it = tid + s * nth;
     ob[s] = -1;
     if (it < total) {
-      const int b = it >> (logM - LOGR), i = it & (MR - 1), k = i & (p - 1);
+      const int b = batch_of(it), i = BF ? it >> lognb : it & (MR - 1), k = i & (p - 1);
       if constexpr (is_io<LD>) {
 #pragma unroll
         for (int r = 0; r < R; ++r) v[s][r] = ld(b, i + r * MR);
@@ -227,7 +231,7 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
   for (int s = 0; s < PER; ++s) {
     if (ob[s] >= 0) {
       if constexpr (is_io<ST>) {
-        const int b = (tid + s * nth) >> (logM - LOGR);
+        const int b = batch_of(tid + s * nth);
 #pragma unroll
         for (int q = 0; q < R; ++q) st(b, ob[s] + q * p, v[s][q]);
       } else if (AL) {
@@ -235,7 +239,7 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
 #pragma unroll
         for (int q = 0; q < R; ++q) dst[q * sstr] = v[s][q];
       } else {
-        const int b = (tid + s * nth) >> (logM - LOGR);
+        const int b = batch_of(tid + s * nth);
         const int e0 = ob[s] - b * bs;
         float2* dst = d + b * bs;
 #pragma unroll
@@ -428,15 +432,15 @@ __device__ void fft_p3(float2* __restrict__ d, int a, int nb, int bs, const floa
 // and pass).  Forward: exp(-2 pi i nk/M); inverse: exp(+...), unscaled.  The caller synchronises before the
 // call; the call ends with a barrier.
 namespace fftp {
-template <bool INV, int SLOTS, bool AL>
+template <bool INV, int SLOTS, bool AL, bool BF = false>
 __device__ __forceinline__ void fft_p_impl(float2* __restrict__ d, int logM, int nb, int bs,
                                            const float2* __restrict__ ptw) {
   int lp = 0;
-  for (; logM - lp >= 4; lp += 4) pass<INV, 16, 4, SLOTS, AL>(d, logM, nb, bs, lp, ptw);
+  for (; logM - lp >= 4; lp += 4) pass<INV, 16, 4, SLOTS, AL, BF>(d, logM, nb, bs, lp, ptw);
   const int rem = logM - lp;
-  if (rem == 3) pass<INV, 8, 3, SLOTS, AL>(d, logM, nb, bs, lp, ptw);
-  else if (rem == 2) pass<INV, 4, 2, SLOTS, AL>(d, logM, nb, bs, lp, ptw);
-  else if (rem == 1) pass<INV, 2, 1, SLOTS, AL>(d, logM, nb, bs, lp, ptw);
+  if (rem == 3) pass<INV, 8, 3, SLOTS, AL, BF>(d, logM, nb, bs, lp, ptw);
+  else if (rem == 2) pass<INV, 4, 2, SLOTS, AL, BF>(d, logM, nb, bs, lp, ptw);
+  else if (rem == 1) pass<INV, 2, 1, SLOTS, AL, BF>(d, logM, nb, bs, lp, ptw);
 }
 }  // namespace fftp
 
@@ -450,7 +454,7 @@ __device__ __forceinline__ auto first_ld(LD ld) {
   else return SmemIO();
 }
 
-template <bool INV, int SLOTS, int LOGM, int LP, class LD, class ST>
+template <bool INV, int SLOTS, bool BF, int LOGM, int LP, class LD, class ST>
 __device__ __forceinline__ void fft_p_from(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw,
                                            LD ld, ST st) {
   constexpr bool AL = LOGM >= 8;
@@ -458,10 +462,10 @@ __device__ __forceinline__ void fft_p_from(float2* __restrict__ d, int nb, int b
   const auto l = first_ld<LP == 0>(ld);
   using L = std::remove_const_t<decltype(l)>;
   if constexpr (left > 4) {
-    pass<INV, 16, 4, SLOTS, AL, L, SmemIO>(d, LOGM, nb, bs, LP, ptw, l, SmemIO());
-    fft_p_from<INV, SLOTS, LOGM, LP + 4, LD, ST>(d, nb, bs, ptw, ld, st);
+    pass<INV, 16, 4, SLOTS, AL, BF, L, SmemIO>(d, LOGM, nb, bs, LP, ptw, l, SmemIO());
+    fft_p_from<INV, SLOTS, BF, LOGM, LP + 4, LD, ST>(d, nb, bs, ptw, ld, st);
   } else {
-    pass<INV, 1 << left, left, SLOTS, AL, L, ST>(d, LOGM, nb, bs, LP, ptw, l, st);
+    pass<INV, 1 << left, left, SLOTS, AL, BF, L, ST>(d, LOGM, nb, bs, LP, ptw, l, st);
   }
 }
 }  // namespace fftp
@@ -469,21 +473,22 @@ __device__ __forceinline__ void fft_p_from(float2* __restrict__ d, int nb, int b
 // FFTs of size 2^logM as fft_p, with the inputs taken through ld and the outputs put through st (the
 // fftp::SmemIO defaults keep them in the buffer).  With st a functor the call ends without a barrier; with ld
 // a functor the caller must not be using the buffer any more when the call starts.
-template <bool INV, int SLOTS = 1, class LD = fftp::SmemIO, class ST = fftp::SmemIO>
+// BF: the batch-fastest thread order of the passes (nb must be a power of two).
+template <bool INV, int SLOTS = 1, bool BF = false, class LD = fftp::SmemIO, class ST = fftp::SmemIO>
 __device__ void fft_p_io(float2* __restrict__ d, int logM, int nb, int bs, const float2* __restrict__ ptw,
                          LD ld = LD(), ST st = ST()) {
   switch (logM) {   // the sizes of the console's transforms run with compile-time strides
-    case 13: fftp::fft_p_from<INV, SLOTS, 13, 0>(d, nb, bs, ptw, ld, st); return;
-    case 12: fftp::fft_p_from<INV, SLOTS, 12, 0>(d, nb, bs, ptw, ld, st); return;
-    case 11: fftp::fft_p_from<INV, SLOTS, 11, 0>(d, nb, bs, ptw, ld, st); return;
-    case 10: fftp::fft_p_from<INV, SLOTS, 10, 0>(d, nb, bs, ptw, ld, st); return;
-    case 9: fftp::fft_p_from<INV, SLOTS, 9, 0>(d, nb, bs, ptw, ld, st); return;
-    case 8: fftp::fft_p_from<INV, SLOTS, 8, 0>(d, nb, bs, ptw, ld, st); return;
+    case 13: fftp::fft_p_from<INV, SLOTS, BF, 13, 0>(d, nb, bs, ptw, ld, st); return;
+    case 12: fftp::fft_p_from<INV, SLOTS, BF, 12, 0>(d, nb, bs, ptw, ld, st); return;
+    case 11: fftp::fft_p_from<INV, SLOTS, BF, 11, 0>(d, nb, bs, ptw, ld, st); return;
+    case 10: fftp::fft_p_from<INV, SLOTS, BF, 10, 0>(d, nb, bs, ptw, ld, st); return;
+    case 9: fftp::fft_p_from<INV, SLOTS, BF, 9, 0>(d, nb, bs, ptw, ld, st); return;
+    case 8: fftp::fft_p_from<INV, SLOTS, BF, 8, 0>(d, nb, bs, ptw, ld, st); return;
     default: break;
   }
   fftp::stage_in<INV>(d, 1 << logM, nb, bs, ld);
-  if (logM >= 8) fftp::fft_p_impl<INV, SLOTS, true>(d, logM, nb, bs, ptw);
-  else fftp::fft_p_impl<INV, SLOTS, false>(d, logM, nb, bs, ptw);
+  if (logM >= 8) fftp::fft_p_impl<INV, SLOTS, true, BF>(d, logM, nb, bs, ptw);
+  else fftp::fft_p_impl<INV, SLOTS, false, BF>(d, logM, nb, bs, ptw);
   fftp::stage_out<INV>(d, 1 << logM, nb, bs, st);
 }
 
