@@ -980,25 +980,37 @@ mg_status autotune_splits(mg_console* c) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   LaunchCtx x = make_ctx(c, nullptr);
+  // With retained spectra every node owns its FFT buffers, so up to kTuneNodes nodes of a size class are timed
+  // together: launches of many nodes run at the throughput of the real stage launches, where one node's
+  // launches (a wave or two of CTAs) would be dominated by their tails.  Without retained spectra the nodes
+  // share one scratch, so one node is timed.
+  constexpr int kTuneNodes = 16;
   for (size_t k = 0; k < classes.size(); ++k) {
     const int pi = rep_of[k];
     HostProc& p = c->procs[pi];
     const HostProc saved = p;
+    std::vector<int> members{pi};
+    for (int qi = 0; c->retain && qi < c->P && (int)members.size() < kTuneNodes; ++qi) {
+      const HostProc& q = c->procs[qi];
+      if (qi != pi && (q.type == T_R || q.type == T_D) && q.f == p.f && q.logN == p.logN) members.push_back(qi);
+    }
     int best = p.logN1;
     float best_ms = 1e30f;
     for (int l1 : saved.splits) {
-      apply_split(p, l1);
-      ProcDev& dv = c->hpd[pi];
-      dv.logN1 = p.logN1;
-      dv.logN2 = p.logN2;
-      dv.colG = p.colG;
-      dv.nfpart = p.nfrows;
-      dv.nbpart = p.nbrows;
-      ProcDev* dptr = c->d_procs + pi;
-      CK(cudaMemcpyAsync(dptr, &dv, sizeof(ProcDev), cudaMemcpyHostToDevice, c->stream));
       ItemList col, pair;
-      for (int i = 0; i < p.nfrows; ++i) col.h.push_back(Item{pi, i});
-      for (int i = 0; i <= (1 << p.logN2) / 2; ++i) pair.h.push_back(Item{pi, i});
+      for (int mi : members) {
+        HostProc& m = c->procs[mi];
+        apply_split(m, l1);
+        ProcDev& dv = c->hpd[mi];
+        dv.logN1 = m.logN1;
+        dv.logN2 = m.logN2;
+        dv.colG = m.colG;
+        dv.nfpart = m.nfrows;
+        dv.nbpart = m.nbrows;
+        CK(cudaMemcpyAsync(c->d_procs + mi, &dv, sizeof(ProcDev), cudaMemcpyHostToDevice, c->stream));
+        for (int i = 0; i < m.nfrows; ++i) col.h.push_back(Item{mi, i});
+        for (int i = 0; i <= (1 << m.logN2) / 2; ++i) pair.h.push_back(Item{mi, i});
+      }
       if (upload_items(c, col) || upload_items(c, pair)) return MG_ERR_CUDA;
       const int n2g = (1 << p.logN2) * p.colG, n1 = p.f << p.logN1, nc = (int)col.h.size(), np_ = (int)pair.h.size();
       auto passes = [&] {
