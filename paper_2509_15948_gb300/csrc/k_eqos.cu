@@ -86,16 +86,17 @@ __global__ void __launch_bounds__(kOsThreads, 2) k_eq_os_fwd(LaunchCtx c, const 
 }
 
 // item = (node, chunk): blocks chunk * kEqChunk ... of B = 6146 samples.  Two padded 8192-point buffers in
-// shared memory (139 KB) and 1024 threads; both forward transforms run as one batch, 16 elements per thread.
-// Per block the spectrum D H is stored for k_eq_os_du, and the running sum of the correlation spectra stays in
-// the item's row of dhspec (each thread owns the same bins in every block, so the read-modify-write is
-// race-free and ordered).  The inverse transform lives in its own kernel: in this loop, next to the forward
+// shared memory and 1024 threads; both forward transforms run as one batch, 16 elements per thread.  Per block
+// the spectrum D H is stored for k_eq_os_du; the running sum of the correlation spectra stays in a third,
+// unpadded 8192-entry buffer (each thread owns the same bins in every block, so the read-modify-write is
+// race-free and ordered) and goes to the item's row of dhspec once (205 KB of shared memory, one CTA per SM).  The inverse transform lives in its own kernel: in this loop, next to the forward
 // transforms, its index arithmetic would be hoisted into registers that spill.
 __global__ void __launch_bounds__(kOsBwdThreads, 1) k_eq_os_bwd(LaunchCtx c, const Item* __restrict__ items) {
   extern __shared__ float2 sm[];
   __shared__ float red[32];
   float2* D = sm;                 // dL/dy_bar on the segment, then its spectrum
   float2* Ub = sm + kOsP;         // u on the block only, then its spectrum
+  float2* acc = sm + 2 * kOsP;    // running sum of the item's correlation spectra, written to dhspec at the end
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   constexpr int B = kOsM - 2 * kEqHalf;   // 6146
@@ -129,10 +130,16 @@ __global__ void __launch_bounds__(kOsBwdThreads, 1) k_eq_os_bwd(LaunchCtx c, con
       const int k = threadIdx.x + t * kOsBwdThreads, e = pidx(k);
       const float2 dk = D[e];
       const float2 prod = cmulc(dk, Ub[e]);
-      dst[k] = blk == b0 ? prod : cadd(dst[k], prod);
+      acc[k] = blk == b0 ? prod : cadd(acc[k], prod);
       g[k] = cscale(dk, P.hspec[k]);
     }
     __syncthreads();   // the next block overwrites the buffers
+  }
+  // each thread writes the bins it accumulated (no barrier needed)
+#pragma unroll 4
+  for (int t = 0; t < kBins; ++t) {
+    const int k = threadIdx.x + t * kOsBwdThreads;
+    dst[k] = acc[k];
   }
   float out[1];
   block_sum<1>(dwacc, red, out);
@@ -190,7 +197,7 @@ void launch_eq_os_fwd(const LaunchCtx& c, const Item* items, int n) {
   if (n) k_eq_os_fwd<<<n, kOsThreads, kOsP * sizeof(float2), c.stream>>>(c, items);
 }
 void launch_eq_os_bwd(const LaunchCtx& c, const Item* items, int n) {
-  if (n) k_eq_os_bwd<<<n, kOsBwdThreads, 2 * kOsP * sizeof(float2), c.stream>>>(c, items);
+  if (n) k_eq_os_bwd<<<n, kOsBwdThreads, (2 * kOsP + kOsM) * sizeof(float2), c.stream>>>(c, items);
 }
 void launch_eq_os_du(const LaunchCtx& c, const Item* items, int n) {
   if (n) k_eq_os_du<<<n, kOsThreads, kOsP * sizeof(float2), c.stream>>>(c, items);
@@ -201,7 +208,7 @@ void launch_eq_dh_reduce(const LaunchCtx& c, const int* procs, int n) {
 void init_eqos_attributes() {
   cudaFuncSetAttribute(k_eq_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, kOsP * (int)sizeof(float2));
   cudaFuncSetAttribute(k_eq_os_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kOsP * (int)sizeof(float2));
-  cudaFuncSetAttribute(k_eq_os_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kOsP * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_eq_os_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (2 * kOsP + kOsM) * (int)sizeof(float2));
   cudaFuncSetAttribute(k_eq_os_du, cudaFuncAttributeMaxDynamicSharedMemorySize, kOsP * (int)sizeof(float2));
   cudaFuncSetAttribute(k_eq_dh_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, kOsP * (int)sizeof(float2));
 }
