@@ -21,9 +21,10 @@ enum ColMode {
 constexpr int kSlots = 8192 / kColThreads;
 
 // Transposition twiddles of the tile's columns, W(n1 k2) = lo[k2 mod 64] hi[k2 / 64] (W = exp(-2 pi i / N),
-// N2 / 64 <= 32 hi entries), both factors from the accurate table; column gg at ctw + gg * kColTwS.  Visible
-// after the caller's next barrier.
-constexpr int kColTwS = 96;
+// N2 / 64 <= 32 hi entries), both factors from the accurate table; column gg at ctw + gg * kColTwS.  The column
+// stride is 4 (mod 16) float2 so that the eight columns x four rows of a warp's lookups spread evenly over the
+// bank pairs.  Visible after the caller's next barrier.
+constexpr int kColTwS = 100;
 __device__ __forceinline__ void col_tw_init(float2* ctw, const ProcDev& P, int n1b, int G, int N2, const Tables& tab) {
   for (int e = threadIdx.x; e < G * kColTwS; e += blockDim.x) {
     const int gg = e / kColTwS, j = e - gg * kColTwS;

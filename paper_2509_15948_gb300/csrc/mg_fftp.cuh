@@ -454,6 +454,8 @@ __device__ __forceinline__ auto first_ld(LD ld) {
   else return SmemIO();
 }
 
+// BF applies to the passes that read or write global memory (the first with ld, the last with st); the passes
+// between keep the batch-major order, whose shared-memory stores are free of bank conflicts.
 template <bool INV, int SLOTS, bool BF, int LOGM, int LP, class LD, class ST>
 __device__ __forceinline__ void fft_p_from(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw,
                                            LD ld, ST st) {
@@ -462,10 +464,10 @@ __device__ __forceinline__ void fft_p_from(float2* __restrict__ d, int nb, int b
   const auto l = first_ld<LP == 0>(ld);
   using L = std::remove_const_t<decltype(l)>;
   if constexpr (left > 4) {
-    pass<INV, 16, 4, SLOTS, AL, BF, L, SmemIO>(d, LOGM, nb, bs, LP, ptw, l, SmemIO());
+    pass<INV, 16, 4, SLOTS, AL, BF && is_io<L>, L, SmemIO>(d, LOGM, nb, bs, LP, ptw, l, SmemIO());
     fft_p_from<INV, SLOTS, BF, LOGM, LP + 4, LD, ST>(d, nb, bs, ptw, ld, st);
   } else {
-    pass<INV, 1 << left, left, SLOTS, AL, BF, L, ST>(d, LOGM, nb, bs, LP, ptw, l, st);
+    pass<INV, 1 << left, left, SLOTS, AL, BF && (is_io<L> || is_io<ST>), L, ST>(d, LOGM, nb, bs, LP, ptw, l, st);
   }
 }
 }  // namespace fftp
