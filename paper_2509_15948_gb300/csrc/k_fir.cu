@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(256) k_dly_adj(LaunchCtx c, const Item* __rest
   __shared__ float dc[kDlyFir];
   __shared__ float red[2 * 32];
   __shared__ float gsum[2];
+  __shared__ float2 zsh[3];   // z^D, z^(D-1), z clamped to the unit disk
   const Item it = items[blockIdx.x];
   const ProcDev& P = c.procs[it.proc];
   const int ch = it.idx / kDlyTaps, m = it.idx % kDlyTaps;
@@ -142,6 +143,22 @@ __global__ void __launch_bounds__(256) k_dly_adj(LaunchCtx c, const Item* __rest
     cm[threadIdx.x] = P.aux[(ch * kDlyTaps + m) * kDlyFir + threadIdx.x];
     dc[threadIdx.x] = dh[d + threadIdx.x];   // tap time d + j - 19 -> index d + j (first tap at -19)
   }
+  // (b, scalars) the powers of z in double, once per block (FP64 is slow; every thread used to repeat them)
+  if (threadIdx.x == 0) {
+    const double zr = pz[0], zi = pz[1];
+    const double rz = sqrt(zr * zr + zi * zi);
+    const double sc = rz > 1.0 ? 1.0 / rz : 1.0;
+    const double hr = zr * sc, hi = zi * sc, hrad = rz * sc;
+    const double th = atan2(hi, hr);
+    double sD, cD, sD1, cD1;
+    sincos((double)D * th, &sD, &cD);
+    sincos((double)(D - 1) * th, &sD1, &cD1);
+    const double pD = hrad > 0.0 ? pow(hrad, (double)D) : 0.0;
+    const double pD1 = hrad > 0.0 ? pow(hrad, (double)(D - 1)) : 0.0;
+    zsh[0] = make_float2((float)(pD * cD), (float)(pD * sD));
+    zsh[1] = make_float2((float)(pD1 * cD1), (float)(pD1 * sD1));
+    zsh[2] = make_float2((float)hr, (float)hi);
+  }
   __syncthreads();
   // (a) log-magnitudes of c_m
   if (threadIdx.x <= kDlyHalf) {
@@ -154,20 +171,8 @@ __global__ void __launch_bounds__(256) k_dly_adj(LaunchCtx c, const Item* __rest
     gz[2 + k] = expf(pz[2 + k]) * (k == 0 ? 1.f : 2.f) * (1.f / kDlyFir) * acc;
   }
   // (b) angular frequency
-  const double zr = pz[0], zi = pz[1];
-  const double rz = sqrt(zr * zr + zi * zi);
-  const double sc = rz > 1.0 ? 1.0 / rz : 1.0;
-  const double hr = zr * sc, hi = zi * sc, hrad = rz * sc;
-  const double th = atan2(hi, hr);
-  double sD, cD, sD1, cD1;
-  sincos((double)D * th, &sD, &cD);
-  sincos((double)(D - 1) * th, &sD1, &cD1);
-  const double pD = hrad > 0.0 ? pow(hrad, (double)D) : 0.0;
-  const double pD1 = hrad > 0.0 ? pow(hrad, (double)(D - 1)) : 0.0;
-  const float2 zD = make_float2((float)(pD * cD), (float)(pD * sD));
-  const float2 zD1 = make_float2((float)(pD1 * cD1), (float)(pD1 * sD1));
-  const float2 zh = make_float2((float)hr, (float)hi);
-  const float2 omz = make_float2(1.f - zD.x, -zD.y);
+  const float2 zD1 = zsh[1], zh = zsh[2];
+  const float2 omz = make_float2(1.f - zsh[0].x, -zsh[0].y);
   double accd[2] = {0.0, 0.0};
   for (int q = threadIdx.x; q < D; q += blockDim.x) {
     float G = 0.f;
@@ -225,6 +230,8 @@ __global__ void __launch_bounds__(256) k_dly_adj(LaunchCtx c, const Item* __rest
     (void)red;
   }
   if (threadIdx.x == 0) {
+    const double zr = pz[0], zi = pz[1];
+    const double rz = sqrt(zr * zr + zi * zi);
     const float gr = gsum[0], gi = gsum[1];
     const float gm = sqrtf(gr * gr + gi * gi);
     float outr = 0.f, outi = 0.f;
