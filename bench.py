@@ -155,6 +155,22 @@ def kernel_src_sha1():
     return h.hexdigest()
 
 
+def aggregate_over_ranks(elapsed_ms: float, units: float, world: int):
+    """Whole-job timing of a weak-scaling run (each rank its own batch): the maximum of the ranks' elapsed times
+    and the sum of the units they processed, over the default process group (NCCL on GPUs, gloo on CPUs).  One
+    rank returns its own values."""
+    if world <= 1:
+        return elapsed_ms, units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -418,12 +434,9 @@ def main():
     stage = con.stage_times()
     fam = con.kernel_times()
     con.set_profiling(False)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms, job_track_seconds = aggregate_over_ranks(elapsed_ms, track_seconds, world)
     ms_per_step = elapsed_ms / args.steps
-    value = world * track_seconds / (ms_per_step / 1e3)
+    value = job_track_seconds / (ms_per_step / 1e3)
     finite = bool(torch.isfinite(losses).all().item())
 
     # roofline of the dominant kernel (largest device time per step): its algorithmic bytes per launch over its
@@ -468,6 +481,8 @@ def main():
         con.set_launch_mode(True)
         con.train_step(lr=1e-2)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(con.stream)
@@ -475,8 +490,9 @@ def main():
             con.train_step(lr=1e-2)
         b.record(con.stream)
         torch.cuda.synchronize()
-        pn_ms = a.elapsed_time(b) / args.per_node_steps
-        per_node = {"value": world * track_seconds / (pn_ms / 1e3), "ms_per_step": pn_ms,
+        pn_total, pn_units = aggregate_over_ranks(a.elapsed_time(b), track_seconds, world)
+        pn_ms = pn_total / args.per_node_steps
+        per_node = {"value": pn_units / (pn_ms / 1e3), "ms_per_step": pn_ms,
                     "batched_speedup": pn_ms / ms_per_step}
         con.set_launch_mode(False)
 
@@ -488,6 +504,8 @@ def main():
         host_losses = torch.empty(con.n_songs, 7, dtype=torch.float32).pin_memory()
         h2d = sum(s.numel() * 4 + t.numel() * 4 for s, t in zip(pinned_src, pinned_tgt))
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             for s in range(con.n_songs):
@@ -495,8 +513,9 @@ def main():
             l = con.train_step(lr=1e-2)
             host_losses.copy_(l, non_blocking=False)
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        e2e = {"value": world * track_seconds / e2e_s, "unit": "track-s/s", "h2d_bytes_per_step": int(h2d),
+        e2e_total_ms, e2e_units = aggregate_over_ranks(1e3 * (time.perf_counter() - t0), track_seconds, world)
+        e2e_s = e2e_total_ms / 1e3 / args.e2e_steps
+        e2e = {"value": e2e_units / e2e_s, "unit": "track-s/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(host_losses.numel() * 4), "ms_per_step": 1e3 * e2e_s}
 
     # ---------------- CPU baseline: the oracle on a bounded sample ----------------
