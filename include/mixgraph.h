@@ -246,6 +246,9 @@ mg_status mg_schedule_io(const int32_t* node_step, const int32_t* order, int32_t
                          const int32_t* edge_src, const int32_t* edge_dst, int32_t n_edges, int32_t* step_begin,
                          int32_t* gather_begin, int32_t* gather_src, int32_t* gather_dst);
 
+/* Message of the last failed call: on console c (valid until the next call on c), or, with c = NULL, of the last
+ * failed call of this host thread that had no console (creation, planning, scheduling).  Never NULL; the
+ * empty string before any failure.  The library owns the string. */
 const char* mg_last_error(const mg_console* c);
 
 #ifdef __cplusplus
