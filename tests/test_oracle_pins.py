@@ -373,3 +373,164 @@ def test_adam_first_step_closed_form():
     g = np.array([0.5, -2.0, 1e-3, 0.0])
     p, m, v = A.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, lr=0.01)
     assert np.allclose(p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)   # m_hat = g, v_hat = g^2
+
+
+def test_adam_later_steps_closed_form():
+    """Kingma-Ba bias correction at t = 2 and 3 (Sec. 5.1 optimiser).  With a constant gradient g the corrected
+    moments are exactly g and g^2 at every t (m_t = (1 - b1^t) g), so every step moves by -lr g / (|g| + eps);
+    with gradients g1 then g2 the corrected moments at t = 2 are (b1 g1 + g2) / (1 + b1) and
+    (b2 g1^2 + g2^2) / (1 + b2) (the geometric sums divided by 1 - b^2 = (1 - b)(1 + b)).  A wrong exponent in
+    either correction, or the moments updated in the other order, fails one of these."""
+    g = np.array([0.5, -2.0, 1e-3, 3.0])
+    p, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in (1, 2, 3):
+        p, m, v = A.adam_step(p, g, m, v, t, lr=0.01)
+        assert np.allclose(p, -0.01 * t * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15), t
+    b1, b2 = 0.9, 0.999
+    g1 = np.array([0.5, -2.0, 1e-3, 3.0])
+    g2 = np.array([-1.5, 0.25, 2e-3, 3.0])
+    p1, m1, v1 = A.adam_step(np.ones(4), g1, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    p2, _, _ = A.adam_step(p1, g2, m1, v1, 2, lr=0.01)
+    mhat = (b1 * g1 + g2) / (1.0 + b1)
+    vhat = (b2 * g1 ** 2 + g2 ** 2) / (1.0 + b2)
+    assert np.allclose(p2, p1 - 0.01 * mhat / (np.sqrt(vhat) + 1e-8), rtol=1e-12, atol=1e-15)
+    # decoupled weight decay: p <- p (1 - lr wd) before the moment step
+    p3, _, _ = A.adam_step(np.full(4, 2.0), g, np.zeros(4), np.zeros(4), 1, lr=0.01, weight_decay=0.1)
+    assert np.allclose(p3, 2.0 * (1 - 0.001) - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------------------------------------------------------
+# Eq. (22) gain staging: closed-form values
+# ------------------------------------------------------------------------------------------------
+
+def test_gain_staging_closed_forms():
+    """Eq. (22): |log ||y_bar_mid||_2 - log ||u_mid||_2| with mid = left + right.
+    * y_bar = 2 u gives ln 2 (not 2 ln 2: the log of the norm, not of the energy);
+    * a sine of amplitude A over whole periods, on both channels, has ||mid||^2 = (2A)^2 L / 2;
+    * the mid is the channel sum: (2x, 0) and (x, x) have the same mid, so the term is 0, while a left-only or
+      per-channel-energy reading would give ln 2 or ln sqrt 2; (x, -x) has a silent mid (the 1e-12 floor)."""
+    r = rng(21)
+    u = t64(r.standard_normal((2, 5000)))
+    assert float(Lo.gain_staging(2.0 * u, u)) == pytest.approx(math.log(2.0), rel=1e-12)
+    assert float(Lo.gain_staging(u, 0.25 * u)) == pytest.approx(math.log(4.0), rel=1e-12)
+    L, A_, B_ = 4800, 0.3, 1.7
+    n = np.arange(L)
+    s = np.sin(2 * np.pi * 12 * n / L)                      # 12 whole periods
+    us, ys = t64(np.stack([A_ * s, A_ * s])), t64(np.stack([B_ * s, B_ * s]))
+    assert float(Lo.log_l2(us[0] + us[1])) == pytest.approx(0.5 * math.log((2 * A_) ** 2 * L / 2), rel=1e-12)
+    assert float(Lo.gain_staging(ys, us)) == pytest.approx(math.log(B_ / A_), rel=1e-12)
+    x = t64(r.standard_normal(3000))
+    both = torch.stack([x, x])
+    left = torch.stack([2.0 * x, torch.zeros_like(x)])
+    assert float(Lo.gain_staging(left, both)) == pytest.approx(0.0, abs=1e-12)
+    anti = torch.stack([x, -x])
+    expect = abs(0.5 * math.log(1e-12) - 0.5 * math.log(float(torch.sum((2 * x) ** 2))))
+    assert float(Lo.gain_staging(anti, both)) == pytest.approx(expect, rel=1e-12)
+
+
+def test_console_gain_staging_sums_lti_nodes():
+    """L_g of a console (Eq. 22 summed over the equalizer, reverb and delay nodes): a flat Eq. (7) response
+    exp(c) is the impulse exp(c) delta (v[0] = 1), so an equalizer with every log-magnitude equal to c scales
+    its input by exp(c) and contributes |c|, whatever its dry/wet weight; gain/pan nodes contribute nothing."""
+    L = 3000
+    r = rng(22)
+    songs = [C.SongSpec(2, 1, [0, -1], L)]
+    src = [r.standard_normal((2, L)).astype(np.float32)]
+    con = C.Console(songs, src, None, None, C.ConsoleDesc(types="eg"))
+    params = np.zeros(con.n_params)
+    consts = {}
+    for p in con.procs:
+        if p.type == "e":
+            c = float(r.uniform(-1.5, 1.5))
+            params[p.offset:p.offset + p.count] = c
+            consts[p.index] = c
+        else:
+            params[p.offset:p.offset + p.count] = r.normal(0, 0.5, p.count)
+    params[con.n_proc_params:] = r.normal(0, 1.0, con.n_procs)
+    with torch.no_grad():
+        res = con.forward(t64(params))
+    assert float(res[0]["Lg"]) == pytest.approx(sum(abs(c) for c in consts.values()), rel=1e-9)
+
+
+# ------------------------------------------------------------------------------------------------
+# Sec. 3.4 reverb decay (Eq. 10), frame by frame
+# ------------------------------------------------------------------------------------------------
+
+def _one_bin_spec(F, k0):
+    spec = torch.zeros(F, 193, dtype=torch.complex128)
+    spec[:, k0] = 1.0
+    return spec
+
+
+@pytest.mark.parametrize("k0", [5, 192])
+def test_reverb_decay_frame_by_frame(k0):
+    """Eq. (10): the mask of frame m (1-based) is exp(H0[k] + (m - 1) H_delta[k]), read with
+    H_delta = -0.05 softplus(p_delta).  A noise spectrum holding 1 in bin k0 of every frame is masked and
+    inverted; at the centre of frame t (0-based, sample t hop + n/2) only that frame's window is nonzero and
+    equals 1 (periodic Hann, hop n/2), and the window-sum there is 1, so the FIR sample is the inverse DFT of
+    the single bin at n/2: (2/n) a_t (-1)^k0 for an inner bin and a_t / n for the Nyquist bin, a_t the mask.
+    So h[centre of frame 0] fixes exp(H0) (no decay at the first frame), and the ratio of consecutive centres
+    is exp(H_delta) whatever the frame.  k0 = 192 is the Nyquist bin, which reuses parameter 191."""
+    n, hop, F = 384, 192, 40
+    L = (F - 1) * hop + n
+    h0m, pdm = 0.7, 0.4              # mid: H0 and p_delta of the probed bin
+    h0s, pds = -0.3, -1.2            # side
+    p = torch.zeros(2, 2, 192, dtype=F64)
+    pk = min(k0, 191)
+    p[0, 0, :] = -9.0                # every other bin is irrelevant (zero noise); keep them distinct anyway
+    p[1, 0, :] = -9.0
+    p[0, 0, pk], p[0, 1, pk] = h0m, pdm
+    p[1, 0, pk], p[1, 1, pk] = h0s, pds
+    spec = torch.stack([_one_bin_spec(F, k0), _one_bin_spec(F, k0)])
+    h = P.reverb_fir(p.reshape(-1), spec, L).numpy()
+    hm, hs = (h[0] + h[1]) / 2, (h[0] - h[1]) / 2           # h_l = h_m + h_s, h_r = h_m - h_s
+    scale = (1.0 / n) if k0 == n // 2 else (2.0 / n) * (-1.0) ** k0
+
+    def softplus(x):
+        return math.log1p(math.exp(x))
+
+    for hx, h0, pd in ((hm, h0m, pdm), (hs, h0s, pds)):
+        centres = np.array([hx[t * hop + n // 2] for t in range(F)])
+        assert centres[0] == pytest.approx(scale * math.exp(h0), rel=1e-10)
+        decay = math.exp(-0.05 * softplus(pd))
+        assert np.allclose(centres[1:] / centres[:-1], decay, rtol=1e-10, atol=0)
+        assert np.allclose(centres, scale * np.exp(h0 - 0.05 * softplus(pd) * np.arange(F)), rtol=1e-10, atol=0)
+
+
+# ------------------------------------------------------------------------------------------------
+# Sec. 5.1 warm-up: which frames the loss keeps
+# ------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("warmup", [0, 1, 127, 128, 129, 1000, 44100])
+def test_warmup_drops_frames_starting_before_it(warmup):
+    """Frames that start before `warmup` samples are dropped (Sec. 5.1 leaves the first second out of the
+    loss).  Checked against a hand count of the frame starts t hop < warmup, and by value: two signals that
+    differ only before the warm-up give a zero loss, while a difference at the second sample of the first kept
+    frame does not (so that frame is not dropped too)."""
+    n_fft, hop = 512, 128
+    L = 60000
+    x = t64(rng(23).standard_normal(L))
+    desc0 = Lo.LossDesc(n_fft=(n_fft,), n_mels=0, a_weighting=False, warmup_samples=0)
+    descw = Lo.LossDesc(n_fft=(n_fft,), n_mels=0, a_weighting=False, warmup_samples=warmup)
+    full = Lo.spectrogram(x, n_fft, desc0)
+    kept = Lo.spectrogram(x, n_fft, descw)
+    starts = [t * hop for t in range(full.shape[0])]
+    dropped = sum(1 for s in starts if s < warmup)
+    assert kept.shape[0] == full.shape[0] - dropped
+    assert torch.equal(kept, full[dropped:])
+    if warmup == 0:
+        return
+    y = torch.stack([x, x.flip(0)])
+    yh = y.clone()
+    yh[:, :warmup] += 0.5                   # differs only before the warm-up
+    parts = Lo.audio_loss(yh, y, Lo.LossDesc(n_fft=(n_fft,), hop_div=4, n_mels=0, a_weighting=False,
+                                             warmup_samples=warmup))
+    assert float(parts["a"]) == 0.0
+    # sample s0 + 1, s0 = ceil(warmup / hop) hop the start of the first kept frame (its window is 0 at s0):
+    # only frames starting at or before it cover it, and of those only the first kept frame is kept
+    s0 = dropped * hop
+    yh2 = y.clone()
+    yh2[:, s0 + 1] += 0.5
+    parts2 = Lo.audio_loss(yh2, y, Lo.LossDesc(n_fft=(n_fft,), hop_div=4, n_mels=0, a_weighting=False,
+                                               warmup_samples=warmup))
+    assert float(parts2["a"]) > 0.0
