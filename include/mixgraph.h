@@ -199,16 +199,20 @@ mg_status mg_debug_read(const mg_console* c, int32_t proc, int32_t what, float* 
  * y_bar = h_e * u (Eqs. 7-8) and w = sigmoid(q), using the same kernels as the console.
  *   d_u:      device [2][L] stereo input (left row, then right row), FP32
  *   d_y:      device [2][L] output (must not overlap d_u)
- *   L:        1 <= L <= 127,001 samples (the 2^17-point FFT must hold the signal and the 2047-tap FIR);
- *             larger L returns MG_ERR_UNSUPPORTED without touching the GPU
+ *   L:        1 <= L <= 128,001 samples (the 2^17-point FFT must hold the signal and the 2047-tap FIR without
+ *             wrap-around: L + 2047 + 1023 + 1 <= 2^17); larger L returns MG_ERR_UNSUPPORTED without touching the GPU
  *   d_params: device [1025]: the 1024 log-magnitudes of Eq. (7), then the dry/wet logit q
  * Scratch: one file-scope __device__ array of about 3.3 MB, held by every GPU that loads the library until the
  * process exits.  Every buffer in it is fully written before it is read within a call, so nothing needs
  * clearing; calls share the array, so calls that overlap on the GPU (on different streams, or on the same
  * device from several threads without ordering) race and must not be issued.
- * The first call on a device, made with that device current, sets the scratch up (symbol address and lookup
- * tables) and synchronises the stream: make that first call before any stream capture.  Later calls are
- * asynchronous on `stream`.  Returns MG_ERR_INVALID for null pointers and MG_ERR_CUDA if a CUDA call fails. */
+ * Every call looks up the array's device address on the current device (cudaGetSymbolAddress, which allocates
+ * nothing).  The first call on a device, made with that device current, builds the lookup tables in the array
+ * and synchronises the stream: make that first call before any stream capture.  If the address ever changes
+ * (the module was reloaded after a device reset), the next call rebuilds the tables the same way.  Later calls
+ * are asynchronous on `stream`.  Returns MG_ERR_INVALID for null pointers, and MG_ERR_CUDA if a CUDA call
+ * fails or if a CUDA error from earlier work on this host thread is still pending on entry (then nothing is
+ * launched and that error is left for its owner to read). */
 mg_status mg_eq_forward_noalloc(const float* d_u, float* d_y, int64_t L, const float* d_params, cudaStream_t stream);
 
 /* Evaluation metrics of every song's mix from the most recent forward (forward_loss, train_step or

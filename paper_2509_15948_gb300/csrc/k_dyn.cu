@@ -78,6 +78,25 @@ __device__ __forceinline__ float gain_law_v(const DynParams& d, float G) {
   return gain_law(d, G, a, b, cc, e);
 }
 
+// Samples of a quad at and beyond L are zeroed on load and skipped on store, so nothing depends on what the
+// padding of a [2][ld] buffer holds.
+__device__ __forceinline__ float4 tail_zero(float4 a, int n, int L) {
+  if (n + 1 >= L) a.y = 0.f;
+  if (n + 2 >= L) a.z = 0.f;
+  if (n + 3 >= L) a.w = 0.f;
+  return a;
+}
+
+__device__ __forceinline__ void store_quad(float* p, int n, int L, float x, float y, float z, float w) {
+  if (n + 4 <= L) {
+    *reinterpret_cast<float4*>(p + n) = make_float4(x, y, z, w);
+    return;
+  }
+  p[n] = x;
+  if (n + 1 < L) p[n + 1] = y;
+  if (n + 2 < L) p[n + 2] = z;
+}
+
 // Loads this thread's 16 consecutive samples of a [2][ld] buffer (zeros at and beyond L).
 __device__ __forceinline__ void load16(const float* base, int ld, int L, int n0, float (&l)[kPer], float (&r)[kPer]) {
 #pragma unroll
@@ -85,8 +104,8 @@ __device__ __forceinline__ void load16(const float* base, int ld, int L, int n0,
     const int n = n0 + 4 * j;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
     if (n < L) {
-      a = *reinterpret_cast<const float4*>(base + n);
-      b = *reinterpret_cast<const float4*>(base + ld + n);
+      a = tail_zero(*reinterpret_cast<const float4*>(base + n), n, L);
+      b = tail_zero(*reinterpret_cast<const float4*>(base + ld + n), n, L);
     }
     l[4 * j] = a.x; l[4 * j + 1] = a.y; l[4 * j + 2] = a.z; l[4 * j + 3] = a.w;
     r[4 * j] = b.x; r[4 * j + 1] = b.y; r[4 * j + 2] = b.z; r[4 * j + 3] = b.w;
@@ -98,8 +117,8 @@ __device__ __forceinline__ void store16(float* base, int ld, int L, int n0, cons
   for (int j = 0; j < kPer / 4; ++j) {
     const int n = n0 + 4 * j;
     if (n < L) {
-      *reinterpret_cast<float4*>(base + n) = make_float4(l[4 * j], l[4 * j + 1], l[4 * j + 2], l[4 * j + 3]);
-      *reinterpret_cast<float4*>(base + ld + n) = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+      store_quad(base, n, L, l[4 * j], l[4 * j + 1], l[4 * j + 2], l[4 * j + 3]);
+      store_quad(base + ld, n, L, r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
     }
   }
 }
@@ -110,7 +129,7 @@ __device__ __forceinline__ void load16m(const float* base, int L, int n0, float 
   for (int j = 0; j < kPer / 4; ++j) {
     const int n = n0 + 4 * j;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (n < L) a = *reinterpret_cast<const float4*>(base + n);
+    if (n < L) a = tail_zero(*reinterpret_cast<const float4*>(base + n), n, L);
     v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
   }
 }
@@ -119,7 +138,7 @@ __device__ __forceinline__ void store16m(float* base, int L, int n0, const float
 #pragma unroll
   for (int j = 0; j < kPer / 4; ++j) {
     const int n = n0 + 4 * j;
-    if (n < L) *reinterpret_cast<float4*>(base + n) = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    if (n < L) store_quad(base, n, L, v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
   }
 }
 

@@ -108,8 +108,7 @@ __global__ void k_na_prep(const float* u, float* y, const float* params, int L, 
 }
 
 struct DeviceScratch {
-  NaLayout* ptr = nullptr;
-  bool ready = false;
+  NaLayout* ptr = nullptr;   // address the tables were built at (null: not built yet)
 };
 std::mutex g_na_mutex;
 DeviceScratch g_na_dev[64];
@@ -123,22 +122,27 @@ extern "C" mg_status mg_eq_forward_noalloc(const float* d_u, float* d_y, int64_t
                                            cudaStream_t stream) {
   if (!d_u || !d_y || !d_params) return MG_ERR_INVALID;
   if (num_samples < 1 || num_samples > kNaMaxSamples) return MG_ERR_UNSUPPORTED;
+  // An error left pending by earlier work on this thread would be indistinguishable from this call's own
+  // launch errors below: refuse to launch, and leave it in place for its owner.
+  if (cudaPeekAtLastError() != cudaSuccess) return MG_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MG_ERR_CUDA;
   NaLayout* S = nullptr;
   {
-    // set-up on the first call on this device (with this device current): symbol address and tables
+    // The symbol's device address is looked up on every call (the lookup allocates nothing): if the module was
+    // reloaded (a device reset, a new context) the array may have moved and lost its tables, which are then
+    // rebuilt.  Building them synchronises the stream, so the first call on a device comes before any capture.
     std::lock_guard<std::mutex> lock(g_na_mutex);
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return MG_ERR_CUDA;
     DeviceScratch& ds = g_na_dev[dev];
-    if (!ds.ready) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return MG_ERR_CUDA;
-      ds.ptr = reinterpret_cast<NaLayout*>(p);
+    if (ds.ptr != reinterpret_cast<NaLayout*>(p)) {
+      ds.ptr = nullptr;
       init_kernel_attributes();
       k_na_tables<<<16, 256, 0, stream>>>();
       if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
       if (cudaStreamSynchronize(stream) != cudaSuccess) return MG_ERR_CUDA;
-      ds.ready = true;
+      ds.ptr = reinterpret_cast<NaLayout*>(p);
     }
     S = ds.ptr;
   }
@@ -169,5 +173,6 @@ extern "C" mg_status mg_eq_forward_noalloc(const float* d_u, float* d_y, int64_t
   launch_col_fwd_audio(x, S->col_items, N1 / G, N2 * G);
   launch_row_conv_fwd(x, S->pair_items, N2 / 2 + 1, N1, false);
   launch_col_inv_out(x, S->col_items, N1 / G, N2 * G);
+  // no error was pending on entry, so whatever is pending now came from these launches
   return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
 }

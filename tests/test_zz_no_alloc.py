@@ -15,6 +15,7 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5   # relative L2, the bound the console's mixes are held to
+MAX_L = 2 ** 17 - 2047 - 1023 - 1   # 128,001: the 2^17-point FFT holds the signal and the 2047-tap FIR
 
 
 def _rel(a, b):
@@ -22,20 +23,22 @@ def _rel(a, b):
 
 
 def test_noalloc_equalizer_matches_console_twice():
+    """Two calls in a row with different lengths (the largest accepted L, a 2^17-point FFT, then a short one
+    with a 2^12-point FFT), so that the second call reuses a scratch array left holding another size's data;
+    each output is compared with the console's equalizer on the same input and parameters."""
     import torch
     import paper_2509_15948_gb300 as M
     lib = M.load_library()
     lib.mg_eq_forward_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_void_p]
     lib.mg_eq_forward_noalloc.restype = ctypes.c_int
-    L = 100_003
-    src = W.song_sources(W.SongLayout(1, 0, [-1], L), (42, 0))
-    tgt = np.zeros((2, L), np.float32)
-    con = M.Console([M.Song(1, 0, [-1], L)], [src], [tgt], None, M.ConsoleConfig(types="e"))
     stream = torch.cuda.Stream()
-    u = torch.as_tensor(np.stack([src[0], src[0]])).cuda().contiguous()
     rng = np.random.default_rng(0)
-    for call in range(2):
+    for call, L in enumerate((MAX_L, 3001)):
+        src = W.song_sources(W.SongLayout(1, 0, [-1], L), (42, call))
+        tgt = np.zeros((2, L), np.float32)
+        con = M.Console([M.Song(1, 0, [-1], L)], [src], [tgt], None, M.ConsoleConfig(types="e"))
+        u = torch.as_tensor(np.stack([src[0], src[0]])).cuda().contiguous()
         params = np.concatenate([rng.uniform(-1.0, 1.0, 1024), [rng.normal()]]).astype(np.float32)
         con.set_params(params)
         _, mixes = con.forward_loss(with_mix=True)
@@ -46,9 +49,9 @@ def test_noalloc_equalizer_matches_console_twice():
         st = lib.mg_eq_forward_noalloc(u.data_ptr(), y.data_ptr(), L, p.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
         assert st == M.MG_OK
         stream.synchronize()
-        assert _rel(y.cpu().numpy(), ref) <= TOL, (call, _rel(y.cpu().numpy(), ref))
-    # sizes beyond the scratch bound are refused before any GPU work
-    big = torch.zeros(2, 200_000, device="cuda")
-    assert lib.mg_eq_forward_noalloc(big.data_ptr(), big.data_ptr(), 200_000, p.data_ptr(),
+        assert _rel(y.cpu().numpy(), ref) <= TOL, (call, L, _rel(y.cpu().numpy(), ref))
+        con.close()
+    # one sample beyond the scratch bound is refused before any GPU work
+    big = torch.zeros(2, MAX_L + 1, device="cuda")
+    assert lib.mg_eq_forward_noalloc(big.data_ptr(), big.data_ptr(), MAX_L + 1, p.data_ptr(),
                                      ctypes.c_void_p(stream.cuda_stream)) == M.MG_ERR_UNSUPPORTED
-    con.close()
