@@ -80,6 +80,54 @@ def model_bytes(layouts, types="ecnsgdr"):
     return tot, per_type
 
 
+# FP32 peak of the GB300 from its unit counts: 152 SMs x 128 FP32 lanes x 2 flops per FMA x the SM clock
+N_SM, FP32_LANES = 152, 128
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    return N_SM * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+
+
+def rfft_flops(n) -> float:
+    """2.5 n log2 n flops per real FFT of size n."""
+    n = float(n)
+    return 2.5 * n * math.log2(n) if n > 1 else 0.0
+
+
+def model_flops(layouts, types="ecnsgdr", fs=FS, n_fft=(512, 2048, 8192), hop_div=4, warmup=0):
+    """Algorithmic FP32 flops of one fwd+bwd step, counting FFTs only (2.5 n log2 n per real FFT of size n):
+    * reverb r and delay d: one FFT convolution per node at the linear-convolution length n = L + Nh - 1
+      (Nh = 2 fs taps for r; 20 slots of round(0.1 fs) plus 38 for d), 12 real FFTs per node and step
+      (forward: u, h and the inverse, per channel; backward: dy, and the inverses to du and dL/dh, per
+      channel); r adds its FIR synthesis, a 384-point inverse STFT of mid and side (Eqs. 9-10) and its adjoint;
+    * equalizer e (2047 taps): overlap-save with 8192-point blocks of 6146 outputs, 8 real FFTs per block
+      (forward: u and the inverse per channel; backward: dy and the inverse to du per channel) plus 4 per node
+      (filter spectrum, inverse of the tap correlation);
+    * loss: per resolution n and frame, the two channels' forward STFTs and their two adjoint inverses
+      (4 real FFTs of n; the target spectra are computed once, M and S follow from L and R by linearity)."""
+    nh_r = int(round(2 * fs))
+    D = int(round(0.1 * fs))
+    nh_d = 20 * D + 38
+    rev_frames = (nh_r - 384) // 192 + 1
+    out = {"e": 0.0, "r": 0.0, "d": 0.0, "loss": 0.0}
+    for l in layouts:
+        chains = l.num_tracks + l.num_subgroups
+        L = l.num_samples
+        if "r" in types:
+            out["r"] += chains * (12 * rfft_flops(L + nh_r - 1) + 4 * rev_frames * rfft_flops(384))
+        if "d" in types:
+            out["d"] += chains * 12 * rfft_flops(L + nh_d - 1)
+        if "e" in types:
+            blocks = -(-L // 6146)
+            out["e"] += chains * (8 * blocks + 4) * rfft_flops(8192)
+        for n in n_fft:
+            hop = n // hop_div
+            frames = (L - n) // hop + 1 if L >= n else 0
+            frames -= min(frames, -(-warmup // hop))
+            out["loss"] += 4 * frames * rfft_flops(n)
+    return out
+
+
 # ------------------------------------------------------------------------------------------------
 # clocks sampling during the timed region
 # ------------------------------------------------------------------------------------------------
@@ -355,6 +403,7 @@ def main():
     ap.add_argument("--songs", type=int, default=64, help="songs of the uneven batch (smaller: profiling cases)")
     ap.add_argument("--profiler-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--prof-steps", type=int, default=3, help="instrumented steps of the stage split")
     ap.add_argument("--per-node-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-baseline-steps", type=int, default=3)
@@ -407,10 +456,7 @@ def main():
     launches_per_step = con.get_info()["launches_per_step"]
 
     # ---------------- timed region (device time, CUDA events on the console's stream) ----------------
-    con.set_profiling(True)
-    con.train_step(lr=1e-2)               # capture the instrumented graph outside the timed region
-    torch.cuda.synchronize()
-    con.reset_kernel_times()
+    # the graph is replayed without per-launch events: the headline carries no instrumentation
     clocks = ClockSampler(dev)
     clocks.start()
     if world > 1:
@@ -431,49 +477,78 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     elapsed_ms = ev0.elapsed_time(ev1)
-    stage = con.stage_times()
-    fam = con.kernel_times()
-    con.set_profiling(False)
     elapsed_ms, job_track_seconds = aggregate_over_ranks(elapsed_ms, track_seconds, world)
     ms_per_step = elapsed_ms / args.steps
     value = job_track_seconds / (ms_per_step / 1e3)
     finite = bool(torch.isfinite(losses).all().item())
 
-    # roofline of the dominant kernel (largest device time per step): its algorithmic bytes per launch over its
-    # CUDA-event time per launch (events on the console stream around each launch of the family); also the
-    # dominant stage against the byte model of 5 streams per node, and the whole step
+    # ---------------- stage split: a separate pass with CUDA events around every launch ----------------
+    prof_steps = max(1, args.prof_steps)
+    con.set_profiling(True)
+    con.train_step(lr=1e-2)               # captures the instrumented graph
+    torch.cuda.synchronize()
+    con.reset_kernel_times()
+    pa = torch.cuda.Event(enable_timing=True)
+    pb = torch.cuda.Event(enable_timing=True)
+    pa.record(con.stream)
+    for _ in range(prof_steps):
+        con.train_step(lr=1e-2)
+    pb.record(con.stream)
+    torch.cuda.synchronize()
+    prof_ms_per_step = pa.elapsed_time(pb) / prof_steps
+    stage = con.stage_times()
+    fam = con.kernel_times()
+    con.set_profiling(False)
+    con.train_step(lr=1e-2)               # back to the uninstrumented graph for the legs below
+    torch.cuda.synchronize()
+
+    # roofline of the dominant stage (largest device time per step among the processor types): its algorithmic
+    # bytes (5 stereo FP32 streams per node-sample) over its CUDA-event time per step; the whole step the same
+    # way; the FP32-ALU fraction of the FFT stages under the flop model; and the four-step row kernel against
+    # the bytes of its own FFT grid (an implementation figure, kept for comparison)
     peak, peak_kind = measured_peaks()
-    proc_stages = {k: v for k, v in stage.items() if k in "ecnsgdr"}
-    dom = max(proc_stages, key=lambda k: proc_stages[k][0])
-    dom_ms_per_step = proc_stages[dom][0] / args.steps
-    dom_bytes = type_bytes[dom]
-    stage_achieved = dom_bytes / (dom_ms_per_step / 1e3) / 1e9
+    stage_step = {k: v[0] / prof_steps for k, v in stage.items()}
+    proc_stages = {k: v for k, v in stage_step.items() if k in "ecnsgdr"}
+    dom = max(proc_stages, key=lambda k: proc_stages[k])
+    dom_ms = proc_stages[dom]
+    stage_achieved = type_bytes[dom] / (dom_ms / 1e3) / 1e9
     step_achieved = tot_bytes / (ms_per_step / 1e3) / 1e9
-    stage_roof = {"stage": dom, "achieved": stage_achieved, "frac": stage_achieved / peak, "model_bytes": dom_bytes,
-                  "ms_per_step": dom_ms_per_step}
-    fam_step = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in fam.items() if v[1] > 0}
-    dom_k = max(fam_step, key=lambda k: fam_step[k][0])
+    sm_clk = clk.get("sm_max_mhz") or 2070.0
+    fpk = fp32_peak_tflops(sm_clk)
+    flops = model_flops(layouts)
+    alu = {}
+    for k, fl in flops.items():
+        t = stage_step.get(k, 0.0)
+        if fl > 0 and t > 0:
+            tf = fl / (t / 1e3) / 1e12
+            alu[k] = {"model_gflop": fl / 1e9, "ms_per_step": t, "achieved_tflops": tf, "frac": tf / fpk}
+    roofline = {"bound": "hbm", "kernel": f"stage {dom} (every fwd+bwd launch of its type, per step)",
+                "achieved": stage_achieved, "peak": peak, "unit": "GB/s", "frac": stage_achieved / peak,
+                "traffic": None, "model_bytes": type_bytes[dom], "ms_per_step": dom_ms,
+                "byte_model": "5 stereo FP32 streams per node-sample (fwd reads u, writes y; bwd reads dy, u, "
+                              "writes du)",
+                "peak_source": f"{peak_kind} hbm_gbs (copy burst)",
+                "step": {"achieved": step_achieved, "frac": step_achieved / peak, "model_bytes": tot_bytes,
+                         "ms_per_step": ms_per_step},
+                "alu": {"peak_tflops": fpk, "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_clk:.0f} MHz",
+                        "flop_model": "FFTs only, 2.5 n log2 n per real FFT of size n", "stages": alu},
+                "instrumented_ms_per_step": prof_ms_per_step}
+    fam_step = {k: (v[0] / prof_steps, v[1] / prof_steps) for k, v in fam.items() if v[1] > 0}
     ptypes = con.processor_types()
     grid_points = sum(int(f) << int(logn) for (f, logn, _), t in zip(con.fft_sizes(), ptypes) if f and t in "dr")
-    if dom_k in KERNEL_BYTES_PER_POINT and grid_points:
-        launches = fam_step[dom_k][1]
-        ms_launch = fam_step[dom_k][0] / launches
-        bytes_launch = KERNEL_BYTES_PER_POINT[dom_k] * grid_points / launches
+    if "row_bwd2" in fam_step and grid_points:
+        launches = fam_step["row_bwd2"][1]
+        ms_launch = fam_step["row_bwd2"][0] / launches
+        bytes_launch = KERNEL_BYTES_PER_POINT["row_bwd2"] * grid_points / launches
         achieved = bytes_launch / (ms_launch / 1e3) / 1e9
         traffic = None
-        if dom_k == "row_bwd2" and ROW_BWD2_DRAM_BYTES_PER_POINT and KERNEL_SRC_SHA1 == kernel_src_sha1():
+        if ROW_BWD2_DRAM_BYTES_PER_POINT and KERNEL_SRC_SHA1 == kernel_src_sha1():
             traffic = ROW_BWD2_DRAM_BYTES_PER_POINT * grid_points / launches
-        roofline = {"bound": "hbm", "kernel": f"k_{dom_k}", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": traffic, "bytes_per_launch": bytes_launch,
-                    "ms_per_launch": ms_launch, "launches_per_step": launches,
-                    "byte_model": f"{KERNEL_BYTES_PER_POINT[dom_k]} B per complex grid point, {grid_points} points",
-                    "peak_source": f"{peak_kind} hbm_gbs (copy burst)"}
-    else:
-        roofline = {"bound": "hbm", "kernel": f"stage '{dom}' (all its fwd+bwd kernels)", "achieved": stage_achieved,
-                    "peak": peak, "unit": "GB/s", "frac": stage_achieved / peak, "traffic": None,
-                    "peak_source": f"{peak_kind} hbm_gbs (copy burst)"}
-    roofline["stage"] = stage_roof
-    roofline["step"] = {"achieved": step_achieved, "frac": step_achieved / peak, "model_bytes": tot_bytes}
+        roofline["kernel_grid"] = {"kernel": "k_row_bwd2", "achieved": achieved, "frac": achieved / peak,
+                                   "traffic": traffic, "bytes_per_launch": bytes_launch, "ms_per_launch": ms_launch,
+                                   "launches_per_step": launches,
+                                   "byte_model": f"{KERNEL_BYTES_PER_POINT['row_bwd2']} B per complex point of the "
+                                                 f"FFT grid, {grid_points} points"}
 
     # ---------------- one launch per node (same kernels, one-by-one processing) ----------------
     per_node = None
@@ -548,8 +623,8 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config, "roofline": roofline,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches_per_step * args.steps),
                 "clocks": clk, "per_node": per_node, "losses_finite": finite,
-                "stages_ms_per_step": {k: v[0] / args.steps for k, v in stage.items()},
-                "kernel_families_ms_per_step": {k: v[0] / args.steps for k, v in fam.items() if v[1] > 0},
+                "stages_ms_per_step": stage_step,
+                "kernel_families_ms_per_step": {k: v[0] for k, v in fam_step.items()},
                 "device_bytes": dev_bytes, "fft_splits": fft_splits, "console_create_s": create_s,
                 "long_song": long_song, "serving": serving}
         print(json.dumps(line), flush=True)

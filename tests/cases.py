@@ -2,6 +2,8 @@
 from __future__ import annotations
 
 import dataclasses
+import json
+import os
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -183,3 +185,20 @@ def grad_groups(case: Case):
             out[t] = np.concatenate(idx)
     out["q"] = np.arange(case.oracle.n_proc_params, case.oracle.n_params)
     return out
+
+
+def record_error(test: str, quantity: str, err: float, plain_bound: float, bound: float, **extra):
+    """Append one measured parity error (with the plain bound of the quantity and the bound the test applied) to
+    the JSON-lines file named by MG_PARITY_REPORT, when that variable is set; a no-op otherwise."""
+    path = os.environ.get("MG_PARITY_REPORT")
+    if not path:
+        return
+    rec = {"test": test, "quantity": quantity, "err": float(err), "plain_bound": float(plain_bound),
+           "bound": float(bound)}
+    rec.update(extra)
+    with open(path, "a") as f:
+        f.write(json.dumps(rec) + "\n")
+
+
+def current_test() -> str:
+    return os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]

@@ -69,3 +69,24 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+
+
+def test_model_flops_counts_ffts_per_stage():
+    """The flop model counts 2.5 n log2 n per real FFT of size n: 12 per reverb / delay node at the linear-
+    convolution length, 8 per 6146-sample equalizer block plus 4 per node, 4 per loss frame and resolution."""
+    import math
+    b = _bench()
+    L = 100_000
+    lay = W.SongLayout(2, 1, [0, 0], L)
+    f = b.model_flops([lay], fs=44100, n_fft=(512,), hop_div=4)
+    rf = lambda n: 2.5 * n * math.log2(n)
+    chains = 3
+    assert f["r"] == pytest.approx(chains * (12 * rf(L + 88200 - 1) + 4 * 458 * rf(384)), rel=1e-12)
+    assert f["d"] == pytest.approx(chains * 12 * rf(L + 20 * 4410 + 38 - 1), rel=1e-12)
+    assert f["e"] == pytest.approx(chains * (8 * math.ceil(L / 6146) + 4) * rf(8192), rel=1e-12)
+    frames = (L - 512) // 128 + 1
+    assert f["loss"] == pytest.approx(4 * frames * rf(512), rel=1e-12)
+    # warm-up drops the frames that start before it
+    fw = b.model_flops([lay], fs=44100, n_fft=(512,), hop_div=4, warmup=1000)
+    assert fw["loss"] == pytest.approx(4 * (frames - math.ceil(1000 / 128)) * rf(512), rel=1e-12)
+    assert b.fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
