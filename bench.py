@@ -310,19 +310,17 @@ def build_console(layouts, rank, per_song_seed=0):
     return con, sources, mixes
 
 
-def serving_run(args, rank):
-    """Serving under a Poisson stream of search jobs (continuous batching, admission by footprint)."""
+def prepare_serving_jobs(args, rank):
+    """Songs of the serving run (drawn like the uneven batch), their sources, reverb noises and targets (each
+    job's ground-truth graph rendered by a console, outside any timed region)."""
     import torch
     import paper_2509_15948_gb300 as M
-    from paper_2509_15948_gb300.serve import Job, Server, latency_summary
-    rng = np.random.default_rng(0x5E + rank)
     layouts = W.layout_uneven_batch(args.serve_jobs, seed=40 + rank)
     bank = source_bank(key=100 + rank)
     sources = [song_sources_from_bank(bank, l, s) for s, l in enumerate(layouts)]
     songs = [M.Song(l.num_tracks, l.num_subgroups, l.track_group, l.num_samples) for l in layouts]
     types = [W.processor_types([l]) for l in layouts]
     noises = [W.reverb_noise((rank, 11, j), sum(t == "r" for t in types[j])) for j in range(len(layouts))]
-    # targets: each job's ground-truth graph rendered by a console (outside the timed region)
     targets = []
     for j, l in enumerate(layouts):
         zeros = [np.zeros((2, l.num_samples), np.float32)]
@@ -334,23 +332,115 @@ def serving_run(args, rank):
         targets.append(mixes[0].cpu().numpy())
         con.close()
     torch.cuda.synchronize()
-    t_arr = np.cumsum(rng.exponential(1.0 / args.serve_rate, len(layouts))) if args.serve_rate > 0 else \
-        np.zeros(len(layouts))
+    return songs, sources, types, noises, targets
+
+
+def serving_run(args, rank, rate, prepared):
+    """Serving under a Poisson stream of search jobs at `rate` jobs/s (0: all at once), with continuous
+    batching and admission by footprint."""
+    import paper_2509_15948_gb300 as M
+    from paper_2509_15948_gb300.serve import Job, Server, latency_summary
+    songs, sources, types, noises, targets = prepared
+    rng = np.random.default_rng(0x5E + rank)
+    n = len(songs)
+    t_arr = np.cumsum(rng.exponential(1.0 / rate, n)) if rate > 0 else np.zeros(n)
     t_arr -= t_arr[0]
     jobs = [Job(j, songs[j], sources[j], targets[j], noises[j], init_params=W.init_params(types[j], (rank, 6, j)),
                 train_steps=args.serve_train_steps, n_iter=args.serve_rounds, finetune_steps=args.serve_finetune_steps,
-                seed=j, arrival=float(t_arr[j])) for j in range(len(layouts))]
+                seed=j, arrival=float(t_arr[j])) for j in range(n)]
     budget = int(args.serve_budget_gb * (1 << 30))
     srv = Server(budget, cfg=M.ConsoleConfig(retain_spectra=-1))
     res = srv.run(jobs)
     out = latency_summary(res)
-    out.update({"arrival_rate_jobs_per_s": args.serve_rate if args.serve_rate > 0 else "burst",
+    out.update({"arrival_rate_jobs_per_s": rate if rate > 0 else "burst",
                 "budget_gb": args.serve_budget_gb, "peak_gb_admitted": srv.peak_in_use / (1 << 30),
                 "peak_concurrent_jobs": srv.peak_active,
                 "schedule": f"{args.serve_train_steps} Adam steps + {args.serve_rounds} x (dry/wet round, "
                             f"{args.serve_finetune_steps} steps)",
                 "jobs_desc": "K~U{4..32}, S~U{1..8}, 5-30 s at 44.1 kHz, one song per job",
                 "mean_pruning_ratio": float(np.mean([r.pruning_ratio for r in res if r.error is None]))})
+    return out
+
+
+def _round_record(trials):
+    return [(t.song, t.type, tuple(int(i) for i in t.candidates), t.la, t.accepted) for t in trials]
+
+
+def search_run(args, rank):
+    """The single-song search: 16 tracks x 10 s in 4 subgroups, the target rendered from a seeded ground-truth
+    graph keeping about a third of the processors; Adam (lr 1e-2) for search_train steps, then search_rounds x
+    {dry/wet round (Alg. 3), prune, search_finetune steps}.  Before the search, from the trained state, one
+    brute-force round and one dry/wet round are timed with one full masked render per trial (one mask per
+    call) and with speculative windows over the batched scorer, and their trial sequences compared."""
+    import torch
+    import paper_2509_15948_gb300 as M
+    from paper_2509_15948_gb300 import search as GS
+    lay = W.layout_single_search()
+    bank = source_bank(key=300 + rank, seconds=10.0)
+    src = song_sources_from_bank(bank, lay, 0)
+    types = W.processor_types([lay])
+    noise = W.reverb_noise((rank, 17), sum(t == "r" for t in types))
+    song = M.Song(lay.num_tracks, lay.num_subgroups, lay.track_group, lay.num_samples)
+    con = M.Console([song], [src], [np.zeros((2, lay.num_samples), np.float32)], noise, M.ConsoleConfig(autotune=1))
+    gt, keep = W.ground_truth(types, (rank, 80))
+    gt[con.n_proc_params:] = 30.0
+    con.set_params(gt)
+    _, mixes = con.forward_loss(mask=keep, with_mix=True)
+    con.update_audio(0, torch.as_tensor(src), mixes[0].clone())
+    con.set_params(W.init_params(types, (rank, 8)))
+    sync = lambda: con.stream.synchronize()
+    out = {"workload": "16 tracks x 10 s, 4 subgroups; Adam lr 1e-2 x %d, then %d x {dry/wet round, prune, %d steps}"
+                       % (args.search_train, args.search_rounds, args.search_finetune)}
+    # training of the search (the first phase), timed
+    t0 = time.perf_counter()
+    res = GS.search(con, 0, args.search_train, 0, lr=1e-2, tau=0.01, seed=rank)
+    sync()
+    out["train_s"] = time.perf_counter() - t0
+    # rounds from the trained state: one trial per call with full renders, then speculative windows
+    l_min = res.l_min
+    rounds = {}
+    for name, fn in (("brute_force", GS.brute_force_round), ("dry_wet", GS.dry_wet_round)):
+        rec = {}
+        for mode, (full, window) in (("per_trial_full_render", (True, 1)), ("batched_windows", (False, 16))):
+            con.set_score_mode(full)
+            fn(con, l_min, 0.01, [GS.SplitMix64(GS.song_seed(rank, 0))], window=window)   # warm-up
+            sync()
+            calls = [0]
+            orig = con.prune_scores
+
+            def counted(masks, _o=orig):
+                calls[0] += 1
+                return _o(masks)
+            con.prune_scores = counted
+            t1 = time.perf_counter()
+            _, _, trials = fn(con, l_min, 0.01, [GS.SplitMix64(GS.song_seed(rank, 0))], window=window)
+            sync()
+            dt = time.perf_counter() - t1
+            con.prune_scores = orig
+            rec[mode] = {"wall_s": dt, "trials": len(trials), "trials_per_s": len(trials) / dt,
+                         "calls": calls[0], "accepted": sum(t.accepted for t in trials), "_seq": _round_record(trials)}
+        con.set_score_mode(False)
+        a, b = rec["per_trial_full_render"], rec["batched_windows"]
+        rec["same_trials"] = a.pop("_seq") == b.pop("_seq")
+        rec["speedup"] = a["wall_s"] / b["wall_s"]
+        rounds[name] = rec
+    out["rounds_from_trained_state"] = rounds
+    # the rest of the search: rounds, pruning and fine-tuning
+    t0 = time.perf_counter()
+    res2 = GS.search(con, args.search_rounds, 0, args.search_finetune, lr=1e-2, tau=0.01, seed=rank,
+                     ramp_steps=(2 * args.search_rounds * args.search_finetune) // 3)
+    sync()
+    out["rounds_and_finetune_s"] = time.perf_counter() - t0
+    out["wall_s"] = out["train_s"] + out["rounds_and_finetune_s"]
+    out["seconds"] = {"train": out["train_s"], "rounds": res2.seconds["rounds"], "finetune": res2.seconds["finetune"]}
+    out["la_after_training"] = float(res.la_final[0])
+    out["la_final"] = float(res2.la_final[0])
+    out["pruning_ratio"] = float(res2.pruning_ratio[0])
+    out["trials_per_round"] = [len(t) for t in res2.trials]
+    out["accepted_per_round"] = [sum(x.accepted for x in t) for t in res2.trials]
+    out["processors"] = int(con.n_processors)
+    out["ground_truth_kept"] = int(np.sum(keep))
+    con.close()
     return out
 
 
@@ -411,9 +501,14 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=16, help="search jobs of the serving run (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=2.0, help="Poisson arrival rate, jobs/s (0: burst)")
     ap.add_argument("--serve-budget-gb", type=float, default=24.0)
+    ap.add_argument("--serve-sweep", default="", help="comma-separated arrival rates (jobs/s, 0 = all at once); "
+                                                       "one serving run per rate over the same jobs")
     ap.add_argument("--serve-train-steps", type=int, default=60)
     ap.add_argument("--serve-rounds", type=int, default=3)
     ap.add_argument("--serve-finetune-steps", type=int, default=20)
+    ap.add_argument("--search-train", type=int, default=2000, help="single-song search: Adam steps (0: skip)")
+    ap.add_argument("--search-rounds", type=int, default=5)
+    ap.add_argument("--search-finetune", type=int, default=500)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -606,16 +701,21 @@ def main():
         cpu = {"value": ts / tt, "unit": "track-s/s", "cores": torch.get_num_threads(), "kind": "oracle",
                "sample": desc + f", {args.cpu_baseline_steps} steps"}
 
-    serving, long_song = None, None
+    serving, long_song, search = None, None, None
     dev_bytes = info["device_bytes"]
-    if args.serve_jobs > 0 or args.long_steps > 0:
+    if args.serve_jobs > 0 or args.long_steps > 0 or args.search_train > 0:
         con.close()
         del con
         torch.cuda.synchronize()
     if args.long_steps > 0:
         long_song = long_song_run(args, rank)
+    if args.search_train > 0:
+        search = search_run(args, rank)
     if args.serve_jobs > 0:
-        serving = serving_run(args, rank)
+        prepared = prepare_serving_jobs(args, rank)
+        rates = [float(r) for r in args.serve_sweep.split(",")] if args.serve_sweep else [args.serve_rate]
+        sweep = [serving_run(args, rank, r, prepared) for r in rates]
+        serving = sweep[0] if len(sweep) == 1 else {"sweep": sweep}
 
     if rank == 0:
         line = {"metric": metric, "value": value, "unit": "track-s/s", "n_gpus": world, "steps": args.steps,
@@ -626,7 +726,7 @@ def main():
                 "stages_ms_per_step": stage_step,
                 "kernel_families_ms_per_step": {k: v[0] for k, v in fam_step.items()},
                 "device_bytes": dev_bytes, "fft_splits": fft_splits, "console_create_s": create_s,
-                "long_song": long_song, "serving": serving}
+                "long_song": long_song, "serving": serving, "search": search}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

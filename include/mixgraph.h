@@ -145,10 +145,23 @@ mg_status mg_forward_loss(mg_console* c, const uint8_t* d_mask, float* d_losses,
  * mg_prune_scores ran after it. */
 mg_status mg_backward(mg_console* c);
 
-/* Masked forwards that score pruning candidates (Alg. 2 Evaluate, Alg. 3): for every mask j in
- * d_masks (device {0,1}[n_masks][P]) the audio loss L_a of every song with w * mask_j.
- * d_la: device [n_masks][n_songs].  Does not touch gradients or Adam state. */
+/* Masked forwards that score pruning candidates (Alg. 2 Evaluate, Alg. 3; the per-node Delta_i of Sec. 7.2):
+ * for every mask j in d_masks (device {0,1}[n_masks][P]) the audio loss L_a of every song with w * mask_j.
+ * d_la: device [n_masks][n_songs].  Does not touch gradients or Adam state.
+ * Batched (the default): the masks are read back to the host (the call synchronises the stream, so it cannot be
+ * captured in a CUDA graph); the console is rendered once under the base mask (per processor, the value most
+ * masks have); then, for all masks at once, only what a mask changes is computed again as forward-only copies
+ * of the nodes (a track chain from its first processor whose mask differs from the base, a subgroup chain from
+ * its first such processor or whole when one of its tracks changed, the mix and the loss of every changed
+ * song), one launch per processor type and level over the copies of every mask, reading the base outputs of the
+ * unchanged nodes.  Every score equals (bitwise) the score of a full render under its mask.  The copies live in
+ * a workspace the console allocates on first use and keeps (grown as needed); masks are processed in chunks
+ * whose copies fit workspace_limit_bytes when set, else 60 % of the free device memory (at most 64 GiB), and a
+ * mask whose copies alone exceed it is scored by a full render.  MG_ERR_OOM if the workspace cannot be
+ * allocated.  With mg_set_score_mode(c, 1), or in one-launch-per-node mode, every mask is a full render. */
 mg_status mg_prune_scores(mg_console* c, const uint8_t* d_masks, int32_t n_masks, float* d_la);
+/* 0: batched scoring (default); 1: one full masked render per mask (stream-ordered, no host synchronisation). */
+mg_status mg_set_score_mode(mg_console* c, int32_t mode);
 
 /* One Adam step (Sec. 5.1; Kingma-Ba bias correction, decoupled weight decay) on all parameters with the
  * gradients of the last mg_backward.  Moments start at zero after create / mg_reset_optimizer. */

@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
         "mg_get_present": [P, U8P],
         "mg_update_audio": [P, I32, P, P, I32],
         "mg_set_launch_mode": [P, I32],
+        "mg_set_score_mode": [P, I32],
         "mg_set_profiling": [P, I32],
         "mg_get_kernel_times": [P, P, P, I32],
         "mg_reset_kernel_times": [P],
@@ -416,6 +417,10 @@ class Console:
 
     def set_launch_mode(self, per_node: bool):
         self._check(self.lib.mg_set_launch_mode(self.h, int(per_node)))
+
+    def set_score_mode(self, full_renders: bool):
+        """prune_scores: False batches the masks over one base render (default); True renders every mask in full."""
+        self._check(self.lib.mg_set_score_mode(self.h, int(full_renders)))
 
     def set_profiling(self, on: bool):
         self._check(self.lib.mg_set_profiling(self.h, int(on)))

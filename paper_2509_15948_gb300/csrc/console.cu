@@ -138,7 +138,16 @@ struct mg_console {
   float* d_hyper = nullptr;
   float* d_alphas = nullptr;
   uint8_t* d_mask = nullptr;
-  float* d_scratch_la = nullptr;
+  float* d_scratch_la = nullptr;   // [n_songs] L_a of every song under the base mask of a candidate scoring call
+  std::vector<size_t> chain_out;   // arena offset of every chain's output (its last present processor, or its input)
+  // candidate scoring: workspace of the forward-only node copies (grown on demand, kept), its byte budget, and
+  // host staging of its tables and of the base mask
+  char* score_ws = nullptr;
+  size_t score_ws_bytes = 0;
+  size_t score_budget = 0;
+  std::vector<char> score_blob;
+  std::vector<uint8_t> score_m0;
+  int score_mode = 0;              // 0: batched candidate scoring, 1: one full masked render per candidate
   ProcDev* d_procs = nullptr;
   SongDev* d_songs = nullptr;
   LossRes* d_res = nullptr;
@@ -664,6 +673,7 @@ mg_status build_tables(mg_console* c) {
     }
     chain_out[ci] = cur;
   }
+  c->chain_out = chain_out;
   // adjoints: chain output adjoint
   std::vector<size_t> chain_dout(c->chains.size()), chain_din(c->chains.size());
   for (int level = 1; level >= 0; --level) {
@@ -1122,6 +1132,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
   CK(cudaMalloc(&c->d_hyper, 8 * sizeof(float)));
   CK(cudaMalloc(&c->d_alphas, 4 * sizeof(float)));
   CK(cudaMalloc(&c->d_mask, std::max(1, c->P)));
+  CK(cudaMalloc(&c->d_scratch_la, sizeof(float) * std::max<size_t>(1, c->songs.size())));
   CK(cudaMemsetAsync(c->d_params, 0, sizeof(float) * c->nparams, c->stream));
   CK(cudaMemsetAsync(c->d_grads, 0, sizeof(float) * c->nparams, c->stream));
   CK(cudaMemsetAsync(c->d_m, 0, sizeof(float) * c->nparams, c->stream));
@@ -1411,6 +1422,7 @@ void destroy_impl(mg_console* c) {
   cudaFree(c->d_alphas);
   cudaFree(c->d_mask);
   cudaFree(c->d_scratch_la);
+  cudaFree(c->score_ws);
 }
 
 void fill_info(const mg_console* c, mg_console_info* o) {
@@ -1424,6 +1436,506 @@ void fill_info(const mg_console* c, mg_console_info* o) {
   o->device_bytes = (int64_t)(c->arena_bytes + c->scratch_bytes + 4 * sizeof(float) * c->nparams);
   o->launches_per_step = c->launches_step;
   o->retains_spectra = c->retain ? 1 : 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// batched candidate scoring (Alg. 2-3 Evaluate, Sec. 7.2 Delta_i)
+// ------------------------------------------------------------------------------------------------
+// The candidate masks of one call differ from a base mask (the per-processor majority of the candidates) in a
+// few processors.  The base is rendered once.  Under candidate j a node's output equals the base output unless
+// the node, or a node upstream of it, has a different mask value; only those nodes are computed again, as
+// forward-only copies ("virtual nodes") with their own output and FFT scratch that read the base outputs where
+// their input did not change:
+//   - a track chain from its first differing processor to its end,
+//   - a subgroup chain from its first differing processor, or all of it when one of its tracks changed (its
+//     mix node m is then summed again),
+//   - the output node o and the loss of every song that changed.
+// The copies of every candidate run in one launch per processor type and level, in console order, with the
+// same kernels, parameters, splits and work items as a full render, so every score is bitwise the score of a
+// full render under that candidate's mask.
+
+// Which parts of the console one candidate changes.
+struct CandPlan {
+  std::vector<std::pair<int, int>> chains;   // (chain, position of its first changed processor)
+  std::vector<int> songs;                    // songs whose mix changes
+  size_t bytes = 0;                          // workspace bytes of its copies, sums, songs and tables
+};
+
+// One chunk of candidates, built on the host: node copies and their work lists, sums, song copies, loss items.
+struct ScoreChunk {
+  std::vector<ProcDev> vp;
+  std::vector<int> vsrc;                     // processor copied by every node copy
+  std::vector<uint8_t> vmask;                // mask value of every node copy
+  std::vector<Stage> stages;                 // level 0 then level 1, types in chain order
+  std::vector<float*> sum_out;
+  std::vector<const float*> sum_in;
+  std::vector<int> sum_beg, sum_L, sum_ld;
+  ItemList m_items, o_items;
+  std::vector<SongDev> vs;
+  std::vector<int4> litems[3];
+  std::vector<int> map;                      // [candidate][song]: song copy, or -1 (unchanged)
+  size_t table_begin = 0;                    // workspace offset of the tables (copied from the host blob)
+  float* vq = nullptr;
+  float* vla = nullptr;
+  int* d_vsrc = nullptr;
+  int* d_map = nullptr;
+  ProcDev* d_vp = nullptr;
+  uint8_t* d_vmask = nullptr;
+  SongDev* d_vs = nullptr;
+  int4* d_litems[3] = {nullptr, nullptr, nullptr};
+  float** d_sum_out = nullptr;
+  const float** d_sum_in = nullptr;
+  int *d_sum_beg = nullptr, *d_sum_L = nullptr, *d_sum_ld = nullptr;
+};
+
+// Bytes of the workspace a node copy of processor pi needs (forward-only buffers) and its work items.
+size_t copy_bytes(const mg_console* c, int pi, size_t* items) {
+  const HostProc& p = c->procs[pi];
+  auto al = [](size_t b) { return (size_t)round_up((int64_t)b, 256); };
+  size_t b = al((size_t)2 * p.ld * sizeof(float)) + al(16 * sizeof(float));
+  size_t it = 0;
+  if (p.nfrows) b += al((size_t)std::max(p.nfrows, p.nfcap) * kNPart * sizeof(float));
+  if (p.type == T_C || p.type == T_N) {
+    b += 2 * al((size_t)p.nchunks * sizeof(float));
+    it = p.nchunks + 1;
+  } else if (p.type == T_G || p.type == T_S) {
+    it = p.nbrows;
+  } else if (p.type == T_E) {
+    it = p.nfrows;
+  } else {
+    const size_t N = (size_t)p.f << p.logN;
+    b += al(N * sizeof(float2)) * (c->retain ? 1 : 2);   // T1, and Hz when the base does not keep it
+    it = ((size_t)p.f << p.logN1) / p.colG + ((size_t)1 << p.logN2) / 2 + 1 + 1;
+  }
+  *items = it;
+  return b;
+}
+
+// The changed chains and songs of candidate mask mj against the base mask m0, and its workspace bytes.
+CandPlan plan_candidate(const mg_console* c, const uint8_t* mj, const uint8_t* m0) {
+  CandPlan cp;
+  auto al = [](size_t b) { return (size_t)round_up((int64_t)b, 256); };
+  auto first_changed = [&](int ci) {
+    const HostChain& ch = c->chains[ci];
+    for (size_t k = 0; k < ch.procs.size(); ++k) {
+      const int pi = ch.procs[k];
+      if (c->procs[pi].present && mj[pi] != m0[pi]) return (int)k;
+    }
+    return -1;
+  };
+  size_t nodes = 0, items = 0;
+  auto add_chain = [&](int ci, int from) {
+    cp.chains.push_back({ci, from});
+    const HostChain& ch = c->chains[ci];
+    for (size_t k = from; k < ch.procs.size(); ++k) {
+      if (!c->procs[ch.procs[k]].present) continue;
+      size_t it = 0;
+      cp.bytes += copy_bytes(c, ch.procs[k], &it);
+      items += it;
+      ++nodes;
+    }
+  };
+  for (size_t si = 0; si < c->songs.size(); ++si) {
+    const HostSong& hs = c->songs[si];
+    bool song_changed = false;
+    std::vector<char> group_in(hs.S, 0);
+    for (int k = 0; k < hs.K; ++k) {
+      const int f = first_changed(hs.tracks_chain[k]);
+      if (f < 0) continue;
+      add_chain(hs.tracks_chain[k], f);
+      song_changed = true;
+      if (hs.group[k] >= 0) group_in[hs.group[k]] = 1;
+    }
+    const size_t st = al((size_t)2 * hs.ld * sizeof(float));
+    const size_t tiles = (hs.L + kElemTile - 1) / kElemTile;
+    for (int g = 0; g < hs.S; ++g) {
+      const int f = group_in[g] ? 0 : first_changed(hs.groups_chain[g]);
+      if (f < 0) continue;
+      add_chain(hs.groups_chain[g], f);
+      song_changed = true;
+      if (group_in[g]) cp.bytes += st + al(sizeof(void*) * (hs.K + 1)) + al(tiles * sizeof(Item)) + al(64);
+    }
+    if (song_changed) {
+      cp.songs.push_back((int)si);
+      cp.bytes += st + al((size_t)3 * std::max(1, hs.lcap) * 6 * sizeof(float)) + al(18 * sizeof(float)) +
+                  al(sizeof(SongDev)) + al(sizeof(void*) * (hs.K + hs.S + 1)) + al(tiles * sizeof(Item)) + al(64);
+      for (int r = 0; r < c->nres; ++r) cp.bytes += al((size_t)hs.litems[r] * sizeof(int4));
+    }
+  }
+  // tables of the node copies: the node table, sources, masks, logits, work items and lists, per-candidate map
+  cp.bytes += al(nodes * sizeof(ProcDev)) + 4 * al(nodes * sizeof(int)) + al(nodes) + al(items * sizeof(Item)) +
+              al(c->songs.size() * sizeof(int)) + al(sizeof(float) * (cp.songs.size() + 1));
+  return cp;
+}
+
+// Bump allocation in the workspace: buffers first, then the tables, whose contents go to a host blob that is
+// copied to the device once per chunk.
+struct WsBuilder {
+  char* base;
+  Bump b;
+  size_t table_begin = 0;
+  std::vector<char>* blob;
+  char* buffer(size_t bytes) { return base + b.take(bytes); }
+  void start_tables() {
+    b.off = (size_t)round_up((int64_t)b.off, 256);
+    table_begin = b.off;
+    blob->clear();
+  }
+  template <class T>
+  T* table(const std::vector<T>& v) {
+    if (v.empty()) return nullptr;
+    const size_t o = b.take(v.size() * sizeof(T));
+    if (blob->size() < o - table_begin + v.size() * sizeof(T)) blob->resize(o - table_begin + v.size() * sizeof(T));
+    std::memcpy(blob->data() + (o - table_begin), v.data(), v.size() * sizeof(T));
+    return reinterpret_cast<T*>(base + o);
+  }
+};
+
+mg_status ensure_score_ws(mg_console* c, size_t bytes) {
+  if (bytes <= c->score_ws_bytes) return MG_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  std::lock_guard<std::mutex> lock(g_device_mutex);
+  if (c->score_ws) cudaFree(c->score_ws);
+  c->score_ws = nullptr;
+  c->score_ws_bytes = 0;
+  const size_t want = (size_t)round_up((int64_t)bytes + ((int64_t)bytes >> 3), 1 << 20);   // 1/8 headroom
+  if (cudaMalloc(&c->score_ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MG_ERR_OOM, "candidate scoring workspace allocation failed");
+  }
+  c->score_ws_bytes = want;
+  CK(cudaMemsetAsync(c->score_ws, 0, want, c->stream));
+  return MG_OK;
+}
+
+// Builds the node copies, sums, song copies and loss items of candidates [j0, j1) in the workspace.
+void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_t* hm, int j0, int j1, ScoreChunk& k) {
+  WsBuilder w{c->score_ws, Bump{}, 0, &c->score_blob};
+  auto A = [&](size_t off) { return c->arena + off; };
+  const int ns = (int)c->songs.size();
+  k.map.assign((size_t)(j1 - j0) * ns, -1);
+  // node copies per (level, type), in candidate order
+  std::vector<int> by_lt[2][NTYPES];
+  for (int j = j0; j < j1; ++j) {
+    const uint8_t* mj = hm + (size_t)j * c->P;
+    const CandPlan& cp = plans[j];
+    std::vector<const float*> chain_y(c->chains.size(), nullptr);   // output of the chain's copy, if any
+    std::vector<const float*> group_in(c->chains.size(), nullptr);   // recomputed input of a subgroup chain
+    auto copy_chain = [&](int ci, int from) {
+      const HostChain& ch = c->chains[ci];
+      const float* cur = group_in[ci] ? group_in[ci] : (const float*)A(ch.o_in);
+      for (int kk = 0; kk < from; ++kk)
+        if (c->procs[ch.procs[kk]].present) cur = c->hpd[ch.procs[kk]].y;
+      for (size_t kk = from; kk < ch.procs.size(); ++kk) {
+        const int pi = ch.procs[kk];
+        const HostProc& p = c->procs[pi];
+        if (!p.present) continue;
+        ProcDev d = c->hpd[pi];
+        const int v = (int)k.vp.size();
+        d.qidx = v;
+        d.u = cur;
+        d.y = (float*)w.buffer((size_t)2 * p.ld * sizeof(float));
+        d.stats = (float*)w.buffer(16 * sizeof(float));
+        d.fpart = p.nfrows ? (float*)w.buffer((size_t)std::max(p.nfrows, p.nfcap) * kNPart * sizeof(float)) : nullptr;
+        d.dy = nullptr;
+        d.du = nullptr;
+        d.gp = nullptr;
+        d.bpart = nullptr;
+        d.dtaps = nullptr;
+        d.rcarry = nullptr;
+        d.dhspec = nullptr;
+        d.eqg = nullptr;
+        d.ybar = nullptr;                    // the equalizer keeps no wet signal for a backward
+        if (p.type == T_C || p.type == T_N) {
+          d.carry = (float*)w.buffer((size_t)p.nchunks * sizeof(float));
+          d.chunkagg = (float*)w.buffer((size_t)p.nchunks * sizeof(float));
+          d.aux = nullptr;
+        }
+        if (p.type == T_R || p.type == T_D) {
+          const size_t N = (size_t)p.f << p.logN;
+          d.T1 = (float2*)w.buffer(N * sizeof(float2));
+          d.T2 = nullptr;
+          if (!c->retain) d.Hz = (float2*)w.buffer(N * sizeof(float2));   // else the base node's kept spectrum
+        }
+        k.vp.push_back(d);
+        k.vsrc.push_back(pi);
+        k.vmask.push_back(mj[pi]);
+        by_lt[p.level][p.type].push_back(v);
+        cur = d.y;
+      }
+      chain_y[ci] = cur;
+    };
+    auto out_of = [&](int ci) { return chain_y[ci] ? chain_y[ci] : (const float*)A(c->chain_out[ci]); };
+    // track chains, then subgroup inputs and chains, then the mix, song by song
+    size_t ci_next = 0;
+    for (int si : cp.songs) {
+      const HostSong& hs = c->songs[si];
+      for (; ci_next < cp.chains.size() && c->chains[cp.chains[ci_next].first].song == si &&
+             c->chains[cp.chains[ci_next].first].level == 0; ++ci_next)
+        copy_chain(cp.chains[ci_next].first, cp.chains[ci_next].second);
+      for (int g = 0; g < hs.S; ++g) {
+        bool changed = false;
+        for (int kk = 0; kk < hs.K; ++kk)
+          if (hs.group[kk] == g && chain_y[hs.tracks_chain[kk]]) changed = true;
+        if (!changed) continue;
+        float* out = (float*)w.buffer((size_t)2 * hs.ld * sizeof(float));
+        const int sid = (int)k.sum_out.size();
+        k.sum_beg.push_back((int)k.sum_in.size());
+        k.sum_out.push_back(out);
+        for (int kk = 0; kk < hs.K; ++kk)
+          if (hs.group[kk] == g) k.sum_in.push_back(out_of(hs.tracks_chain[kk]));
+        k.sum_L.push_back(hs.L);
+        k.sum_ld.push_back(hs.ld);
+        k.m_items.beg.push_back((int)k.m_items.h.size());
+        for (int t = 0; t < (hs.L + kElemTile - 1) / kElemTile; ++t) k.m_items.h.push_back(Item{sid, t});
+        group_in[hs.groups_chain[g]] = out;
+      }
+      for (; ci_next < cp.chains.size() && c->chains[cp.chains[ci_next].first].song == si; ++ci_next)
+        copy_chain(cp.chains[ci_next].first, cp.chains[ci_next].second);
+      // the mix and the song copy
+      float* mix = (float*)w.buffer((size_t)2 * hs.ld * sizeof(float));
+      const int sid = (int)k.sum_out.size();
+      k.sum_beg.push_back((int)k.sum_in.size());
+      k.sum_out.push_back(mix);
+      for (int g = 0; g < hs.S; ++g) k.sum_in.push_back(out_of(hs.groups_chain[g]));
+      for (int kk = 0; kk < hs.K; ++kk)
+        if (hs.group[kk] < 0) k.sum_in.push_back(out_of(hs.tracks_chain[kk]));
+      k.sum_L.push_back(hs.L);
+      k.sum_ld.push_back(hs.ld);
+      k.o_items.beg.push_back((int)k.o_items.h.size());
+      for (int t = 0; t < (hs.L + kElemTile - 1) / kElemTile; ++t) k.o_items.h.push_back(Item{sid, t});
+      SongDev sd = c->hsd[si];
+      const int vsi = (int)k.vs.size();
+      sd.mix = mix;
+      sd.dmix = nullptr;
+      for (int r = 0; r < 3; ++r) sd.Yh[r] = nullptr;
+      sd.lpart = (float*)w.buffer((size_t)3 * sd.lcap * 6 * sizeof(float));
+      sd.coef = (float*)w.buffer(18 * sizeof(float));
+      k.vs.push_back(sd);
+      for (int r = 0; r < c->nres; ++r) {
+        const int per = 8192 / c->desc.n_fft[r];
+        for (int t = hs.first[r]; t < hs.nframes[r]; t += per)
+          k.litems[r].push_back(make_int4(vsi, r, t, std::min(per, hs.nframes[r] - t)));
+      }
+      k.map[(size_t)(j - j0) * ns + si] = vsi;
+    }
+  }
+  k.sum_beg.push_back((int)k.sum_in.size());
+  k.m_items.beg.push_back((int)k.m_items.h.size());
+  k.o_items.beg.push_back((int)k.o_items.h.size());
+  const int V = (int)k.vp.size();
+  k.vq = (float*)w.buffer(sizeof(float) * std::max(1, V));
+  k.vla = (float*)w.buffer(sizeof(float) * std::max<size_t>(1, k.vs.size()));
+  // work lists per (level, type)
+  k.stages.clear();
+  for (int level = 0; level < 2; ++level)
+    for (int t = 0; t < NTYPES; ++t) {
+      if (by_lt[level][t].empty()) continue;
+      Stage st;
+      st.level = level;
+      st.type = t;
+      st.procs.h = by_lt[level][t];
+      if (t == T_R || t == T_D) st.groups.push_back(LtiGroup{});
+      for (int v : by_lt[level][t]) {
+        const ProcDev& d = k.vp[v];
+        if (t == T_G || t == T_S || t == T_C || t == T_N) {
+          st.elem.beg.push_back((int)st.elem.h.size());
+          const int nt = (t == T_C || t == T_N) ? d.nchunks : (d.L + kElemTile - 1) / kElemTile;
+          for (int i = 0; i < nt; ++i) st.elem.h.push_back(Item{v, i});
+        } else if (t == T_E) {
+          st.osf.beg.push_back((int)st.osf.h.size());
+          for (int i = 0; i < d.nfpart; ++i) st.osf.h.push_back(Item{v, i});
+        } else {
+          LtiGroup& g = st.groups[0];
+          g.procs.h.push_back(v);
+          g.col.beg.push_back((int)g.col.h.size());
+          g.rowpair.beg.push_back((int)g.rowpair.h.size());
+          const int N1 = d.f << d.logN1, N2 = 1 << d.logN2;
+          for (int i = 0; i < N1 / d.colG; ++i) g.col.h.push_back(Item{v, i});
+          for (int i = 0; i <= N2 / 2; ++i) g.rowpair.h.push_back(Item{v, i});
+          g.col.maxv = std::max(g.col.maxv, N2 * d.colG);
+          g.rowpair.maxv = std::max(g.rowpair.maxv, N1);
+        }
+      }
+      st.elem.beg.push_back((int)st.elem.h.size());
+      st.osf.beg.push_back((int)st.osf.h.size());
+      for (auto& g : st.groups) {
+        g.col.beg.push_back((int)g.col.h.size());
+        g.rowpair.beg.push_back((int)g.rowpair.h.size());
+      }
+      k.stages.push_back(std::move(st));
+    }
+  // tables
+  w.start_tables();
+  k.table_begin = w.table_begin;
+  k.d_vp = w.table(k.vp);
+  k.d_vsrc = w.table(k.vsrc);
+  k.d_vmask = w.table(k.vmask);
+  k.d_map = w.table(k.map);
+  k.d_vs = w.table(k.vs);
+  for (int r = 0; r < 3; ++r) k.d_litems[r] = w.table(k.litems[r]);
+  k.d_sum_out = w.table(k.sum_out);
+  k.d_sum_in = w.table(k.sum_in);
+  k.d_sum_beg = w.table(k.sum_beg);
+  k.d_sum_L = w.table(k.sum_L);
+  k.d_sum_ld = w.table(k.sum_ld);
+  k.m_items.d = w.table(k.m_items.h);
+  k.o_items.d = w.table(k.o_items.h);
+  for (auto& st : k.stages) {
+    st.procs.d = w.table(st.procs.h);
+    st.elem.d = w.table(st.elem.h);
+    st.osf.d = w.table(st.osf.h);
+    for (auto& g : st.groups) {
+      g.procs.d = w.table(g.procs.h);
+      g.col.d = w.table(g.col.h);
+      g.rowpair.d = w.table(g.rowpair.h);
+    }
+  }
+}
+
+// Forward of the node copies of one (level, type): the stage's kernels without the parameter-only work (FIR
+// synthesis, equalizer spectrum; with kept spectra also the filter transform), which the copies share with the
+// nodes they copy.
+void vstage_forward(mg_console* c, const LaunchCtx& x, Stage& s) {
+  StageScope scope(c, s.type);
+  switch (s.type) {
+    case T_G:
+    case T_S:
+      run_items(c, F_GS_FWD, s.elem, [&](const Item* it, int n) { launch_gs_fwd(x, it, n); });
+      break;
+    case T_C:
+    case T_N:
+      run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd_agg(x, it, n); });
+      run_procs(c, F_DYN_FWD, s.procs, [&](const int* p, int n) { launch_dyn_fwd_carry(x, p, n); });
+      run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd_apply(x, it, n); });
+      break;
+    case T_E:
+      run_items(c, F_EQ_OS_FWD, s.osf, [&](const Item* it, int n) { launch_eq_os_fwd(x, it, n); });
+      break;
+    default:
+      for (auto& g : s.groups) {
+        if (!c->retain) {
+          run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
+          run_items(c, F_ROW_HZ, g.rowpair, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowpair.maxv); });
+        }
+        run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_audio(x, it, n, g.col.maxv); });
+        run_items(c, F_ROW_CONV, g.rowpair, [&](const Item* it, int n) { launch_row_conv_fwd(x, it, n, g.rowpair.maxv, false); });
+        run_items(c, F_COL_OUT, g.col, [&](const Item* it, int n) { launch_col_inv_out(x, it, n, g.col.maxv); });
+      }
+  }
+}
+
+// The score budget: the workspace limit of the descriptor when set, else 60 % of the device memory free at the
+// first scoring call (at most 64 GiB).
+size_t score_budget(mg_console* c) {
+  if (c->score_budget) return c->score_budget;
+  if (c->desc.workspace_limit_bytes > 0) {
+    c->score_budget = (size_t)c->desc.workspace_limit_bytes;
+  } else {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)1 << 30;
+    const size_t b = std::min((size_t)(0.6 * (double)(free_b + c->score_ws_bytes)), (size_t)64 << 30);
+    c->score_budget = std::max(b, (size_t)64 << 20);
+  }
+  return c->score_budget;
+}
+
+// Full masked render of one candidate (no copies): the path of a candidate whose copies alone exceed the budget.
+void score_full(mg_console* c, const uint8_t* d_mask_j, float* d_la_row) {
+  cudaMemcpyAsync(c->d_mask, d_mask_j, c->P, cudaMemcpyDeviceToDevice, c->stream);
+  LaunchCtx x = make_ctx(c, c->d_mask);
+  render(c, x);
+  loss_forward(c, x, 2, nullptr, d_la_row, 1);
+}
+
+mg_status prune_scores_batched(mg_console* c, const uint8_t* d_masks, int n_masks, float* d_la) {
+  const int P = c->P, ns = (int)c->songs.size();
+  std::vector<uint8_t> hm((size_t)n_masks * P);
+  CK(cudaMemcpyAsync(hm.data(), d_masks, hm.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (uint8_t& v : hm) v = v ? 1 : 0;
+  // base mask: per processor the value most candidates have (ties: 1)
+  c->score_m0.assign(P, 1);
+  bool all_ones = true;
+  for (int i = 0; i < P; ++i) {
+    int ones = 0;
+    for (int j = 0; j < n_masks; ++j) ones += hm[(size_t)j * P + i];
+    c->score_m0[i] = 2 * ones >= n_masks ? 1 : 0;
+    all_ones = all_ones && c->score_m0[i];
+  }
+  std::vector<CandPlan> plans(n_masks);
+  for (int j = 0; j < n_masks; ++j) plans[j] = plan_candidate(c, hm.data() + (size_t)j * P, c->score_m0.data());
+  // the base render and its losses
+  if (!all_ones) CK(cudaMemcpyAsync(c->d_mask, c->score_m0.data(), P, cudaMemcpyHostToDevice, c->stream));
+  {
+    LaunchCtx xb = make_ctx(c, all_ones ? nullptr : c->d_mask);
+    if (!(c->fwd_valid && all_ones)) render(c, xb);
+    loss_forward(c, xb, 2, nullptr, c->d_scratch_la, 1);
+  }
+  // candidates in chunks whose copies fit the budget; a candidate that alone exceeds it is rendered in full
+  const size_t budget = score_budget(c);
+  std::vector<int> full;
+  int j = 0;
+  while (j < n_masks) {
+    if (plans[j].bytes + (64 << 10) > budget) {
+      full.push_back(j++);
+      continue;
+    }
+    int j1 = j;
+    size_t bytes = 64 << 10;
+    while (j1 < n_masks && plans[j1].bytes + (64 << 10) <= budget && bytes + plans[j1].bytes <= budget)
+      bytes += plans[j1++].bytes;
+    if (ensure_score_ws(c, bytes) != MG_OK) return MG_ERR_OOM;
+    ScoreChunk k;
+    build_chunk(c, plans, hm.data(), j, j1, k);
+    if (!c->score_blob.empty())
+      CK(cudaMemcpyAsync(c->score_ws + k.table_begin, c->score_blob.data(), c->score_blob.size(),
+                         cudaMemcpyHostToDevice, c->stream));
+    const int V = (int)k.vp.size();
+    LaunchCtx xv = make_ctx(c, k.d_vmask);
+    xv.procs = k.d_vp;
+    xv.q = k.vq;
+    if (V > 0) {
+      run(c, F_MISC, [&] { launch_gather_q(c->stream, c->d_params + c->npp, k.d_vsrc, k.vq, V); });
+      for (int level = 0; level < 2; ++level) {
+        if (level == 1 && !k.m_items.h.empty()) {
+          StageScope scope(c, 8);
+          run_items(c, F_SUM, k.m_items, [&](const Item* it, int n) {
+            launch_sum(c->stream, k.d_sum_out, k.d_sum_in, k.d_sum_beg, k.d_sum_L, k.d_sum_ld, it, n);
+          });
+        }
+        for (auto& st : k.stages)
+          if (st.level == level) vstage_forward(c, xv, st);
+      }
+    }
+    if (!k.vs.empty()) {
+      {
+        StageScope scope(c, 8);
+        run_items(c, F_SUM, k.o_items, [&](const Item* it, int n) {
+          launch_sum(c->stream, k.d_sum_out, k.d_sum_in, k.d_sum_beg, k.d_sum_L, k.d_sum_ld, it, n);
+        });
+      }
+      StageScope scope(c, 7);
+      for (int r = 0; r < c->nres; ++r)
+        if (!k.litems[r].empty())
+          run(c, F_LOSS_FWD, [&] {
+            launch_loss_frames(xv, k.d_vs, c->d_res, k.d_litems[r], (int)k.litems[r].size(), 1, c->loss_max_dy);
+          });
+      run(c, F_FINALIZE, [&] {
+        launch_loss_finalize_mode(xv, k.d_vs, (int)k.vs.size(), c->d_res, c->nres, c->d_alphas, 2, nullptr, k.vla, 1);
+      });
+    }
+    run(c, F_MISC, [&] {
+      launch_score_scatter(c->stream, k.d_map, k.vla, c->d_scratch_la, d_la + (size_t)j * ns, (j1 - j) * ns, ns);
+    });
+    CK(cudaGetLastError());
+    // the next chunk's tables overwrite these: the host copy of the next blob is ordered after this chunk's
+    // kernels on the stream, and the blob itself is staged before cudaMemcpyAsync returns
+    j = j1;
+  }
+  for (int jj : full) score_full(c, d_masks + (size_t)jj * P, d_la + (size_t)jj * ns);
+  CK(cudaGetLastError());
+  return MG_OK;
 }
 
 }  // namespace
@@ -1571,14 +2083,22 @@ mg_status mg_backward(mg_console* c) {
 
 mg_status mg_prune_scores(mg_console* c, const uint8_t* d_masks, int32_t n_masks, float* d_la) {
   if (!c || !d_masks || !d_la || n_masks < 0) return fail(c, MG_ERR_INVALID, "null pointer or negative count");
-  for (int j = 0; j < n_masks; ++j) {
-    CK(cudaMemcpyAsync(c->d_mask, d_masks + (size_t)j * c->P, c->P, cudaMemcpyDeviceToDevice, c->stream));
-    LaunchCtx x = make_ctx(c, c->d_mask);
-    render(c, x);
-    loss_forward(c, x, 2, nullptr, d_la + (size_t)j * c->songs.size(), 1);
+  if (n_masks == 0) return MG_OK;
+  mg_status st = MG_OK;
+  if (c->per_node || c->score_mode == 1) {
+    // one full masked render per candidate
+    for (int j = 0; j < n_masks; ++j) score_full(c, d_masks + (size_t)j * c->P, d_la + (size_t)j * c->songs.size());
+    CK(cudaGetLastError());
+  } else {
+    st = prune_scores_batched(c, d_masks, n_masks, d_la);
   }
   c->fwd_valid = false;
-  CK(cudaGetLastError());
+  return st;
+}
+
+mg_status mg_set_score_mode(mg_console* c, int32_t mode) {
+  if (!c || mode < 0 || mode > 1) return fail(c, MG_ERR_INVALID, "score mode must be 0 or 1");
+  c->score_mode = mode;
   return MG_OK;
 }
 

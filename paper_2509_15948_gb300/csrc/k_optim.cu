@@ -191,4 +191,26 @@ void launch_set_hyper(cudaStream_t st, float* hyper, float alpha_p, float lr, fl
   k_set_hyper<<<1, 1, 0, st>>>(hyper, alpha_p, lr, b1, b2, eps, wd, which);
 }
 
+// Candidate scoring: the dry/wet logit of every forward-only node copy, gathered from the processor it copies
+// (the copies carry their own mask values and index these by their own position).
+__global__ void k_gather_q(const float* __restrict__ q, const int* __restrict__ src, float* __restrict__ dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = q[src[i]];
+}
+void launch_gather_q(cudaStream_t st, const float* q, const int* src, float* dst, int n) {
+  if (n) k_gather_q<<<(n + 255) / 256, 256, 0, st>>>(q, src, dst, n);
+}
+
+// Candidate scoring: out[j][s] = L_a of the copy of song s that candidate j changed (map >= 0), else the song's
+// L_a under the base mask.
+__global__ void k_score_scatter(const int* __restrict__ map, const float* __restrict__ vla,
+                                const float* __restrict__ base_la, float* __restrict__ out, int n, int nsongs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = map[i] >= 0 ? vla[map[i]] : base_la[i % nsongs];
+}
+void launch_score_scatter(cudaStream_t st, const int* map, const float* vla, const float* base_la, float* out, int n,
+                          int nsongs) {
+  if (n) k_score_scatter<<<(n + 255) / 256, 256, 0, st>>>(map, vla, base_la, out, n, nsongs);
+}
+
 }  // namespace mg

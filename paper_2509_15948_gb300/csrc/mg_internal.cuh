@@ -203,5 +203,9 @@ void launch_adam2(cudaStream_t, const float* hyper, int* step, float* p, const f
 void launch_set_hyper(cudaStream_t, float* hyper, float alpha_p, float lr, float b1, float b2, float eps, float wd,
                       int which);
 void launch_copy_mix(cudaStream_t, const SongDev* songs, int nsongs, float* out, const int64_t* offs);
+// candidate scoring
+void launch_gather_q(cudaStream_t, const float* q, const int* src, float* dst, int n);
+void launch_score_scatter(cudaStream_t, const int* map, const float* vla, const float* base_la, float* out, int n,
+                          int nsongs);
 
 }  // namespace mg

@@ -1,10 +1,11 @@
 """Mixing-graph search (Alg. 2 with brute-force sampling, Alg. 3 with dry/wet sampling, and the hybrid of the
 two; Sec. 6.1-6.3) on the CUDA console.
 
-Every song of a console runs its own search.  The songs advance in lockstep: one masked forward
-(mg_prune_scores with a single mask over all processors) evaluates the current trial of every song at once,
-because a song's audio loss L_a depends only on its own processors.  Training between rounds is the console's
-CUDA-graph step (forward, backward, Adam).
+Every song of a console runs its own search.  The songs advance together: one mg_prune_scores call evaluates
+the next trials of every song at once, because a song's audio loss L_a depends only on its own processors, and
+each song submits a window of its next trials drawn on the assumption that they fail (_run_trials), which the
+batched scorer evaluates over one base render.  The decisions equal those of one trial at a time.  Training
+between rounds is the console's CUDA-graph step (forward, backward, Adam).
 
 Readings where the paper is silent:
   * N_t is fixed when the round starts; the candidate count is k = max(1, floor(N_t r_t + 0.5)) capped at
@@ -105,16 +106,81 @@ class _SongRound:
             self.removed.update(cand)
             drop = set(cand)
             self.V[t] = [i for i in self.V[t] if i not in drop]
-        elif len(cand) > 1:
+            self.pending = None
+        else:
+            self.fail()
+        return t, cand, ok
+
+    def fail(self):
+        """The state after the pending trial fails: r_t halves (k > 1) or the type leaves T_c (k = 1)."""
+        t, cand = self.pending
+        if len(cand) > 1:
             self.r[t] /= 2.0
         else:
             self.tc.remove(t)
         self.pending = None
-        return t, cand, ok
+
+    def clone(self) -> "_SongRound":
+        c = _SongRound.__new__(_SongRound)
+        c.w, c.tc, c.V, c.N, c.r = self.w, list(self.tc), {t: list(v) for t, v in self.V.items()}, self.N, dict(self.r)
+        c.removed, c.l_min, c.rng, c.pending = set(self.removed), self.l_min, SplitMix64(0), self.pending
+        c.rng.s = self.rng.s
+        return c
+
+    def candidates(self):
+        return self.pending[1]
+
+
+def _run_trials(con, songs, tau: float, window: int, on_trial) -> None:
+    """Runs the trials of every song's round (objects with advance / resolve / fail / clone / candidates).
+
+    Every prune_scores call carries, per song, its next trials up to the song's window, drawn on a copy of its
+    state on the assumption that each of them fails (the next trial of a round follows from the state alone).
+    The results are taken in order up to the song's first accepted trial: every mask taken up to there is
+    exactly the mask of a one-trial-at-a-time round (a song's L_a depends only on its own processors), so the
+    decisions and scores are those of that round; the song's later masks lacked the accepted candidates and
+    are discarded.  A song's window doubles (up to `window`) when all its trials were taken and shrinks to
+    twice what was taken otherwise.  window = 1 is the plain round, one mask per call."""
+    P = con.n_processors
+    active = [sr.advance() for sr in songs]
+    win = [min(window, 4)] * len(songs)
+    while any(active):
+        chains = []
+        for s, sr in enumerate(songs):
+            chain = []
+            if active[s]:
+                st = sr.clone()
+                while True:
+                    chain.append(st.candidates())
+                    if len(chain) >= win[s]:
+                        break
+                    st.fail()
+                    if not st.advance():
+                        break
+            chains.append(chain)
+        masks = np.ones((max(len(c) for c in chains), P), np.uint8)
+        for s, sr in enumerate(songs):
+            for i in sr.removed:
+                masks[:, i] = 0
+            for b, cand in enumerate(chains[s]):
+                for i in cand:
+                    masks[b, i] = 0
+        la = con.prune_scores(masks).cpu().numpy().astype(np.float64)
+        for s, sr in enumerate(songs):
+            taken = 0
+            for b, cand in enumerate(chains[s]):
+                assert tuple(sr.candidates()) == tuple(cand)
+                ok = on_trial(s, sr, float(la[b, s]))
+                taken += 1
+                active[s] = sr.advance()
+                if ok or not active[s]:
+                    break
+            if chains[s]:
+                win[s] = min(window, 2 * win[s]) if taken == len(chains[s]) else max(1, min(window, 2 * taken))
 
 
 def dry_wet_round(con, l_min: Sequence[float], tau: float, rngs: Sequence[SplitMix64],
-                  w: Optional[np.ndarray] = None) -> tuple:
+                  w: Optional[np.ndarray] = None, window: int = 16) -> tuple:
     """One pruning round of Alg. 3 for every song of `con`, in lockstep.
 
     Returns (keep mask [P] uint8 over all processors, updated L_min per song, list of Trial)."""
@@ -129,22 +195,12 @@ def dry_wet_round(con, l_min: Sequence[float], tau: float, rngs: Sequence[SplitM
         procs = [i for i in range(P) if song_of[i] == s and present[i]]
         songs.append(_SongRound(procs, types, w, l_min[s], rngs[s]))
     trials: List[Trial] = []
-    active = [sr.advance() for sr in songs]
-    while any(active):
-        mask = np.ones(P, np.uint8)
-        for s, sr in enumerate(songs):
-            for i in sr.removed:
-                mask[i] = 0
-            if active[s]:
-                for i in sr.pending[1]:
-                    mask[i] = 0
-        la = con.prune_scores(mask[None, :])[0].cpu().numpy().astype(np.float64)
-        for s, sr in enumerate(songs):
-            if not active[s]:
-                continue
-            t, cand, ok = sr.resolve(float(la[s]), tau)
-            trials.append(Trial(s, t, cand, float(la[s]), ok))
-            active[s] = sr.advance()
+
+    def on_trial(s, sr, la):
+        t, cand, ok = sr.resolve(la, tau)
+        trials.append(Trial(s, t, cand, la, ok))
+        return ok
+    _run_trials(con, songs, tau, window, on_trial)
     keep = present.astype(np.uint8).copy()
     for sr in songs:
         for i in sr.removed:
@@ -179,11 +235,25 @@ class _SongBrute:
         self.pending = None
         return v, ok
 
+    def fail(self):
+        self.pool.remove(self.pending)
+        self.pending = None
 
-def brute_force_round(con, l_min: Sequence[float], tau: float, rngs: Sequence[SplitMix64]) -> tuple:
-    """One pruning round with brute-force sampling for every song of `con`, in lockstep: each masked forward
-    tries one processor of every song whose pool is not empty.  Pool in ascending processor order,
-    v = pool[next() mod |pool|], a tried processor leaves the pool whatever the outcome.
+    def clone(self) -> "_SongBrute":
+        c = _SongBrute.__new__(_SongBrute)
+        c.pool, c.removed, c.l_min, c.pending = list(self.pool), set(self.removed), self.l_min, self.pending
+        c.rng = SplitMix64(0)
+        c.rng.s = self.rng.s
+        return c
+
+    def candidates(self):
+        return (self.pending,)
+
+
+def brute_force_round(con, l_min: Sequence[float], tau: float, rngs: Sequence[SplitMix64], window: int = 16) -> tuple:
+    """One pruning round with brute-force sampling for every song of `con`: every processor of a song is tried
+    alone, one at a time.  Pool in ascending processor order, v = pool[next() mod |pool|], a tried processor
+    leaves the pool whatever the outcome.  Trials are submitted in speculative windows (_run_trials).
     Returns (keep mask [P], updated L_min per song, list of Trial)."""
     types = con.processor_types()
     _, _, song_of = con.layout()
@@ -192,21 +262,12 @@ def brute_force_round(con, l_min: Sequence[float], tau: float, rngs: Sequence[Sp
     songs = [_SongBrute([i for i in range(P) if song_of[i] == s and present[i]], l_min[s], rngs[s])
              for s in range(con.n_songs)]
     trials: List[Trial] = []
-    active = [sr.advance() for sr in songs]
-    while any(active):
-        mask = np.ones(P, np.uint8)
-        for s, sr in enumerate(songs):
-            for i in sr.removed:
-                mask[i] = 0
-            if active[s]:
-                mask[sr.pending] = 0
-        la = con.prune_scores(mask[None, :])[0].cpu().numpy().astype(np.float64)
-        for s, sr in enumerate(songs):
-            if not active[s]:
-                continue
-            v, ok = sr.resolve(float(la[s]), tau)
-            trials.append(Trial(s, types[v], (v,), float(la[s]), ok))
-            active[s] = sr.advance()
+
+    def on_trial(s, sr, la):
+        v, ok = sr.resolve(la, tau)
+        trials.append(Trial(s, types[v], (v,), la, ok))
+        return ok
+    _run_trials(con, songs, tau, window, on_trial)
     keep = present.astype(np.uint8).copy()
     for sr in songs:
         for i in sr.removed:
@@ -294,7 +355,8 @@ def alpha_p_at(step: int, ramp_steps: int, alpha_p_max: float) -> float:
 
 def search(con, n_iter: int, train_steps: int, finetune_steps: int, lr: float = 1e-2, tau: float = 0.01,
            seed: int = 0, alpha_p_max: float = 1e-4, ramp_steps: Optional[int] = None,
-           method: str = "dry_wet", feeder: Optional[CropFeeder] = None, eval_con=None) -> SearchResult:
+           method: str = "dry_wet", feeder: Optional[CropFeeder] = None, eval_con=None,
+           window: int = 16) -> SearchResult:
     """Alg. 2 / Alg. 3 on every song of `con`: train, L_min from the unmasked graph, then n_iter rounds of
     {pruning round, structural prune, fine-tuning}.  method: "dry_wet" (Alg. 3), "brute_force" (every
     processor tried alone) or "hybrid" (brute force on every 4th round, dry/wet otherwise; the paper's
@@ -345,7 +407,7 @@ def search(con, n_iter: int, train_steps: int, finetune_steps: int, lr: float = 
         t0 = time.perf_counter()
         sync_eval()
         brute = method == "brute_force" or (method == "hybrid" and uses_brute_force(it))
-        keep, l_min, trials = (brute_force_round if brute else dry_wet_round)(ev, l_min, tau, rngs)
+        keep, l_min, trials = (brute_force_round if brute else dry_wet_round)(ev, l_min, tau, rngs, window=window)
         con.prune(keep)
         if eval_con is not None:
             eval_con.prune(keep)

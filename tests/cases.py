@@ -27,31 +27,36 @@ class Case:
     n_fft: Sequence[int]
     n_mels: int
     oracle: OC.Console
+    fs: int = W.FS
+    warmup: int = 0
 
 
 def make_case(layouts: Sequence[W.SongLayout], types: str = "ecnsgdr", seed: int = 0, n_fft=(512, 2048, 8192),
-              n_mels: int = 96, a_weighting: bool = True, warmup: int = 0, param_key=None) -> Case:
+              n_mels: int = 96, a_weighting: bool = True, warmup: int = 0, param_key=None, fs: int = W.FS) -> Case:
     layouts = list(layouts)
     songs = [OC.SongSpec(l.num_tracks, l.num_subgroups, l.track_group, l.num_samples) for l in layouts]
-    sources = [W.song_sources(l, (seed, i)) for i, l in enumerate(layouts)]
+    sources = [W.song_sources(l, (seed, i), fs) for i, l in enumerate(layouts)]
     ptypes = W.processor_types(layouts, types)
     n_rev = sum(t == "r" for t in ptypes)
-    noise = W.reverb_noise((seed,), max(1, n_rev)) if n_rev else None
-    ldesc = OL.LossDesc(n_fft=tuple(n_fft), n_mels=n_mels, a_weighting=a_weighting, warmup_samples=warmup)
-    desc = OC.ConsoleDesc(types=types, loss=ldesc)
+    noise = W.reverb_noise((seed,), max(1, n_rev), fs) if n_rev else None
+    ldesc = OL.LossDesc(sample_rate=float(fs), n_fft=tuple(n_fft), n_mels=n_mels, a_weighting=a_weighting,
+                        warmup_samples=warmup)
+    desc = OC.ConsoleDesc(sample_rate=float(fs), types=types, loss=ldesc)
     gt, keep = W.ground_truth(ptypes, (seed, 77))
     targets = OC.Console(songs, sources, None, noise, desc).render_targets(gt, keep)
     oracle = OC.Console(songs, sources, targets, noise, desc)
     params = W.init_params(ptypes, (seed, 5) if param_key is None else param_key)
-    return Case(layouts, types, sources, targets, noise, ptypes, params, tuple(n_fft), n_mels, oracle)
+    return Case(layouts, types, sources, targets, noise, ptypes, params, tuple(n_fft), n_mels, oracle, fs, warmup)
 
 
 def gpu_console(case: Case, **cfg_kw):
+    """The CUDA console of a case: same songs, sources, targets, noises, sample rate and loss settings."""
     import paper_2509_15948_gb300 as M
     songs = [M.Song(l.num_tracks, l.num_subgroups, l.track_group, l.num_samples) for l in case.layouts]
-    cfg = M.ConsoleConfig(types=case.types, n_fft=case.n_fft, n_mels=case.n_mels, **cfg_kw)
-    con = M.Console(songs, case.sources, case.targets, case.noise, cfg)
-    return con
+    kw = dict(types=case.types, n_fft=case.n_fft, n_mels=case.n_mels, sample_rate=float(case.fs),
+              warmup_samples=case.warmup)
+    kw.update(cfg_kw)
+    return M.Console(songs, case.sources, case.targets, case.noise, M.ConsoleConfig(**kw))
 
 
 def rel_l2(a, b) -> float:
@@ -118,12 +123,13 @@ def oracle_with_delay_taps(case: Case, alpha_p: float):
     return losses, grads, mixes, taps
 
 
-def delay_term_rms(case: Case, alpha_p: float = 1e-3, D: int = 4410, n0: int = -19) -> dict:
+def delay_term_rms(case: Case, alpha_p: float = 1e-3, D: int = None, n0: int = -19) -> dict:
     """Per delay processor and channel: rms over the tap lags of A[j] = sum_n |dL/dy_bar[n]| |u[n - j]|, the
     magnitudes of the terms whose sum is dL/dh[j] (dL/dy_bar taken as w dL/dy from the oracle's intermediates).
     Near an optimum dL/dh cancels strongly (A is 4-2000x its rms), and FP32 rounding of the upstream adjoint
     bounds dL/dh's accuracy by a fraction of A rather than of dL/dh."""
     import torch
+    D = D or int(round(0.1 * case.fs))
     params = torch.tensor(np.asarray(case.params, np.float64), requires_grad=True)
     res = case.oracle.forward(params, alpha_p=alpha_p, keep_outputs=True)
     for r in res:
@@ -151,11 +157,12 @@ def delay_term_rms(case: Case, alpha_p: float = 1e-3, D: int = 4410, n0: int = -
     return out
 
 
-def delay_slot_conditioning(case: Case, taps: dict, D: int = 4410, term_rms: dict = None):
+def delay_slot_conditioning(case: Case, taps: dict, D: int = None, term_rms: dict = None):
     """Per delay processor, channel and tap m: kappa = |g_m| / (rms(dL/dh) ||c_m|| ||s'||), the ratio of the
     Eq. (19) inner product g_m to its Cauchy-Schwarz scale (how far g_m stands above cancellation).  With
     term_rms (delay_term_rms) the scale uses the rms of the summed term magnitudes instead of rms(dL/dh)."""
     from oracle import processors as OP
+    D = D or int(round(0.1 * case.fs))
     out = {}
     for p in case.oracle.procs:
         if p.type != "d":

@@ -84,13 +84,20 @@ def test_splitmix64_matches_published_output():
     assert g.next() == 0xE220A8397B1DCDAF
 
 
+@pytest.mark.parametrize("window", [1, 3, 16])
 @pytest.mark.parametrize("tau", [0.0, 0.01])
-def test_lockstep_round_equals_per_song_oracle_rounds(tau):
+def test_lockstep_round_equals_per_song_oracle_rounds(tau, window):
+    """Speculative windows (several trials per song and call, taken up to the first accepted one) give the
+    one-trial-at-a-time decisions; window 1 is one call per trial step."""
     con = FakeConsole([3, 1, 5, 2], seed=7)
     l_min = [float(np.float32(b)) for b in con.base]
     rngs = [GS.SplitMix64(GS.song_seed(11, s)) for s in range(con.n_songs)]
-    keep, lm, trials = GS.dry_wet_round(con, l_min, tau, rngs)
-    assert con.calls == max(sum(1 for t in trials if t.song == s) for s in range(con.n_songs))
+    keep, lm, trials = GS.dry_wet_round(con, l_min, tau, rngs, window=window)
+    steps = max(sum(1 for t in trials if t.song == s) for s in range(con.n_songs))
+    if window == 1:
+        assert con.calls == steps
+    else:
+        assert con.calls < steps
     for s in range(con.n_songs):
         idx, m, olm, trace = oracle_song_round(con, s, l_min[s], tau, GS.song_seed(11, s))
         mine = [(t.type, tuple(int(i) for i in t.candidates), t.la, t.accepted) for t in trials if t.song == s]
@@ -117,12 +124,15 @@ def test_alpha_p_ramp():
     assert GS.alpha_p_at(400, 100, 1e-4) == 1e-4
 
 
+@pytest.mark.parametrize("window", [1, 4, 16])
 @pytest.mark.parametrize("tau", [0.0, 0.01])
-def test_lockstep_brute_force_equals_per_song_oracle_rounds(tau):
+def test_lockstep_brute_force_equals_per_song_oracle_rounds(tau, window):
     con = FakeConsole([2, 1, 3], seed=5)
     l_min = [float(np.float32(b)) for b in con.base]
     rngs = [GS.SplitMix64(GS.song_seed(4, s)) for s in range(con.n_songs)]
-    keep, lm, trials = GS.brute_force_round(con, l_min, tau, rngs)
+    keep, lm, trials = GS.brute_force_round(con, l_min, tau, rngs, window=window)
+    if window > 1:
+        assert con.calls < max(sum(1 for t in trials if t.song == s) for s in range(con.n_songs))
     for s in range(con.n_songs):
         idx = np.nonzero(con.song == s)[0]
 
