@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <array>
 #include <mutex>
@@ -30,12 +31,12 @@ constexpr int kParamCount[NTYPES] = {1024, 4, 4, 1, 2, 880, 768};
 enum Family {
   F_GS_FWD, F_GS_BWD, F_SUM, F_DYN_FWD, F_DYN_BWD, F_EQ_FIR, F_DLY_FIR, F_REV_FIR, F_FIR_ADJ, F_COL_FWD, F_ROW_HZ,
   F_ROW_CONV, F_COL_OUT, F_COL_DYBAR, F_ROW_BWD2, F_COL_DU, F_COL_DH, F_LOSS_FWD, F_LOSS_BWD, F_LOSS_GATHER,
-  F_FINALIZE, F_ADAM, F_MISC, F_EQ_OS_FWD, F_EQ_OS_BWD, F_EQ_OS_DU, F_COUNT
+  F_FINALIZE, F_ADAM, F_MISC, F_EQ_OS_FWD, F_EQ_OS_BWD, F_EQ_OS_DU, F_SCALE, F_COUNT
 };
 const char* kFamilyNames[F_COUNT] = {
     "gs_fwd", "gs_bwd", "sum", "dyn_fwd", "dyn_bwd", "eq_fir", "dly_fir", "rev_fir", "fir_adj", "col_fwd", "row_hz",
     "row_conv", "col_out", "col_dybar", "row_bwd2", "col_du", "col_dh", "loss_fwd", "loss_bwd", "loss_gather",
-    "finalize", "adam", "misc", "eq_os_fwd", "eq_os_bwd", "eq_os_du"};
+    "finalize", "adam", "misc", "eq_os_fwd", "eq_os_bwd", "eq_os_du", "chan_scale"};
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int ilog2_ceil(int64_t x) {
@@ -148,6 +149,8 @@ struct mg_console {
   std::vector<char> score_blob;
   std::vector<uint8_t> score_m0;
   int score_mode = 0;              // 0: batched candidate scoring, 1: one full masked render per candidate
+  bool debug_sync = false;         // MG_DEBUG_SYNC=1 in the environment: synchronise and check after every launch
+  bool debug_reported = false;
   ProcDev* d_procs = nullptr;
   SongDev* d_songs = nullptr;
   LossRes* d_res = nullptr;
@@ -442,6 +445,16 @@ void run(mg_console* c, int fam, F&& f) {
   }
   f();
   ++c->launches;
+  if (c->debug_sync && !c->capturing) {
+    // diagnostic mode: wait for every launch and report the first one that fails
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    const cudaError_t l = cudaPeekAtLastError();
+    if ((e != cudaSuccess || l != cudaSuccess) && !c->debug_reported) {
+      c->debug_reported = true;
+      std::fprintf(stderr, "mixgraph: launch %d (family %s, stage %d) failed: %s\n", c->launches, kFamilyNames[fam],
+                   c->cur_stage, cudaGetErrorString(e != cudaSuccess ? e : l));
+    }
+  }
   if (c->profiling) {
     cudaEventRecordWithFlags(e1, c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
     auto pr = std::make_pair(fam + F_COUNT * c->cur_stage, std::make_pair(e0, e1));
@@ -493,6 +506,7 @@ void lti_forward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
     run_items(c, F_DLY_FIR, g.firtaps, [&](const Item* it, int n) { launch_dly_fir(x, it, n); });
   }
   if (type == T_R) run_items(c, F_REV_FIR, g.revfir, [&](const Item* it, int n) { launch_rev_fir(x, it, n); });
+  run_procs(c, F_SCALE, g.procs, [&](const int* p, int n) { launch_chan_scale(x, p, n, 0); });
   run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
   run_items(c, F_ROW_HZ, g.rowpair, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowpair.maxv); });
   run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_audio(x, it, n, g.col.maxv); });
@@ -506,6 +520,7 @@ void lti_forward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
 }
 
 void lti_backward(mg_console* c, const LaunchCtx& x, int type, LtiGroup& g) {
+  run_procs(c, F_SCALE, g.procs, [&](const int* p, int n) { launch_chan_scale(x, p, n, 1); });
   if (c->retain) {
     run_items(c, F_COL_DYBAR, g.col, [&](const Item* it, int n) { launch_col_dybar_keep(x, it, n, g.col.maxv); });
   } else {
@@ -916,7 +931,7 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
   size_t scratch_need = 0;
   for (auto& p : c->procs) {
     p.o_y = b.take((size_t)2 * p.ld * sizeof(float));
-    p.o_stats = b.take(16 * sizeof(float));
+    p.o_stats = b.take(kStatsFloats * sizeof(float));
     if (p.nfrows) p.o_fpart = b.take((size_t)std::max(p.nfrows, p.nfcap) * kNPart * sizeof(float));
     if (p.nbrows) p.o_bpart = b.take((size_t)std::max(p.nbrows, p.nfcap) * kNPart * sizeof(float));
     if (p.type == T_E || p.type == T_R || p.type == T_D) {
@@ -1475,6 +1490,7 @@ struct ScoreChunk {
   std::vector<int4> litems[3];
   std::vector<int> map;                      // [candidate][song]: song copy, or -1 (unchanged)
   size_t table_begin = 0;                    // workspace offset of the tables (copied from the host blob)
+  size_t end = 0;                            // workspace bytes the chunk uses
   float* vq = nullptr;
   float* vla = nullptr;
   int* d_vsrc = nullptr;
@@ -1492,7 +1508,7 @@ struct ScoreChunk {
 size_t copy_bytes(const mg_console* c, int pi, size_t* items) {
   const HostProc& p = c->procs[pi];
   auto al = [](size_t b) { return (size_t)round_up((int64_t)b, 256); };
-  size_t b = al((size_t)2 * p.ld * sizeof(float)) + al(16 * sizeof(float));
+  size_t b = al((size_t)2 * p.ld * sizeof(float)) + al(kStatsFloats * sizeof(float));
   size_t it = 0;
   if (p.nfrows) b += al((size_t)std::max(p.nfrows, p.nfcap) * kNPart * sizeof(float));
   if (p.type == T_C || p.type == T_N) {
@@ -1501,6 +1517,7 @@ size_t copy_bytes(const mg_console* c, int pi, size_t* items) {
   } else if (p.type == T_G || p.type == T_S) {
     it = p.nbrows;
   } else if (p.type == T_E) {
+    b += al((size_t)2 * p.ld * sizeof(float));   // the wet signal the equalizer forward stores
     it = p.nfrows;
   } else {
     const size_t N = (size_t)p.f << p.logN;
@@ -1635,7 +1652,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
         d.qidx = v;
         d.u = cur;
         d.y = (float*)w.buffer((size_t)2 * p.ld * sizeof(float));
-        d.stats = (float*)w.buffer(16 * sizeof(float));
+        d.stats = (float*)w.buffer(kStatsFloats * sizeof(float));
         d.fpart = p.nfrows ? (float*)w.buffer((size_t)std::max(p.nfrows, p.nfcap) * kNPart * sizeof(float)) : nullptr;
         d.dy = nullptr;
         d.du = nullptr;
@@ -1645,7 +1662,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
         d.rcarry = nullptr;
         d.dhspec = nullptr;
         d.eqg = nullptr;
-        d.ybar = nullptr;                    // the equalizer keeps no wet signal for a backward
+        d.ybar = p.type == T_E ? (float*)w.buffer((size_t)2 * p.ld * sizeof(float)) : nullptr;
         if (p.type == T_C || p.type == T_N) {
           d.carry = (float*)w.buffer((size_t)p.nchunks * sizeof(float));
           d.chunkagg = (float*)w.buffer((size_t)p.nchunks * sizeof(float));
@@ -1791,6 +1808,73 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
       g.rowpair.d = w.table(g.rowpair.h);
     }
   }
+  k.end = w.b.off;
+}
+
+// Host check of a chunk before anything is copied or launched: every device pointer of the node copies, sums and
+// song copies lies in the arena, the spectra scratch, the workspace or the parameter buffer, and every work item
+// indexes an existing node copy within its range.  Returns an empty string when the chunk is consistent.
+std::string check_chunk(const mg_console* c, const ScoreChunk& k) {
+  auto in = [&](const void* p, size_t bytes) {
+    const char* q = static_cast<const char*>(p);
+    auto inside = [&](const char* b, size_t n) { return b && q >= b && q + bytes <= b + n; };
+    return inside(c->arena, c->arena_bytes) || inside(c->scratch, c->scratch_bytes) ||
+           inside(c->score_ws, c->score_ws_bytes) ||
+           inside(reinterpret_cast<const char*>(c->d_params), sizeof(float) * (size_t)c->nparams);
+  };
+  if (k.end > c->score_ws_bytes) return "chunk exceeds the scoring workspace";
+  for (size_t v = 0; v < k.vp.size(); ++v) {
+    const ProcDev& d = k.vp[v];
+    const size_t st = (size_t)2 * d.ld * sizeof(float);
+    if (!in(d.u, st) || !in(d.y, st) || !in(d.stats, kStatsFloats * sizeof(float)) || !in(d.p, sizeof(float)))
+      return "node copy " + std::to_string(v) + ": signal or parameter pointer out of range";
+    if (d.fpart && !in(d.fpart, (size_t)d.nfpart * kNPart * sizeof(float)))
+      return "node copy " + std::to_string(v) + ": partials out of range";
+    if ((d.type == T_C || d.type == T_N) &&
+        (!in(d.carry, (size_t)d.nchunks * 4) || !in(d.chunkagg, (size_t)d.nchunks * 4)))
+      return "node copy " + std::to_string(v) + ": scan carries out of range";
+    if (d.type == T_R || d.type == T_D) {
+      const size_t N = (size_t)d.f << d.logN;
+      if (!in(d.T1, N * sizeof(float2)) || !in(d.Hz, N * sizeof(float2)) ||
+          !in(d.taps, (size_t)2 * d.Nh * sizeof(float)))
+        return "node copy " + std::to_string(v) + ": FFT buffers out of range";
+    }
+    if (d.type == T_E && (!in(d.hspec, kEqOsM * sizeof(float)) || !in(d.ybar, st)))
+      return "node copy " + std::to_string(v) + ": equalizer spectrum or wet signal out of range";
+  }
+  const int V = (int)k.vp.size();
+  for (const auto& st : k.stages) {
+    for (int v : st.procs.h)
+      if (v < 0 || v >= V) return "stage list indexes a missing node copy";
+    for (const Item& it : st.elem.h) {
+      const ProcDev& d = k.vp[it.proc];
+      const int lim = (st.type == T_C || st.type == T_N) ? d.nchunks : (d.L + kElemTile - 1) / kElemTile;
+      if (it.proc < 0 || it.proc >= V || it.idx < 0 || it.idx >= lim) return "elementwise item out of range";
+    }
+    for (const Item& it : st.osf.h)
+      if (it.proc < 0 || it.proc >= V || it.idx < 0 || it.idx >= k.vp[it.proc].nfpart) return "equalizer item out of range";
+    for (const auto& g : st.groups) {
+      for (const Item& it : g.col.h) {
+        const ProcDev& d = k.vp[it.proc];
+        if (it.idx < 0 || it.idx >= (d.f << d.logN1) / d.colG) return "column item out of range";
+      }
+      for (const Item& it : g.rowpair.h)
+        if (it.idx < 0 || it.idx > (1 << k.vp[it.proc].logN2) / 2) return "row item out of range";
+    }
+  }
+  for (size_t s = 0; s + 1 < k.sum_beg.size(); ++s) {
+    const size_t st = (size_t)2 * k.sum_ld[s] * sizeof(float);
+    if (!in(k.sum_out[s], st)) return "sum output out of range";
+    for (int j = k.sum_beg[s]; j < k.sum_beg[s + 1]; ++j)
+      if (!in(k.sum_in[j], st)) return "sum input out of range";
+  }
+  for (const SongDev& sd : k.vs)
+    if (!in(sd.mix, (size_t)2 * sd.ld * sizeof(float)) || !in(sd.lpart, (size_t)18 * sd.lcap * sizeof(float)))
+      return "song copy buffers out of range";
+  for (int r = 0; r < 3; ++r)
+    for (const int4& it : k.litems[r])
+      if (it.x < 0 || it.x >= (int)k.vs.size()) return "loss item indexes a missing song copy";
+  return std::string();
 }
 
 // Forward of the node copies of one (level, type): the stage's kernels without the parameter-only work (FIR
@@ -1814,6 +1898,7 @@ void vstage_forward(mg_console* c, const LaunchCtx& x, Stage& s) {
       break;
     default:
       for (auto& g : s.groups) {
+        run_procs(c, F_SCALE, g.procs, [&](const int* p, int n) { launch_chan_scale(x, p, n, 0); });
         if (!c->retain) {
           run_items(c, F_COL_FWD, g.col, [&](const Item* it, int n) { launch_col_fwd_taps(x, it, n, g.col.maxv); });
           run_items(c, F_ROW_HZ, g.rowpair, [&](const Item* it, int n) { launch_row_fwd_hz(x, it, n, g.rowpair.maxv); });
@@ -1888,6 +1973,10 @@ mg_status prune_scores_batched(mg_console* c, const uint8_t* d_masks, int n_mask
     if (ensure_score_ws(c, bytes) != MG_OK) return MG_ERR_OOM;
     ScoreChunk k;
     build_chunk(c, plans, hm.data(), j, j1, k);
+    if (k.end > c->score_ws_bytes || c->debug_sync) {
+      const std::string bad = check_chunk(c, k);
+      if (!bad.empty()) return fail(c, MG_ERR_INVALID, "candidate scoring: " + bad);
+    }
     if (!c->score_blob.empty())
       CK(cudaMemcpyAsync(c->score_ws + k.table_begin, c->score_blob.data(), c->score_blob.size(),
                          cudaMemcpyHostToDevice, c->stream));
@@ -1971,6 +2060,10 @@ mg_status mg_console_create(const mg_console_desc* desc, const mg_song_desc* son
   mg_console* c = new (std::nothrow) mg_console();
   if (!c) return fail(nullptr, MG_ERR_OOM, "host allocation failed");
   c->stream = stream;
+  {
+    const char* dbg = std::getenv("MG_DEBUG_SYNC");
+    c->debug_sync = dbg && dbg[0] == '1';
+  }
   mg_status st = validate(c, desc, songs, n_songs);
   if (st == MG_OK) {
     std::lock_guard<std::mutex> lock(g_device_mutex);

@@ -1,4 +1,7 @@
 // Column passes of the four-step FFT convolution (see k_conv_common.cuh).
+#include <cstdint>
+#include <cstdio>
+
 #include "k_conv_common.cuh"
 
 namespace mg {
@@ -74,10 +77,12 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   if (MODE == COL_FWD_AUDIO || MODE == COL_FWD_TAPS) {   // forward pass of the input or the taps, in place
     const float* u = P.u;
     const int L = P.L, ld = P.ld;
+    const float2 sc = chan_scale(P, MODE == COL_FWD_AUDIO ? kScaleU : kScaleH);
     fft_p_io<false, 1, true>(sm, logN2, G, cs, c.tab.ptw, [&](int gg, int n2) {
       const int64_t n = n1b + gg + (int64_t)N1 * n2;
-      if (MODE == COL_FWD_AUDIO) return n < L ? make_float2(u[n], u[ld + n]) : make_float2(0.f, 0.f);
-      return tap_at(P, n, N);
+      if (MODE == COL_FWD_AUDIO) return n < L ? make_float2(u[n] * sc.x, u[ld + n] * sc.y) : make_float2(0.f, 0.f);
+      const float2 t = tap_at(P, n, N);
+      return make_float2(t.x * sc.x, t.y * sc.y);
     }, tw_store(MODE == COL_FWD_TAPS ? P.Hz : P.T1));
     return;
   }
@@ -90,6 +95,10 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   }
 
   const float inv_n = ldexpf(1.f, -P.logN) / (float)P.f;
+  // 1/N divided by the channel scales of the two transformed operands (exact: the scales are powers of two)
+  const float2 su = chan_scale(P, kScaleU), sh = chan_scale(P, kScaleH), sd = chan_scale(P, kScaleD);
+  const float2 inv_uh = make_float2(inv_n / (su.x * sh.x), inv_n / (su.y * sh.y));
+  auto unscale = [](float2 v, float2 s) { return make_float2(v.x * s.x, v.y * s.y); };
   if (kOut) {
     const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
     float acc[2] = {0.f, 0.f};
@@ -109,7 +118,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
       for (int j = 0; j < 4; ++j) {
         const int64_t n = pos(h + j);
         if (!live(h + j) || n >= P.L) continue;
-        const float2 yb = cscale(col[pidx(row_of(h + j))], inv_n);
+        const float2 yb = unscale(col[pidx(row_of(h + j))], inv_uh);
         if (MODE == COL_INV_OUT_KEEP) P.T2[n] = yb;
         P.y[n] = w * yb.x + wd * ul[j];
         P.y[P.ld + n] = w * yb.y + wd * ur[j];
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
         yb[j] = make_float2(0.f, 0.f);
         gl[j] = gr[j] = ul[j] = ur[j] = 0.f;
         if (live(h + j) && n < P.L) {
-          yb[j] = MODE == COL_DYBAR_KEEP ? P.T2[n] : cscale(col[pidx(row_of(h + j))], inv_n);
+          yb[j] = MODE == COL_DYBAR_KEEP ? P.T2[n] : unscale(col[pidx(row_of(h + j))], inv_uh);
           gl[j] = P.dy[n];
           gr[j] = P.dy[P.ld + n];
           ul[j] = P.u[n];
@@ -155,7 +164,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
         acc[0] += gl[j] * (yb[j].x - ul[j]) + gr[j] * (yb[j].y - ur[j]);
         const float gm = c1 * (yb[j].x + yb[j].y);
         // rows past the signal are zero (gl = gr = 0 and y_bar = 0 there)
-        col[pidx(row_of(h + j))] = make_float2(w * gl[j] + gm, w * gr[j] + gm);
+        col[pidx(row_of(h + j))] = make_float2(sd.x * (w * gl[j] + gm), sd.y * (w * gr[j] + gm));
       }
     }
     float out[1];
@@ -167,6 +176,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   if (MODE == COL_DU) {
     const float wd = dry_wet_d(c, P.qidx);
     const float c2 = P.stats[3];
+    const float2 inv_dh = make_float2(inv_n / (sd.x * sh.x), inv_n / (sd.y * sh.y));
 #pragma unroll 1
     for (int h = 0; h < kSlots; h += 4) {
       float gl[4], gr[4], um[4];
@@ -184,7 +194,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
       for (int j = 0; j < 4; ++j) {
         const int64_t n = pos(h + j);
         if (!live(h + j) || n >= P.L) continue;
-        const float2 dw = cscale(col[pidx(row_of(h + j))], inv_n);
+        const float2 dw = unscale(col[pidx(row_of(h + j))], inv_dh);
         P.du[n] = wd * gl[j] + dw.x + um[j];
         P.du[P.ld + n] = wd * gr[j] + dw.y + um[j];
       }
@@ -192,6 +202,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
     return;
   }
   if (MODE == COL_DH) {
+    const float2 inv_du = make_float2(inv_n / (sd.x * su.x), inv_n / (sd.y * su.y));
 #pragma unroll 4
     for (int s = 0; s < kSlots; ++s) {
       if (!live(s)) continue;
@@ -202,10 +213,62 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
       if (j >= 0 && j < P.Nh) {
         // dL/dh[t] = sum_n dL/dy_bar[n] u[n - t] is identically zero for lags t >= L: store the exact zero
         // instead of the FFT rounding residue (the delay's Eq. 19 direction takes sgn(0) = 0 there)
-        const float2 v = (j + P.n0 >= P.L) ? make_float2(0.f, 0.f) : cscale(col[pidx(row_of(s))], inv_n);
+        const float2 v = (j + P.n0 >= P.L) ? make_float2(0.f, 0.f) : unscale(col[pidx(row_of(s))], inv_du);
         P.dtaps[j] = v.x;
         P.dtaps[P.Nh + j] = v.y;
       }
+    }
+  }
+}
+
+// Channel scales of one node (one CTA per node): per channel the energy of an evenly spread quarter of the
+// signal's 32-byte sectors (four consecutive samples out of every 32), and the power of two s = 2^-floor(e / 2),
+// e the binary exponent of that energy, which brings the channel near unit energy; 1 for a silent channel.
+// which 0: the input u and the taps (in the stereo form the transforms use); 1: dL/dy.  Fixed-order sums.
+__device__ __forceinline__ float pow2_scale(float e) {
+  if (!(e > 0.f) || !isfinite(e)) return 1.f;
+  const int x = ilogbf(e);
+  return ldexpf(1.f, -((x >= 0 ? x : x - 1) / 2));
+}
+
+__global__ void __launch_bounds__(256) k_chan_scale(LaunchCtx c, const int* __restrict__ procs, int which) {
+  __shared__ float red[4 * 32];
+  const ProcDev& P = c.procs[procs[blockIdx.x]];
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const float* x = which == 0 ? P.u : P.dy;
+  // self-check of the operands: a missing or misaligned signal, a row stride shorter than the signal, or missing
+  // taps skip the node (its scales stay as they were) and are reported
+  if (x == nullptr || ((uintptr_t)x & 15) != 0 || P.ld < P.L || (P.ld & 3) != 0 || P.stats == nullptr ||
+      (which == 0 && P.taps == nullptr)) {
+    if (threadIdx.x == 0)
+      printf("k_chan_scale: node %d which %d skipped (x %p, L %d, ld %d, taps %p, stats %p)\n", procs[blockIdx.x], which,
+             (const void*)x, P.L, P.ld, (const void*)P.taps, (const void*)P.stats);
+    return;
+  }
+  const int nq = P.L >> 2;                    // whole quads of samples
+  for (int q = threadIdx.x * 8; q < nq; q += blockDim.x * 8) {
+    const float4 a = reinterpret_cast<const float4*>(x)[q];
+    const float4 b = reinterpret_cast<const float4*>(x + P.ld)[q];
+    acc[0] += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+    acc[1] += b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w;
+  }
+  if (which == 0)
+    for (int j = threadIdx.x; j < P.Nh; j += blockDim.x) {
+      const float2 t = tap_at(P, (int64_t)j + P.n0 >= 0 ? (int64_t)j + P.n0 : fft_len(P) + j + P.n0, fft_len(P));
+      acc[2] += t.x * t.x;
+      acc[3] += t.y * t.y;
+    }
+  float out[4];
+  block_sum<4>(acc, red, out);
+  if (threadIdx.x == 0) {
+    if (which == 0) {
+      P.stats[kScaleU] = pow2_scale(out[0]);
+      P.stats[kScaleU + 1] = pow2_scale(out[1]);
+      P.stats[kScaleH] = pow2_scale(out[2]);
+      P.stats[kScaleH + 1] = pow2_scale(out[3]);
+    } else {
+      P.stats[kScaleD] = pow2_scale(out[0]);
+      P.stats[kScaleD + 1] = pow2_scale(out[1]);
     }
   }
 }
@@ -232,6 +295,9 @@ void init_col_attributes() {
   cudaFuncSetAttribute(k_col<COL_DYBAR_KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
+void launch_chan_scale(const LaunchCtx& c, const int* procs, int n, int which) {
+  if (n) k_chan_scale<<<n, 256, 0, c.stream>>>(c, procs, which);
+}
 void launch_col_fwd_audio(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_FWD_AUDIO>(c, items, n, m); }
 void launch_col_fwd_taps(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_FWD_TAPS>(c, items, n, m); }
 void launch_col_inv_out(const LaunchCtx& c, const Item* items, int n, int m) { launch_col<COL_INV_OUT>(c, items, n, m); }

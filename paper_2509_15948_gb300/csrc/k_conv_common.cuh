@@ -10,7 +10,10 @@
 // inverse row FFT immediately, the inverse column pass returns to natural time order.
 // Both channels travel as one complex signal z = left + i right; a stereo FIR (h_l, h_r) acts on the packed
 // spectrum as Y[k] = Z[k] A[k] + conj(Z[-k]) B[k] with A = (H_l + H_r)/2, B = (H_l - H_r)/2, where the
-// mirror bin -k sits in row N2 - k2.
+// mirror bin -k sits in row N2 - k2.  The rounding error of a packed transform scales with the larger channel,
+// so before packing every channel of u, of the taps and of dL/dy_bar is multiplied by a power of two that
+// brings the channels to a common level (k_chan_scale); the products are bilinear per channel, and the output
+// passes divide by the product of the scales involved, exactly.
 #pragma once
 #include <algorithm>
 
@@ -66,6 +69,12 @@ __device__ __forceinline__ float2 tap_at(const ProcDev& P, int64_t n, int64_t N)
   const float b = P.taps[P.Nh + j];
   if (P.type == T_R) return make_float2(a + b, a - b);   // h_l = h_m + h_s, h_r = h_m - h_s
   return make_float2(a, b);
+}
+
+// Channel scales of a packed transform (left, right): powers of two set by k_chan_scale, or 1 before it ran.
+__device__ __forceinline__ float2 chan_scale(const ProcDev& P, int slot) {
+  const float a = P.stats[slot], b = P.stats[slot + 1];
+  return make_float2(a > 0.f ? a : 1.f, b > 0.f ? b : 1.f);
 }
 
 // Packed-stereo FIR spectra at a bin and its mirror: A = (H_l + H_r)/2, B = (H_l - H_r)/2.

@@ -68,10 +68,8 @@ __global__ void __launch_bounds__(kOsThreads, 2) k_eq_os_fwd(LaunchCtx c, const 
     const int t = j - kEqHalf, s = s0 + t;
     if (t < 0 || t >= B || s >= L) return;
     const float2 yb = cscale(v, inv);
-    if (ybar) {                 // kept for the backward (null for forward-only copies of a node)
-      ybar[s] = yb.x;
-      ybar[ld + s] = yb.y;
-    }
+    ybar[s] = yb.x;
+    ybar[ld + s] = yb.y;
     const float ul = u[s], ur = u[ld + s];
     y[s] = w * yb.x + wd * ul;
     y[ld + s] = w * yb.y + wd * ur;

@@ -33,7 +33,7 @@ struct NaLayout {
   float cos_eq[kEqTaps];
   float hann_eq[kEqTaps];
   float taps[2 * kEqTaps];
-  float stats[16];
+  float stats[kStatsFloats];                 // the channel scales stay 0 here: the transforms use scale 1
   float fpart[kNaMaxCol * kNPart];
   float hyper[8];
   ProcDev proc;

@@ -11,6 +11,10 @@ constexpr int kTwLog = 13;                 // shared twiddle table exp(-2 pi i j
 constexpr int kTwN = 1 << kTwLog;
 constexpr int kTwFineLog = 26;            // fine table exp(-2 pi i j / 2^26), j < 8192: twiddles of N <= 2^26
 constexpr int kNPart = 8;                  // partial sums per work item
+// Per-node statistics: 0 E_ybar_mid, 1 E_u_mid, 2 c1, 3 c2, 4..11 backward sums, 16..21 the channel scales of
+// the packed stereo transforms (u, taps, dL/dy_bar; left then right)
+constexpr int kStatsFloats = 32;
+constexpr int kScaleU = 16, kScaleH = 18, kScaleD = 20;
 constexpr int kEqTaps = 2047;              // Sec. 3.3
 constexpr int kEqHalf = 1023;
 constexpr int kEqParams = 1024;
@@ -53,7 +57,8 @@ struct ProcDev {
   float* fpart;                            // forward partials  [items][kNPart]
   float* bpart;                            // backward partials [items][kNPart]
   int nfpart, nbpart;                      // number of partial rows written by the main pass
-  float* stats;                            // [8]: 0 E_ybar_mid, 1 E_u_mid, 2 c1, 3 c2, 4.. backward sums
+  float* stats;                            // [kStatsFloats]: 0 E_ybar_mid, 1 E_u_mid, 2 c1, 3 c2, 4.. backward sums,
+                                           // kScaleU.. channel scales of the packed transforms
   // LTI processors (r, d): four-step FFT convolution of size N = N1 * N2 = f 2^logN, N1 = f 2^logN1 (rows),
   // N2 = 2^logN2 (columns), f in {1, 3}
   int logN, logN1, logN2, colG;            // colG: columns per column-pass work item
@@ -187,6 +192,8 @@ void launch_col_inv_out_keep(const LaunchCtx&, const Item* items, int n, int max
 void launch_col_dybar_keep(const LaunchCtx&, const Item* items, int n, int maxN2G);
 void launch_row_bwd2(const LaunchCtx&, const Item* items, int n, int maxN1);
 void launch_col_du(const LaunchCtx&, const Item* items, int n, int maxN2G);
+// channel scales of the packed stereo transforms: which 0 = input u and taps (forward), 1 = dL/dy (backward)
+void launch_chan_scale(const LaunchCtx&, const int* procs, int n, int which);
 void launch_col_dh(const LaunchCtx&, const Item* items, int n, int maxN2G);
 // reductions, loss, optimiser
 void launch_node_stats(const LaunchCtx&, const int* procs, int n, int fwd);

@@ -66,39 +66,6 @@ def rel_l2(a, b) -> float:
     return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a - b))
 
 
-def gain_term_magnitudes(case: Case, alpha_p: float = 1e-3) -> dict:
-    """For the gain/pan (Eq. 4) and imager (Eqs. 5-6) parameters: sum over samples of the magnitudes of the
-    terms whose sum is the gradient, dL/dp_c = sum_n dL/dy_c[n] w e^{p_c} u_c[n] (g) and
-    dL/dp = sum_n w e^p (u_l - u_r)[n] (dL/dy_l - dL/dy_r)[n] / 2 (s), from the oracle's intermediates.
-    Near an optimum these gradients cancel strongly, and FP32 rounding of the adjoint then bounds their
-    accuracy by a fraction of this sum rather than of the gradient."""
-    import torch
-    params = torch.tensor(np.asarray(case.params, np.float64), requires_grad=True)
-    res = case.oracle.forward(params, alpha_p=alpha_p, keep_outputs=True)
-    outs = [r["outputs"] for r in res]
-    for o in outs:
-        for v in o.values():
-            if isinstance(v, torch.Tensor) and v.requires_grad:
-                v.retain_grad()
-    sum(r["total"] for r in res).backward()
-    procs = case.oracle.procs
-    q = np.asarray(case.params, np.float64)[case.oracle.n_proc_params:]
-    mags = {"g": [], "s": []}
-    for p in procs:
-        if p.type not in mags:
-            continue
-        o = outs[p.song]
-        u = o[p.index - 1].detach().numpy()      # the chain's previous processor (s before g, n before s)
-        dy = o[p.index].grad.numpy()
-        w = 1.0 / (1.0 + np.exp(-q[p.index]))
-        pp = np.asarray(case.params, np.float64)[p.offset:p.offset + p.count]
-        if p.type == "g":
-            mags["g"].append(np.abs(dy * w * np.exp(pp)[:, None] * u).sum(axis=1))
-        else:
-            mags["s"].append(np.array([np.abs(w * np.exp(pp[0]) * (u[0] - u[1]) * (dy[0] - dy[1]) / 2).sum()]))
-    return {k: np.concatenate(v) for k, v in mags.items() if v}
-
-
 def oracle_with_delay_taps(case: Case, alpha_p: float):
     """Oracle losses, gradients and mixes, plus for every delay processor the oracle's dL/dh (taps) and its
     39-tap FIRs c_m (captured from the forward/backward of the same call)."""

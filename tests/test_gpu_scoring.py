@@ -59,12 +59,26 @@ def test_batched_scores_equal_full_renders(retain):
     con.forward_loss()
     again = con.prune_scores(masks)
     assert torch.equal(again, full)
-    # the masked losses agree with the oracle
+    # the masked losses agree with the oracle, within the parity bound plus the FP32 floor of the log-spectral
+    # term (the change of the oracle's L_a when its mix moves by white noise of relative L2 1e-5): this case has
+    # near-silent stretches whose log magnitudes make that floor large
     for j in (1, len(masks) - 3):
-        ol, _ = case.oracle.losses(case.params, mask=masks[j])
+        ol, mixes = case.oracle.losses(case.params, mask=masks[j])
         for s in range(2):
-            assert abs(float(full[j, s]) - ol[s, 0]) / ol[s, 0] <= LOSS_TOL, (j, s, float(full[j, s]), ol[s, 0])
+            floor = la_floor(case, mixes[s], s, ol[s, 0])
+            err = abs(float(full[j, s]) - ol[s, 0])
+            assert err <= LOSS_TOL * ol[s, 0] + floor, (j, s, float(full[j, s]), ol[s, 0], floor)
     con.close()
+
+
+def la_floor(case, mix, s, la):
+    import torch
+    from oracle import loss as OL
+    m = torch.tensor(mix, dtype=torch.float64)
+    noise = torch.tensor(np.random.default_rng(0).standard_normal(m.shape))
+    noise *= 1e-5 * m.norm() / noise.norm()
+    tgt = torch.tensor(case.targets[s], dtype=torch.float64)
+    return abs(float(OL.audio_loss(m + noise, tgt, case.oracle.desc.loss)["a"]) - la)
 
 
 def test_batched_scores_in_chunks_and_full_fallback():

@@ -4,12 +4,11 @@ The round is replayed twice: (a) through the oracle's round logic with the GPU's
 must give the identical trial sequence and pruned set; (b) trial by trial with the oracle's FP64 L_a at the
 same masks and parameters.  Alg. 3 decides on d = L_a(trial) - L_min < tau, a difference of two losses of
 nearly the same mix, so (b) holds d to the gradient bound (1e-3 relative, plus 1e-6 of L_a for rounding,
-plus the L_a floor below) and requires the same decision wherever |d - tau| exceeds twice that bound.  With no near-tie the oracle's own
-search takes the same decisions in the same order, so its pruned set is the GPU's.  L_a itself is held to
-the mix bound propagated through the loss: 1e-5 (times the channel conditioning) relative, plus the change
-of the oracle's L_a when its mix moves by white noise of relative L2 1e-5 (the log-spectral term of Eq. 21
-is sensitive on near-silent bins, so FP32 rounding of the mix shifts L_a by a nearly constant amount that
-cancels in d)."""
+plus the L_a floor below) and requires the same decision wherever |d - tau| exceeds twice that bound.  With no
+near-tie the oracle's own search takes the same decisions in the same order, so its pruned set is the GPU's.
+L_a itself is held to 1e-5 relative plus the change of the oracle's L_a when its mix moves by white noise of
+relative L2 1e-5 (the log-spectral term of Eq. 21 is sensitive on near-silent bins, so FP32 rounding of the mix
+shifts L_a by a nearly constant amount that cancels in d)."""
 import numpy as np
 import pytest
 import torch
@@ -24,15 +23,6 @@ pytestmark = pytest.mark.gpu
 
 LA_TOL = 1e-5
 D_TOL = 1e-3
-
-
-def conditioning(mix, row):
-    """k_la of the parity tests: the per-set terms scale the mix's relative error by ||(l,r)|| / ||x||."""
-    lr = np.linalg.norm(mix)
-    kap = {"Llr": 1.0, "Lm": lr / max(np.linalg.norm(mix[0] + mix[1]), 1e-30),
-           "Ls": lr / max(np.linalg.norm(mix[0] - mix[1]), 1e-30)}
-    alphas = {"Llr": 0.5, "Lm": 0.25, "Ls": 0.25}
-    return max(1.0, sum(alphas[x] * row[i + 1] * kap[x] for i, x in enumerate(alphas)) / max(row[0], 1e-30))
 
 
 def test_dry_wet_round_matches_oracle():
@@ -73,14 +63,14 @@ def test_dry_wet_round_matches_oracle():
     noise *= 1e-5 * mix.norm() / noise.norm()
     floor = abs(float(OL.audio_loss(mix + noise, tgt, case.oracle.desc.loss)["a"]) - full[0, 0])
     l_min_o, l_min_g = full[0, 0], l_min0
-    assert abs(l_min_g - l_min_o) <= LA_TOL * conditioning(mixes[0], full[0]) * abs(l_min_o) + floor
+    assert abs(l_min_g - l_min_o) <= LA_TOL * abs(l_min_o) + floor
     removed, near_ties = set(), 0
     for t in trials:
         mask = np.ones(P, np.uint8)
         mask[list(removed | set(t.candidates))] = 0
         row, mix_t = case.oracle.losses(params, mask=mask)
         la_o = row[0, 0]
-        assert abs(t.la - la_o) <= LA_TOL * conditioning(mix_t[0], row[0]) * abs(la_o) + floor, (t, la_o, floor)
+        assert abs(t.la - la_o) <= LA_TOL * abs(la_o) + floor, (t, la_o, floor)
         d_g, d_o = t.la - l_min_g, la_o - l_min_o
         tol = D_TOL * abs(d_o) + 1e-6 * abs(la_o) + floor
         assert abs(d_g - d_o) <= tol, (t, d_g, d_o, tol)
