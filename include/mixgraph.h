@@ -263,6 +263,43 @@ mg_status mg_schedule_io(const int32_t* node_step, const int32_t* order, int32_t
                          const int32_t* edge_src, const int32_t* edge_dst, int32_t n_edges, int32_t* step_begin,
                          int32_t* gather_begin, int32_t* gather_src, int32_t* gather_dst);
 
+/* ---- General processing graphs on the GPU (Sec. 2, Sec. 4, Alg. 1) ----
+ * A graph of one song: input nodes (one dry track each, duplicated to both channels), processor nodes of the types
+ * 0..6 = "ecnsgdr" (Sec. 3, each followed by its dry/wet blend), mix nodes and exactly one output node.  Every node's
+ * input is the sum of its predecessors' outputs (Eq. 3); the output node's input is the mix y_hat, scored by the
+ * console's objective (Eqs. 20-23, 26).  The processors are the graph's processor nodes in ascending node index: the
+ * canonical order of the parameters (each processor's parameters, then one dry/wet logit per processor) and of the
+ * masks.  Execution follows the batched schedule of Alg. 1 (mg_schedule_graph): per step one aggregation launch
+ * for the nodes with several predecessors (gather and aggregate) and one launch per kernel over the step's
+ * processors (process and store); the backward pass walks the steps in reverse, summing the input adjoints of
+ * nodes with several successors. */
+enum { MG_NODE_INPUT = 7, MG_NODE_MIX = 8, MG_NODE_OUTPUT = 9 };
+
+typedef struct {
+  int32_t n_nodes;
+  const int32_t* node_type;    /* host [n_nodes]: 0..6 processor types, MG_NODE_INPUT, MG_NODE_MIX, MG_NODE_OUTPUT */
+  const int32_t* input_track;  /* host [n_nodes]: for input nodes the source track in [0, K); ignored otherwise */
+  int32_t n_edges;
+  const int32_t* edge_src;     /* host [n_edges]: edge_src[i] -> edge_dst[i] */
+  const int32_t* edge_dst;
+  int32_t schedule;            /* MG_SCHED_GREEDY or MG_SCHED_BEAM */
+  int32_t beam_width;          /* beam search width (>= 1) */
+} mg_graph_desc;
+
+/* Host-only planning of a graph console (no GPU): sizes as mg_plan; step_type (host [n_nodes] or NULL) receives the
+ * schedule's type sequence and n_steps (or NULL) its length.  MG_ERR_INVALID for a bad graph: node types out of
+ * range, not exactly one output node, an input node with a predecessor or without a valid track, a processor, mix
+ * or output node without a predecessor, an output node with a successor, an edge out of range or a self loop, a
+ * cycle. */
+mg_status mg_graph_plan(const mg_console_desc* desc, const mg_graph_desc* graph, const mg_song_desc* song,
+                        mg_console_info* out, int32_t* step_type, int32_t* n_steps);
+
+/* Console over one song whose structure is `graph` (song->num_subgroups and song->track_group are ignored; the
+ * type_mask of desc is ignored: the processors are the graph's).  Every other entry point applies to it; candidate
+ * scoring (mg_prune_scores) renders every mask in full.  Allocation and synchronisation as mg_console_create. */
+mg_status mg_graph_console_create(const mg_console_desc* desc, const mg_graph_desc* graph, const mg_song_desc* song,
+                                  cudaStream_t stream, mg_console** out);
+
 /* Message of the last failed call: on console c (valid until the next call on c), or, with c = NULL, of the last
  * failed call of this host thread that had no console (creation, planning, scheduling).  Never NULL; the
  * empty string before any failure.  The library owns the string. */

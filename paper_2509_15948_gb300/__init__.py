@@ -46,6 +46,38 @@ class ConsoleDesc(ctypes.Structure):
                 ("autotune", ctypes.c_int32)]
 
 
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("node_type", ctypes.POINTER(ctypes.c_int32)),
+                ("input_track", ctypes.POINTER(ctypes.c_int32)), ("n_edges", ctypes.c_int32),
+                ("edge_src", ctypes.POINTER(ctypes.c_int32)), ("edge_dst", ctypes.POINTER(ctypes.c_int32)),
+                ("schedule", ctypes.c_int32), ("beam_width", ctypes.c_int32)]
+
+
+NODE_INPUT, NODE_MIX, NODE_OUTPUT = 7, 8, 9
+
+
+@dataclasses.dataclass
+class Graph:
+    """A processing graph of one song (Sec. 2): node types (0..6 processor types "ecnsgdr", NODE_INPUT, NODE_MIX,
+    NODE_OUTPUT), the source track of every input node (-1 elsewhere), edges (src, dst), and the schedule of
+    Alg. 1 ("greedy" or "beam")."""
+    node_type: Sequence[int]
+    input_track: Sequence[int]
+    edges: Sequence[tuple]
+    schedule: str = "greedy"
+    beam_width: int = 8
+
+    def desc(self):
+        n, m = len(self.node_type), len(self.edges)
+        keep = [(ctypes.c_int32 * max(1, n))(*[int(t) for t in self.node_type]),
+                (ctypes.c_int32 * max(1, n))(*[int(t) for t in self.input_track]),
+                (ctypes.c_int32 * max(1, m))(*[int(e[0]) for e in self.edges]),
+                (ctypes.c_int32 * max(1, m))(*[int(e[1]) for e in self.edges])]
+        d = GraphDesc(n, keep[0], keep[1], m, keep[2], keep[3], {"greedy": 0, "beam": 1}[self.schedule],
+                      int(self.beam_width))
+        return d, keep
+
+
 class ConsoleInfo(ctypes.Structure):
     _fields_ = [("n_songs", ctypes.c_int32), ("n_processors", ctypes.c_int32), ("n_proc_params", ctypes.c_int64),
                 ("n_params", ctypes.c_int64), ("n_reverbs", ctypes.c_int32), ("total_samples", ctypes.c_int64),
@@ -95,6 +127,10 @@ def load_library(path: str = LIB_PATH):
         "mg_reset_kernel_times": [P],
         "mg_debug_read": [P, I32, I32, P, I64],
         "mg_get_stage_times": [P, P, P, I32],
+        "mg_graph_plan": [ctypes.POINTER(ConsoleDesc), ctypes.POINTER(GraphDesc), ctypes.POINTER(SongDesc),
+                          ctypes.POINTER(ConsoleInfo), P, P],
+        "mg_graph_console_create": [ctypes.POINTER(ConsoleDesc), ctypes.POINTER(GraphDesc), ctypes.POINTER(SongDesc),
+                                    P, ctypes.POINTER(P)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -163,7 +199,8 @@ def _song_array(songs: Sequence[Song], src_ptrs=None, tgt_ptrs=None, on_device=0
     arr = (SongDesc * len(songs))()
     keep = []
     for i, s in enumerate(songs):
-        tg = (ctypes.c_int32 * s.num_tracks)(*[int(g) for g in s.track_group])
+        groups = list(s.track_group) if s.track_group else [-1] * s.num_tracks
+        tg = (ctypes.c_int32 * s.num_tracks)(*[int(g) for g in groups])
         keep.append(tg)
         arr[i].num_tracks = s.num_tracks
         arr[i].num_subgroups = s.num_subgroups
@@ -216,12 +253,30 @@ def plan(songs: Sequence[Song], cfg: ConsoleConfig = ConsoleConfig()) -> dict:
     return {f: getattr(info, f) for f, _ in ConsoleInfo._fields_}
 
 
+def graph_plan(graph: Graph, song: Song, cfg: ConsoleConfig = ConsoleConfig()) -> dict:
+    """Host-only planning of a graph console (no GPU): sizes as plan() and the schedule's type sequence."""
+    lib = load_library()
+    arr, _keep = _song_array([song])
+    gd, _gkeep = graph.desc()
+    info = ConsoleInfo()
+    steps = np.zeros(max(1, len(graph.node_type)), np.int32)
+    n = ctypes.c_int32()
+    st = lib.mg_graph_plan(ctypes.byref(_desc(cfg)), ctypes.byref(gd), arr, ctypes.byref(info), steps.ctypes.data,
+                           ctypes.byref(n))
+    if st != MG_OK:
+        raise MgError(st, lib.mg_last_error(None).decode())
+    out = {f: getattr(info, f) for f, _ in ConsoleInfo._fields_}
+    out["steps"] = steps[:n.value].tolist()
+    return out
+
+
 class Console:
     """A batch of songs on one GPU.  sources: per song float32 [K][L] (numpy or torch); targets: [2][L];
-    reverb_noise: float32 [n_reverbs][2][2 fs] (required when reverbs are enabled)."""
+    reverb_noise: float32 [n_reverbs][2][2 fs] (required when reverbs are enabled).  With graph (a Graph), the
+    console is the general processing graph of one song (songs holds that one Song; its subgroups are ignored)."""
 
     def __init__(self, songs: Sequence[Song], sources, targets, reverb_noise=None, cfg: ConsoleConfig = ConsoleConfig(),
-                 device: Optional[int] = None, stream=None):
+                 device: Optional[int] = None, stream=None, graph: Optional[Graph] = None):
         import torch
         self.torch = torch
         if not torch.cuda.is_available():
@@ -251,8 +306,14 @@ class Console:
         # being captured by another console on another thread is not disturbed
         torch.cuda.current_stream(dev).synchronize()
         h = ctypes.c_void_p()
-        st = self.lib.mg_console_create(ctypes.byref(_desc(cfg, noise_ptr, 1)), arr, len(self.songs),
-                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if graph is not None:
+            assert len(self.songs) == 1, "a graph console holds one song"
+            gd, self._graph_keep = graph.desc()
+            st = self.lib.mg_graph_console_create(ctypes.byref(_desc(cfg, noise_ptr, 1)), ctypes.byref(gd), arr,
+                                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        else:
+            st = self.lib.mg_console_create(ctypes.byref(_desc(cfg, noise_ptr, 1)), arr, len(self.songs),
+                                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         if st != MG_OK:
             raise MgError(st, self.lib.mg_last_error(None).decode())
         self.h = h

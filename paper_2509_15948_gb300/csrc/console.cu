@@ -102,6 +102,15 @@ struct LtiGroup {
   ItemList col, rowpair, firtaps, dlyadj, revfir;
 };
 
+// A node of a general processing graph (Sec. 2): input, processor, mix or output, its edges, and the arena
+// buffers its wiring needs: the sum of its inputs (more than one predecessor), the sum of its successors'
+// input adjoints (more than one successor), and a processor's own input adjoint.
+struct GNode {
+  int type = 0, track = -1, proc = -1, step = 0;
+  std::vector<int> preds, succs;
+  size_t o_agg = 0, o_dsum = 0, o_du = 0;
+};
+
 struct Stage {
   int level, type;
   ProcList procs;
@@ -148,6 +157,17 @@ struct mg_console {
   size_t score_budget = 0;
   std::vector<char> score_blob;
   std::vector<uint8_t> score_m0;
+  // general processing graph (Sec. 2, Sec. 4): nodes, the batched schedule (Alg. 1) as steps of one type each,
+  // per step the aggregation sums of the forward and the adjoint sums of the backward, one source buffer per
+  // track, and a zero buffer (the adjoint of an output nothing reads)
+  bool is_graph = false;
+  std::vector<GNode> gn;
+  std::vector<int> gstep_type;
+  std::vector<std::vector<int>> gstep_nodes;
+  std::vector<int> gstep_stage;
+  std::vector<ItemList> gstep_fsum, gstep_bsum;
+  std::vector<size_t> o_src;
+  size_t o_zero = 0;
   int score_mode = 0;              // 0: batched candidate scoring, 1: one full masked render per candidate
   bool debug_sync = false;         // MG_DEBUG_SYNC=1 in the environment: synchronise and check after every launch
   bool debug_reported = false;
@@ -243,7 +263,7 @@ void apply_split(HostProc& p, int logN1) {
   p.nbrows = p.nfrows;
 }
 
-mg_status validate(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
+mg_status validate(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n, bool graph = false) {
   if (!d || !s || n <= 0) return fail(c, MG_ERR_INVALID, "null descriptor or no songs");
   if (!(d->sample_rate > 1000.0 && d->sample_rate < 1e6)) return fail(c, MG_ERR_INVALID, "sample_rate out of range");
   if (d->type_mask & ~0x7Fu) return fail(c, MG_ERR_INVALID, "type_mask has bits beyond the 7 processor types");
@@ -265,12 +285,173 @@ mg_status validate(mg_console* c, const mg_console_desc* d, const mg_song_desc* 
     if (s[i].num_tracks < 1 || s[i].num_subgroups < 0) return fail(c, MG_ERR_INVALID, "song needs >= 1 track");
     if (s[i].num_samples < 1 || s[i].num_samples > (1 << 22) - 200000)
       return fail(c, MG_ERR_UNSUPPORTED, "num_samples must be in [1, 3994304]");
+    if (graph) continue;   // a graph's structure comes from its nodes and edges
     if (!s[i].track_group) return fail(c, MG_ERR_INVALID, "track_group is null");
     for (int k = 0; k < s[i].num_tracks; ++k)
       if (s[i].track_group[k] < -1 || s[i].track_group[k] >= s[i].num_subgroups)
         return fail(c, MG_ERR_INVALID, "track_group entry out of range");
   }
   return MG_OK;
+}
+
+// Work decomposition of one processor of L samples (p.type, p.L set): FIR span and FFT size of the LTI types
+// (N = f 2^logN >= L + taps, the smaller of 2^k and 3 2^k'; rows N1 = f 2^logN1, columns N2 = 2^logN2; the
+// autotuner's candidate splits), overlap-save blocks of the equalizer, scan chunks of the dynamics, tiles of
+// the elementwise types.
+void size_proc(HostProc& p, double fs) {
+  const int t = p.type;
+  const int D = (int)std::llround(0.1 * fs);
+  const int revlen = (int)std::llround(2.0 * fs);
+  if (t == T_E || t == T_R || t == T_D) {
+    if (t == T_E) { p.n0 = -kEqHalf; p.Nh = kEqTaps; }
+    if (t == T_D) { p.n0 = -kDlyHalf; p.Nh = kDlyTaps * D + kDlyFir - 1; }
+    if (t == T_R) { p.n0 = 0; p.Nh = revlen; p.nframes = (revlen - kRevFft) / kRevHop + 1; }
+    // N = f 2^logN >= L + taps: the smaller of 2^k and 3 2^k'; rows N1 = f 2^logN1, columns N2 = 2^logN2
+    const int64_t need = (int64_t)p.L + p.Nh + std::abs(p.n0) + 1;
+    const int k2 = std::max(12, ilog2_ceil(need));
+    const int k3 = std::max(11, ilog2_ceil((need + 2) / 3));
+    if (t != T_E && ((int64_t)3 << k3) < ((int64_t)1 << k2)) {
+      p.f = 3;
+      p.logN = k3;
+      p.logN2 = std::min(10, (k3 + 1) / 2);
+      p.logN1 = k3 - p.logN2;
+    } else {
+      p.f = 1;
+      p.logN = k2;
+      p.logN1 = (k2 + 1) / 2;
+      p.logN2 = k2 / 2;
+    }
+    p.colG = std::min(8, std::min(8192 >> p.logN2, 1 << p.logN1));
+    if (t == T_E) {   // single-pass overlap-save in shared memory (no global FFT scratch)
+      p.nfrows = (p.L + kEqOsFwdBlock - 1) / kEqOsFwdBlock;
+      p.nbrows = (p.nfrows + kEqChunk - 1) / kEqChunk;   // backward items: chunks of forward blocks
+    } else {
+      p.nfrows = (p.f << p.logN1) / p.colG;
+      p.nbrows = p.nfrows;
+      p.scratch_bytes = (size_t)3 * ((size_t)p.f << p.logN) * sizeof(float2);
+      // autotuner candidates: the default split and its neighbours; partial sums sized for all of them
+      p.splits.clear();
+      p.nfcap = p.nfrows;
+      for (int dl = -2; dl <= 2; ++dl) {
+        const int l1 = p.logN1 + dl;
+        if (!split_ok(p.f, p.logN, l1)) continue;
+        HostProc q = p;
+        apply_split(q, l1);
+        p.splits.push_back(l1);
+        p.nfcap = std::max(p.nfcap, q.nfrows);
+      }
+    }
+  } else if (t == T_C || t == T_N) {
+    p.nchunks = (p.L + kDynChunk - 1) / kDynChunk;
+    p.nbrows = p.nchunks;
+  } else {
+    p.nbrows = (p.L + kElemTile - 1) / kElemTile;
+  }
+}
+
+// Graph planning (host): one song, its processors in node order (the canonical order of the parameters), each
+// sized like a console processor, and the batched schedule of Alg. 1 (greedy or beam, schedule.cu) as steps.
+mg_status plan_graph(mg_console* c, const mg_console_desc* d, const mg_graph_desc* g, const mg_song_desc* s) {
+  c->is_graph = true;
+  c->desc = *d;
+  c->nres = d->n_resolutions;
+  const double fs = d->sample_rate;
+  c->songs.clear();
+  c->procs.clear();
+  c->chains.clear();
+  c->nrev = 0;
+  HostSong hs;
+  hs.K = s->num_tracks;
+  hs.S = 0;
+  hs.L = (int)s->num_samples;
+  hs.ld = (int)round_up(hs.L, 64);
+  hs.group.assign(hs.K, -1);
+  hs.pbeg = 0;
+  hs.track_seconds = (double)hs.K * hs.L / fs;
+  c->track_seconds = hs.track_seconds;
+  c->total_samples = hs.L;
+  const int n = g->n_nodes;
+  c->gn.assign(n, GNode{});
+  for (int v = 0; v < n; ++v) {
+    c->gn[v].type = g->node_type[v];
+    c->gn[v].track = g->node_type[v] == MG_NODE_INPUT ? g->input_track[v] : -1;
+  }
+  for (int e = 0; e < g->n_edges; ++e) {
+    c->gn[g->edge_src[e]].succs.push_back(g->edge_dst[e]);
+    c->gn[g->edge_dst[e]].preds.push_back(g->edge_src[e]);
+  }
+  std::vector<int> step_type(std::max(1, n)), node_step(std::max(1, n)), order(std::max(1, n));
+  int nsteps = 0;
+  if (mg_schedule_graph(g->node_type, n, g->edge_src, g->edge_dst, g->n_edges, g->schedule, g->beam_width,
+                        step_type.data(), &nsteps, node_step.data(), order.data()) != MG_OK)
+    return fail(c, MG_ERR_INVALID, "graph has a cycle or invalid edges");
+  c->gstep_type.assign(step_type.begin(), step_type.begin() + nsteps);
+  c->gstep_nodes.assign(nsteps, {});
+  for (int v = 0; v < n; ++v) {
+    c->gn[v].step = node_step[v];
+    c->gstep_nodes[node_step[v]].push_back(v);
+  }
+  int64_t poff = 0;
+  for (int v = 0; v < n; ++v) {
+    const int t = c->gn[v].type;
+    if (t >= NTYPES) continue;
+    HostProc p;
+    p.type = t;
+    p.song = 0;
+    p.chain = -1;
+    p.level = c->gn[v].step;
+    p.qidx = (int)c->procs.size();
+    p.rev = t == T_R ? c->nrev++ : -1;
+    p.poff = poff;
+    poff += kParamCount[t];
+    p.L = hs.L;
+    p.ld = hs.ld;
+    size_proc(p, fs);
+    c->gn[v].proc = (int)c->procs.size();
+    c->procs.push_back(p);
+  }
+  hs.pend = (int)c->procs.size();
+  c->songs.push_back(hs);
+  c->P = (int)c->procs.size();
+  c->npp = poff;
+  c->nparams = poff + c->P;
+  return MG_OK;
+}
+
+// Checks of a graph description: node types, one output, edges in range and without self loops, inputs without
+// predecessors and with a valid track, every processor, mix and the output with at least one predecessor, the
+// output without successors.  Cycles are found by the scheduler.
+mg_status validate_graph(mg_console* c, const mg_console_desc* d, const mg_graph_desc* g, const mg_song_desc* s) {
+  if (!d || !g || !s) return fail(c, MG_ERR_INVALID, "null descriptor");
+  if (g->n_nodes < 2 || !g->node_type || (g->n_edges > 0 && (!g->edge_src || !g->edge_dst)) || g->n_edges < 0)
+    return fail(c, MG_ERR_INVALID, "graph needs nodes and edges");
+  if (s->num_tracks < 1 || s->num_samples < 1 || s->num_samples > (1 << 22) - 200000)
+    return fail(c, MG_ERR_INVALID, "song needs >= 1 track and 1..3994304 samples");
+  std::vector<int> np(g->n_nodes, 0), ns(g->n_nodes, 0);
+  int outputs = 0;
+  for (int e = 0; e < g->n_edges; ++e) {
+    const int a = g->edge_src[e], b = g->edge_dst[e];
+    if (a < 0 || b < 0 || a >= g->n_nodes || b >= g->n_nodes || a == b) return fail(c, MG_ERR_INVALID, "edge out of range");
+    ++ns[a];
+    ++np[b];
+  }
+  for (int v = 0; v < g->n_nodes; ++v) {
+    const int t = g->node_type[v];
+    if (t < 0 || t > MG_NODE_OUTPUT) return fail(c, MG_ERR_INVALID, "node type out of range");
+    if (t == MG_NODE_INPUT) {
+      if (!g->input_track || g->input_track[v] < 0 || g->input_track[v] >= s->num_tracks)
+        return fail(c, MG_ERR_INVALID, "input node without a valid track");
+      if (np[v]) return fail(c, MG_ERR_INVALID, "input node with a predecessor");
+    } else if (np[v] == 0) {
+      return fail(c, MG_ERR_INVALID, "processor, mix or output node without a predecessor");
+    }
+    if (t == MG_NODE_OUTPUT) {
+      ++outputs;
+      if (ns[v]) return fail(c, MG_ERR_INVALID, "output node with a successor");
+    }
+  }
+  if (outputs != 1) return fail(c, MG_ERR_INVALID, "a graph needs exactly one output node");
+  return validate(c, d, s, 1, true);
 }
 
 void plan(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
@@ -319,51 +500,7 @@ void plan(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n)
         poff += kParamCount[t];
         p.L = hs.L;
         p.ld = hs.ld;
-        if (t == T_E || t == T_R || t == T_D) {
-          if (t == T_E) { p.n0 = -kEqHalf; p.Nh = kEqTaps; }
-          if (t == T_D) { p.n0 = -kDlyHalf; p.Nh = kDlyTaps * D + kDlyFir - 1; }
-          if (t == T_R) { p.n0 = 0; p.Nh = revlen; p.nframes = (revlen - kRevFft) / kRevHop + 1; }
-          // N = f 2^logN >= L + taps: the smaller of 2^k and 3 2^k'; rows N1 = f 2^logN1, columns N2 = 2^logN2
-          const int64_t need = (int64_t)p.L + p.Nh + std::abs(p.n0) + 1;
-          const int k2 = std::max(12, ilog2_ceil(need));
-          const int k3 = std::max(11, ilog2_ceil((need + 2) / 3));
-          if (t != T_E && ((int64_t)3 << k3) < ((int64_t)1 << k2)) {
-            p.f = 3;
-            p.logN = k3;
-            p.logN2 = std::min(10, (k3 + 1) / 2);
-            p.logN1 = k3 - p.logN2;
-          } else {
-            p.f = 1;
-            p.logN = k2;
-            p.logN1 = (k2 + 1) / 2;
-            p.logN2 = k2 / 2;
-          }
-          p.colG = std::min(8, std::min(8192 >> p.logN2, 1 << p.logN1));
-          if (t == T_E) {   // single-pass overlap-save in shared memory (no global FFT scratch)
-            p.nfrows = (p.L + kEqOsFwdBlock - 1) / kEqOsFwdBlock;
-            p.nbrows = (p.nfrows + kEqChunk - 1) / kEqChunk;   // backward items: chunks of forward blocks
-          } else {
-            p.nfrows = (p.f << p.logN1) / p.colG;
-            p.nbrows = p.nfrows;
-            p.scratch_bytes = (size_t)3 * ((size_t)p.f << p.logN) * sizeof(float2);
-            // autotuner candidates: the default split and its neighbours; partial sums sized for all of them
-            p.splits.clear();
-            p.nfcap = p.nfrows;
-            for (int dl = -2; dl <= 2; ++dl) {
-              const int l1 = p.logN1 + dl;
-              if (!split_ok(p.f, p.logN, l1)) continue;
-              HostProc q = p;
-              apply_split(q, l1);
-              p.splits.push_back(l1);
-              p.nfcap = std::max(p.nfcap, q.nfrows);
-            }
-          }
-        } else if (t == T_C || t == T_N) {
-          p.nchunks = (p.L + kDynChunk - 1) / kDynChunk;
-          p.nbrows = p.nchunks;
-        } else {
-          p.nbrows = (p.L + kElemTile - 1) / kElemTile;
-        }
+        size_proc(p, fs);
         hc.procs.push_back((int)c->procs.size());
         c->procs.push_back(p);
       }
@@ -588,7 +725,28 @@ void stage_backward(mg_console* c, const LaunchCtx& x, Stage& s) {
   }
 }
 
+void run_sums(mg_console* c, const ItemList& items) {
+  run_items(c, F_SUM, items, [&](const Item* it, int n) {
+    launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n);
+  });
+}
+
+// Forward of a graph: per schedule step the aggregation sums, then the step's processors (Alg. 1).
+void render_graph(mg_console* c, const LaunchCtx& x) {
+  for (size_t k = 0; k < c->gstep_type.size(); ++k) {
+    {
+      StageScope scope(c, 8);
+      run_sums(c, c->gstep_fsum[k]);
+    }
+    if (c->gstep_stage[k] >= 0) stage_forward(c, x, c->stages[c->gstep_stage[k]]);
+  }
+}
+
 void render(mg_console* c, const LaunchCtx& x) {
+  if (c->is_graph) {
+    render_graph(c, x);
+    return;
+  }
   for (int level = 0; level < 2; ++level) {
     if (level == 1 && !c->sum_m_items.h.empty()) {
       StageScope scope(c, 8);
@@ -633,9 +791,20 @@ void backward_pass(mg_console* c, const LaunchCtx& x) {
               [&](const Item* it, int n) { launch_loss_gather(x, c->d_songs, c->d_res, c->nres, it, n); });
   }
   run(c, F_MISC, [&] { cudaMemsetAsync(c->d_grads, 0, sizeof(float) * c->nparams, c->stream); });
-  for (int level = 1; level >= 0; --level)
-    for (int i = (int)c->stages.size() - 1; i >= 0; --i)
-      if (c->stages[i].level == level) stage_backward(c, x, c->stages[i]);
+  if (c->is_graph) {
+    // per schedule step in reverse: the adjoint sums, then the step's processors
+    for (int k = (int)c->gstep_type.size() - 1; k >= 0; --k) {
+      {
+        StageScope scope(c, 8);
+        run_sums(c, c->gstep_bsum[k]);
+      }
+      if (c->gstep_stage[k] >= 0) stage_backward(c, x, c->stages[c->gstep_stage[k]]);
+    }
+  } else {
+    for (int level = 1; level >= 0; --level)
+      for (int i = (int)c->stages.size() - 1; i >= 0; --i)
+        if (c->stages[i].level == level) stage_backward(c, x, c->stages[i]);
+  }
   run_procs(c, F_FINALIZE, c->all_present, [&](const int* p, int n) { launch_node_stats(x, p, n, 0); });
   run_procs(c, F_FINALIZE, c->all_present,
             [&](const int* p, int n) { launch_grad_finalize2(x, p, n, c->d_grads + c->npp); });
@@ -668,8 +837,141 @@ mg_status upload(mg_console* c, std::vector<T>& h, T** d) {
 mg_status upload_items(mg_console* c, ItemList& L) { return upload(c, L.h, &L.d); }
 mg_status upload_procs(mg_console* c, ProcList& L) { return upload(c, L.h, &L.d); }
 
+mg_status build_graph_tables(mg_console* c);
+
+// Node-table entry of processor pi: everything but its wiring (u, y, dy, du, present), from the arena layout.
+void fill_procdev(mg_console* c, int pi) {
+  auto A = [&](size_t off) { return c->arena + off; };
+  HostProc& p = c->procs[pi];
+  ProcDev& d = c->hpd[pi];
+  d.type = p.type;
+  d.song = p.song;
+  d.qidx = p.qidx;
+  d.rev = p.rev;
+  d.L = p.L;
+  d.ld = p.ld;
+  d.p = c->d_params + p.poff;
+  d.gp = c->d_grads + p.poff;
+  d.stats = (float*)A(p.o_stats);
+  d.fpart = p.nfrows ? (float*)A(p.o_fpart) : nullptr;
+  d.bpart = p.nbrows ? (float*)A(p.o_bpart) : nullptr;
+  d.nfpart = p.nfrows;
+  d.nbpart = p.nbrows;
+  d.logN = p.logN;
+  d.logN1 = p.logN1;
+  d.logN2 = p.logN2;
+  d.f = p.f;
+  for (int r = 0; r < 3; ++r) {   // exp(-2 pi i r / N), N = 3 2^logN (used when f = 3)
+    const double ang = -2.0 * 3.14159265358979323846 * r / (3.0 * std::ldexp(1.0, p.logN));
+    d.c3n[r] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  d.colG = p.colG;
+  d.n0 = p.n0;
+  d.Nh = p.Nh;
+  if (p.scratch_bytes) {
+    const size_t N = (size_t)p.f << p.logN;
+    d.T1 = (float2*)(c->scratch + p.o_scratch);
+    d.T2 = d.T1 + N;
+    d.Hz = d.T2 + N;
+  }
+  if (p.type == T_E || p.type == T_R || p.type == T_D) {
+    d.taps = (float*)A(p.o_taps);
+    d.dtaps = (float*)A(p.o_dtaps);
+  }
+  if (p.type == T_E) {
+    d.hspec = (float*)A(p.o_hspec);
+    d.ybar = (float*)A(p.o_ybar);
+    d.dhspec = (float2*)A(p.o_dhspec);
+    d.eqg = (float2*)A(p.o_eqg);
+  }
+  d.aux = p.o_aux ? (float*)A(p.o_aux) : nullptr;
+  d.carry = p.nchunks ? (float*)A(p.o_carry) : nullptr;
+  d.rcarry = p.nchunks ? (float*)A(p.o_rcarry) : nullptr;
+  d.chunkagg = p.nchunks ? (float*)A(p.o_cagg) : nullptr;
+  d.nchunks = p.nchunks;
+  d.nspec = p.type == T_R ? (const float2*)A(p.o_nspec) : nullptr;
+  d.nframes = p.nframes;
+}
+
+// Work lists of one stage (st.level, st.type, st.procs.h set): tiles or scan chunks, overlap-save blocks, or LTI
+// groups with their FFT scratch offsets (groups under the workspace limit when the spectra are not kept).
+mg_status make_stage(mg_console* c, Stage& st) {
+  const int t = st.type;
+  const int64_t limit = c->desc.workspace_limit_bytes > 0 ? c->desc.workspace_limit_bytes : INT64_MAX;
+  if (t == T_G || t == T_S || t == T_C || t == T_N) {
+    for (int pi : st.procs.h) {
+      st.elem.beg.push_back((int)st.elem.h.size());
+      const int nt = (t == T_C || t == T_N) ? c->procs[pi].nchunks : c->procs[pi].nbrows;
+      for (int i = 0; i < nt; ++i) st.elem.h.push_back(Item{pi, i});
+    }
+    st.elem.beg.push_back((int)st.elem.h.size());
+    if (upload_items(c, st.elem) || upload_procs(c, st.procs)) return MG_ERR_CUDA;
+  } else if (t == T_E) {
+    // equalizer: overlap-save blocks (forward and backward blockings differ)
+    for (int pi : st.procs.h) {
+      st.osf.beg.push_back((int)st.osf.h.size());
+      st.osb.beg.push_back((int)st.osb.h.size());
+      for (int i = 0; i < c->procs[pi].nfrows; ++i) st.osf.h.push_back(Item{pi, i});
+      for (int i = 0; i < c->procs[pi].nbrows; ++i) st.osb.h.push_back(Item{pi, i});
+    }
+    st.osf.beg.push_back((int)st.osf.h.size());
+    st.osb.beg.push_back((int)st.osb.h.size());
+    if (upload_items(c, st.osf) || upload_items(c, st.osb) || upload_procs(c, st.procs)) return MG_ERR_CUDA;
+  } else {
+    // LTI: groups under the workspace limit, each with its own scratch offsets
+    size_t used = 0;
+    LtiGroup g;
+    auto close = [&]() -> mg_status {
+      if (g.procs.h.empty()) return MG_OK;
+      for (ItemList* L : {&g.col, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
+        L->beg.push_back((int)L->h.size());
+      if (upload_procs(c, g.procs) || upload_items(c, g.col) ||
+          upload_items(c, g.rowpair) || upload_items(c, g.firtaps) || upload_items(c, g.dlyadj) ||
+          upload_items(c, g.revfir))
+        return MG_ERR_CUDA;
+      st.groups.push_back(g);
+      g = LtiGroup{};
+      used = 0;
+      return MG_OK;
+    };
+    for (int pi : st.procs.h) {
+      HostProc& p = c->procs[pi];
+      if (!c->retain) {   // retained spectra: the offsets fixed at creation, one group per stage
+        if (used > 0 && (int64_t)(used + p.scratch_bytes) > limit)
+          if (close() != MG_OK) return MG_ERR_CUDA;
+        p.o_scratch = used;
+        used += p.scratch_bytes;
+      }
+      ProcDev& d = c->hpd[pi];
+      const size_t N = (size_t)p.f << p.logN;
+      d.T1 = (float2*)(c->scratch + p.o_scratch);
+      d.T2 = d.T1 + N;
+      d.Hz = d.T2 + N;
+      g.procs.h.push_back(pi);
+      const int N1 = p.f << p.logN1, N2 = 1 << p.logN2;
+      for (ItemList* L : {&g.col, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
+        L->beg.push_back((int)L->h.size());
+      for (int i = 0; i < N1 / p.colG; ++i) g.col.h.push_back(Item{pi, i});
+      g.col.maxv = std::max(g.col.maxv, N2 * p.colG);
+      for (int i = 0; i <= N2 / 2; ++i) g.rowpair.h.push_back(Item{pi, i});
+      g.rowpair.maxv = std::max(g.rowpair.maxv, N1);
+      if (t == T_D) {
+        for (int i = 0; i < (p.Nh + 255) / 256; ++i) g.firtaps.h.push_back(Item{pi, i});
+        for (int i = 0; i < 2 * kDlyTaps; ++i) g.dlyadj.h.push_back(Item{pi, i});
+      }
+      if (t == T_R) {
+        const int ng = (p.nframes + kRevFG - 1) / kRevFG;
+        for (int i = 0; i < ng; ++i) g.revfir.h.push_back(Item{pi, i});
+      }
+    }
+    if (close() != MG_OK) return MG_ERR_CUDA;
+  }
+  return MG_OK;
+}
+
 // Pointers of the node table for the current structure (present processors), stage lists and launch lists.
 mg_status build_tables(mg_console* c) {
+  if (c->is_graph) return build_graph_tables(c);
   auto A = [&](size_t off) { return c->arena + off; };
   c->hpd.assign(c->P, ProcDev{});
   // forward / backward wiring per chain
@@ -714,57 +1016,7 @@ mg_status build_tables(mg_console* c) {
       chain_din[ci] = cur;
     }
   }
-  for (int pi = 0; pi < c->P; ++pi) {
-    HostProc& p = c->procs[pi];
-    ProcDev& d = c->hpd[pi];
-    d.type = p.type;
-    d.song = p.song;
-    d.qidx = p.qidx;
-    d.rev = p.rev;
-    d.L = p.L;
-    d.ld = p.ld;
-    d.p = c->d_params + p.poff;
-    d.gp = c->d_grads + p.poff;
-    d.stats = (float*)A(p.o_stats);
-    d.fpart = p.nfrows ? (float*)A(p.o_fpart) : nullptr;
-    d.bpart = p.nbrows ? (float*)A(p.o_bpart) : nullptr;
-    d.nfpart = p.nfrows;
-    d.nbpart = p.nbrows;
-    d.logN = p.logN;
-    d.logN1 = p.logN1;
-    d.logN2 = p.logN2;
-    d.f = p.f;
-    for (int r = 0; r < 3; ++r) {   // exp(-2 pi i r / N), N = 3 2^logN (used when f = 3)
-      const double ang = -2.0 * 3.14159265358979323846 * r / (3.0 * std::ldexp(1.0, p.logN));
-      d.c3n[r] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-    }
-    d.colG = p.colG;
-    d.n0 = p.n0;
-    d.Nh = p.Nh;
-    if (p.scratch_bytes) {
-      const size_t N = (size_t)p.f << p.logN;
-      d.T1 = (float2*)(c->scratch + p.o_scratch);
-      d.T2 = d.T1 + N;
-      d.Hz = d.T2 + N;
-    }
-    if (p.type == T_E || p.type == T_R || p.type == T_D) {
-      d.taps = (float*)A(p.o_taps);
-      d.dtaps = (float*)A(p.o_dtaps);
-    }
-    if (p.type == T_E) {
-      d.hspec = (float*)A(p.o_hspec);
-      d.ybar = (float*)A(p.o_ybar);
-      d.dhspec = (float2*)A(p.o_dhspec);
-      d.eqg = (float2*)A(p.o_eqg);
-    }
-    d.aux = p.o_aux ? (float*)A(p.o_aux) : nullptr;
-    d.carry = p.nchunks ? (float*)A(p.o_carry) : nullptr;
-    d.rcarry = p.nchunks ? (float*)A(p.o_rcarry) : nullptr;
-    d.chunkagg = p.nchunks ? (float*)A(p.o_cagg) : nullptr;
-    d.nchunks = p.nchunks;
-    d.nspec = p.type == T_R ? (const float2*)A(p.o_nspec) : nullptr;
-    d.nframes = p.nframes;
-  }
+  for (int pi = 0; pi < c->P; ++pi) fill_procdev(c, pi);
   if (upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
 
   // sums: m per subgroup (level 1 inputs), o per song
@@ -821,77 +1073,135 @@ mg_status build_tables(mg_console* c) {
         if (t == T_E || t == T_R || t == T_D) c->all_lti_present.h.push_back(pi);
       }
       if (st.procs.h.empty()) continue;
-      if (t == T_G || t == T_S || t == T_C || t == T_N) {
-        for (int pi : st.procs.h) {
-          st.elem.beg.push_back((int)st.elem.h.size());
-          const int nt = (t == T_C || t == T_N) ? c->procs[pi].nchunks : c->procs[pi].nbrows;
-          for (int i = 0; i < nt; ++i) st.elem.h.push_back(Item{pi, i});
-        }
-        st.elem.beg.push_back((int)st.elem.h.size());
-        if (upload_items(c, st.elem) || upload_procs(c, st.procs)) return MG_ERR_CUDA;
-      } else if (t == T_E) {
-        // equalizer: overlap-save blocks (forward and backward blockings differ)
-        for (int pi : st.procs.h) {
-          st.osf.beg.push_back((int)st.osf.h.size());
-          st.osb.beg.push_back((int)st.osb.h.size());
-          for (int i = 0; i < c->procs[pi].nfrows; ++i) st.osf.h.push_back(Item{pi, i});
-          for (int i = 0; i < c->procs[pi].nbrows; ++i) st.osb.h.push_back(Item{pi, i});
-        }
-        st.osf.beg.push_back((int)st.osf.h.size());
-        st.osb.beg.push_back((int)st.osb.h.size());
-        if (upload_items(c, st.osf) || upload_items(c, st.osb) || upload_procs(c, st.procs)) return MG_ERR_CUDA;
-      } else {
-        // LTI: groups under the workspace limit, each with its own scratch offsets
-        size_t used = 0;
-        LtiGroup g;
-        auto close = [&]() -> mg_status {
-          if (g.procs.h.empty()) return MG_OK;
-          for (ItemList* L : {&g.col, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
-            L->beg.push_back((int)L->h.size());
-          if (upload_procs(c, g.procs) || upload_items(c, g.col) ||
-              upload_items(c, g.rowpair) || upload_items(c, g.firtaps) || upload_items(c, g.dlyadj) ||
-              upload_items(c, g.revfir))
-            return MG_ERR_CUDA;
-          st.groups.push_back(g);
-          g = LtiGroup{};
-          used = 0;
-          return MG_OK;
-        };
-        for (int pi : st.procs.h) {
-          HostProc& p = c->procs[pi];
-          if (!c->retain) {   // retained spectra: the offsets fixed at creation, one group per stage
-            if (used > 0 && (int64_t)(used + p.scratch_bytes) > limit)
-              if (close() != MG_OK) return MG_ERR_CUDA;
-            p.o_scratch = used;
-            used += p.scratch_bytes;
-          }
-          ProcDev& d = c->hpd[pi];
-          const size_t N = (size_t)p.f << p.logN;
-          d.T1 = (float2*)(c->scratch + p.o_scratch);
-          d.T2 = d.T1 + N;
-          d.Hz = d.T2 + N;
-          g.procs.h.push_back(pi);
-          const int N1 = p.f << p.logN1, N2 = 1 << p.logN2;
-          for (ItemList* L : {&g.col, &g.rowpair, &g.firtaps, &g.dlyadj, &g.revfir})
-            L->beg.push_back((int)L->h.size());
-          for (int i = 0; i < N1 / p.colG; ++i) g.col.h.push_back(Item{pi, i});
-          g.col.maxv = std::max(g.col.maxv, N2 * p.colG);
-          for (int i = 0; i <= N2 / 2; ++i) g.rowpair.h.push_back(Item{pi, i});
-          g.rowpair.maxv = std::max(g.rowpair.maxv, N1);
-          if (t == T_D) {
-            for (int i = 0; i < (p.Nh + 255) / 256; ++i) g.firtaps.h.push_back(Item{pi, i});
-            for (int i = 0; i < 2 * kDlyTaps; ++i) g.dlyadj.h.push_back(Item{pi, i});
-          }
-          if (t == T_R) {
-            const int ng = (p.nframes + kRevFG - 1) / kRevFG;
-            for (int i = 0; i < ng; ++i) g.revfir.h.push_back(Item{pi, i});
-          }
-        }
-        if (close() != MG_OK) return MG_ERR_CUDA;
-      }
+      if (make_stage(c, st) != MG_OK) return MG_ERR_CUDA;
       c->stages.push_back(st);
     }
   // scratch pointers changed with grouping: re-upload the node table
+  if (upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
+  if (upload_procs(c, c->all_present) || upload_procs(c, c->all_lti_present)) return MG_ERR_CUDA;
+  return MG_OK;
+}
+
+// Graph wiring (Alg. 1: gather, aggregate, process, store).  A node's input is its one predecessor's output in
+// place, or the sum of its predecessors' outputs (an aggregation sum in the node's step); an input node's output
+// is its track's source, a mix node's its input, a processor's its own buffer (its input when removed by
+// pruning), and the output node's sum is the song's mix.  In the backward pass the adjoint of a node's output is
+// its one successor's input adjoint in place, or the sum of its successors' input adjoints (an adjoint sum in
+// the node's step), or zero when nothing reads it; a processor writes its own input adjoint, a mix node passes
+// its output adjoint through, the output node's input adjoint is the mix adjoint.  Sums read their inputs in
+// edge order.  Stages are the schedule's processor steps.
+mg_status build_graph_tables(mg_console* c) {
+  auto A = [&](size_t off) { return c->arena + off; };
+  const HostSong& hs = c->songs[0];
+  const int n = (int)c->gn.size();
+  c->hpd.assign(c->P, ProcDev{});
+  for (int pi = 0; pi < c->P; ++pi) fill_procdev(c, pi);
+  c->sum_out.h.clear(); c->sum_in.h.clear(); c->sum_beg.h.clear(); c->sum_L.h.clear(); c->sum_ld.h.clear();
+  const int nsteps = (int)c->gstep_type.size();
+  c->gstep_fsum.assign(nsteps, ItemList{});
+  c->gstep_bsum.assign(nsteps, ItemList{});
+  c->gstep_stage.assign(nsteps, -1);
+  int sid = 0;
+  auto add_sum = [&](size_t out, const std::vector<size_t>& ins, ItemList& items) {
+    c->sum_beg.h.push_back((int)c->sum_in.h.size());
+    c->sum_out.h.push_back((float*)A(out));
+    for (size_t o : ins) c->sum_in.h.push_back((const float*)A(o));
+    c->sum_L.h.push_back(hs.L);
+    c->sum_ld.h.push_back(hs.ld);
+    items.beg.push_back((int)items.h.size());
+    for (int t = 0; t < (hs.L + kElemTile - 1) / kElemTile; ++t) items.h.push_back(Item{sid, t});
+    ++sid;
+  };
+  // forward: outputs in schedule order
+  std::vector<size_t> out(n, 0), in(n, 0);
+  for (int k = 0; k < nsteps; ++k)
+    for (int v : c->gstep_nodes[k]) {
+      GNode& g = c->gn[v];
+      if (g.type == MG_NODE_INPUT) {
+        out[v] = c->o_src[g.track];
+        continue;
+      }
+      std::vector<size_t> ins;
+      for (int u : g.preds) ins.push_back(out[u]);
+      if (g.type == MG_NODE_OUTPUT) {
+        add_sum(hs.o_mix, ins, c->gstep_fsum[k]);
+        continue;
+      }
+      in[v] = g.preds.size() == 1 ? out[g.preds[0]] : g.o_agg;
+      if (g.preds.size() > 1) add_sum(g.o_agg, ins, c->gstep_fsum[k]);
+      if (g.type == MG_NODE_MIX) {
+        out[v] = in[v];
+        continue;
+      }
+      HostProc& p = c->procs[g.proc];
+      ProcDev& d = c->hpd[g.proc];
+      d.present = p.present;
+      out[v] = p.present ? p.o_y : in[v];
+      d.u = (const float*)A(in[v]);
+      d.y = (float*)A(p.o_y);
+    }
+  // backward: input adjoints in reverse schedule order
+  std::vector<size_t> din(n, 0), dout(n, 0);
+  for (int k = nsteps - 1; k >= 0; --k)
+    for (int v : c->gstep_nodes[k]) {
+      GNode& g = c->gn[v];
+      if (g.type == MG_NODE_OUTPUT) {
+        din[v] = hs.o_dmix;
+        continue;
+      }
+      if (g.type == MG_NODE_INPUT) continue;
+      if (g.succs.empty()) {
+        dout[v] = c->o_zero;
+      } else if (g.succs.size() == 1) {
+        dout[v] = din[g.succs[0]];
+      } else {
+        std::vector<size_t> ins;
+        for (int w : g.succs) ins.push_back(din[w]);
+        add_sum(g.o_dsum, ins, c->gstep_bsum[k]);
+        dout[v] = g.o_dsum;
+      }
+      if (g.type == MG_NODE_MIX) {
+        din[v] = dout[v];
+        continue;
+      }
+      const HostProc& p = c->procs[g.proc];
+      ProcDev& d = c->hpd[g.proc];
+      din[v] = p.present ? g.o_du : dout[v];
+      d.dy = (const float*)A(dout[v]);
+      d.du = (float*)A(g.o_du);
+    }
+  c->sum_beg.h.push_back((int)c->sum_in.h.size());
+  if (upload(c, c->sum_out.h, &c->sum_out.d) || upload(c, c->sum_in.h, &c->sum_in.d) ||
+      upload(c, c->sum_beg.h, &c->sum_beg.d) || upload(c, c->sum_L.h, &c->sum_L.d) ||
+      upload(c, c->sum_ld.h, &c->sum_ld.d))
+    return MG_ERR_CUDA;
+  for (int k = 0; k < nsteps; ++k) {
+    c->gstep_fsum[k].beg.push_back((int)c->gstep_fsum[k].h.size());
+    c->gstep_bsum[k].beg.push_back((int)c->gstep_bsum[k].h.size());
+    if (upload_items(c, c->gstep_fsum[k]) || upload_items(c, c->gstep_bsum[k])) return MG_ERR_CUDA;
+  }
+  // stages: the present processors of every processor step
+  c->stages.clear();
+  c->all_present = ProcList{};
+  c->all_lti_present = ProcList{};
+  for (int pi = 0; pi < c->P; ++pi)
+    if (c->procs[pi].present) {
+      c->all_present.h.push_back(pi);
+      const int t = c->procs[pi].type;
+      if (t == T_E || t == T_R || t == T_D) c->all_lti_present.h.push_back(pi);
+    }
+  for (int k = 0; k < nsteps; ++k) {
+    if (c->gstep_type[k] >= NTYPES) continue;
+    Stage st;
+    st.level = k;
+    st.type = c->gstep_type[k];
+    for (int v : c->gstep_nodes[k])
+      if (c->procs[c->gn[v].proc].present) st.procs.h.push_back(c->gn[v].proc);
+    if (st.procs.h.empty()) continue;
+    if (make_stage(c, st) != MG_OK) return MG_ERR_CUDA;
+    c->gstep_stage[k] = (int)c->stages.size();
+    c->stages.push_back(st);
+  }
   if (upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
   if (upload_procs(c, c->all_present) || upload_procs(c, c->all_lti_present)) return MG_ERR_CUDA;
   return MG_OK;
@@ -958,9 +1268,23 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
       p.o_cagg = b.take(p.nchunks * sizeof(float));
     }
   }
+  if (c->is_graph) {
+    const size_t st = (size_t)2 * c->songs[0].ld * sizeof(float);
+    c->o_src.assign(c->songs[0].K, 0);
+    for (auto& o : c->o_src) o = b.take(st);
+    c->o_zero = b.take(st);
+    for (auto& v : c->gn) {
+      const bool proc = v.type < NTYPES;
+      if ((proc || v.type == MG_NODE_MIX) && v.preds.size() > 1) v.o_agg = b.take(st);
+      if (v.type != MG_NODE_INPUT && v.type != MG_NODE_OUTPUT && v.succs.size() > 1) v.o_dsum = b.take(st);
+      if (proc) v.o_du = b.take(st);
+    }
+  }
   const int64_t limit = d->workspace_limit_bytes > 0 ? d->workspace_limit_bytes : INT64_MAX;
   size_t worst = 0;
-  for (int level = 0; level < 2; ++level)
+  int levels = 2;
+  for (auto& p : c->procs) levels = std::max(levels, p.level + 1);
+  for (int level = 0; level < levels; ++level)
     for (int t : {T_R, T_D}) {
       size_t used = 0;
       for (auto& p : c->procs) {
@@ -1099,7 +1423,7 @@ mg_status autotune_splits(mg_console* c) {
 }
 
 mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
-  plan(c, d, s, n);
+  if (!c->is_graph) plan(c, d, s, n);
   init_kernel_attributes();
   init_loss_attributes();
   init_fir_attributes();
@@ -1375,7 +1699,8 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
       CK(cudaMemcpyAsync(tmp, s[si].sources, need * sizeof(float),
                          s[si].on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
       for (int k = 0; k < hs.K; ++k)
-        launch_ingest(c->stream, tmp + (size_t)k * hs.L, (float*)(c->arena + c->chains[hs.tracks_chain[k]].o_in), hs.L, hs.ld);
+        launch_ingest(c->stream, tmp + (size_t)k * hs.L,
+                      (float*)(c->arena + (c->is_graph ? c->o_src[k] : c->chains[hs.tracks_chain[k]].o_in)), hs.L, hs.ld);
       if (s[si].target) {
         CK(cudaMemcpy2DAsync(c->arena + hs.o_tgt, (size_t)hs.ld * sizeof(float), s[si].target, (size_t)hs.L * sizeof(float),
                              (size_t)hs.L * sizeof(float), 2,
@@ -2082,6 +2407,59 @@ mg_status mg_console_create(const mg_console_desc* desc, const mg_song_desc* son
   return MG_OK;
 }
 
+mg_status mg_graph_plan(const mg_console_desc* desc, const mg_graph_desc* graph, const mg_song_desc* song,
+                        mg_console_info* out, int32_t* step_type, int32_t* n_steps) {
+  if (!out) return fail(nullptr, MG_ERR_INVALID, "out is null");
+  mg_console tmp;
+  mg_status st = validate_graph(&tmp, desc, graph, song);
+  if (st == MG_OK) st = plan_graph(&tmp, desc, graph, song);
+  if (st != MG_OK) {
+    g_static_err = tmp.err;
+    return st;
+  }
+  fill_info(&tmp, out);
+  size_t shared_scratch = 0, keep_scratch = 0;
+  const size_t arena = layout_arena(&tmp, desc, &shared_scratch, &keep_scratch);
+  const bool keep = desc->retain_spectra == 1;
+  out->device_bytes = (int64_t)console_device_bytes(&tmp, arena, keep ? keep_scratch : shared_scratch);
+  out->launches_per_step = 0;
+  out->retains_spectra = keep ? 1 : 0;
+  if (n_steps) *n_steps = (int32_t)tmp.gstep_type.size();
+  if (step_type)
+    for (size_t k = 0; k < tmp.gstep_type.size(); ++k) step_type[k] = tmp.gstep_type[k];
+  return MG_OK;
+}
+
+mg_status mg_graph_console_create(const mg_console_desc* desc, const mg_graph_desc* graph, const mg_song_desc* song,
+                                  cudaStream_t stream, mg_console** out) {
+  if (!out) return fail(nullptr, MG_ERR_INVALID, "out is null");
+  *out = nullptr;
+  mg_console* c = new (std::nothrow) mg_console();
+  if (!c) return fail(nullptr, MG_ERR_OOM, "host allocation failed");
+  c->stream = stream;
+  {
+    const char* dbg = std::getenv("MG_DEBUG_SYNC");
+    c->debug_sync = dbg && dbg[0] == '1';
+  }
+  mg_status st = validate_graph(c, desc, graph, song);
+  if (st == MG_OK) st = plan_graph(c, desc, graph, song);
+  if (st == MG_OK) {
+    std::lock_guard<std::mutex> lock(g_device_mutex);
+    st = create_impl(c, desc, song, 1);
+  }
+  if (st != MG_OK) {
+    g_static_err = c->err;
+    {
+      std::lock_guard<std::mutex> lock(g_device_mutex);
+      destroy_impl(c);
+    }
+    delete c;
+    return st;
+  }
+  *out = c;
+  return MG_OK;
+}
+
 mg_status mg_console_destroy(mg_console* c) {
   if (!c) return MG_ERR_INVALID;
   cudaStreamSynchronize(c->stream);
@@ -2178,7 +2556,7 @@ mg_status mg_prune_scores(mg_console* c, const uint8_t* d_masks, int32_t n_masks
   if (!c || !d_masks || !d_la || n_masks < 0) return fail(c, MG_ERR_INVALID, "null pointer or negative count");
   if (n_masks == 0) return MG_OK;
   mg_status st = MG_OK;
-  if (c->per_node || c->score_mode == 1) {
+  if (c->per_node || c->score_mode == 1 || c->is_graph) {
     // one full masked render per candidate
     for (int j = 0; j < n_masks; ++j) score_full(c, d_masks + (size_t)j * c->P, d_la + (size_t)j * c->songs.size());
     CK(cudaGetLastError());
@@ -2295,7 +2673,7 @@ mg_status mg_update_audio(mg_console* c, int32_t song, const float* sources, con
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   // mono sources go to the left row of each track input, then ingest duplicates them to both rows
   for (int t = 0; t < hs.K; ++t) {
-    float* dst = (float*)(c->arena + c->chains[hs.tracks_chain[t]].o_in);
+    float* dst = (float*)(c->arena + (c->is_graph ? c->o_src[t] : c->chains[hs.tracks_chain[t]].o_in));
     CK(cudaMemcpyAsync(dst, sources + (size_t)t * hs.L, sizeof(float) * hs.L, k, c->stream));
     CK(cudaMemcpyAsync(dst + hs.ld, sources + (size_t)t * hs.L, sizeof(float) * hs.L, k, c->stream));
   }

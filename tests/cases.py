@@ -11,6 +11,7 @@ import numpy as np
 import workloads as W
 from oracle import console as OC
 from oracle import loss as OL
+from oracle import graph as OG
 
 LOSS_FIELDS = ("La", "Llr", "Lm", "Ls", "Lg", "Lp", "total")
 
@@ -176,3 +177,70 @@ def record_error(test: str, quantity: str, err: float, plain_bound: float, bound
 
 def current_test() -> str:
     return os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+
+
+def console_graph(layout, types="ecnsgdr"):
+    """The console of one song as a graph (Sec. 1.2): input -> chain per track, mix node -> chain per subgroup,
+    output summing the subgroup chains, then the ungrouped tracks; processors numbered in the console's
+    canonical order."""
+    chain = [t for t in "ecnsgdr" if t in types]
+    ntype, track, edges = [], [], []
+
+    def node(t, k=-1):
+        ntype.append(t)
+        track.append(k)
+        return len(ntype) - 1
+
+    def add_chain(src):
+        last = src
+        for t in chain:
+            v = node("ecnsgdr".index(t))
+            edges.append((last, v))
+            last = v
+        return last
+    K, S = layout.num_tracks, layout.num_subgroups
+    inputs = [node(OG.INPUT, k) for k in range(K)]
+    # processors must come in canonical order (tracks' chains, then subgroups' chains), so nodes are created
+    # chain by chain; the mix nodes get their edges after the track chains exist
+    track_out = [add_chain(inputs[k]) for k in range(K)]
+    group_out = []
+    for g in range(S):
+        m = node(OG.MIX)
+        for k in range(K):
+            if layout.track_group[k] == g:
+                edges.append((track_out[k], m))
+        group_out.append(add_chain(m))
+    o = node(OG.OUTPUT)
+    for g in range(S):
+        edges.append((group_out[g], o))
+    for k in range(K):
+        if layout.track_group[k] < 0:
+            edges.append((track_out[k], o))
+    return ntype, track, edges
+
+
+def random_dag(n_tracks: int, n_proc: int, n_mix: int, seed: int):
+    """A seeded random processing graph: the inputs, then processors (every type at least once) and mix nodes in a
+    random order, each with one to three predecessors among the nodes before it, and the output fed by every
+    node nothing else reads (so that every node reaches the output).  Edges run from lower to higher index."""
+    rng = np.random.default_rng(seed)
+    ntype = [OG.INPUT] * n_tracks
+    track = list(range(n_tracks))
+    kinds = list(range(7)) + [int(t) for t in rng.integers(0, 7, n_proc - 7)] + [OG.MIX] * n_mix
+    rng.shuffle(kinds)
+    edges = []
+    for t in kinds:
+        v = len(ntype)
+        k = int(rng.integers(1, 4))
+        preds = sorted(set(int(u) for u in rng.integers(0, v, k)))
+        edges += [(u, v) for u in preds]
+        ntype.append(int(t))
+        track.append(-1)
+    o = len(ntype)
+    ntype.append(OG.OUTPUT)
+    track.append(-1)
+    has_succ = {u for u, _ in edges}
+    for v in range(o):
+        if v not in has_succ:
+            edges.append((v, o))
+    return ntype, track, edges

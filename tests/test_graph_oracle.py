@@ -11,48 +11,9 @@ import workloads as W
 from oracle import console as OC
 from oracle import graph as OG
 from oracle import loss as OL
+from tests.cases import console_graph
 
 INPUT, MIX, OUTPUT = OG.INPUT, OG.MIX, OG.OUTPUT
-
-
-def console_graph(layout, types="ecnsgdr"):
-    """The console of one song as a graph (Sec. 1.2): input -> chain per track, mix node -> chain per subgroup,
-    output summing the subgroup chains, then the ungrouped tracks; processors numbered in the console's
-    canonical order."""
-    chain = [t for t in "ecnsgdr" if t in types]
-    ntype, track, edges = [], [], []
-
-    def node(t, k=-1):
-        ntype.append(t)
-        track.append(k)
-        return len(ntype) - 1
-
-    def add_chain(src):
-        last = src
-        for t in chain:
-            v = node("ecnsgdr".index(t))
-            edges.append((last, v))
-            last = v
-        return last
-    K, S = layout.num_tracks, layout.num_subgroups
-    inputs = [node(INPUT, k) for k in range(K)]
-    # processors must come in canonical order (tracks' chains, then subgroups' chains), so nodes are created
-    # chain by chain; the mix nodes get their edges after the track chains exist
-    track_out = [add_chain(inputs[k]) for k in range(K)]
-    group_out = []
-    for g in range(S):
-        m = node(MIX)
-        for k in range(K):
-            if layout.track_group[k] == g:
-                edges.append((track_out[k], m))
-        group_out.append(add_chain(m))
-    o = node(OUTPUT)
-    for g in range(S):
-        edges.append((group_out[g], o))
-    for k in range(K):
-        if layout.track_group[k] < 0:
-            edges.append((track_out[k], o))
-    return ntype, track, edges
 
 
 def test_topological_order_is_the_plain_definition():
