@@ -157,6 +157,17 @@ struct mg_console {
   size_t score_budget = 0;
   std::vector<char> score_blob;
   std::vector<uint8_t> score_m0;
+  // the last batched scoring call's surviving chunk: its base mask, the candidates' masks, per (candidate, song)
+  // the node outputs a candidate recomputed (arena destination, workspace source) and its song copy, so that a
+  // next call whose base mask equals, song by song, the old base or one of these candidates starts from them
+  struct ScoreKeep {
+    bool valid = false;
+    std::vector<uint8_t> m0, masks;
+    int nc = 0;
+    std::vector<std::vector<std::pair<char*, const char*>>> promo;   // [cand * n_songs + song]
+    std::vector<int> vsong;                                         // [cand * n_songs + song]
+    const float* vla = nullptr;
+  } score_keep;
   // general processing graph (Sec. 2, Sec. 4): nodes, the batched schedule (Alg. 1) as steps of one type each,
   // per step the aggregation sums of the forward and the adjoint sums of the backward, one source buffer per
   // track, and a zero buffer (the adjoint of an output nothing reads)
@@ -1814,6 +1825,7 @@ struct ScoreChunk {
   std::vector<SongDev> vs;
   std::vector<int4> litems[3];
   std::vector<int> map;                      // [candidate][song]: song copy, or -1 (unchanged)
+  std::vector<std::vector<std::pair<char*, const char*>>> promo;   // [candidate][song]: (arena, copy) buffers
   size_t table_begin = 0;                    // workspace offset of the tables (copied from the host blob)
   size_t end = 0;                            // workspace bytes the chunk uses
   float* vq = nullptr;
@@ -1956,6 +1968,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
   auto A = [&](size_t off) { return c->arena + off; };
   const int ns = (int)c->songs.size();
   k.map.assign((size_t)(j1 - j0) * ns, -1);
+  k.promo.assign((size_t)(j1 - j0) * ns, {});
   // node copies per (level, type), in candidate order
   std::vector<int> by_lt[2][NTYPES];
   for (int j = j0; j < j1; ++j) {
@@ -2003,6 +2016,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
         k.vsrc.push_back(pi);
         k.vmask.push_back(mj[pi]);
         by_lt[p.level][p.type].push_back(v);
+        k.promo[(size_t)(j - j0) * ns + p.song].push_back({A(p.o_y), (const char*)d.y});
         cur = d.y;
       }
       chain_y[ci] = cur;
@@ -2031,6 +2045,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
         k.m_items.beg.push_back((int)k.m_items.h.size());
         for (int t = 0; t < (hs.L + kElemTile - 1) / kElemTile; ++t) k.m_items.h.push_back(Item{sid, t});
         group_in[hs.groups_chain[g]] = out;
+        k.promo[(size_t)(j - j0) * ns + si].push_back({A(c->chains[hs.groups_chain[g]].o_in), (const char*)out});
       }
       for (; ci_next < cp.chains.size() && c->chains[cp.chains[ci_next].first].song == si; ++ci_next)
         copy_chain(cp.chains[ci_next].first, cp.chains[ci_next].second);
@@ -2060,6 +2075,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
           k.litems[r].push_back(make_int4(vsi, r, t, std::min(per, hs.nframes[r] - t)));
       }
       k.map[(size_t)(j - j0) * ns + si] = vsi;
+      k.promo[(size_t)(j - j0) * ns + si].push_back({A(hs.o_mix), (const char*)mix});
     }
   }
   k.sum_beg.push_back((int)k.sum_in.size());
@@ -2258,6 +2274,35 @@ void score_full(mg_console* c, const uint8_t* d_mask_j, float* d_la_row) {
   loss_forward(c, x, 2, nullptr, d_la_row, 1);
 }
 
+// Makes the arena hold the base render of mask m0 from the last call's surviving chunk, without rendering: per
+// song, nothing to do when m0 equals the old base there; the recomputed outputs and the L_a of a candidate whose
+// mask equals m0 there are copied in (device to device, on the stream).  False (nothing copied) when some song
+// matches neither.
+bool promote_base(mg_console* c, const std::vector<uint8_t>& m0) {
+  auto& kp = c->score_keep;
+  const int ns = (int)c->songs.size();
+  std::vector<int> pick(ns, -1);
+  for (int si = 0; si < ns; ++si) {
+    const int b = c->songs[si].pbeg, e = c->songs[si].pend;
+    auto same = [&](const uint8_t* m) { return std::equal(m0.begin() + b, m0.begin() + e, m + b); };
+    if (same(kp.m0.data())) continue;
+    for (int j = 0; j < kp.nc && pick[si] < 0; ++j)
+      if (kp.vsong[(size_t)j * ns + si] >= 0 && same(kp.masks.data() + (size_t)j * c->P)) pick[si] = j;
+    if (pick[si] < 0) return false;
+  }
+  for (int si = 0; si < ns; ++si) {
+    if (pick[si] < 0) continue;
+    const size_t bytes = (size_t)2 * c->songs[si].ld * sizeof(float);
+    for (const auto& cp : kp.promo[(size_t)pick[si] * ns + si])
+      if (cudaMemcpyAsync(cp.first, cp.second, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) return false;
+    const int vs = kp.vsong[(size_t)pick[si] * ns + si];
+    if (cudaMemcpyAsync(c->d_scratch_la + si, kp.vla + vs, sizeof(float), cudaMemcpyDeviceToDevice, c->stream) !=
+        cudaSuccess)
+      return false;
+  }
+  return true;
+}
+
 mg_status prune_scores_batched(mg_console* c, const uint8_t* d_masks, int n_masks, float* d_la) {
   const int P = c->P, ns = (int)c->songs.size();
   std::vector<uint8_t> hm((size_t)n_masks * P);
@@ -2275,9 +2320,13 @@ mg_status prune_scores_batched(mg_console* c, const uint8_t* d_masks, int n_mask
   }
   std::vector<CandPlan> plans(n_masks);
   for (int j = 0; j < n_masks; ++j) plans[j] = plan_candidate(c, hm.data() + (size_t)j * P, c->score_m0.data());
-  // the base render and its losses
-  if (!all_ones) CK(cudaMemcpyAsync(c->d_mask, c->score_m0.data(), P, cudaMemcpyHostToDevice, c->stream));
-  {
+  // the base: kept from the last call where, song by song, the new base mask equals the old base or one of its
+  // candidates (whose recomputed outputs are copied into the arena), else rendered
+  bool base_ready = false;
+  if (c->score_keep.valid) base_ready = promote_base(c, c->score_m0);
+  c->score_keep.valid = false;
+  if (!base_ready) {
+    if (!all_ones) CK(cudaMemcpyAsync(c->d_mask, c->score_m0.data(), P, cudaMemcpyHostToDevice, c->stream));
     LaunchCtx xb = make_ctx(c, all_ones ? nullptr : c->d_mask);
     if (!(c->fwd_valid && all_ones)) render(c, xb);
     loss_forward(c, xb, 2, nullptr, c->d_scratch_la, 1);
@@ -2345,6 +2394,16 @@ mg_status prune_scores_batched(mg_console* c, const uint8_t* d_masks, int n_mask
     CK(cudaGetLastError());
     // the next chunk's tables overwrite these: the host copy of the next blob is ordered after this chunk's
     // kernels on the stream, and the blob itself is staged before cudaMemcpyAsync returns
+    if (j1 == n_masks && full.empty()) {     // the last chunk survives until the next call
+      auto& kp = c->score_keep;
+      kp.m0 = c->score_m0;
+      kp.nc = j1 - j;
+      kp.masks.assign(hm.begin() + (size_t)j * P, hm.begin() + (size_t)j1 * P);
+      kp.promo = std::move(k.promo);
+      kp.vsong = k.map;
+      kp.vla = k.vla;
+      kp.valid = true;
+    }
     j = j1;
   }
   for (int jj : full) score_full(c, d_masks + (size_t)jj * P, d_la + (size_t)jj * ns);
@@ -2511,6 +2570,7 @@ static mg_status copy_vec(mg_console* c, float* dst, const float* src, int64_t n
 mg_status mg_set_params(mg_console* c, const float* params, int64_t n, int32_t on_device) {
   mg_status s = copy_vec(c, c ? c->d_params : nullptr, params, n, on_device, true);
   if (s == MG_OK) c->fwd_valid = false;
+  if (c) c->score_keep.valid = false;
   return s;
 }
 mg_status mg_get_params(const mg_console* c, float* out, int64_t n, int32_t on_device) {
@@ -2527,6 +2587,7 @@ mg_status mg_set_alpha_p(mg_console* c, float alpha_p) {
   c->alpha_p = alpha_p;
   launch_set_hyper(c->stream, c->d_hyper, alpha_p, 0, 0, 0, 0, 0, 0);
   c->fwd_valid = false;
+  c->score_keep.valid = false;
   CK(cudaGetLastError());
   return MG_OK;
 }
@@ -2540,6 +2601,7 @@ mg_status mg_forward_loss(mg_console* c, const uint8_t* d_mask, float* d_losses,
   if (d_mix) run(c, F_MISC, [&] { launch_copy_mix(c->stream, c->d_songs, (int)c->songs.size(), d_mix, c->d_mixoff); });
   CK(cudaGetLastError());
   c->fwd_valid = d_mask == nullptr;
+  c->score_keep.valid = false;
   return MG_OK;
 }
 
@@ -2557,6 +2619,7 @@ mg_status mg_prune_scores(mg_console* c, const uint8_t* d_masks, int32_t n_masks
   if (n_masks == 0) return MG_OK;
   mg_status st = MG_OK;
   if (c->per_node || c->score_mode == 1 || c->is_graph) {
+    c->score_keep.valid = false;
     // one full masked render per candidate
     for (int j = 0; j < n_masks; ++j) score_full(c, d_masks + (size_t)j * c->P, d_la + (size_t)j * c->songs.size());
     CK(cudaGetLastError());
@@ -2578,6 +2641,7 @@ mg_status mg_adam_step(mg_console* c, float lr, float beta1, float beta2, float 
   launch_set_hyper(c->stream, c->d_hyper, 0, lr, beta1, beta2, eps, weight_decay, 1);
   run(c, F_ADAM, [&] { launch_adam2(c->stream, c->d_hyper, c->d_step, c->d_params, c->d_grads, c->d_m, c->d_v, c->nparams); });
   c->fwd_valid = false;
+  c->score_keep.valid = false;
   CK(cudaGetLastError());
   return MG_OK;
 }
@@ -2600,6 +2664,7 @@ mg_status mg_train_step(mg_console* c, float lr, float beta1, float beta2, float
     backward_pass(c, x);
     run(c, F_ADAM, [&] { launch_adam2(c->stream, c->d_hyper, c->d_step, c->d_params, c->d_grads, c->d_m, c->d_v, c->nparams); });
     c->fwd_valid = false;
+    c->score_keep.valid = false;
     CK(cudaGetLastError());
     return MG_OK;
   }
@@ -2634,6 +2699,7 @@ mg_status mg_train_step(mg_console* c, float lr, float beta1, float beta2, float
     for (auto& pr : c->graph_pairs) accumulate_pair(c, pr.first, pr.second.first, pr.second.second);
   }
   c->fwd_valid = false;
+  c->score_keep.valid = false;
   return MG_OK;
 }
 
@@ -2649,6 +2715,7 @@ mg_status mg_prune(mg_console* c, const uint8_t* h_keep) {
     c->graph = nullptr;
   }
   c->fwd_valid = false;
+  c->score_keep.valid = false;
   CK(cudaStreamSynchronize(c->stream));
   return MG_OK;
 }
@@ -2689,6 +2756,7 @@ mg_status mg_update_audio(mg_console* c, int32_t song, const float* sources, con
     launch_loss_finalize_mode(x, c->d_songs + song, 1, c->d_res, c->nres, c->d_alphas, 0, nullptr, nullptr, 0);
   }
   c->fwd_valid = false;
+  c->score_keep.valid = false;
   CK(cudaGetLastError());
   return MG_OK;
 }

@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
 }
 
 // Channel scales of one node (one CTA per node): per channel the energy of an evenly spread quarter of the
-// signal's 32-byte sectors (four consecutive samples out of every 32), and the power of two s = 2^-floor(e / 2),
+// signal's 32-byte sectors (four consecutive samples out of every 32) or of every 8th tap (the scale only needs the
+// order of magnitude), and the power of two s = 2^-floor(e / 2),
 // e the binary exponent of that energy, which brings the channel near unit energy; 1 for a silent channel.
 // which 0: the input u and the taps (in the stereo form the transforms use); 1: dL/dy.  Fixed-order sums.
 __device__ __forceinline__ float pow2_scale(float e) {
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(256) k_chan_scale(LaunchCtx c, const int* __re
     acc[1] += b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w;
   }
   if (which == 0)
-    for (int j = threadIdx.x; j < P.Nh; j += blockDim.x) {
+    for (int j = threadIdx.x * 8; j < P.Nh; j += blockDim.x * 8) {   // every 8th tap
       const float2 t = tap_at(P, (int64_t)j + P.n0 >= 0 ? (int64_t)j + P.n0 : fft_len(P) + j + P.n0, fft_len(P));
       acc[2] += t.x * t.x;
       acc[3] += t.y * t.y;

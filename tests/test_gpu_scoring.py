@@ -117,3 +117,45 @@ def test_pruned_console_scores():
     full = con.prune_scores(masks).clone()
     assert torch.equal(batched, full)
     con.close()
+
+
+def test_consecutive_calls_start_from_the_last_candidates():
+    """A call whose base mask equals, song by song, the previous call's base or one of its masks starts from that
+    mask's recomputed outputs instead of rendering (the search rounds do this after every accepted trial).  Every
+    score still equals a full render bitwise, also after a call whose base matches nothing before it and after an
+    unmasked forward in between."""
+    import torch
+    lays = [W.SongLayout(3, 1, [0, -1, 0], 25011), W.SongLayout(2, 1, [0, 0], 19999)]
+    case = make_case(lays, seed=15)
+    con = gpu_console(case)
+    ref = gpu_console(case)
+    for c in (con, ref):
+        c.set_params(case.params)
+    ref.set_score_mode(True)
+    P = con.n_processors
+    _, _, song = con.layout()
+    rng = np.random.default_rng(6)
+
+    def singles(base, idx):
+        out = np.repeat(base[None, :], len(idx), axis=0)
+        for r, i in enumerate(idx):
+            out[r, i] = 0
+        return out
+    base = np.ones(P, np.uint8)
+    seq = [singles(base, [1, 5, 9, 30])]
+    base2 = seq[0][1].copy()                      # the second mask of the first call becomes the base
+    base2[song == 1] = seq[0][3][song == 1]       # and song 1 takes the fourth mask's state
+    seq.append(singles(base2, [2, 12, 33]))
+    seq.append(singles(base2, [3, 4]))            # same base as the call before
+    other = np.ones(P, np.uint8)
+    other[rng.choice(P, 6, replace=False)] = 0    # matches nothing before: rendered
+    seq.append(singles(other, [0, 7, 31]))
+    for k, masks in enumerate(seq):
+        if k == 3:
+            con.forward_loss()                    # an unmasked forward in between
+        got = con.prune_scores(masks)
+        want = ref.prune_scores(masks)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want), (k, (got - want).abs().max().item())
+    con.close()
+    ref.close()
