@@ -180,6 +180,8 @@ struct mg_console {
   std::vector<size_t> o_src;
   size_t o_zero = 0;
   int score_mode = 0;              // 0: batched candidate scoring, 1: one full masked render per candidate
+  int elem_tile = kElemTile;       // samples per work item of the elementwise kernels and sums (packing tuner)
+  int loss_per[3] = {0, 0, 0};     // frames per loss work item per resolution (packing tuner; 0: 8192 / n_fft)
   bool debug_sync = false;         // MG_DEBUG_SYNC=1 in the environment: synchronise and check after every launch
   bool debug_reported = false;
   ProcDev* d_procs = nullptr;
@@ -357,6 +359,7 @@ void size_proc(HostProc& p, double fs) {
     p.nbrows = p.nchunks;
   } else {
     p.nbrows = (p.L + kElemTile - 1) / kElemTile;
+    p.nfcap = (p.L + kElemTileMin - 1) / kElemTileMin;   // partial-sum rows for every candidate tile
   }
 }
 
@@ -643,6 +646,7 @@ LaunchCtx make_ctx(mg_console* c, const uint8_t* mask) {
   x.hyper = c->d_hyper;
   x.alpha_g = c->desc.alpha_g;
   x.fs = c->desc.sample_rate;
+  x.elem_tile = c->elem_tile;
   x.tab = c->tab;
   return x;
 }
@@ -738,7 +742,7 @@ void stage_backward(mg_console* c, const LaunchCtx& x, Stage& s) {
 
 void run_sums(mg_console* c, const ItemList& items) {
   run_items(c, F_SUM, items, [&](const Item* it, int n) {
-    launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n);
+    launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n, c->elem_tile);
   });
 }
 
@@ -762,7 +766,7 @@ void render(mg_console* c, const LaunchCtx& x) {
     if (level == 1 && !c->sum_m_items.h.empty()) {
       StageScope scope(c, 8);
       run_items(c, F_SUM, c->sum_m_items, [&](const Item* it, int n) {
-        launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n);
+        launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n, c->elem_tile);
       });
     }
     for (auto& s : c->stages)
@@ -770,7 +774,7 @@ void render(mg_console* c, const LaunchCtx& x) {
   }
   StageScope scope(c, 8);
   run_items(c, F_SUM, c->sum_o_items, [&](const Item* it, int n) {
-    launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n);
+    launch_sum(c->stream, c->sum_out.d, c->sum_in.d, c->sum_beg.d, c->sum_L.d, c->sum_ld.d, it, n, c->elem_tile);
   });
 }
 
@@ -1041,7 +1045,7 @@ mg_status build_tables(mg_console* c) {
     c->sum_L.h.push_back(L);
     c->sum_ld.h.push_back(ld);
     items.beg.push_back((int)items.h.size());
-    for (int t = 0; t < (L + kElemTile - 1) / kElemTile; ++t) items.h.push_back(Item{sid, t});
+    for (int t = 0; t < (L + c->elem_tile - 1) / c->elem_tile; ++t) items.h.push_back(Item{sid, t});
     ++sid;
   };
   for (auto& s : c->songs)
@@ -1120,7 +1124,7 @@ mg_status build_graph_tables(mg_console* c) {
     c->sum_L.h.push_back(hs.L);
     c->sum_ld.h.push_back(hs.ld);
     items.beg.push_back((int)items.h.size());
-    for (int t = 0; t < (hs.L + kElemTile - 1) / kElemTile; ++t) items.h.push_back(Item{sid, t});
+    for (int t = 0; t < (hs.L + c->elem_tile - 1) / c->elem_tile; ++t) items.h.push_back(Item{sid, t});
     ++sid;
   };
   // forward: outputs in schedule order
@@ -1231,9 +1235,10 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
       const int nf = d->n_fft[r], hop = nf / d->hop_div;
       hs.nframes[r] = hs.L >= nf ? (hs.L - nf) / hop + 1 : 0;
       hs.first[r] = std::min(hs.nframes[r], (int)((d->warmup_samples + hop - 1) / hop));
-      const int per = 8192 / nf;
+      if (c->loss_per[r] <= 0) c->loss_per[r] = 8192 / nf;
+      const int per = c->loss_per[r], per_min = std::max(1, 8192 / nf / kLossPerDiv);
       hs.litems[r] = (hs.nframes[r] - hs.first[r] + per - 1) / per;
-      hs.lcap = std::max(hs.lcap, hs.litems[r]);
+      hs.lcap = std::max(hs.lcap, (hs.nframes[r] - hs.first[r] + per_min - 1) / per_min);   // every candidate
       const int nbands = d->n_mels > 0 ? d->n_mels : nf / 2 + 1;
       hs.o_Y[r] = b.take((size_t)std::max(1, hs.nframes[r]) * nbands * 4 * sizeof(float));
       hs.o_Yh[r] = b.take((size_t)std::max(1, hs.nframes[r]) * nbands * 4 * sizeof(float));
@@ -1433,6 +1438,130 @@ mg_status autotune_splits(mg_console* c) {
   return MG_OK;
 }
 
+// Loss work items for the current frames per item (song-major within each resolution, so one song's items are
+// one contiguous range), with the per-song item counts and the resolutions' item length on the device.
+mg_status build_loss_items(mg_console* c) {
+  c->song_litems.assign(c->songs.size(), std::array<int2, 3>{});
+  for (int r = 0; r < c->nres; ++r) {
+    auto& L = c->loss_items[r];
+    L.h.clear();
+    const int per = c->loss_per[r];
+    c->hres[r].per = per;
+    for (size_t si = 0; si < c->songs.size(); ++si) {
+      HostSong& hs = c->songs[si];
+      const int first = (int)L.h.size();
+      for (int t = hs.first[r]; t < hs.nframes[r]; t += per)
+        L.h.push_back(make_int4((int)si, r, t, std::min(per, hs.nframes[r] - t)));
+      c->song_litems[si][r] = make_int2(first, (int)L.h.size() - first);
+      hs.litems[r] = (int)L.h.size() - first;
+      c->hsd[si].litems[r] = hs.litems[r];
+    }
+    if (upload(c, L.h, &L.d) != MG_OK) return MG_ERR_CUDA;
+  }
+  if (upload(c, c->hsd, &c->d_songs) != MG_OK || upload(c, c->hres, &c->d_res) != MG_OK) return MG_ERR_CUDA;
+  return MG_OK;
+}
+
+// Packing tuner: the samples per work item (one CTA) of the gain/pan and imager kernels and of the sums, which
+// decides how the nodes of those stages are cut into CTAs.  Every candidate from kElemTileMin to 16384 samples runs
+// the forward and backward launches of those stages and the sums over all nodes (the minimum of three timed
+// repetitions after one warm-up) on the console's own buffers; the fastest is kept.  The arena holds the partial
+// sums of the smallest tile, so every candidate fits.
+mg_status autotune_packing(mg_console* c) {
+  bool any = false;
+  for (const auto& p : c->procs) any = any || p.type == T_G || p.type == T_S;
+  if (!any) return MG_OK;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = c->elem_tile;
+  float best_ms = 1e30f;
+  auto set_tile = [&](int tile) -> mg_status {
+    c->elem_tile = tile;
+    for (auto& p : c->procs)
+      if (p.type == T_G || p.type == T_S) p.nbrows = (p.L + tile - 1) / tile;
+    return build_tables(c);
+  };
+  for (int tile = kElemTileMin; tile <= 16384; tile *= 2) {
+    if (set_tile(tile) != MG_OK) return MG_ERR_CUDA;
+    LaunchCtx x = make_ctx(c, nullptr);
+    auto pass = [&] {
+      for (auto& st : c->stages)
+        if (st.type == T_G || st.type == T_S) {
+          stage_forward(c, x, st);
+          stage_backward(c, x, st);
+        }
+      if (c->is_graph) {
+        for (size_t k = 0; k < c->gstep_fsum.size(); ++k) {
+          run_sums(c, c->gstep_fsum[k]);
+          run_sums(c, c->gstep_bsum[k]);
+        }
+      } else {
+        run_sums(c, c->sum_m_items);
+        run_sums(c, c->sum_o_items);
+      }
+    };
+    pass();
+    float ms = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      CK(cudaEventRecord(e0, c->stream));
+      pass();
+      CK(cudaEventRecord(e1, c->stream));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      ms = std::min(ms, t);
+    }
+    CK(cudaGetLastError());
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = tile;
+    }
+  }
+  if (set_tile(best) != MG_OK) return MG_ERR_CUDA;
+  // frames per loss work item: 8192 / n_fft (one 8192-point buffer per CTA), half or a quarter of it; the loss
+  // forward and its adjoint over all songs
+  int best_div = 1;
+  best_ms = 1e30f;
+  auto set_div = [&](int div) -> mg_status {
+    for (int r = 0; r < c->nres; ++r) c->loss_per[r] = std::max(1, 8192 / c->hres[r].nfft / div);
+    return build_loss_items(c);
+  };
+  for (int div = 1; div <= kLossPerDiv; div *= 2) {
+    if (set_div(div) != MG_OK) return MG_ERR_CUDA;
+    LaunchCtx x = make_ctx(c, nullptr);
+    auto pass = [&] {
+      for (int r = 0; r < c->nres; ++r) {
+        auto& L = c->loss_items[r];
+        if (L.h.empty()) continue;
+        launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), 1, c->loss_max_dy);
+        launch_loss_frames(x, c->d_songs, c->d_res, L.d, (int)L.h.size(), 2, c->loss_max_dy);
+      }
+    };
+    pass();
+    float ms = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      CK(cudaEventRecord(e0, c->stream));
+      pass();
+      CK(cudaEventRecord(e1, c->stream));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      ms = std::min(ms, t);
+    }
+    CK(cudaGetLastError());
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_div = div;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (set_div(best_div) != MG_OK) return MG_ERR_CUDA;
+  CK(cudaStreamSynchronize(c->stream));
+  return MG_OK;
+}
+
 mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_desc* s, int n) {
   if (!c->is_graph) plan(c, d, s, n);
   init_kernel_attributes();
@@ -1561,6 +1690,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     R.nfft = nf;
     R.log_nfft = ilog2_ceil(nf);
     R.hop = nf / d->hop_div;
+    R.per = c->loss_per[r];
     std::vector<float> win(nf), aw2(nb);
     const double PI = 3.14159265358979323846;
     for (int j = 0; j < nf; ++j) win[j] = (float)(0.5 * (1.0 - std::cos(2 * PI * j / nf)));
@@ -1636,21 +1766,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     moff += 2 * (int64_t)hs.L;
   }
   if (upload(c, c->hsd, &c->d_songs) || upload(c, mixoff, &c->d_mixoff)) return MG_ERR_CUDA;
-  // loss items (song-major within each resolution, so one song's items are one contiguous range)
-  c->song_litems.assign(c->songs.size(), std::array<int2, 3>{});
-  for (int r = 0; r < c->nres; ++r) {
-    auto& L = c->loss_items[r];
-    L.h.clear();
-    const int per = 8192 / d->n_fft[r];
-    for (size_t si = 0; si < c->songs.size(); ++si) {
-      const HostSong& hs = c->songs[si];
-      const int first = (int)L.h.size();
-      for (int t = hs.first[r]; t < hs.nframes[r]; t += per)
-        L.h.push_back(make_int4((int)si, r, t, std::min(per, hs.nframes[r] - t)));
-      c->song_litems[si][r] = make_int2(first, (int)L.h.size() - first);
-    }
-    if (upload(c, L.h, &L.d) != MG_OK) return MG_ERR_CUDA;
-  }
+  if (build_loss_items(c) != MG_OK) return MG_ERR_CUDA;
   c->gather_items = ItemList{};
   for (size_t si = 0; si < c->songs.size(); ++si) {
     c->gather_items.beg.push_back((int)c->gather_items.h.size());
@@ -1744,6 +1860,7 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
   }
   // ---- FFT split autotuner ----
   if (d->autotune && autotune_splits(c) != MG_OK) return MG_ERR_CUDA;
+  if (d->autotune && autotune_packing(c) != MG_OK) return MG_ERR_CUDA;
   // ---- target spectrograms ----
   {
     LaunchCtx x = make_ctx(c, nullptr);
@@ -1901,7 +2018,7 @@ CandPlan plan_candidate(const mg_console* c, const uint8_t* mj, const uint8_t* m
       if (hs.group[k] >= 0) group_in[hs.group[k]] = 1;
     }
     const size_t st = al((size_t)2 * hs.ld * sizeof(float));
-    const size_t tiles = (hs.L + kElemTile - 1) / kElemTile;
+    const size_t tiles = (hs.L + kElemTileMin - 1) / kElemTileMin;
     for (int g = 0; g < hs.S; ++g) {
       const int f = group_in[g] ? 0 : first_changed(hs.groups_chain[g]);
       if (f < 0) continue;
@@ -2043,7 +2160,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
         k.sum_L.push_back(hs.L);
         k.sum_ld.push_back(hs.ld);
         k.m_items.beg.push_back((int)k.m_items.h.size());
-        for (int t = 0; t < (hs.L + kElemTile - 1) / kElemTile; ++t) k.m_items.h.push_back(Item{sid, t});
+        for (int t = 0; t < (hs.L + c->elem_tile - 1) / c->elem_tile; ++t) k.m_items.h.push_back(Item{sid, t});
         group_in[hs.groups_chain[g]] = out;
         k.promo[(size_t)(j - j0) * ns + si].push_back({A(c->chains[hs.groups_chain[g]].o_in), (const char*)out});
       }
@@ -2060,7 +2177,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
       k.sum_L.push_back(hs.L);
       k.sum_ld.push_back(hs.ld);
       k.o_items.beg.push_back((int)k.o_items.h.size());
-      for (int t = 0; t < (hs.L + kElemTile - 1) / kElemTile; ++t) k.o_items.h.push_back(Item{sid, t});
+      for (int t = 0; t < (hs.L + c->elem_tile - 1) / c->elem_tile; ++t) k.o_items.h.push_back(Item{sid, t});
       SongDev sd = c->hsd[si];
       const int vsi = (int)k.vs.size();
       sd.mix = mix;
@@ -2070,7 +2187,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
       sd.coef = (float*)w.buffer(18 * sizeof(float));
       k.vs.push_back(sd);
       for (int r = 0; r < c->nres; ++r) {
-        const int per = 8192 / c->desc.n_fft[r];
+        const int per = c->loss_per[r];
         for (int t = hs.first[r]; t < hs.nframes[r]; t += per)
           k.litems[r].push_back(make_int4(vsi, r, t, std::min(per, hs.nframes[r] - t)));
       }
@@ -2098,7 +2215,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
         const ProcDev& d = k.vp[v];
         if (t == T_G || t == T_S || t == T_C || t == T_N) {
           st.elem.beg.push_back((int)st.elem.h.size());
-          const int nt = (t == T_C || t == T_N) ? d.nchunks : (d.L + kElemTile - 1) / kElemTile;
+          const int nt = (t == T_C || t == T_N) ? d.nchunks : (d.L + c->elem_tile - 1) / c->elem_tile;
           for (int i = 0; i < nt; ++i) st.elem.h.push_back(Item{v, i});
         } else if (t == T_E) {
           st.osf.beg.push_back((int)st.osf.h.size());
@@ -2189,7 +2306,7 @@ std::string check_chunk(const mg_console* c, const ScoreChunk& k) {
       if (v < 0 || v >= V) return "stage list indexes a missing node copy";
     for (const Item& it : st.elem.h) {
       const ProcDev& d = k.vp[it.proc];
-      const int lim = (st.type == T_C || st.type == T_N) ? d.nchunks : (d.L + kElemTile - 1) / kElemTile;
+      const int lim = (st.type == T_C || st.type == T_N) ? d.nchunks : (d.L + c->elem_tile - 1) / c->elem_tile;
       if (it.proc < 0 || it.proc >= V || it.idx < 0 || it.idx >= lim) return "elementwise item out of range";
     }
     for (const Item& it : st.osf.h)
@@ -2364,7 +2481,7 @@ mg_status prune_scores_batched(mg_console* c, const uint8_t* d_masks, int n_mask
         if (level == 1 && !k.m_items.h.empty()) {
           StageScope scope(c, 8);
           run_items(c, F_SUM, k.m_items, [&](const Item* it, int n) {
-            launch_sum(c->stream, k.d_sum_out, k.d_sum_in, k.d_sum_beg, k.d_sum_L, k.d_sum_ld, it, n);
+            launch_sum(c->stream, k.d_sum_out, k.d_sum_in, k.d_sum_beg, k.d_sum_L, k.d_sum_ld, it, n, c->elem_tile);
           });
         }
         for (auto& st : k.stages)
@@ -2375,7 +2492,7 @@ mg_status prune_scores_batched(mg_console* c, const uint8_t* d_masks, int n_mask
       {
         StageScope scope(c, 8);
         run_items(c, F_SUM, k.o_items, [&](const Item* it, int n) {
-          launch_sum(c->stream, k.d_sum_out, k.d_sum_in, k.d_sum_beg, k.d_sum_L, k.d_sum_ld, it, n);
+          launch_sum(c->stream, k.d_sum_out, k.d_sum_in, k.d_sum_beg, k.d_sum_L, k.d_sum_ld, it, n, c->elem_tile);
         });
       }
       StageScope scope(c, 7);

@@ -14,8 +14,8 @@ __global__ void __launch_bounds__(256) k_gs_fwd(LaunchCtx c, const Item* __restr
   const float4* ur = reinterpret_cast<const float4*>(P.u + P.ld);
   float4* yl = reinterpret_cast<float4*>(P.y);
   float4* yr = reinterpret_cast<float4*>(P.y + P.ld);
-  const int v0 = it.idx * (kElemTile / 4);
-  const int vend = min(v0 + kElemTile / 4, (P.L + 3) >> 2);
+  const int v0 = it.idx * (c.elem_tile / 4);
+  const int vend = min(v0 + c.elem_tile / 4, (P.L + 3) >> 2);
   if (P.type == T_G) {
     const float gl = expf(P.p[0]), gr = expf(P.p[1]);
     for (int v = v0 + threadIdx.x; v < vend; v += blockDim.x) {
@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(256) k_gs_bwd(LaunchCtx c, const Item* __restr
   const float4* gr4 = reinterpret_cast<const float4*>(P.dy + P.ld);
   float4* dl = reinterpret_cast<float4*>(P.du);
   float4* dr = reinterpret_cast<float4*>(P.du + P.ld);
-  const int v0 = it.idx * (kElemTile / 4);
-  const int vend = min(v0 + kElemTile / 4, (P.L + 3) >> 2);
+  const int v0 = it.idx * (c.elem_tile / 4);
+  const int vend = min(v0 + c.elem_tile / 4, (P.L + 3) >> 2);
   float acc[2] = {0.f, 0.f};
   if (P.type == T_G) {
     const float kl = wd + w * expf(P.p[0]), kr = wd + w * expf(P.p[1]);
@@ -103,12 +103,12 @@ __global__ void __launch_bounds__(256) k_gs_bwd(LaunchCtx c, const Item* __restr
 
 // Eq. (3) sums: out[s] = sum over its inputs (mix node m and output node o).
 __global__ void __launch_bounds__(256) k_sum(float* const* outs, const float* const* ins, const int* in_beg,
-                                             const int* Ls, const int* lds, const Item* items) {
+                                             const int* Ls, const int* lds, const Item* items, int tile) {
   const Item it = items[blockIdx.x];
   const int s = it.proc, L = Ls[s], ld = lds[s];
   const int beg = in_beg[s], end = in_beg[s + 1];
-  const int v0 = it.idx * (kElemTile / 4);
-  const int vend = min(v0 + kElemTile / 4, (L + 3) >> 2);
+  const int v0 = it.idx * (tile / 4);
+  const int vend = min(v0 + tile / 4, (L + 3) >> 2);
   float4* ol = reinterpret_cast<float4*>(outs[s]);
   float4* orr = reinterpret_cast<float4*>(outs[s] + ld);
   for (int v = v0 + threadIdx.x; v < vend; v += blockDim.x) {
@@ -149,8 +149,8 @@ void launch_gs_bwd(const LaunchCtx& c, const Item* items, int n) {
   if (n) k_gs_bwd<<<n, 256, 0, c.stream>>>(c, items);
 }
 void launch_sum(cudaStream_t st, float* const* outs, const float* const* ins, const int* in_beg, const int* L,
-                const int* ld, const Item* items, int n) {
-  if (n) k_sum<<<n, 256, 0, st>>>(outs, ins, in_beg, L, ld, items);
+                const int* ld, const Item* items, int n, int tile) {
+  if (n) k_sum<<<n, 256, 0, st>>>(outs, ins, in_beg, L, ld, items, tile);
 }
 void launch_ingest(cudaStream_t st, const float* mono, float* stereo, int L, int ld) {
   k_ingest<<<min(1024, (L + 255) / 256), 256, 0, st>>>(mono, stereo, L, ld);

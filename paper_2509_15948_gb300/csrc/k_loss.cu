@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
     float out[6];
     block_sum<6>(acc, red, out);
     if (threadIdx.x == 0) {
-      // partial row: the items of one (song, resolution) cover consecutive groups of 8192 / n_fft frames
-      const int row = (t0 - S.first_frame[it.y]) / (8192 >> R.log_nfft);
+      // partial row: the items of one (song, resolution) cover consecutive groups of R.per frames
+      const int row = (t0 - S.first_frame[it.y]) / R.per;
       for (int j = 0; j < 6; ++j) S.lpart[((size_t)it.y * S.lcap + row) * 6 + j] = out[j];
     }
     return;

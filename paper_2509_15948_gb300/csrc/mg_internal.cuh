@@ -28,7 +28,9 @@ constexpr int kRevBins = 193;
 constexpr int kRevParams = 192;
 constexpr int kRevFG = 16;                 // frames per reverb work item
 constexpr int kDynChunk = 4096;            // samples per envelope-scan work item (256 threads x 16)
-constexpr int kElemTile = 4096;            // samples per elementwise work item
+constexpr int kElemTile = 4096;            // samples per elementwise work item (default; tuned per console)
+constexpr int kElemTileMin = 1024;         // smallest candidate of the packing tuner
+constexpr int kLossPerDiv = 4;             // loss work items hold 8192 / n_fft frames, or down to a quarter of that
 constexpr float kEnvEps = 1e-8f;           // G_u = ln(g + eps)
 constexpr int kLossFrameBuf = 8192 + 512 + 128;   // padded frames of one loss work item (float2)
 // floats of the loss adjoint's band gradients that fit next to the frames in the 227 KB of shared memory a
@@ -89,6 +91,7 @@ struct ProcDev {
 
 struct LossRes {                           // one STFT resolution of Eq. (21)
   int nfft, log_nfft, hop, nbands;
+  int per;                                 // frames per work item (at most 8192 / nfft; packing tuner)
   const float* win;                        // [nfft] periodic Hann
   const float* aw2;                        // [nfft/2+1] squared A-weighting gain
   const int* band_beg;                     // [nbands+1] CSR over (bin, weight) by band
@@ -141,6 +144,7 @@ struct LaunchCtx {
   const float* hyper;                      // device: 0 alpha_p, 1 lr, 2 beta1, 3 beta2, 4 eps, 5 weight decay
   float alpha_g;
   double fs;
+  int elem_tile;                           // samples per work item of the gain/pan and imager kernels
   Tables tab;
 };
 
@@ -148,7 +152,7 @@ struct LaunchCtx {
 void launch_gs_fwd(const LaunchCtx&, const Item* items, int n);
 void launch_gs_bwd(const LaunchCtx&, const Item* items, int n);
 void launch_sum(cudaStream_t, float* const* outs, const float* const* ins, const int* in_beg, const int* L,
-                const int* ld, const Item* items, int n);
+                const int* ld, const Item* items, int n, int tile);
 void launch_ingest(cudaStream_t, const float* mono, float* stereo, int L, int ld);
 // envelope scans
 void launch_dyn_fwd_agg(const LaunchCtx&, const Item* items, int n);

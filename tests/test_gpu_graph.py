@@ -76,10 +76,13 @@ def _la_floor(oracle, mix, la):
     return abs(float(OL.audio_loss(m + noise, oracle.target, oracle.desc.loss)["a"]) - la)
 
 
-@pytest.mark.parametrize("seed", [1, 2])
+@pytest.mark.parametrize("seed", [1, 2, 4])
 def test_random_graph_matches_oracle(seed):
     """A seeded random DAG (3 inputs, 14 processors of every type, 2 mix nodes, nodes with up to three inputs
-    and several outputs read): mix, losses and gradients against the FP64 graph oracle."""
+    and several outputs read): mix, losses and gradients against the FP64 graph oracle.  Seed 1's ground truth
+    keeps no stereo processor, so its target is exactly mono: the target's side channel is the 1e-8 magnitude
+    floor of Eq. (21), which FP32 roundoff of the packed transform (the side spectrum formed as X_L - X_R) reaches,
+    so L_s, and L_a and the total that contain it, are not compared there (as for mono consoles)."""
     ntype, track, edges = random_dag(3, 14, 2, seed)
     L = 30011
     src, tgt, noise, oracle, params, ptypes = _oracle_case(ntype, track, edges, 3, L, seed)
@@ -93,7 +96,10 @@ def test_random_graph_matches_oracle(seed):
     gg = con.get_grads().cpu().numpy()
     assert rel_l2(mixes[0].cpu().numpy(), omix) <= MIX_TOL
     floor = _la_floor(oracle, omix, ol[0, 0])
+    mono_target = np.array_equal(tgt[0], tgt[1])
     for j, name in enumerate(("La", "Llr", "Lm", "Ls")):
+        if mono_target and name in ("La", "Ls"):
+            continue
         tol = LOSS_TOL * abs(ol[0, j]) + floor if name == "La" else SET_TOL * abs(ol[0, j])
         assert abs(gl[j] - ol[0, j]) <= tol, (name, gl[j], ol[0, j])
     assert abs(gl[4] - ol[0, 4]) <= LOSS_TOL * sum(t in "erd" for t in ptypes)      # L_g, per LTI node
