@@ -163,6 +163,14 @@ mg_status mg_prune_scores(mg_console* c, const uint8_t* d_masks, int32_t n_masks
 /* 0: batched scoring (default); 1: one full masked render per mask (stream-ordered, no host synchronisation). */
 mg_status mg_set_score_mode(mg_console* c, int32_t mode);
 
+/* Test hook of the compressor / gate scans (the paper has no counterpart).  Their chunks pass the envelope state
+ * from one CTA to the next; every wait for a neighbour's state is bounded (about half a second), after which the
+ * kernel sets an error word and continues with a zero state, and the next mg_forward_loss, mg_backward,
+ * mg_train_step or mg_prune_scores returns MG_ERR_TIMEOUT.  With on = 1 the first chunk of every such launch does
+ * not publish its state, so that the wait of the second chunk runs out; on = 0 restores normal operation and
+ * clears a reported timeout.  The console stays usable throughout. */
+mg_status mg_debug_chain_hold(mg_console* c, int32_t on);
+
 /* One Adam step (Sec. 5.1; Kingma-Ba bias correction, decoupled weight decay) on all parameters with the
  * gradients of the last mg_backward.  Moments start at zero after create / mg_reset_optimizer. */
 mg_status mg_adam_step(mg_console* c, float lr, float beta1, float beta2, float eps, float weight_decay);

@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH):
         "mg_update_audio": [P, I32, P, P, I32],
         "mg_set_launch_mode": [P, I32],
         "mg_set_score_mode": [P, I32],
+        "mg_debug_chain_hold": [P, I32],
         "mg_set_profiling": [P, I32],
         "mg_get_kernel_times": [P, P, P, I32],
         "mg_reset_kernel_times": [P],
@@ -478,6 +479,10 @@ class Console:
 
     def set_launch_mode(self, per_node: bool):
         self._check(self.lib.mg_set_launch_mode(self.h, int(per_node)))
+
+    def debug_chain_hold(self, on: bool):
+        """Test hook: the first chunk of every envelope-scan launch withholds its state (see mixgraph.h)."""
+        self._check(self.lib.mg_debug_chain_hold(self.h, int(on)))
 
     def set_score_mode(self, full_renders: bool):
         """prune_scores: False batches the masks over one base render (default); True renders every mask in full."""

@@ -55,7 +55,8 @@ struct HostProc {
   int nfcap = 0;                 // partial-sum rows allocated (the largest column-item count of the candidate splits)
   std::vector<int> splits;       // candidate row exponents logN1 of the FFT convolution (autotuner)
   // arena offsets (bytes)
-  size_t o_y = 0, o_stats = 0, o_fpart = 0, o_bpart = 0, o_taps = 0, o_dtaps = 0, o_aux = 0, o_carry = 0, o_rcarry = 0,
+  size_t o_cflag = 0;        // published states of the chained scans (c, n)
+  size_t o_y = 0, o_stats = 0, o_fpart = 0, o_bpart = 0, o_taps = 0, o_dtaps = 0, o_aux = 0, o_carry = 0,
          o_cagg = 0, o_nspec = 0, o_hspec = 0, o_ybar = 0, o_dhspec = 0, o_eqg = 0;
   size_t scratch_bytes = 0;  // T1 + T2 + Hz
   size_t o_scratch = 0;      // offset inside the shared LTI scratch
@@ -115,6 +116,8 @@ struct Stage {
   int level, type;
   ProcList procs;
   ItemList elem;                 // g, s, c, n (tile / chunk items)
+  ItemList elem_rev;             // c, n: chunk items in reverse order per node (the chained backward)
+  ItemList chain_f, chain_b;     // c, n: the same chunks in rounds across nodes (batched launches)
   ItemList osf, osb;             // e: overlap-save blocks of the forward and backward kernels
   std::vector<LtiGroup> groups;  // e, r, d
 };
@@ -181,6 +184,10 @@ struct mg_console {
   size_t o_zero = 0;
   int score_mode = 0;              // 0: batched candidate scoring, 1: one full masked render per candidate
   int elem_tile = kElemTile;       // samples per work item of the elementwise kernels and sums (packing tuner)
+  unsigned* d_chain = nullptr;     // launch generation and work ticket of the chained scans
+  int* h_err = nullptr;            // host-mapped error word of the chained scans' bounded waits
+  int* d_err = nullptr;
+  int chain_hold = 0;              // test hook (mg_debug_chain_hold)
   int loss_per[3] = {0, 0, 0};     // frames per loss work item per resolution (packing tuner; 0: 8192 / n_fft)
   bool debug_sync = false;         // MG_DEBUG_SYNC=1 in the environment: synchronise and check after every launch
   bool debug_reported = false;
@@ -647,6 +654,9 @@ LaunchCtx make_ctx(mg_console* c, const uint8_t* mask) {
   x.alpha_g = c->desc.alpha_g;
   x.fs = c->desc.sample_rate;
   x.elem_tile = c->elem_tile;
+  x.chain = c->d_chain;
+  x.err = c->d_err;
+  x.chain_hold = c->chain_hold;
   x.tab = c->tab;
   return x;
 }
@@ -702,9 +712,7 @@ void stage_forward(mg_console* c, const LaunchCtx& x, Stage& s) {
       break;
     case T_C:
     case T_N:
-      run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd_agg(x, it, n); });
-      run_procs(c, F_DYN_FWD, s.procs, [&](const int* p, int n) { launch_dyn_fwd_carry(x, p, n); });
-      run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd_apply(x, it, n); });
+      run_items(c, F_DYN_FWD, c->per_node ? s.elem : s.chain_f, [&](const Item* it, int n) { launch_dyn_fwd(x, it, n); });
       break;
     case T_E:
       run_procs(c, F_EQ_FIR, s.procs, [&](const int* p, int n) { launch_eq_fir(x, p, n); });
@@ -725,9 +733,7 @@ void stage_backward(mg_console* c, const LaunchCtx& x, Stage& s) {
       break;
     case T_C:
     case T_N:
-      run_items(c, F_DYN_BWD, s.elem, [&](const Item* it, int n) { launch_dyn_bwd_agg(x, it, n); });
-      run_procs(c, F_DYN_BWD, s.procs, [&](const int* p, int n) { launch_dyn_bwd_carry(x, p, n); });
-      run_items(c, F_DYN_BWD, s.elem, [&](const Item* it, int n) { launch_dyn_bwd_apply(x, it, n); });
+      run_items(c, F_DYN_BWD, c->per_node ? s.elem_rev : s.chain_b, [&](const Item* it, int n) { launch_dyn_bwd(x, it, n); });
       break;
     case T_E:
       run_items(c, F_EQ_OS_BWD, s.osb, [&](const Item* it, int n) { launch_eq_os_bwd(x, it, n); });
@@ -901,11 +907,30 @@ void fill_procdev(mg_console* c, int pi) {
   }
   d.aux = p.o_aux ? (float*)A(p.o_aux) : nullptr;
   d.carry = p.nchunks ? (float*)A(p.o_carry) : nullptr;
-  d.rcarry = p.nchunks ? (float*)A(p.o_rcarry) : nullptr;
   d.chunkagg = p.nchunks ? (float*)A(p.o_cagg) : nullptr;
+  d.cflag = p.nchunks ? (unsigned long long*)A(p.o_cflag) : nullptr;
   d.nchunks = p.nchunks;
   d.nspec = p.type == T_R ? (const float2*)A(p.o_nspec) : nullptr;
   d.nframes = p.nframes;
+}
+
+// Chunk items of the chained envelope scans in rounds: round r holds chunk r (forward) or chunk n - 1 - r
+// (backward) of every node with more than r chunks.  Consecutive tickets then belong to different nodes, and the
+// chunk whose state a CTA waits for was drawn a round earlier; in node-major order the resident CTAs would all
+// be consecutive chunks of one node and wait on each other in turn.
+template <class F>
+void chain_rounds(const std::vector<int>& procs, F&& nchunks, ItemList& fwd, ItemList* rev) {
+  int rounds = 0;
+  for (int p : procs) rounds = std::max(rounds, nchunks(p));
+  for (int r = 0; r < rounds; ++r)
+    for (int p : procs) {
+      const int n = nchunks(p);
+      if (r >= n) continue;
+      fwd.h.push_back(Item{p, r});
+      if (rev) rev->h.push_back(Item{p, n - 1 - r});
+    }
+  fwd.beg = {0, (int)fwd.h.size()};
+  if (rev) rev->beg = {0, (int)rev->h.size()};
 }
 
 // Work lists of one stage (st.level, st.type, st.procs.h set): tiles or scan chunks, overlap-save blocks, or LTI
@@ -916,11 +941,19 @@ mg_status make_stage(mg_console* c, Stage& st) {
   if (t == T_G || t == T_S || t == T_C || t == T_N) {
     for (int pi : st.procs.h) {
       st.elem.beg.push_back((int)st.elem.h.size());
+      st.elem_rev.beg.push_back((int)st.elem_rev.h.size());
       const int nt = (t == T_C || t == T_N) ? c->procs[pi].nchunks : c->procs[pi].nbrows;
       for (int i = 0; i < nt; ++i) st.elem.h.push_back(Item{pi, i});
+      if (t == T_C || t == T_N)
+        for (int i = nt - 1; i >= 0; --i) st.elem_rev.h.push_back(Item{pi, i});
     }
     st.elem.beg.push_back((int)st.elem.h.size());
-    if (upload_items(c, st.elem) || upload_procs(c, st.procs)) return MG_ERR_CUDA;
+    st.elem_rev.beg.push_back((int)st.elem_rev.h.size());
+    if (t == T_C || t == T_N)
+      chain_rounds(st.procs.h, [&](int pi) { return c->procs[pi].nchunks; }, st.chain_f, &st.chain_b);
+    if (upload_items(c, st.elem) || upload_items(c, st.elem_rev) || upload_items(c, st.chain_f) ||
+        upload_items(c, st.chain_b) || upload_procs(c, st.procs))
+      return MG_ERR_CUDA;
   } else if (t == T_E) {
     // equalizer: overlap-save blocks (forward and backward blockings differ)
     for (int pi : st.procs.h) {
@@ -1279,8 +1312,8 @@ size_t layout_arena(mg_console* c, const mg_console_desc* d, size_t* shared_scra
       p.o_nspec = b.take((size_t)2 * p.nframes * kRevBins * sizeof(float2));
     }
     if (p.nchunks) {
+      p.o_cflag = b.take(p.nchunks * sizeof(unsigned long long));
       p.o_carry = b.take(p.nchunks * sizeof(float));
-      p.o_rcarry = b.take(p.nchunks * sizeof(float));
       p.o_cagg = b.take(p.nchunks * sizeof(float));
     }
   }
@@ -1612,6 +1645,11 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
   CK(cudaMalloc(&c->d_alphas, 4 * sizeof(float)));
   CK(cudaMalloc(&c->d_mask, std::max(1, c->P)));
   CK(cudaMalloc(&c->d_scratch_la, sizeof(float) * std::max<size_t>(1, c->songs.size())));
+  CK(cudaMalloc(&c->d_chain, 2 * sizeof(unsigned)));
+  CK(cudaMemsetAsync(c->d_chain, 0, 2 * sizeof(unsigned), c->stream));
+  CK(cudaHostAlloc(&c->h_err, sizeof(int), cudaHostAllocMapped));
+  *c->h_err = 0;
+  CK(cudaHostGetDevicePointer(&c->d_err, c->h_err, 0));
   CK(cudaMemsetAsync(c->d_params, 0, sizeof(float) * c->nparams, c->stream));
   CK(cudaMemsetAsync(c->d_grads, 0, sizeof(float) * c->nparams, c->stream));
   CK(cudaMemsetAsync(c->d_m, 0, sizeof(float) * c->nparams, c->stream));
@@ -1891,6 +1929,8 @@ void destroy_impl(mg_console* c) {
   cudaFree(c->d_mask);
   cudaFree(c->d_scratch_la);
   cudaFree(c->score_ws);
+  cudaFree(c->d_chain);
+  if (c->h_err) cudaFreeHost(c->h_err);
 }
 
 void fill_info(const mg_console* c, mg_console_info* o) {
@@ -1945,6 +1985,8 @@ struct ScoreChunk {
   std::vector<std::vector<std::pair<char*, const char*>>> promo;   // [candidate][song]: (arena, copy) buffers
   size_t table_begin = 0;                    // workspace offset of the tables (copied from the host blob)
   size_t end = 0;                            // workspace bytes the chunk uses
+  unsigned long long* flags = nullptr;       // published states of the chained scans of the node copies
+  size_t flags_bytes = 0;
   float* vq = nullptr;
   float* vla = nullptr;
   int* d_vsrc = nullptr;
@@ -1966,7 +2008,7 @@ size_t copy_bytes(const mg_console* c, int pi, size_t* items) {
   size_t it = 0;
   if (p.nfrows) b += al((size_t)std::max(p.nfrows, p.nfcap) * kNPart * sizeof(float));
   if (p.type == T_C || p.type == T_N) {
-    b += 2 * al((size_t)p.nchunks * sizeof(float));
+    b += 2 * al((size_t)p.nchunks * sizeof(float)) + (size_t)p.nchunks * sizeof(unsigned long long);   // + states
     it = p.nchunks + 1;
   } else if (p.type == T_G || p.type == T_S) {
     it = p.nbrows;
@@ -2088,6 +2130,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
   k.promo.assign((size_t)(j1 - j0) * ns, {});
   // node copies per (level, type), in candidate order
   std::vector<int> by_lt[2][NTYPES];
+  std::vector<std::pair<int, int>> flag_nodes;   // (node copy, chunks) of the chained scans
   for (int j = j0; j < j1; ++j) {
     const uint8_t* mj = hm + (size_t)j * c->P;
     const CandPlan& cp = plans[j];
@@ -2114,7 +2157,6 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
         d.gp = nullptr;
         d.bpart = nullptr;
         d.dtaps = nullptr;
-        d.rcarry = nullptr;
         d.dhspec = nullptr;
         d.eqg = nullptr;
         d.ybar = p.type == T_E ? (float*)w.buffer((size_t)2 * p.ld * sizeof(float)) : nullptr;
@@ -2122,6 +2164,7 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
           d.carry = (float*)w.buffer((size_t)p.nchunks * sizeof(float));
           d.chunkagg = (float*)w.buffer((size_t)p.nchunks * sizeof(float));
           d.aux = nullptr;
+          flag_nodes.push_back({(int)k.vp.size(), p.nchunks});
         }
         if (p.type == T_R || p.type == T_D) {
           const size_t N = (size_t)p.f << p.logN;
@@ -2199,6 +2242,13 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
   k.m_items.beg.push_back((int)k.m_items.h.size());
   k.o_items.beg.push_back((int)k.o_items.h.size());
   const int V = (int)k.vp.size();
+  // one contiguous region of publication flags, cleared before the chunk runs
+  size_t nflags = 0;
+  for (const auto& fn : flag_nodes) nflags += fn.second;
+  k.flags = (unsigned long long*)w.buffer(sizeof(unsigned long long) * std::max<size_t>(1, nflags));
+  k.flags_bytes = sizeof(unsigned long long) * std::max<size_t>(1, nflags);
+  for (size_t f = 0, off = 0; f < flag_nodes.size(); off += flag_nodes[f].second, ++f)
+    k.vp[flag_nodes[f].first].cflag = k.flags + off;
   k.vq = (float*)w.buffer(sizeof(float) * std::max(1, V));
   k.vla = (float*)w.buffer(sizeof(float) * std::max<size_t>(1, k.vs.size()));
   // work lists per (level, type)
@@ -2213,7 +2263,9 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
       if (t == T_R || t == T_D) st.groups.push_back(LtiGroup{});
       for (int v : by_lt[level][t]) {
         const ProcDev& d = k.vp[v];
-        if (t == T_G || t == T_S || t == T_C || t == T_N) {
+        if ((t == T_C || t == T_N) && !c->per_node) {
+          continue;   // in rounds below
+        } else if (t == T_G || t == T_S || t == T_C || t == T_N) {
           st.elem.beg.push_back((int)st.elem.h.size());
           const int nt = (t == T_C || t == T_N) ? d.nchunks : (d.L + c->elem_tile - 1) / c->elem_tile;
           for (int i = 0; i < nt; ++i) st.elem.h.push_back(Item{v, i});
@@ -2233,6 +2285,8 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
         }
       }
       st.elem.beg.push_back((int)st.elem.h.size());
+      if ((t == T_C || t == T_N) && !c->per_node)
+        chain_rounds(st.procs.h, [&](int v) { return k.vp[v].nchunks; }, st.elem, nullptr);
       st.osf.beg.push_back((int)st.osf.h.size());
       for (auto& g : st.groups) {
         g.col.beg.push_back((int)g.col.h.size());
@@ -2289,7 +2343,8 @@ std::string check_chunk(const mg_console* c, const ScoreChunk& k) {
     if (d.fpart && !in(d.fpart, (size_t)d.nfpart * kNPart * sizeof(float)))
       return "node copy " + std::to_string(v) + ": partials out of range";
     if ((d.type == T_C || d.type == T_N) &&
-        (!in(d.carry, (size_t)d.nchunks * 4) || !in(d.chunkagg, (size_t)d.nchunks * 4)))
+        (!in(d.carry, (size_t)d.nchunks * 4) || !in(d.chunkagg, (size_t)d.nchunks * 4) ||
+         !in(d.cflag, (size_t)d.nchunks * 8)))
       return "node copy " + std::to_string(v) + ": scan carries out of range";
     if (d.type == T_R || d.type == T_D) {
       const size_t N = (size_t)d.f << d.logN;
@@ -2347,9 +2402,7 @@ void vstage_forward(mg_console* c, const LaunchCtx& x, Stage& s) {
       break;
     case T_C:
     case T_N:
-      run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd_agg(x, it, n); });
-      run_procs(c, F_DYN_FWD, s.procs, [&](const int* p, int n) { launch_dyn_fwd_carry(x, p, n); });
-      run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd_apply(x, it, n); });
+      run_items(c, F_DYN_FWD, s.elem, [&](const Item* it, int n) { launch_dyn_fwd(x, it, n); });
       break;
     case T_E:
       run_items(c, F_EQ_OS_FWD, s.osf, [&](const Item* it, int n) { launch_eq_os_fwd(x, it, n); });
@@ -2472,6 +2525,7 @@ mg_status prune_scores_batched(mg_console* c, const uint8_t* d_masks, int n_mask
       CK(cudaMemcpyAsync(c->score_ws + k.table_begin, c->score_blob.data(), c->score_blob.size(),
                          cudaMemcpyHostToDevice, c->stream));
     const int V = (int)k.vp.size();
+    CK(cudaMemsetAsync(k.flags, 0, k.flags_bytes, c->stream));
     LaunchCtx xv = make_ctx(c, k.d_vmask);
     xv.procs = k.d_vp;
     xv.q = k.vq;
@@ -2711,6 +2765,8 @@ mg_status mg_set_alpha_p(mg_console* c, float alpha_p) {
 
 mg_status mg_forward_loss(mg_console* c, const uint8_t* d_mask, float* d_losses, float* d_mix) {
   if (!c) return MG_ERR_INVALID;
+  if (c->h_err && *(volatile int*)c->h_err)
+    return fail(c, MG_ERR_TIMEOUT, "a chained envelope scan waited longer than its limit; the last results are not valid");
   if (d_mask) CK(cudaMemcpyAsync(c->d_mask, d_mask, c->P, cudaMemcpyDeviceToDevice, c->stream));
   LaunchCtx x = make_ctx(c, d_mask ? c->d_mask : nullptr);
   render(c, x);
@@ -2724,6 +2780,8 @@ mg_status mg_forward_loss(mg_console* c, const uint8_t* d_mask, float* d_losses,
 
 mg_status mg_backward(mg_console* c) {
   if (!c) return MG_ERR_INVALID;
+  if (c->h_err && *(volatile int*)c->h_err)
+    return fail(c, MG_ERR_TIMEOUT, "a chained envelope scan waited longer than its limit; the last results are not valid");
   if (!c->fwd_valid) return fail(c, MG_ERR_STATE, "mg_backward needs a preceding unmasked mg_forward_loss with unchanged state");
   LaunchCtx x = make_ctx(c, nullptr);
   backward_pass(c, x);
@@ -2733,6 +2791,8 @@ mg_status mg_backward(mg_console* c) {
 
 mg_status mg_prune_scores(mg_console* c, const uint8_t* d_masks, int32_t n_masks, float* d_la) {
   if (!c || !d_masks || !d_la || n_masks < 0) return fail(c, MG_ERR_INVALID, "null pointer or negative count");
+  if (c->h_err && *(volatile int*)c->h_err)
+    return fail(c, MG_ERR_TIMEOUT, "a chained envelope scan waited longer than its limit; the last results are not valid");
   if (n_masks == 0) return MG_OK;
   mg_status st = MG_OK;
   if (c->per_node || c->score_mode == 1 || c->is_graph) {
@@ -2745,6 +2805,17 @@ mg_status mg_prune_scores(mg_console* c, const uint8_t* d_masks, int32_t n_masks
   }
   c->fwd_valid = false;
   return st;
+}
+
+mg_status mg_debug_chain_hold(mg_console* c, int32_t on) {
+  if (!c) return MG_ERR_INVALID;
+  c->chain_hold = on ? 1 : 0;
+  if (!on && c->h_err) *(volatile int*)c->h_err = 0;   // releasing the hold also clears a reported timeout
+  if (c->graph) {                                      // the captured step holds the old setting
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return MG_OK;
 }
 
 mg_status mg_set_score_mode(mg_console* c, int32_t mode) {
@@ -2773,6 +2844,8 @@ mg_status mg_reset_optimizer(mg_console* c) {
 
 mg_status mg_train_step(mg_console* c, float lr, float beta1, float beta2, float eps, float weight_decay, float* d_losses) {
   if (!c) return MG_ERR_INVALID;
+  if (c->h_err && *(volatile int*)c->h_err)
+    return fail(c, MG_ERR_TIMEOUT, "a chained envelope scan waited longer than its limit; the last results are not valid");
   launch_set_hyper(c->stream, c->d_hyper, 0, lr, beta1, beta2, eps, weight_decay, 1);
   if (c->per_node) {  // one-by-one processing runs eagerly (no graph)
     LaunchCtx x = make_ctx(c, nullptr);

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   }
 
   const float inv_n = ldexpf(1.f, -P.logN) / (float)P.f;
-  // 1/N divided by the channel scales of the two transformed operands (exact: the scales are powers of two)
+  // 1/N divided by the channel scales of the two transformed operands
   const float2 su = chan_scale(P, kScaleU), sh = chan_scale(P, kScaleH), sd = chan_scale(P, kScaleD);
   const float2 inv_uh = make_float2(inv_n / (su.x * sh.x), inv_n / (su.y * sh.y));
   auto unscale = [](float2 v, float2 s) { return make_float2(v.x * s.x, v.y * s.y); };
@@ -221,15 +221,16 @@ __global__ void __launch_bounds__(kColThreads, 2) k_col(LaunchCtx c, const Item*
   }
 }
 
-// Channel scales of one node (one CTA per node): per channel the energy of an evenly spread quarter of the
-// signal's 32-byte sectors (four consecutive samples out of every 32) or of every 8th tap (the scale only needs the
-// order of magnitude), and the power of two s = 2^-floor(e / 2),
-// e the binary exponent of that energy, which brings the channel near unit energy; 1 for a silent channel.
+// Channel scales of one node (one CTA per node): per channel the energy of four consecutive samples out of every
+// 128, and of the taps: every 32nd tap of the reverb's dense FIR, all 20 x 39 nonzero taps c_m of the delay's
+// sparse one (a stride would miss whole 39-tap windows).  The scale s = 1/sqrt(e) brings that energy to one, so
+// both channels of a packed transform sit at the same level up to the sampling error of the estimate; 1 for a
+// silent channel.  (Power-of-two scales, exact to apply, left the channels up to 2x apart in amplitude, and the
+// weaker channel's error moved by that factor with the estimate's rounding.)
 // which 0: the input u and the taps (in the stereo form the transforms use); 1: dL/dy.  Fixed-order sums.
-__device__ __forceinline__ float pow2_scale(float e) {
+__device__ __forceinline__ float unit_scale(float e) {
   if (!(e > 0.f) || !isfinite(e)) return 1.f;
-  const int x = ilogbf(e);
-  return ldexpf(1.f, -((x >= 0 ? x : x - 1) / 2));
+  return 1.f / sqrtf(e);
 }
 
 __global__ void __launch_bounds__(256) k_chan_scale(LaunchCtx c, const int* __restrict__ procs, int which) {
@@ -240,21 +241,27 @@ __global__ void __launch_bounds__(256) k_chan_scale(LaunchCtx c, const int* __re
   // self-check of the operands: a missing or misaligned signal, a row stride shorter than the signal, or missing
   // taps skip the node (its scales stay as they were) and are reported
   if (x == nullptr || ((uintptr_t)x & 15) != 0 || P.ld < P.L || (P.ld & 3) != 0 || P.stats == nullptr ||
-      (which == 0 && P.taps == nullptr)) {
+      (which == 0 && P.taps == nullptr) || (which == 0 && P.type == T_D && P.aux == nullptr)) {
     if (threadIdx.x == 0)
       printf("k_chan_scale: node %d which %d skipped (x %p, L %d, ld %d, taps %p, stats %p)\n", procs[blockIdx.x], which,
              (const void*)x, P.L, P.ld, (const void*)P.taps, (const void*)P.stats);
     return;
   }
   const int nq = P.L >> 2;                    // whole quads of samples
-  for (int q = threadIdx.x * 8; q < nq; q += blockDim.x * 8) {
+  for (int q = threadIdx.x * 32; q < nq; q += blockDim.x * 32) {   // every 32nd quad
     const float4 a = reinterpret_cast<const float4*>(x)[q];
     const float4 b = reinterpret_cast<const float4*>(x + P.ld)[q];
     acc[0] += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
     acc[1] += b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w;
   }
-  if (which == 0)
-    for (int j = threadIdx.x * 8; j < P.Nh; j += blockDim.x * 8) {   // every 8th tap
+  if (which == 0 && P.type == T_D) {
+    for (int j = threadIdx.x; j < kDlyTaps * kDlyFir; j += blockDim.x) {   // c_m of both channels
+      const float a = P.aux[j], b = P.aux[kDlyTaps * kDlyFir + j];
+      acc[2] += a * a;
+      acc[3] += b * b;
+    }
+  } else if (which == 0)
+    for (int j = threadIdx.x * 32; j < P.Nh; j += blockDim.x * 32) {   // every 32nd tap
       const float2 t = tap_at(P, (int64_t)j + P.n0 >= 0 ? (int64_t)j + P.n0 : fft_len(P) + j + P.n0, fft_len(P));
       acc[2] += t.x * t.x;
       acc[3] += t.y * t.y;
@@ -263,13 +270,13 @@ __global__ void __launch_bounds__(256) k_chan_scale(LaunchCtx c, const int* __re
   block_sum<4>(acc, red, out);
   if (threadIdx.x == 0) {
     if (which == 0) {
-      P.stats[kScaleU] = pow2_scale(out[0]);
-      P.stats[kScaleU + 1] = pow2_scale(out[1]);
-      P.stats[kScaleH] = pow2_scale(out[2]);
-      P.stats[kScaleH + 1] = pow2_scale(out[3]);
+      P.stats[kScaleU] = unit_scale(out[0]);
+      P.stats[kScaleU + 1] = unit_scale(out[1]);
+      P.stats[kScaleH] = unit_scale(out[2]);
+      P.stats[kScaleH + 1] = unit_scale(out[3]);
     } else {
-      P.stats[kScaleD] = pow2_scale(out[0]);
-      P.stats[kScaleD + 1] = pow2_scale(out[1]);
+      P.stats[kScaleD] = unit_scale(out[0]);
+      P.stats[kScaleD + 1] = unit_scale(out[1]);
     }
   }
 }

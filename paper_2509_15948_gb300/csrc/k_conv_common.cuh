@@ -11,9 +11,9 @@
 // Both channels travel as one complex signal z = left + i right; a stereo FIR (h_l, h_r) acts on the packed
 // spectrum as Y[k] = Z[k] A[k] + conj(Z[-k]) B[k] with A = (H_l + H_r)/2, B = (H_l - H_r)/2, where the
 // mirror bin -k sits in row N2 - k2.  The rounding error of a packed transform scales with the larger channel,
-// so before packing every channel of u, of the taps and of dL/dy_bar is multiplied by a power of two that
-// brings the channels to a common level (k_chan_scale); the products are bilinear per channel, and the output
-// passes divide by the product of the scales involved, exactly.
+// so before packing every channel of u, of the taps and of dL/dy_bar is multiplied by a scale that brings the
+// channels to a common level (k_chan_scale); the products are bilinear per channel, and the output passes
+// divide by the product of the scales involved (two roundings, far below the transforms' own).
 #pragma once
 #include <algorithm>
 
@@ -71,7 +71,7 @@ __device__ __forceinline__ float2 tap_at(const ProcDev& P, int64_t n, int64_t N)
   return make_float2(a, b);
 }
 
-// Channel scales of a packed transform (left, right): powers of two set by k_chan_scale, or 1 before it ran.
+// Channel scales of a packed transform (left, right), set by k_chan_scale; 1 before it ran.
 __device__ __forceinline__ float2 chan_scale(const ProcDev& P, int slot) {
   const float a = P.stats[slot], b = P.stats[slot + 1];
   return make_float2(a > 0.f ? a : 1.f, b > 0.f ? b : 1.f);

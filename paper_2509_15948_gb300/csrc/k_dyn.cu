@@ -1,13 +1,18 @@
 // Compressor (Sec. 3.5) and noisegate (Sec. 3.6): the exact one-pole envelope recursion of Eq. (11),
-// g[n] = alpha g[n-1] + (1 - alpha) x[n], x = (u_l + u_r)^2, evaluated as a chunked linear scan:
-//   pass 1 (agg):   every 4096-sample chunk computes its zero-start end state,
-//   pass 2 (carry): one thread per node chains the chunk states (g entering each chunk),
-//   pass 3 (apply): every chunk rescans from its carried state with a warp-shuffle scan of the
-//                   per-thread states (decay alpha^16 per thread), then applies the gain law
-//                   (Eqs. 13-16) and Eq. (15), fused with the dry/wet blend.
-// The adjoint runs the same structure in reverse: lambda[n] = dL/dg[n] + alpha lambda[n+1].  Its first pass
-// also does all the per-sample work that does not depend on lambda (the gain law, its partials, dL/dg and
-// the lambda-free part of du, kept in global memory), so the third pass is only the two recursions.
+// g[n] = alpha g[n-1] + (1 - alpha) x[n], x = (u_l + u_r)^2, evaluated as a chained single-pass scan over chunks
+// of 4096 samples.  CTAs take chunks in list order from a launch-wide ticket, so the chunk a CTA depends on was
+// taken earlier by a CTA that is running or finished.  A CTA
+//   1. computes its chunk's zero-start end state (a warp-shuffle scan of the per-thread states, decay alpha^16
+//      per thread),
+//   2. waits (bounded) for the state entering its chunk, published by the CTA of the previous chunk, and
+//      publishes the state entering the next chunk, g_next = A g_in + agg (A = alpha^4096); the stage's chunks are
+//      listed in rounds across nodes, so that wait is normally over before it starts,
+//   3. rescans its chunk from that state and applies the gain law (Eqs. 13-16) and Eq. (15), fused with the
+//      dry/wet blend; it re-reads its own input, which the first step brought into L2.
+// The adjoint runs the same way in reverse: lambda[n] = dL/dg[n] + alpha lambda[n+1], chunks in reverse order.
+// Its first step also does the per-sample work that does not depend on lambda (the gain law, its partials,
+// dL/dg and the lambda-free part of du), staged in global memory for the same CTA's last step.  A wait that
+// runs out (about half a second) sets a host-visible error word and continues with a zero state.
 #include "mg_fft.cuh"
 
 namespace mg {
@@ -214,9 +219,60 @@ __device__ __forceinline__ float scan_rev_excl(float r, float lna, float carry, 
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) k_dyn_fwd_agg(LaunchCtx c, const Item* __restrict__ items) {
+constexpr long long kChainWaitCycles = 1000000000LL;   // about half a second at the SM clock
+
+__global__ void k_chain_begin(unsigned* chain) {
+  chain[0] += 1u;   // a new launch generation: flags of earlier launches no longer match
+  chain[1] = 0u;    // the work ticket
+}
+
+// Work item of this CTA in ticket order (thread 0 draws, the block reads it after the barrier).
+__device__ __forceinline__ Item take_item(const LaunchCtx& c, const Item* items, int* s_idx, unsigned* s_gen) {
+  if (threadIdx.x == 0) {
+    *s_idx = (int)atomicAdd(&c.chain[1], 1u);
+    *s_gen = *(volatile unsigned*)&c.chain[0];
+  }
+  __syncthreads();
+  return items[*s_idx];
+}
+
+// Thread 0: the state entering chunk k (0 for the first chunk of the direction), once the CTA of the neighbouring
+// chunk has published it; then the state entering the next chunk, published for its CTA.  A published state is one
+// 64-bit word, the launch generation in the high half and the float's bits in the low half, written and read as a
+// whole: the value arrives with its flag, and no fence is needed between them.  keep (forward only) receives the
+// state entering chunk k for the backward.
+__device__ __forceinline__ float chain_link(const LaunchCtx& c, const ProcDev& P, int k, int next, bool first,
+                                            float agg, float A, unsigned gen, bool hold, float* keep) {
+  float in = 0.f;
+  if (!first) {
+    volatile unsigned long long* f = P.cflag + k;
+    const long long t0 = clock64();
+    unsigned long long w = *f;
+    while ((unsigned)(w >> 32) != gen) {
+      if (clock64() - t0 > kChainWaitCycles) {
+        *(volatile int*)c.err = 1;
+        w = 0ull;   // continue from a zero state
+        break;
+      }
+      __nanosleep(32);
+      w = *f;
+    }
+    in = __uint_as_float((unsigned)w);
+  }
+  if (next >= 0 && next < P.nchunks && !hold)
+    *(volatile unsigned long long*)(P.cflag + next) =
+        ((unsigned long long)gen << 32) | __float_as_uint(fmaf(A, in, agg));
+  if (keep) keep[k] = in;
+  return in;
+}
+
+// Forward: chunk aggregate, chained state, rescan with the gain law.
+__global__ void __launch_bounds__(kThreads, 4) k_dyn_fwd(LaunchCtx c, const Item* __restrict__ items) {
   __shared__ float red[32];
-  const Item it = items[blockIdx.x];
+  __shared__ int s_idx;
+  __shared__ unsigned s_gen;
+  __shared__ float s_in;
+  const Item it = take_item(c, items, &s_idx, &s_gen);
   const ProcDev& P = c.procs[it.proc];
   const DynParams d = dyn_params(P);
   const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
@@ -231,38 +287,14 @@ __global__ void __launch_bounds__(kThreads) k_dyn_fwd_agg(LaunchCtx c, const Ite
   float v[1] = {s * expf((float)(kPer * (kThreads - 1 - (int)threadIdx.x)) * d.lna)};
   float out[1];
   block_sum<1>(v, red, out);
-  if (threadIdx.x == 0) P.chunkagg[it.idx] = out[0];
-}
-
-__global__ void k_dyn_fwd_carry(LaunchCtx c, const int* __restrict__ procs, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const ProcDev& P = c.procs[procs[i]];
-  const DynParams d = dyn_params(P);
-  const float A = expf((float)kDynChunk * d.lna);
-  float g = 0.f;
-  for (int k = 0; k < P.nchunks; ++k) {
-    P.carry[k] = g;
-    g = A * g + P.chunkagg[k];
+  if (threadIdx.x == 0) {
+    const float A = expf((float)kDynChunk * d.lna);
+    s_in = chain_link(c, P, it.idx, it.idx + 1, it.idx == 0, out[0], A, s_gen, c.chain_hold && s_idx == 0, P.carry);
   }
-}
-
-__global__ void __launch_bounds__(kThreads, 4) k_dyn_fwd_apply(LaunchCtx c, const Item* __restrict__ items) {
-  __shared__ float sm[16];
-  const Item it = items[blockIdx.x];
-  const ProcDev& P = c.procs[it.proc];
-  const DynParams d = dyn_params(P);
+  __syncthreads();
   const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
-  const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
-  float l[kPer], r[kPer];
-  load16(P.u, P.ld, P.L, n0, l, r);
-  float s = 0.f;
-#pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const float m = l[j] + r[j];
-    s = d.alpha * s + d.beta * (m * m);
-  }
-  float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
+  float g = scan_fwd_excl(s, d.lna, s_in, red);
+  load16(P.u, P.ld, P.L, n0, l, r);   // again, from L2
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const float m = l[j] + r[j];
@@ -295,74 +327,61 @@ __device__ __forceinline__ float dyn_dg(const DynParams& d, float w, float g, fl
   return dE * (dG - 1.f) * __frcp_rn(g + kEnvEps);
 }
 
-// Backward, pass 1: everything that does not depend on lambda.  Per sample dL/dg (to aux) and the part of du
-// without the envelope term, w.r.t. both channels (to du); per chunk the zero-start lambda aggregate and the
-// partials of dL/dT, dL/dW, dL/dR and dL/dw.
-__global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_agg(LaunchCtx c, const Item* __restrict__ items) {
+// Backward.  Step 1, everything that does not depend on lambda: per sample dL/dg (to aux) and the part of du
+// without the envelope term (to du), the partials of dL/dT, dL/dW, dL/dR and dL/dw, and the chunk's zero-start
+// lambda aggregate.  Step 2, the chained lambda state from the right.  Step 3: lambda[n] = dL/dg[n] +
+// alpha lambda[n+1] from that state, du += 2 beta lambda m on both channels, and the partial of
+// dL/dalpha = sum lambda[n] (g[n-1] - x[n]); u, aux and du come back from L2.
+__global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd(LaunchCtx c, const Item* __restrict__ items) {
   __shared__ float sm[32 * 5];
-  const Item it = items[blockIdx.x];
+  __shared__ int s_idx;
+  __shared__ unsigned s_gen;
+  __shared__ float s_in;
+  const Item it = take_item(c, items, &s_idx, &s_gen);
   const ProcDev& P = c.procs[it.proc];
   const DynParams d = dyn_params(P);
   const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
-  float l[kPer], r[kPer], gl[kPer], gr[kPer];
-  load16(P.u, P.ld, P.L, n0, l, r);
-  load16(P.dy, P.ld, P.L, n0, gl, gr);
-  float s = 0.f;
+  {
+    float l[kPer], r[kPer], gl[kPer], gr[kPer];
+    load16(P.u, P.ld, P.L, n0, l, r);
+    load16(P.dy, P.ld, P.L, n0, gl, gr);
+    float s = 0.f;
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const float m = l[j] + r[j];
-    s = d.alpha * s + d.beta * (m * m);
-  }
-  float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
-  float dg[kPer];
-  DynAdj acc = {0.f, 0.f, 0.f, 0.f};
+    for (int j = 0; j < kPer; ++j) {
+      const float m = l[j] + r[j];
+      s = d.alpha * s + d.beta * (m * m);
+    }
+    float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
+    float dg[kPer];
+    DynAdj acc = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const float m = l[j] + r[j];
-    g = d.alpha * g + d.beta * (m * m);
-    float gain;
-    dg[j] = dyn_dg(d, w, g, l[j], r[j], gl[j], gr[j], gain, acc);
-    l[j] = wd * gl[j] + gain * (w * gl[j]);
-    r[j] = wd * gr[j] + gain * (w * gr[j]);
-  }
-  store16(P.du, P.ld, P.L, n0, l, r);
-  store16m(P.aux, P.L, n0, dg);
-  float lam = 0.f;
+    for (int j = 0; j < kPer; ++j) {
+      const float m = l[j] + r[j];
+      g = d.alpha * g + d.beta * (m * m);
+      float gain;
+      dg[j] = dyn_dg(d, w, g, l[j], r[j], gl[j], gr[j], gain, acc);
+      l[j] = wd * gl[j] + gain * (w * gl[j]);
+      r[j] = wd * gr[j] + gain * (w * gr[j]);
+    }
+    store16(P.du, P.ld, P.L, n0, l, r);
+    store16m(P.aux, P.L, n0, dg);
+    float lam = 0.f;
 #pragma unroll
-  for (int j = kPer - 1; j >= 0; --j) lam = dg[j] + d.alpha * lam;
-  float v[5] = {lam * expf((float)(kPer * threadIdx.x) * d.lna), acc.dT, acc.dW, acc.dR, acc.dw};
-  float out[5];
-  block_sum<5>(v, sm, out);
-  if (threadIdx.x == 0) {
-    P.chunkagg[it.idx] = out[0];
-    float* bp = P.bpart + (size_t)it.idx * kNPart;
+    for (int j = kPer - 1; j >= 0; --j) lam = dg[j] + d.alpha * lam;
+    float v[5] = {lam * expf((float)(kPer * threadIdx.x) * d.lna), acc.dT, acc.dW, acc.dR, acc.dw};
+    float out[5];
+    block_sum<5>(v, sm, out);
+    if (threadIdx.x == 0) {
+      float* bp = P.bpart + (size_t)it.idx * kNPart;
 #pragma unroll
-    for (int j = 1; j < 5; ++j) bp[j] = out[j];
+      for (int j = 1; j < 5; ++j) bp[j] = out[j];
+      const float A = expf((float)kDynChunk * d.lna);
+      s_in = chain_link(c, P, it.idx, it.idx - 1, it.idx == P.nchunks - 1, out[0], A, s_gen,
+                        c.chain_hold && s_idx == 0, nullptr);
+    }
   }
-}
-
-__global__ void k_dyn_bwd_carry(LaunchCtx c, const int* __restrict__ procs, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const ProcDev& P = c.procs[procs[i]];
-  const DynParams d = dyn_params(P);
-  const float A = expf((float)kDynChunk * d.lna);
-  float lam = 0.f;
-  for (int k = P.nchunks - 1; k >= 0; --k) {
-    P.rcarry[k] = lam;
-    lam = P.chunkagg[k] + A * lam;
-  }
-}
-
-// Backward, pass 3: lambda[n] = dL/dg[n] + alpha lambda[n+1] from the chunk's carried state, then
-// du += 2 beta lambda m on both channels and the partial of dL/dalpha = sum lambda[n] (g[n-1] - x[n]).
-__global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_apply(LaunchCtx c, const Item* __restrict__ items) {
-  __shared__ float sm[32];
-  const Item it = items[blockIdx.x];
-  const ProcDev& P = c.procs[it.proc];
-  const DynParams d = dyn_params(P);
-  const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
+  __syncthreads();   // this CTA's du and aux stores are visible to its own loads below
   float l[kPer], r[kPer], dg[kPer];
   load16(P.u, P.ld, P.L, n0, l, r);
   load16m(P.aux, P.L, n0, dg);
@@ -385,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_apply(LaunchCtx c, cons
   float rl = 0.f;
 #pragma unroll
   for (int j = kPer - 1; j >= 0; --j) rl = dg[j] + d.alpha * rl;
-  float lam = scan_rev_excl(rl, d.lna, P.rcarry[it.idx], sm);   // lambda entering the last sample from the right
+  float lam = scan_rev_excl(rl, d.lna, s_in, sm);   // lambda entering the last sample from the right
   float dalpha = 0.f;
 #pragma unroll
   for (int j = kPer - 1; j >= 0; --j) {
@@ -402,23 +421,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd_apply(LaunchCtx c, cons
   if (threadIdx.x == 0) P.bpart[(size_t)it.idx * kNPart] = out[0];
 }
 
-void launch_dyn_fwd_agg(const LaunchCtx& c, const Item* items, int n) {
-  if (n) k_dyn_fwd_agg<<<n, kThreads, 0, c.stream>>>(c, items);
+void launch_dyn_fwd(const LaunchCtx& c, const Item* items, int n) {
+  if (!n) return;
+  k_chain_begin<<<1, 1, 0, c.stream>>>(c.chain);
+  k_dyn_fwd<<<n, kThreads, 0, c.stream>>>(c, items);
 }
-void launch_dyn_fwd_carry(const LaunchCtx& c, const int* procs, int n) {
-  if (n) k_dyn_fwd_carry<<<(n + 63) / 64, 64, 0, c.stream>>>(c, procs, n);
-}
-void launch_dyn_fwd_apply(const LaunchCtx& c, const Item* items, int n) {
-  if (n) k_dyn_fwd_apply<<<n, kThreads, 0, c.stream>>>(c, items);
-}
-void launch_dyn_bwd_agg(const LaunchCtx& c, const Item* items, int n) {
-  if (n) k_dyn_bwd_agg<<<n, kThreads, 0, c.stream>>>(c, items);
-}
-void launch_dyn_bwd_carry(const LaunchCtx& c, const int* procs, int n) {
-  if (n) k_dyn_bwd_carry<<<(n + 63) / 64, 64, 0, c.stream>>>(c, procs, n);
-}
-void launch_dyn_bwd_apply(const LaunchCtx& c, const Item* items, int n) {
-  if (n) k_dyn_bwd_apply<<<n, kThreads, 0, c.stream>>>(c, items);
+void launch_dyn_bwd(const LaunchCtx& c, const Item* items, int n) {
+  if (!n) return;
+  k_chain_begin<<<1, 1, 0, c.stream>>>(c.chain);
+  k_dyn_bwd<<<n, kThreads, 0, c.stream>>>(c, items);
 }
 
 }  // namespace mg

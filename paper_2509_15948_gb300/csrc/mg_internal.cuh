@@ -76,8 +76,8 @@ struct ProcDev {
                                            // compressor, noisegate: dL/dg per sample)
   // envelope scans (c, n)
   float* carry;                            // [nchunks] forward state entering each chunk
-  float* rcarry;                           // [nchunks] reverse state entering each chunk from the right
   float* chunkagg;                         // [nchunks] per-chunk aggregates
+  unsigned long long* cflag;               // [nchunks] chained-scan states: launch generation << 32 | state bits
   int nchunks;
   // reverb
   const float2* nspec;                     // [2][F][193] STFT of the fixed mid/side noise
@@ -145,6 +145,9 @@ struct LaunchCtx {
   float alpha_g;
   double fs;
   int elem_tile;                           // samples per work item of the gain/pan and imager kernels
+  unsigned* chain;                         // device [2]: launch generation and work ticket of the chained scans
+  int* err;                                // host-mapped error word: 1 = a chained scan's wait ran out
+  int chain_hold;                          // test hook: the first work item does not publish its state
   Tables tab;
 };
 
@@ -154,13 +157,9 @@ void launch_gs_bwd(const LaunchCtx&, const Item* items, int n);
 void launch_sum(cudaStream_t, float* const* outs, const float* const* ins, const int* in_beg, const int* L,
                 const int* ld, const Item* items, int n, int tile);
 void launch_ingest(cudaStream_t, const float* mono, float* stereo, int L, int ld);
-// envelope scans
-void launch_dyn_fwd_agg(const LaunchCtx&, const Item* items, int n);
-void launch_dyn_fwd_carry(const LaunchCtx&, const int* procs, int n);
-void launch_dyn_fwd_apply(const LaunchCtx&, const Item* items, int n);
-void launch_dyn_bwd_agg(const LaunchCtx&, const Item* items, int n);
-void launch_dyn_bwd_carry(const LaunchCtx&, const int* procs, int n);
-void launch_dyn_bwd_apply(const LaunchCtx&, const Item* items, int n);
+// envelope scans: chained single-pass forward (items in chunk order) and backward (items in reverse chunk order)
+void launch_dyn_fwd(const LaunchCtx&, const Item* items, int n);
+void launch_dyn_bwd(const LaunchCtx&, const Item* items, int n);
 // LTI processors
 void launch_eq_fir(const LaunchCtx&, const int* procs, int n);
 void launch_eq_fir_adj(const LaunchCtx&, const int* procs, int n);

@@ -170,7 +170,7 @@ def record_error(test: str, quantity: str, err: float, plain_bound: float, bound
         return
     rec = {"test": test, "quantity": quantity, "err": float(err), "plain_bound": float(plain_bound),
            "bound": float(bound)}
-    rec.update(extra)
+    rec.update({k: v.item() if hasattr(v, "item") else v for k, v in extra.items()})
     with open(path, "a") as f:
         f.write(json.dumps(rec) + "\n")
 

@@ -50,46 +50,77 @@ def channel_conditioning(mix):
     return {"Llr": 1.0, "Lm": lr / m if m > 0 else np.inf, "Ls": lr / s if s > 0 else np.inf}
 
 
-def check_delay(case, og, gg, taps, term_rms=None):
-    """Delay gradients: the 20 log-magnitudes of every c_m are held to the gradient bound; the z entries are
-    the Eq. (19) direction sgn(g_m) + gamma (|z| - 1) z/|z|, whose accuracy is set by how far g_m stands above
-    cancellation: measured |direction error| <= 5e-4 / kappa (kappa from delay_slot_conditioning); slots with
-    kappa < 1e-3 are below what FP32 resolves and are only checked for a valid direction."""
+def _window_norms(x, w):
+    """||x[q : q + w]||_2 for every q (sliding windows of length w)."""
+    c = np.concatenate([[0.0], np.cumsum(np.asarray(x, np.float64) ** 2)])
+    return np.sqrt(np.maximum(c[w:] - c[:-w], 0.0))
+
+
+def check_delay(case, og, gg, taps, con, term_rms=None, proc_map=None):
+    """Delay gradients (Sec. 3.7, Eq. 19).
+    * The 20 log-magnitudes of every c_m: the gradient bound.
+    * dL/dh, the FIR tap gradient that the FFT correlation computes (read back from the GPU), against the
+      oracle's: relative L2 per channel within the gradient bound.  Near an optimum (term_rms given) dL/dh is a
+      correlation that cancels 100x or more, so the bound adds 1e-4 of the rms summed term magnitude A: the
+      worst-case relative error of three FP32 radix-2 transforms of up to 2^21 points is about
+      15 log2(N) 2^-24 = 1.9e-5 of the terms, and the upstream adjoint's own FP32 error is of the same order
+      (measured 2.2e-5 of A).
+    * The z entries, sgn(g_m) + gamma (|z| - 1) z/|z| with g_m = sum_q G_q conj(s'_q) and
+      G_q = sum_j dL/dh[m D + q + j] c_m[j]: the direction normalises g_m, so an error e of dL/dh moves it by at
+      most 2 |dg| / |g_m| with |dg| <= sum_q ||e[m D + q : m D + q + 39]|| ||c_m|| |s'_q| (Cauchy-Schwarz).
+      Each entry is held to the gradient bound plus that propagation of the measured dL/dh error (e = GPU minus
+      oracle); kappa = |g_m| / (rms(dL/dh) ||c_m|| ||s'||) is recorded with the error.
+    proc_map: the console's processor index of each of the case's processors (default: the same index)."""
+    from oracle import processors as OP
+    D = int(round(0.1 * case.fs))
     kap = delay_slot_conditioning(case, taps, term_rms=term_rms)
-    lm_idx, worst = [], 0.0
-    worst_plain, worst_k, n_low = 0.0, 0.0, 0
+    t = current_test()
+    lm_idx = []
+    worst_plain, worst_k, worst_over_bound, n_prop = 0.0, 0.0, 0.0, 0
     for p in case.oracle.procs:
         if p.type != "d":
             continue
+        dh_o, cvals = taps[p.index]
+        cp = p.index if proc_map is None else int(proc_map[p.index])
+        dh_g = con.debug_read(cp, 2, dh_o.shape).astype(np.float64)
         blk = np.arange(p.offset, p.offset + p.count).reshape(2, 20, 22)
         lm_idx.append(blk[:, :, 2:].ravel())
         for ch in range(2):
+            e_dh = rel_l2(dh_g[ch], dh_o[ch])
+            rms_o = np.sqrt(np.mean(dh_o[ch] ** 2))
+            floor = 1e-4 * term_rms[p.index][ch] / rms_o if term_rms is not None and rms_o > 0 else 0.0
+            record_error(t, "grad d dL/dh (FIR taps)", e_dh, GRAD_TOL, GRAD_TOL + floor, proc=p.index, ch=ch)
+            assert e_dh <= GRAD_TOL + floor, ("dL/dh", p.index, ch, e_dh, floor)
+            wn = _window_norms(dh_g[ch] - dh_o[ch], 39)
             for m in range(20):
                 zi = blk[ch, m, :2]
-                err = np.linalg.norm(gg[zi] - og[zi])
-                k = kap[p.index][ch, m]
                 z = case.params[zi].astype(np.float64)
                 r = np.linalg.norm(z)
                 radial = 0.01 * (r - 1.0) * z / r if r > 0 else 0.0 * z
                 sg = np.linalg.norm(gg[zi] - radial)
                 assert np.isfinite(gg[zi]).all() and (sg < 1e-5 or abs(sg - 1.0) < 1e-4), (p.index, ch, m, sg)
-                if k >= 1e-3:
-                    assert err <= max(1e-3, 5e-4 / k), (p.index, ch, m, k, err)
-                    worst = max(worst, err * k)
-                    if err > worst_plain:
-                        worst_plain, worst_k = err, k
-                else:
-                    n_low += 1
-    t = current_test()
-    record_error(t, "grad d z direction (abs, slots with kappa >= 1e-3)", worst_plain, GRAD_TOL,
-                 max(1e-3, 5e-4 / worst_k) if worst_k > 0 else GRAD_TOL, kappa=worst_k, slots_below_1e_3=n_low,
-                 worst_err_times_kappa=worst)
+                zc = complex(z[0], z[1])
+                sp = OP.surrogate_impulse_dz(zc / max(1.0, abs(zc)), D)
+                G = np.lib.stride_tricks.sliding_window_view(dh_o[ch, m * D: m * D + D + 38], 39) @ cvals[ch, m]
+                g_abs = abs(np.sum(G * np.conj(sp)))
+                prop = 2.0 * np.sum(wn[m * D: m * D + D] * np.abs(sp)) * np.linalg.norm(cvals[ch, m])
+                prop = prop / g_abs if g_abs > 0 else np.inf
+                bound = GRAD_TOL + prop
+                err = np.linalg.norm(gg[zi] - og[zi])
+                if np.isfinite(bound):
+                    assert err <= bound, (p.index, ch, m, kap[p.index][ch, m], err, bound)
+                    worst_over_bound = max(worst_over_bound, err / bound)
+                n_prop += prop > GRAD_TOL
+                if err > worst_plain:
+                    worst_plain, worst_k = err, kap[p.index][ch, m]
+    record_error(t, "grad d z direction (abs)", worst_plain, GRAD_TOL, GRAD_TOL, kappa=worst_k,
+                 worst_err_over_bound=worst_over_bound, slots_where_dh_error_dominates=n_prop)
     if lm_idx:
         idx = np.concatenate(lm_idx)
         e = rel_l2(gg[idx], og[idx])
         record_error(t, "grad d log-magnitudes", e, GRAD_TOL, GRAD_TOL)
         assert e <= GRAD_TOL, ("grad d log-magnitudes", e)
-    return worst
+    return worst_plain
 
 
 def check(case, alpha_p=1e-3, skip_losses=(), check_grads=True, grad_floor=False, **cfg):
@@ -98,7 +129,8 @@ def check(case, alpha_p=1e-3, skip_losses=(), check_grads=True, grad_floor=False
                          grad_floor)
 
 
-def check_results(case, oracle_res, gpu_res, con, alpha_p=1e-3, skip_losses=(), check_grads=True, grad_floor=False):
+def check_results(case, oracle_res, gpu_res, con, alpha_p=1e-3, skip_losses=(), check_grads=True, grad_floor=False,
+                  proc_map=None):
     """Mixes, loss terms and gradients of the CUDA path against the oracle's, with every measured error
     recorded against the plain bound (record_error)."""
     (ol, og, omix, taps), (gl, gg, gmix) = oracle_res, gpu_res
@@ -136,7 +168,7 @@ def check_results(case, oracle_res, gpu_res, con, alpha_p=1e-3, skip_losses=(), 
     if check_grads:
         for name, idx in grad_groups(case).items():
             if name == "d":
-                check_delay(case, og, gg, taps, delay_term_rms(case, alpha_p) if grad_floor else None)
+                check_delay(case, og, gg, taps, con, delay_term_rms(case, alpha_p) if grad_floor else None, proc_map)
                 continue
             e = rel_l2(gg[idx], og[idx])
             record_error(t, f"grad {name}", e, GRAD_TOL, GRAD_TOL)
@@ -308,3 +340,38 @@ def test_song_alone_equals_song_in_batch():
                           [gb[batch.oracle.n_proc_params + np.array([p.index for p in sel])]])
     assert np.array_equal(g1, gsel)
     assert len(types) == con.n_processors
+
+
+def test_envelope_scan_wait_timeout_is_reported_and_recoverable():
+    """The compressor and gate scans hand the envelope state (Eq. 11) from one 4096-sample chunk's CTA to the
+    next through a flag that the next CTA waits on for at most about half a second.  With the test hook the first
+    chunk of a launch withholds its state: the second chunk's wait runs out, the next call reports MG_ERR_TIMEOUT,
+    the context stays usable, and once the hook is released the console computes bitwise what it computed
+    before, forward and backward."""
+    import torch
+    import paper_2509_15948_gb300 as M
+    case = make_case([W.SongLayout(2, 0, [-1, -1], 20011)], types="cn", seed=71)
+    con = gpu_console(case)
+    con.set_params(case.params)
+    l0, m0 = con.forward_loss(with_mix=True)
+    l0, m0 = l0.clone(), m0[0].clone()
+    con.backward()
+    g0 = con.get_grads().clone()
+    for phase in ("forward", "backward"):
+        if phase == "backward":
+            con.forward_loss()
+        con.debug_chain_hold(True)
+        if phase == "forward":
+            con.forward_loss()
+        else:
+            con.backward()
+        torch.cuda.synchronize()
+        with pytest.raises(M.MgError) as e:
+            con.forward_loss()
+        assert e.value.status == M.MG_ERR_TIMEOUT
+        con.debug_chain_hold(False)
+        l1, m1 = con.forward_loss(with_mix=True)
+        con.backward()
+        torch.cuda.synchronize()
+        assert torch.equal(l1, l0) and torch.equal(m1[0], m0) and torch.equal(con.get_grads(), g0), phase
+    con.close()

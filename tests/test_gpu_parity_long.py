@@ -100,8 +100,9 @@ def test_batch_with_arena_past_4gib():
     gl = losses.cpu().numpy()
     gm = [m.cpu().numpy() for m in mixes]
     for s in range(copies):
-        _, pidx = _song_slices(con, s)
-        check_results(single, (ol, og, omix, taps), (gl[s:s + 1], g[pidx], [gm[s]]), con, alpha_p=1e-3)
+        procs_s, pidx = _song_slices(con, s)
+        check_results(single, (ol, og, omix, taps), (gl[s:s + 1], g[pidx], [gm[s]]), con, alpha_p=1e-3,
+                      proc_map=procs_s)
         assert np.array_equal(gm[s], gm[0]) and np.array_equal(gl[s], gl[0]) and np.array_equal(g[pidx],
                                                                                                  g[_song_slices(con, 0)[1]])
     con.close()
@@ -156,7 +157,7 @@ def test_benchmark_batch_sampled_songs():
         oc = OC.Console([spec], [sources[s]], [tgt], nz)
         single = Case([lay], "ecnsgdr", [sources[s]], [tgt], nz, [p.type for p in sel], p0[pidx].copy(),
                       (512, 2048, 8192), 96, oc)
-        singles[s] = (single, oracle_with_delay_taps(single, alpha_p), pidx)
+        singles[s] = (single, oracle_with_delay_taps(single, alpha_p), pidx, [p.index for p in sel])
     con = M.Console([M.Song(l.num_tracks, l.num_subgroups, l.track_group, l.num_samples) for l in layouts], sources,
                     targets, noise, M.ConsoleConfig(autotune=1))
     assert con.get_info()["retains_spectra"] == 1
@@ -169,8 +170,9 @@ def test_benchmark_batch_sampled_songs():
     losses_f, mixes = con.forward_loss(with_mix=True)
     assert torch.equal(losses_f, losses_g)
     for s in SAMPLED_SONGS:
-        single, ores, pidx = singles[s]
-        check_results(single, ores, (gl[s:s + 1], g[pidx], [mixes[s].cpu().numpy()]), con, alpha_p=alpha_p)
+        single, ores, pidx, pmap = singles[s]
+        check_results(single, ores, (gl[s:s + 1], g[pidx], [mixes[s].cpu().numpy()]), con, alpha_p=alpha_p,
+                      proc_map=pmap)
     con.close()
     del con
     _free_device()
