@@ -147,15 +147,27 @@ __device__ __forceinline__ void store16m(float* base, int L, int n0, const float
   }
 }
 
+// Decay powers of one node, computed once per CTA: dl[j] = alpha^(16 j) (j < 32, one thread's samples apart) and
+// dw[j] = alpha^(512 j) (j < 8, one warp's samples apart), each expf(n ln alpha) of its exact exponent n.
+constexpr int kDecay = 40;
+__device__ __forceinline__ void init_decay(float* dec, float lna) {
+  if (threadIdx.x < kDecay) {
+    const int t = threadIdx.x;
+    dec[t] = expf((float)(t < 32 ? kPer * t : kPer * 32 * (t - 32)) * lna);
+  }
+  __syncthreads();
+}
+
 // Exclusive forward scan over the block: returns the state entering this thread's first sample, given the
 // per-thread zero-start end states s (each spanning 16 samples) and the chunk's entering state.
-__device__ __forceinline__ float scan_fwd_excl(float s, float lna, float carry, float* sm /* >= 8 floats */) {
+__device__ __forceinline__ float scan_fwd_excl(float s, const float* dl, const float* dw, float carry,
+                                               float* sm /* >= 16 floats */) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float inc = s;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const float v = __shfl_up_sync(0xffffffffu, inc, off);
-    if (lane >= off) inc += v * expf((float)(kPer * off) * lna);
+    if (lane >= off) inc += v * dl[off];
   }
   if (lane == 31) sm[wid] = inc;
   __syncthreads();
@@ -165,32 +177,32 @@ __device__ __forceinline__ float scan_fwd_excl(float s, float lna, float carry, 
 #pragma unroll
     for (int off = 1; off < kThreads / 32; off <<= 1) {
       const float v = __shfl_up_sync(0xffffffffu, ti, off);
-      if (lane >= off) ti += v * expf((float)(kPer * 32 * off) * lna);
+      if (lane >= off) ti += v * dw[off];
     }
     // exclusive warp prefix, with the chunk carry folded in
     float ex = __shfl_up_sync(0xffffffffu, ti, 1);
     if (lane == 0) ex = 0.f;
-    ex += carry * expf((float)(kPer * 32 * lane) * lna);
+    ex += carry * dw[lane & 7];
     if (lane < kThreads / 32) sm[8 + lane] = ex;
   }
   __syncthreads();
   const float win = sm[8 + wid];   // state entering the warp
   float ex = __shfl_up_sync(0xffffffffu, inc, 1);
   if (lane == 0) ex = 0.f;
-  const float res = ex + win * expf((float)(kPer * lane) * lna);
+  const float res = ex + win * dl[lane];
   __syncthreads();
   return res;
 }
 
 // Exclusive reverse scan: state entering this thread's last sample from the right.
-__device__ __forceinline__ float scan_rev_excl(float r, float lna, float carry, float* sm) {
+__device__ __forceinline__ float scan_rev_excl(float r, const float* dl, const float* dw, float carry, float* sm) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int nw = kThreads / 32;
   float inc = r;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const float v = __shfl_down_sync(0xffffffffu, inc, off);
-    if (lane + off < 32) inc += v * expf((float)(kPer * off) * lna);
+    if (lane + off < 32) inc += v * dl[off];
   }
   if (lane == 0) sm[wid] = inc;
   __syncthreads();
@@ -201,18 +213,18 @@ __device__ __forceinline__ float scan_rev_excl(float r, float lna, float carry, 
 #pragma unroll
     for (int off = 1; off < nw; off <<= 1) {
       const float v = __shfl_down_sync(0xffffffffu, ti, off);
-      if (lane + off < nw) ti += v * expf((float)(kPer * 32 * off) * lna);
+      if (lane + off < nw) ti += v * dw[off];
     }
     float ex = __shfl_down_sync(0xffffffffu, ti, 1);
     if (lane >= nw - 1) ex = 0.f;
-    ex += carry * expf((float)(kPer * 32 * (nw - 1 - lane)) * lna);
+    ex += carry * dw[(nw - 1 - lane) & 7];
     if (lane < nw) sm[8 + lane] = ex;
   }
   __syncthreads();
   const float win = sm[8 + wid];
   float ex = __shfl_down_sync(0xffffffffu, inc, 1);
   if (lane == 31) ex = 0.f;
-  const float res = ex + win * expf((float)(kPer * (31 - lane)) * lna);
+  const float res = ex + win * dl[31 - lane];
   __syncthreads();
   return res;
 }
@@ -272,9 +284,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_dyn_fwd(LaunchCtx c, const Item
   __shared__ int s_idx;
   __shared__ unsigned s_gen;
   __shared__ float s_in;
+  __shared__ float dec[kDecay];
   const Item it = take_item(c, items, &s_idx, &s_gen);
   const ProcDev& P = c.procs[it.proc];
   const DynParams d = dyn_params(P);
+  init_decay(dec, d.lna);
   const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
   float l[kPer], r[kPer];
   load16(P.u, P.ld, P.L, n0, l, r);
@@ -284,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_dyn_fwd(LaunchCtx c, const Item
     const float m = l[j] + r[j];
     s = d.alpha * s + d.beta * (m * m);
   }
-  float v[1] = {s * expf((float)(kPer * (kThreads - 1 - (int)threadIdx.x)) * d.lna)};
+  float v[1] = {s * (dec[31 - (threadIdx.x & 31)] * dec[32 + 7 - (threadIdx.x >> 5)])};   // alpha^(16 (255 - t))
   float out[1];
   block_sum<1>(v, red, out);
   if (threadIdx.x == 0) {
@@ -293,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_dyn_fwd(LaunchCtx c, const Item
   }
   __syncthreads();
   const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
-  float g = scan_fwd_excl(s, d.lna, s_in, red);
+  float g = scan_fwd_excl(s, dec, dec + 32, s_in, red);
   load16(P.u, P.ld, P.L, n0, l, r);   // again, from L2
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
@@ -327,49 +341,71 @@ __device__ __forceinline__ float dyn_dg(const DynParams& d, float w, float g, fl
   return dE * (dG - 1.f) * __frcp_rn(g + kEnvEps);
 }
 
+// One quad of a [2][ld] buffer's channel row at sample n (n a multiple of 4; zeros at and beyond L).
+__device__ __forceinline__ float4 load_quad(const float* row, int n, int L) {
+  return n < L ? tail_zero(*reinterpret_cast<const float4*>(row + n), n, L) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float q_at(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+
 // Backward.  Step 1, everything that does not depend on lambda: per sample dL/dg (to aux) and the part of du
 // without the envelope term (to du), the partials of dL/dT, dL/dW, dL/dR and dL/dw, and the chunk's zero-start
 // lambda aggregate.  Step 2, the chained lambda state from the right.  Step 3: lambda[n] = dL/dg[n] +
 // alpha lambda[n+1] from that state, du += 2 beta lambda m on both channels, and the partial of
-// dL/dalpha = sum lambda[n] (g[n-1] - x[n]); u, aux and du come back from L2.
-__global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd(LaunchCtx c, const Item* __restrict__ items) {
+// dL/dalpha = sum lambda[n] (g[n-1] - x[n]); u, aux and du come back from L1 / L2.  Steps 1 and 3 stream their
+// samples a quad at a time, so a thread holds its 16 samples' mid signal and envelope terms only in step 3.
+__global__ void __launch_bounds__(kThreads, 3) k_dyn_bwd(LaunchCtx c, const Item* __restrict__ items) {
   __shared__ float sm[32 * 5];
   __shared__ int s_idx;
   __shared__ unsigned s_gen;
   __shared__ float s_in;
+  __shared__ float dec[kDecay];
   const Item it = take_item(c, items, &s_idx, &s_gen);
   const ProcDev& P = c.procs[it.proc];
   const DynParams d = dyn_params(P);
+  init_decay(dec, d.lna);
   const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
+  const int L = P.L, ld = P.ld;
   {
-    float l[kPer], r[kPer], gl[kPer], gr[kPer];
-    load16(P.u, P.ld, P.L, n0, l, r);
-    load16(P.dy, P.ld, P.L, n0, gl, gr);
     float s = 0.f;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const float m = l[j] + r[j];
-      s = d.alpha * s + d.beta * (m * m);
+    for (int q = 0; q < kPer / 4; ++q) {
+      const float4 a = load_quad(P.u, n0 + 4 * q, L), b = load_quad(P.u + ld, n0 + 4 * q, L);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float m = q_at(a, e) + q_at(b, e);
+        s = d.alpha * s + d.beta * (m * m);
+      }
     }
-    float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
-    float dg[kPer];
+    float g = scan_fwd_excl(s, dec, dec + 32, P.carry[it.idx], sm);
     DynAdj acc = {0.f, 0.f, 0.f, 0.f};
+    float lam = 0.f, pw = 1.f;   // zero-start lambda entering the thread's first sample: sum_j alpha^j dL/dg[j]
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const float m = l[j] + r[j];
-      g = d.alpha * g + d.beta * (m * m);
-      float gain;
-      dg[j] = dyn_dg(d, w, g, l[j], r[j], gl[j], gr[j], gain, acc);
-      l[j] = wd * gl[j] + gain * (w * gl[j]);
-      r[j] = wd * gr[j] + gain * (w * gr[j]);
+    for (int q = 0; q < kPer / 4; ++q) {
+      const int n = n0 + 4 * q;
+      const float4 a = load_quad(P.u, n, L), b = load_quad(P.u + ld, n, L);
+      const float4 ga = load_quad(P.dy, n, L), gb = load_quad(P.dy + ld, n, L);
+      float dl[4], dr[4], dgq[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float ul = q_at(a, e), ur = q_at(b, e), gl = q_at(ga, e), gr = q_at(gb, e);
+        const float m = ul + ur;
+        g = d.alpha * g + d.beta * (m * m);
+        float gain;
+        dgq[e] = dyn_dg(d, w, g, ul, ur, gl, gr, gain, acc);
+        dl[e] = wd * gl + gain * (w * gl);
+        dr[e] = wd * gr + gain * (w * gr);
+        lam = fmaf(pw, dgq[e], lam);
+        pw *= d.alpha;
+      }
+      if (n < L) {
+        store_quad(P.du, n, L, dl[0], dl[1], dl[2], dl[3]);
+        store_quad(P.du + ld, n, L, dr[0], dr[1], dr[2], dr[3]);
+        store_quad(P.aux, n, L, dgq[0], dgq[1], dgq[2], dgq[3]);
+      }
     }
-    store16(P.du, P.ld, P.L, n0, l, r);
-    store16m(P.aux, P.L, n0, dg);
-    float lam = 0.f;
-#pragma unroll
-    for (int j = kPer - 1; j >= 0; --j) lam = dg[j] + d.alpha * lam;
-    float v[5] = {lam * expf((float)(kPer * threadIdx.x) * d.lna), acc.dT, acc.dW, acc.dR, acc.dw};
+    float v[5] = {lam * (dec[threadIdx.x & 31] * dec[32 + (threadIdx.x >> 5)]), acc.dT, acc.dW, acc.dR, acc.dw};
     float out[5];
     block_sum<5>(v, sm, out);
     if (threadIdx.x == 0) {
@@ -382,19 +418,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd(LaunchCtx c, const Item
     }
   }
   __syncthreads();   // this CTA's du and aux stores are visible to its own loads below
-  float l[kPer], r[kPer], dg[kPer];
-  load16(P.u, P.ld, P.L, n0, l, r);
-  load16m(P.aux, P.L, n0, dg);
-  float m[kPer];
+  float m[kPer], ex[kPer];
   float s = 0.f;
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    m[j] = l[j] + r[j];
-    s = d.alpha * s + d.beta * (m[j] * m[j]);
+  for (int q = 0; q < kPer / 4; ++q) {
+    const float4 a = load_quad(P.u, n0 + 4 * q, L), b = load_quad(P.u + ld, n0 + 4 * q, L);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      m[4 * q + e] = q_at(a, e) + q_at(b, e);
+      s = d.alpha * s + d.beta * (m[4 * q + e] * m[4 * q + e]);
+    }
   }
-  load16(P.du, P.ld, P.L, n0, l, r);
-  float g = scan_fwd_excl(s, d.lna, P.carry[it.idx], sm);
-  float ex[kPer];
+  float g = scan_fwd_excl(s, dec, dec + 32, P.carry[it.idx], sm);
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
     const float x = m[j] * m[j];
@@ -403,18 +438,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_dyn_bwd(LaunchCtx c, const Item
   }
   float rl = 0.f;
 #pragma unroll
-  for (int j = kPer - 1; j >= 0; --j) rl = dg[j] + d.alpha * rl;
-  float lam = scan_rev_excl(rl, d.lna, s_in, sm);   // lambda entering the last sample from the right
+  for (int q = kPer / 4 - 1; q >= 0; --q) {
+    const float4 dg = load_quad(P.aux, n0 + 4 * q, L);
+#pragma unroll
+    for (int e = 3; e >= 0; --e) rl = q_at(dg, e) + d.alpha * rl;
+  }
+  float lam = scan_rev_excl(rl, dec, dec + 32, s_in, sm);   // lambda entering the last sample from the right
   float dalpha = 0.f;
 #pragma unroll
-  for (int j = kPer - 1; j >= 0; --j) {
-    lam = dg[j] + d.alpha * lam;
-    dalpha += lam * ex[j];
-    const float dx2m = d.beta * lam * 2.f * m[j];
-    l[j] += dx2m;
-    r[j] += dx2m;
+  for (int q = kPer / 4 - 1; q >= 0; --q) {
+    const int n = n0 + 4 * q;
+    const float4 dg = load_quad(P.aux, n, L);
+    const float4 a = load_quad(P.du, n, L), b = load_quad(P.du + ld, n, L);
+    float dl[4] = {a.x, a.y, a.z, a.w}, dr[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int e = 3; e >= 0; --e) {
+      const int j = 4 * q + e;
+      lam = q_at(dg, e) + d.alpha * lam;
+      dalpha += lam * ex[j];
+      const float dx2m = d.beta * lam * 2.f * m[j];
+      dl[e] += dx2m;
+      dr[e] += dx2m;
+    }
+    if (n < L) {
+      store_quad(P.du, n, L, dl[0], dl[1], dl[2], dl[3]);
+      store_quad(P.du + ld, n, L, dr[0], dr[1], dr[2], dr[3]);
+    }
   }
-  store16(P.du, P.ld, P.L, n0, l, r);
   float v[1] = {dalpha};
   float out[1];
   block_sum<1>(v, sm, out);
