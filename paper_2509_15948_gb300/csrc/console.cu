@@ -17,6 +17,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/mixgraph.h"
 #include "mg_internal.cuh"
 #include "mg_fftp.cuh"
@@ -190,6 +193,7 @@ struct mg_console {
   int chain_hold = 0;              // test hook (mg_debug_chain_hold)
   int loss_per[3] = {0, 0, 0};     // frames per loss work item per resolution (packing tuner; 0: 8192 / n_fft)
   bool debug_sync = false;         // MG_DEBUG_SYNC=1 in the environment: synchronise and check after every launch
+  bool dyn_tma = true;             // TMA staging of the compressor / gate forward (MG_DYN_TMA=0: plain loads)
   bool debug_reported = false;
   ProcDev* d_procs = nullptr;
   SongDev* d_songs = nullptr;
@@ -844,6 +848,36 @@ struct Bump {
   }
 };
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (nothing links the driver library); nullptr when
+// the driver does not offer it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of a compressor / gate input u ([2][ld] floats) as 2 ld / 32 rows of 128 bytes, copied in boxes of
+// 128 rows (one channel of a 4096-sample chunk) with the 128-byte swizzle; rows past the buffer read as zeros.
+bool encode_dyn_map(CUtensorMap* m, const float* u, int ld) {
+  const auto enc = tensor_map_encoder();
+  if (!enc || !u || ld % 64 || (reinterpret_cast<uintptr_t>(u) & 255)) return false;
+  const cuuint64_t dims[2] = {32, (cuuint64_t)(2 * (int64_t)ld / 32)};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {32, (cuuint32_t)(kDynChunk / 32)};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(u), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Device copy of a host table.  Earlier copies stay allocated until the console is destroyed (tables are
 // rebuilt only by mg_prune), so no pointer captured in a graph or kernel argument ever dangles.
 template <class T>
@@ -856,6 +890,36 @@ mg_status upload(mg_console* c, std::vector<T>& h, T** d) {
   return MG_OK;
 }
 mg_status upload_items(mg_console* c, ItemList& L) { return upload(c, L.h, &L.d); }
+
+// Tensor maps of the present compressors' and gates' input u and output adjoint dL/dy (from the node table),
+// uploaded to a fresh table; a node whose maps cannot be encoded keeps nullptr and reads global memory directly.
+mg_status attach_dyn_maps(mg_console* c) {
+  std::vector<CUtensorMap> maps;
+  std::vector<std::pair<int, int>> owner;   // (processor, 0 u / 1 dL/dy)
+  for (int pi = 0; pi < c->P; ++pi) {
+    ProcDev& d = c->hpd[pi];
+    d.umap = nullptr;
+    d.dymap = nullptr;
+    const HostProc& p = c->procs[pi];
+    if (!c->dyn_tma || !p.present || (p.type != T_C && p.type != T_N)) continue;
+    CUtensorMap m;
+    if (encode_dyn_map(&m, d.u, p.ld)) {
+      maps.push_back(m);
+      owner.push_back({pi, 0});
+    }
+    if (encode_dyn_map(&m, d.dy, p.ld)) {
+      maps.push_back(m);
+      owner.push_back({pi, 1});
+    }
+  }
+  CUtensorMap* dm = nullptr;
+  if (upload(c, maps, &dm) != MG_OK) return MG_ERR_CUDA;
+  for (size_t k = 0; k < owner.size(); ++k) {
+    if (owner[k].second == 0) c->hpd[owner[k].first].umap = dm + k;
+    else c->hpd[owner[k].first].dymap = dm + k;
+  }
+  return MG_OK;
+}
 mg_status upload_procs(mg_console* c, ProcList& L) { return upload(c, L.h, &L.d); }
 
 mg_status build_graph_tables(mg_console* c);
@@ -1065,7 +1129,7 @@ mg_status build_tables(mg_console* c) {
     }
   }
   for (int pi = 0; pi < c->P; ++pi) fill_procdev(c, pi);
-  if (upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
+  if (attach_dyn_maps(c) != MG_OK || upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
 
   // sums: m per subgroup (level 1 inputs), o per song
   c->sum_out.h.clear(); c->sum_in.h.clear(); c->sum_beg.h.clear(); c->sum_L.h.clear(); c->sum_ld.h.clear();
@@ -1125,7 +1189,7 @@ mg_status build_tables(mg_console* c) {
       c->stages.push_back(st);
     }
   // scratch pointers changed with grouping: re-upload the node table
-  if (upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
+  if (attach_dyn_maps(c) != MG_OK || upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
   if (upload_procs(c, c->all_present) || upload_procs(c, c->all_lti_present)) return MG_ERR_CUDA;
   return MG_OK;
 }
@@ -1250,7 +1314,7 @@ mg_status build_graph_tables(mg_console* c) {
     c->gstep_stage[k] = (int)c->stages.size();
     c->stages.push_back(st);
   }
-  if (upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
+  if (attach_dyn_maps(c) != MG_OK || upload(c, c->hpd, &c->d_procs) != MG_OK) return MG_ERR_CUDA;
   if (upload_procs(c, c->all_present) || upload_procs(c, c->all_lti_present)) return MG_ERR_CUDA;
   return MG_OK;
 }
@@ -1986,6 +2050,8 @@ struct ScoreChunk {
   size_t table_begin = 0;                    // workspace offset of the tables (copied from the host blob)
   size_t end = 0;                            // workspace bytes the chunk uses
   unsigned long long* flags = nullptr;       // published states of the chained scans of the node copies
+  std::vector<CUtensorMap> umaps;            // tensor maps of the compressor / gate copies' inputs
+  std::vector<std::pair<int, int>> umap_of;  // (node copy, map)
   size_t flags_bytes = 0;
   float* vq = nullptr;
   float* vla = nullptr;
@@ -2008,7 +2074,8 @@ size_t copy_bytes(const mg_console* c, int pi, size_t* items) {
   size_t it = 0;
   if (p.nfrows) b += al((size_t)std::max(p.nfrows, p.nfcap) * kNPart * sizeof(float));
   if (p.type == T_C || p.type == T_N) {
-    b += 2 * al((size_t)p.nchunks * sizeof(float)) + (size_t)p.nchunks * sizeof(unsigned long long);   // + states
+    b += 2 * al((size_t)p.nchunks * sizeof(float)) + (size_t)p.nchunks * sizeof(unsigned long long) +
+         sizeof(CUtensorMap);   // + states, + tensor map
     it = p.nchunks + 1;
   } else if (p.type == T_G || p.type == T_S) {
     it = p.nbrows;
@@ -2165,6 +2232,13 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
           d.chunkagg = (float*)w.buffer((size_t)p.nchunks * sizeof(float));
           d.aux = nullptr;
           flag_nodes.push_back({(int)k.vp.size(), p.nchunks});
+          d.umap = nullptr;
+          d.dymap = nullptr;
+          CUtensorMap m;
+          if (c->dyn_tma && encode_dyn_map(&m, d.u, p.ld)) {
+            k.umap_of.push_back({(int)k.vp.size(), (int)k.umaps.size()});
+            k.umaps.push_back(m);
+          }
         }
         if (p.type == T_R || p.type == T_D) {
           const size_t N = (size_t)p.f << p.logN;
@@ -2297,6 +2371,10 @@ void build_chunk(mg_console* c, const std::vector<CandPlan>& plans, const uint8_
   // tables
   w.start_tables();
   k.table_begin = w.table_begin;
+  {
+    CUtensorMap* dm = w.table(k.umaps);
+    for (const auto& um : k.umap_of) k.vp[um.first].umap = dm + um.second;
+  }
   k.d_vp = w.table(k.vp);
   k.d_vsrc = w.table(k.vsrc);
   k.d_vmask = w.table(k.vmask);
@@ -2618,6 +2696,8 @@ mg_status mg_console_create(const mg_console_desc* desc, const mg_song_desc* son
   {
     const char* dbg = std::getenv("MG_DEBUG_SYNC");
     c->debug_sync = dbg && dbg[0] == '1';
+    const char* tma = std::getenv("MG_DYN_TMA");
+    c->dyn_tma = !(tma && tma[0] == '0');
   }
   mg_status st = validate(c, desc, songs, n_songs);
   if (st == MG_OK) {
@@ -2670,6 +2750,8 @@ mg_status mg_graph_console_create(const mg_console_desc* desc, const mg_graph_de
   {
     const char* dbg = std::getenv("MG_DEBUG_SYNC");
     c->debug_sync = dbg && dbg[0] == '1';
+    const char* tma = std::getenv("MG_DYN_TMA");
+    c->dyn_tma = !(tma && tma[0] == '0');
   }
   mg_status st = validate_graph(c, desc, graph, song);
   if (st == MG_OK) st = plan_graph(c, desc, graph, song);

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row_conv(LaunchCtx c, const 
 
 void init_kernel_attributes() {
   init_col_attributes();
+  init_dyn_attributes();
   cudaFuncSetAttribute(k_row_fwd_hz, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));
   cudaFuncSetAttribute(k_row_conv<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));
   cudaFuncSetAttribute(k_row_conv<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * pstride(kMaxRow) * (int)sizeof(float2));

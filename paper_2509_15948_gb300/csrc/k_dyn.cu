@@ -8,7 +8,8 @@
 //      publishes the state entering the next chunk, g_next = A g_in + agg (A = alpha^4096); the stage's chunks are
 //      listed in rounds across nodes, so that wait is normally over before it starts,
 //   3. rescans its chunk from that state and applies the gain law (Eqs. 13-16) and Eq. (15), fused with the
-//      dry/wet blend; it re-reads its own input, which the first step brought into L2.
+//      dry/wet blend.  The forward's input arrives by TMA (a bulk tensor copy into shared memory, read by both
+//      steps) when the node has a tensor map, else by plain loads with the rescan from L2.
 // The adjoint runs the same way in reverse: lambda[n] = dL/dg[n] + alpha lambda[n+1], chunks in reverse order.
 // Its first step also does the per-sample work that does not depend on lambda (the gain law, its partials,
 // dL/dg and the lambda-free part of du), staged in global memory for the same CTA's last step.  A wait that
@@ -100,51 +101,6 @@ __device__ __forceinline__ void store_quad(float* p, int n, int L, float x, floa
   p[n] = x;
   if (n + 1 < L) p[n + 1] = y;
   if (n + 2 < L) p[n + 2] = z;
-}
-
-// Loads this thread's 16 consecutive samples of a [2][ld] buffer (zeros at and beyond L).
-__device__ __forceinline__ void load16(const float* base, int ld, int L, int n0, float (&l)[kPer], float (&r)[kPer]) {
-#pragma unroll
-  for (int j = 0; j < kPer / 4; ++j) {
-    const int n = n0 + 4 * j;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-    if (n < L) {
-      a = tail_zero(*reinterpret_cast<const float4*>(base + n), n, L);
-      b = tail_zero(*reinterpret_cast<const float4*>(base + ld + n), n, L);
-    }
-    l[4 * j] = a.x; l[4 * j + 1] = a.y; l[4 * j + 2] = a.z; l[4 * j + 3] = a.w;
-    r[4 * j] = b.x; r[4 * j + 1] = b.y; r[4 * j + 2] = b.z; r[4 * j + 3] = b.w;
-  }
-}
-
-__device__ __forceinline__ void store16(float* base, int ld, int L, int n0, const float (&l)[kPer], const float (&r)[kPer]) {
-#pragma unroll
-  for (int j = 0; j < kPer / 4; ++j) {
-    const int n = n0 + 4 * j;
-    if (n < L) {
-      store_quad(base, n, L, l[4 * j], l[4 * j + 1], l[4 * j + 2], l[4 * j + 3]);
-      store_quad(base + ld, n, L, r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
-    }
-  }
-}
-
-// The same for a mono buffer of L samples.
-__device__ __forceinline__ void load16m(const float* base, int L, int n0, float (&v)[kPer]) {
-#pragma unroll
-  for (int j = 0; j < kPer / 4; ++j) {
-    const int n = n0 + 4 * j;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (n < L) a = tail_zero(*reinterpret_cast<const float4*>(base + n), n, L);
-    v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
-  }
-}
-
-__device__ __forceinline__ void store16m(float* base, int L, int n0, const float (&v)[kPer]) {
-#pragma unroll
-  for (int j = 0; j < kPer / 4; ++j) {
-    const int n = n0 + 4 * j;
-    if (n < L) store_quad(base, n, L, v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-  }
 }
 
 // Decay powers of one node, computed once per CTA: dl[j] = alpha^(16 j) (j < 32, one thread's samples apart) and
@@ -278,8 +234,75 @@ __device__ __forceinline__ float chain_link(const LaunchCtx& c, const ProcDev& P
   return in;
 }
 
-// Forward: chunk aggregate, chained state, rescan with the gain law.
+__device__ __forceinline__ float q_at(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+
+// ---- TMA staging of a forward chunk ----
+// With a tensor map of the node's input u (rows of 32 floats = 128 bytes, both channels: 2 ld / 32 rows), one
+// thread stages the chunk's 128 rows of each channel into shared memory with two bulk tensor copies
+// (cp.async.bulk.tensor, 128-byte swizzle) completing on an mbarrier.  Rows past the tensor read as zeros; rows of
+// the left channel past its ld read the right channel's first rows, and every sample at or beyond L is masked
+// anyway.  The swizzle stores the 16-byte chunk c of row r at chunk c ^ (r mod 8), so the quads a thread reads
+// (row t / 2, chunks 4 (t mod 2) + j) fall on distinct bank groups within each quarter warp.
+constexpr int kChanBytes = kDynChunk * 4;                  // one channel of a chunk, 16 KB
+constexpr int kDynFwdSmem = 2 * kChanBytes + 1024;         // both channels + alignment slack of the swizzle
+constexpr int kDynBwdSmem = 4 * kChanBytes + 1024;         // u and dL/dy, both channels
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void stage_init(unsigned long long* bar, unsigned bytes) {
+  const unsigned b = smem_u32(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
+
+// Both channels of chunk idx of the buffer behind `map` ([2][ld] floats) into dst (left) and dst + 16 KB (right).
+__device__ __forceinline__ void stage_copy(const void* map, int ld, int idx, float* dst, unsigned long long* bar) {
+  const unsigned b = smem_u32(bar), d = smem_u32(dst);
+  const unsigned long long m = reinterpret_cast<unsigned long long>(map);
+  const int r0 = idx * (kDynChunk / 32), r1 = ld / 32 + r0;
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(d), "l"(m), "r"(0), "r"(r0), "r"(b) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(d + kChanBytes), "l"(m), "r"(0), "r"(r1), "r"(b) : "memory");
+}
+
+// Bounded wait for the staged chunk (phase 0 of the mbarrier): false when it did not arrive in time.
+__device__ __forceinline__ bool stage_wait(const unsigned long long* bar) {
+  const unsigned b = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(b) : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kChainWaitCycles) return false;
+  }
+}
+
+// Quad q of thread t's 16 samples of channel ch in a swizzled stage.
+__device__ __forceinline__ float4* stage_at(float* stage, int ch, int t, int q) {
+  const int row = t >> 1, chunk = ((t & 1) << 2) | q;
+  return reinterpret_cast<float4*>(reinterpret_cast<char*>(stage) + ch * kChanBytes + row * 128 +
+                                   ((chunk ^ (row & 7)) << 4));
+}
+__device__ __forceinline__ float4 stage_quad(const float* stage, int ch, int t, int q) {
+  return *stage_at(const_cast<float*>(stage), ch, t, q);
+}
+
+__device__ __forceinline__ float4 mask_quad(float4 v, int n, int L) {
+  return n < L ? tail_zero(v, n, L) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Forward: chunk aggregate, chained state, rescan with the gain law.  The chunk comes from the TMA stage when the
+// node has a tensor map (read twice from shared memory), else from global memory (the rescan from L2).
 __global__ void __launch_bounds__(kThreads, 4) k_dyn_fwd(LaunchCtx c, const Item* __restrict__ items) {
+  extern __shared__ unsigned char dsm[];
+  float* stage = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) unsigned long long bar;
   __shared__ float red[32];
   __shared__ int s_idx;
   __shared__ unsigned s_gen;
@@ -287,38 +310,69 @@ __global__ void __launch_bounds__(kThreads, 4) k_dyn_fwd(LaunchCtx c, const Item
   __shared__ float dec[kDecay];
   const Item it = take_item(c, items, &s_idx, &s_gen);
   const ProcDev& P = c.procs[it.proc];
+  const bool tma = P.umap != nullptr;
+  if (tma && threadIdx.x == 0) {
+    stage_init(&bar, 2 * kChanBytes);
+    stage_copy(P.umap, P.ld, it.idx, stage, &bar);
+  }
   const DynParams d = dyn_params(P);
-  init_decay(dec, d.lna);
-  const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
-  float l[kPer], r[kPer];
-  load16(P.u, P.ld, P.L, n0, l, r);
+  init_decay(dec, d.lna);   // its barrier also publishes the mbarrier's initialisation
+  const int t = threadIdx.x, n0 = it.idx * kDynChunk + t * kPer, L = P.L, ld = P.ld;
+  if (tma) {
+    const bool late = !stage_wait(&bar);
+    if (__syncthreads_or(late)) {   // the copies did not arrive: report, let them land (bounded), skip the chunk
+      if (t == 0) {
+        *(volatile int*)c.err = 1;
+        stage_wait(&bar);
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  auto quad = [&](int ch, int q) {
+    const int n = n0 + 4 * q;
+    if (tma) return mask_quad(stage_quad(stage, ch, t, q), n, L);
+    return n < L ? tail_zero(*reinterpret_cast<const float4*>(P.u + ch * ld + n), n, L) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
   float s = 0.f;
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const float m = l[j] + r[j];
-    s = d.alpha * s + d.beta * (m * m);
+  for (int q = 0; q < kPer / 4; ++q) {
+    const float4 a = quad(0, q), b = quad(1, q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float m = q_at(a, e) + q_at(b, e);
+      s = d.alpha * s + d.beta * (m * m);
+    }
   }
-  float v[1] = {s * (dec[31 - (threadIdx.x & 31)] * dec[32 + 7 - (threadIdx.x >> 5)])};   // alpha^(16 (255 - t))
+  float v[1] = {s * (dec[31 - (t & 31)] * dec[32 + 7 - (t >> 5)])};   // alpha^(16 (255 - t))
   float out[1];
   block_sum<1>(v, red, out);
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     const float A = expf((float)kDynChunk * d.lna);
     s_in = chain_link(c, P, it.idx, it.idx + 1, it.idx == 0, out[0], A, s_gen, c.chain_hold && s_idx == 0, P.carry);
   }
   __syncthreads();
   const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
   float g = scan_fwd_excl(s, dec, dec + 32, s_in, red);
-  load16(P.u, P.ld, P.L, n0, l, r);   // again, from L2
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const float m = l[j] + r[j];
-    g = d.alpha * g + d.beta * (m * m);
-    const float Gu = logf(g + kEnvEps);
-    const float gain = expf(gain_law_v(d, Gu) - Gu);
-    l[j] = w * (gain * l[j]) + wd * l[j];
-    r[j] = w * (gain * r[j]) + wd * r[j];
+  for (int q = 0; q < kPer / 4; ++q) {
+    const float4 a = quad(0, q), b = quad(1, q);   // again: shared memory, or L2
+    float yl[4], yr[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float ul = q_at(a, e), ur = q_at(b, e), m = ul + ur;
+      g = d.alpha * g + d.beta * (m * m);
+      const float Gu = logf(g + kEnvEps);
+      const float gain = expf(gain_law_v(d, Gu) - Gu);
+      yl[e] = w * (gain * ul) + wd * ul;
+      yr[e] = w * (gain * ur) + wd * ur;
+    }
+    const int n = n0 + 4 * q;
+    if (n < L) {
+      store_quad(P.y, n, L, yl[0], yl[1], yl[2], yl[3]);
+      store_quad(P.y + ld, n, L, yr[0], yr[1], yr[2], yr[3]);
+    }
   }
-  store16(P.y, P.ld, P.L, n0, l, r);
 }
 
 // dL/dg at one sample, plus accumulation of the gain-law parameter partials and dw.
@@ -346,15 +400,19 @@ __device__ __forceinline__ float4 load_quad(const float* row, int n, int L) {
   return n < L ? tail_zero(*reinterpret_cast<const float4*>(row + n), n, L) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__device__ __forceinline__ float q_at(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
-
 // Backward.  Step 1, everything that does not depend on lambda: per sample dL/dg (to aux) and the part of du
-// without the envelope term (to du), the partials of dL/dT, dL/dW, dL/dR and dL/dw, and the chunk's zero-start
-// lambda aggregate.  Step 2, the chained lambda state from the right.  Step 3: lambda[n] = dL/dg[n] +
-// alpha lambda[n+1] from that state, du += 2 beta lambda m on both channels, and the partial of
-// dL/dalpha = sum lambda[n] (g[n-1] - x[n]); u, aux and du come back from L1 / L2.  Steps 1 and 3 stream their
-// samples a quad at a time, so a thread holds its 16 samples' mid signal and envelope terms only in step 3.
+// without the envelope term, the partials of dL/dT, dL/dW, dL/dR and dL/dw, and the chunk's zero-start lambda
+// aggregate.  Step 2, the chained lambda state from the right.  Step 3: lambda[n] = dL/dg[n] + alpha lambda[n+1]
+// from that state, du += 2 beta lambda m on both channels, and the partial of dL/dalpha =
+// sum lambda[n] (g[n-1] - x[n]).  With tensor maps of u and dL/dy the chunk of both arrives by TMA: step 1 reads
+// them from shared memory and leaves its part of du over dL/dy there, step 3 reads u and that part back from
+// shared memory and dL/dg from L2, and du is written once.  Without maps u and dL/dy are read from global memory
+// and step 1's part of du goes through global memory.  Both steps stream a quad at a time.
 __global__ void __launch_bounds__(kThreads, 3) k_dyn_bwd(LaunchCtx c, const Item* __restrict__ items) {
+  extern __shared__ unsigned char dsm[];
+  float* stage = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
+  float* dstage = stage + 2 * kDynChunk;   // dL/dy, then step 1's part of du
+  __shared__ __align__(8) unsigned long long bar;
   __shared__ float sm[32 * 5];
   __shared__ int s_idx;
   __shared__ unsigned s_gen;
@@ -362,16 +420,36 @@ __global__ void __launch_bounds__(kThreads, 3) k_dyn_bwd(LaunchCtx c, const Item
   __shared__ float dec[kDecay];
   const Item it = take_item(c, items, &s_idx, &s_gen);
   const ProcDev& P = c.procs[it.proc];
+  const bool tma = P.umap != nullptr && P.dymap != nullptr;
+  if (tma && threadIdx.x == 0) {
+    stage_init(&bar, 4 * kChanBytes);
+    stage_copy(P.umap, P.ld, it.idx, stage, &bar);
+    stage_copy(P.dymap, P.ld, it.idx, dstage, &bar);
+  }
   const DynParams d = dyn_params(P);
-  init_decay(dec, d.lna);
+  init_decay(dec, d.lna);   // its barrier also publishes the mbarrier's initialisation
   const float w = dry_wet_w(c, P.qidx), wd = dry_wet_d(c, P.qidx);
-  const int n0 = it.idx * kDynChunk + threadIdx.x * kPer;
-  const int L = P.L, ld = P.ld;
+  const int t = threadIdx.x, n0 = it.idx * kDynChunk + t * kPer, L = P.L, ld = P.ld;
+  if (tma) {
+    const bool late = !stage_wait(&bar);
+    if (__syncthreads_or(late)) {   // the copies did not arrive: report, let them land (bounded), skip the chunk
+      if (t == 0) {
+        *(volatile int*)c.err = 1;
+        stage_wait(&bar);
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  auto uq = [&](int ch, int q) {
+    const int n = n0 + 4 * q;
+    return tma ? mask_quad(stage_quad(stage, ch, t, q), n, L) : load_quad(P.u + ch * ld, n, L);
+  };
   {
     float s = 0.f;
 #pragma unroll
     for (int q = 0; q < kPer / 4; ++q) {
-      const float4 a = load_quad(P.u, n0 + 4 * q, L), b = load_quad(P.u + ld, n0 + 4 * q, L);
+      const float4 a = uq(0, q), b = uq(1, q);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float m = q_at(a, e) + q_at(b, e);
@@ -384,8 +462,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_dyn_bwd(LaunchCtx c, const Item
 #pragma unroll
     for (int q = 0; q < kPer / 4; ++q) {
       const int n = n0 + 4 * q;
-      const float4 a = load_quad(P.u, n, L), b = load_quad(P.u + ld, n, L);
-      const float4 ga = load_quad(P.dy, n, L), gb = load_quad(P.dy + ld, n, L);
+      const float4 a = uq(0, q), b = uq(1, q);
+      const float4 ga = tma ? mask_quad(stage_quad(dstage, 0, t, q), n, L) : load_quad(P.dy, n, L);
+      const float4 gb = tma ? mask_quad(stage_quad(dstage, 1, t, q), n, L) : load_quad(P.dy + ld, n, L);
       float dl[4], dr[4], dgq[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -399,16 +478,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_dyn_bwd(LaunchCtx c, const Item
         lam = fmaf(pw, dgq[e], lam);
         pw *= d.alpha;
       }
+      if (tma) {
+        *stage_at(dstage, 0, t, q) = make_float4(dl[0], dl[1], dl[2], dl[3]);
+        *stage_at(dstage, 1, t, q) = make_float4(dr[0], dr[1], dr[2], dr[3]);
+      }
       if (n < L) {
-        store_quad(P.du, n, L, dl[0], dl[1], dl[2], dl[3]);
-        store_quad(P.du + ld, n, L, dr[0], dr[1], dr[2], dr[3]);
+        if (!tma) {
+          store_quad(P.du, n, L, dl[0], dl[1], dl[2], dl[3]);
+          store_quad(P.du + ld, n, L, dr[0], dr[1], dr[2], dr[3]);
+        }
         store_quad(P.aux, n, L, dgq[0], dgq[1], dgq[2], dgq[3]);
       }
     }
-    float v[5] = {lam * (dec[threadIdx.x & 31] * dec[32 + (threadIdx.x >> 5)]), acc.dT, acc.dW, acc.dR, acc.dw};
+    float v[5] = {lam * (dec[t & 31] * dec[32 + (t >> 5)]), acc.dT, acc.dW, acc.dR, acc.dw};
     float out[5];
     block_sum<5>(v, sm, out);
-    if (threadIdx.x == 0) {
+    if (t == 0) {
       float* bp = P.bpart + (size_t)it.idx * kNPart;
 #pragma unroll
       for (int j = 1; j < 5; ++j) bp[j] = out[j];
@@ -422,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_dyn_bwd(LaunchCtx c, const Item
   float s = 0.f;
 #pragma unroll
   for (int q = 0; q < kPer / 4; ++q) {
-    const float4 a = load_quad(P.u, n0 + 4 * q, L), b = load_quad(P.u + ld, n0 + 4 * q, L);
+    const float4 a = uq(0, q), b = uq(1, q);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       m[4 * q + e] = q_at(a, e) + q_at(b, e);
@@ -449,7 +534,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_dyn_bwd(LaunchCtx c, const Item
   for (int q = kPer / 4 - 1; q >= 0; --q) {
     const int n = n0 + 4 * q;
     const float4 dg = load_quad(P.aux, n, L);
-    const float4 a = load_quad(P.du, n, L), b = load_quad(P.du + ld, n, L);
+    const float4 a = tma ? stage_quad(dstage, 0, t, q) : load_quad(P.du, n, L);
+    const float4 b = tma ? stage_quad(dstage, 1, t, q) : load_quad(P.du + ld, n, L);
     float dl[4] = {a.x, a.y, a.z, a.w}, dr[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int e = 3; e >= 0; --e) {
@@ -468,18 +554,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_dyn_bwd(LaunchCtx c, const Item
   float v[1] = {dalpha};
   float out[1];
   block_sum<1>(v, sm, out);
-  if (threadIdx.x == 0) P.bpart[(size_t)it.idx * kNPart] = out[0];
+  if (t == 0) P.bpart[(size_t)it.idx * kNPart] = out[0];
+}
+
+void init_dyn_attributes() {
+  cudaFuncSetAttribute(k_dyn_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynBwdSmem);
 }
 
 void launch_dyn_fwd(const LaunchCtx& c, const Item* items, int n) {
   if (!n) return;
   k_chain_begin<<<1, 1, 0, c.stream>>>(c.chain);
-  k_dyn_fwd<<<n, kThreads, 0, c.stream>>>(c, items);
+  k_dyn_fwd<<<n, kThreads, kDynFwdSmem, c.stream>>>(c, items);
 }
 void launch_dyn_bwd(const LaunchCtx& c, const Item* items, int n) {
   if (!n) return;
   k_chain_begin<<<1, 1, 0, c.stream>>>(c.chain);
-  k_dyn_bwd<<<n, kThreads, 0, c.stream>>>(c, items);
+  k_dyn_bwd<<<n, kThreads, kDynBwdSmem, c.stream>>>(c, items);
 }
 
 }  // namespace mg

@@ -78,6 +78,8 @@ struct ProcDev {
   float* carry;                            // [nchunks] forward state entering each chunk
   float* chunkagg;                         // [nchunks] per-chunk aggregates
   unsigned long long* cflag;               // [nchunks] chained-scan states: launch generation << 32 | state bits
+  const void* umap;                        // c, n: tensor map (TMA) of u as rows of 32 floats, or nullptr
+  const void* dymap;                       // c, n: the same of dL/dy (backward), or nullptr
   int nchunks;
   // reverb
   const float2* nspec;                     // [2][F][193] STFT of the fixed mid/side noise
@@ -171,6 +173,7 @@ void launch_rev_adj(const LaunchCtx&, const Item* items, int n);
 void launch_rev_adj_fin(const LaunchCtx&, const int* procs, int n);
 void launch_rev_noise_stft(const LaunchCtx&, const Item* items, int n, const float* noise, int noise_len);
 void init_col_attributes();      // column passes of the four-step convolution (called by the last)
+void init_dyn_attributes();      // compressor / gate scans (called by the last)
 void init_row_bwd_attributes();  // backward row pass (called by the next)
 void init_kernel_attributes();
 void init_loss_attributes();
