@@ -273,11 +273,12 @@ mg_status fail(mg_console* c, mg_status s, const std::string& msg) {
 // planning (host only)
 // ------------------------------------------------------------------------------------------------
 // Four-step split of N = f 2^logN into rows N1 = f 2^logN1 and columns N2 = 2^logN2; a split is valid when the
-// rows fit the row kernels (N1 <= 2048, or 3072 with the factor 3), a column tile holds at least one column
-// (N2 <= 8192) and both factors are at least 8 (16 for the rows, one radix-16 pass).
+// rows fit the row kernels (N1 <= 2048, 3072 with the factor 3, 2560 with the factor 5), a column tile holds at
+// least one column (N2 <= 8192) and both factors are at least 8 (16 for the rows, one radix-16 pass).
 bool split_ok(int f, int logN, int logN1) {
   const int logN2 = logN - logN1;
-  return logN1 >= 4 && logN2 >= 3 && logN2 <= 13 && (f << logN1) <= (f == 1 ? 2048 : 3072);
+  const int max_a = f == 1 ? 11 : (f == 3 ? kPtw3MaxA : kPtw5MaxA);
+  return logN1 >= 4 && logN2 >= 3 && logN2 <= 13 && logN1 <= max_a;
 }
 void apply_split(HostProc& p, int logN1) {
   p.logN1 = logN1;
@@ -330,11 +331,20 @@ void size_proc(HostProc& p, double fs) {
     if (t == T_E) { p.n0 = -kEqHalf; p.Nh = kEqTaps; }
     if (t == T_D) { p.n0 = -kDlyHalf; p.Nh = kDlyTaps * D + kDlyFir - 1; }
     if (t == T_R) { p.n0 = 0; p.Nh = revlen; p.nframes = (revlen - kRevFft) / kRevHop + 1; }
-    // N = f 2^logN >= L + taps: the smaller of 2^k and 3 2^k'; rows N1 = f 2^logN1, columns N2 = 2^logN2
+    // N = f 2^logN >= L + taps: the smallest of 2^k, 3 2^k' and 5 2^k''; rows N1 = f 2^logN1, columns
+    // N2 = 2^logN2
     const int64_t need = (int64_t)p.L + p.Nh + std::abs(p.n0) + 1;
     const int k2 = std::max(12, ilog2_ceil(need));
     const int k3 = std::max(11, ilog2_ceil((need + 2) / 3));
-    if (t != T_E && ((int64_t)3 << k3) < ((int64_t)1 << k2)) {
+    const int k5 = std::max(10, ilog2_ceil((need + 4) / 5));
+    const int64_t n2 = (int64_t)1 << k2, n3 = (int64_t)3 << k3, n5 = (int64_t)5 << k5;
+    // 5 2^k'' when the rows fit (N1 = 5 2^logN1 <= 2560 with N2 <= 2^10)
+    if (t != T_E && n5 < n3 && n5 < n2 && k5 - std::min(10, (k5 + 1) / 2) <= kPtw5MaxA) {
+      p.f = 5;
+      p.logN = k5;
+      p.logN2 = std::min(10, (k5 + 1) / 2);
+      p.logN1 = k5 - p.logN2;
+    } else if (t != T_E && n3 < n2) {
       p.f = 3;
       p.logN = k3;
       p.logN2 = std::min(10, (k3 + 1) / 2);
@@ -946,9 +956,9 @@ void fill_procdev(mg_console* c, int pi) {
   d.logN1 = p.logN1;
   d.logN2 = p.logN2;
   d.f = p.f;
-  for (int r = 0; r < 3; ++r) {   // exp(-2 pi i r / N), N = 3 2^logN (used when f = 3)
-    const double ang = -2.0 * 3.14159265358979323846 * r / (3.0 * std::ldexp(1.0, p.logN));
-    d.c3n[r] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  for (int r = 0; r < 5; ++r) {   // exp(-2 pi i r / N), N = f 2^logN, r < f (used when f = 3, 5)
+    const double ang = -2.0 * 3.14159265358979323846 * r / ((double)std::max(1, p.f) * std::ldexp(1.0, p.logN));
+    d.cfn[r] = r < p.f ? make_float2((float)std::cos(ang), (float)std::sin(ang)) : make_float2(1.f, 0.f);
   }
   d.colG = p.colG;
   d.n0 = p.n0;
@@ -1761,20 +1771,26 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
         c3[a * 3 + r] = make_float2((float)std::cos(ang), (float)std::sin(ang));
       }
     c->tab.c3 = (const float2*)up_table(c3.data(), c3.size() * sizeof(float2));
-    std::vector<float2> ptw(kPtwCount), ptw3(kPtw3Count);
+    std::vector<float2> ptw(kPtwCount), ptw3(kPtw3Count), ptw5(kPtw5Count);
     for (int e = 0; e < kPtwCount; ++e) ptw[e] = tw[ptw_source(e)];
-    for (int a = 1; a <= kPtw3MaxA; ++a)
-      for (int lp2 = 0; lp2 < a; lp2 += 4) {
-        const int logr = std::min(4, a - lp2), p = 3 << lp2;
-        for (int r = 0; r < logr; ++r)
-          for (int k = 0; k < p; ++k) {
-            const int64_t m = ((int64_t)k << r) << (a - lp2 - logr);
-            const double ang = -2.0 * PI * (double)m / (3.0 * std::ldexp(1.0, a));
-            ptw3[ptw3_base(a, lp2) + r * p + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-          }
-      }
+    // pass twiddles of the F 2^a-point transforms (layout of ptwf_base), in double then rounded
+    auto fill_ptwf = [&](std::vector<float2>& t, int f, int max_a) {
+      for (int a = 1; a <= max_a; ++a)
+        for (int lp2 = 0; lp2 < a; lp2 += 4) {
+          const int logr = std::min(4, a - lp2), p = f << lp2;
+          for (int r = 0; r < logr; ++r)
+            for (int k = 0; k < p; ++k) {
+              const int64_t m = ((int64_t)k << r) << (a - lp2 - logr);
+              const double ang = -2.0 * PI * (double)m / ((double)f * std::ldexp(1.0, a));
+              t[ptwf_base(f, a, lp2) + r * p + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            }
+        }
+    };
+    fill_ptwf(ptw3, 3, kPtw3MaxA);
+    fill_ptwf(ptw5, 5, kPtw5MaxA);
     c->tab.ptw = (const float2*)up_table(ptw.data(), ptw.size() * sizeof(float2));
     c->tab.ptw3 = (const float2*)up_table(ptw3.data(), ptw3.size() * sizeof(float2));
+    c->tab.ptw5 = (const float2*)up_table(ptw5.data(), ptw5.size() * sizeof(float2));
     c->tab.cos_eq = (const float*)up_table(ceq.data(), ceq.size() * sizeof(float));
     c->tab.cos_dl = (const float*)up_table(cdl.data(), cdl.size() * sizeof(float));
     c->tab.rev_win = (const float*)up_table(hwin.data(), hwin.size() * sizeof(float));
@@ -1782,7 +1798,8 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     c->tab.hann_eq = (const float*)up_table(heq.data(), heq.size() * sizeof(float));
     c->tab.hann_dl = (const float*)up_table(hdl.data(), hdl.size() * sizeof(float));
     c->tab.dly_w = (const float2*)up_table(dw.data(), dw.size() * sizeof(float2));
-    if (!c->tab.tw || !c->tab.twf || !c->tab.c3 || !c->tab.ptw || !c->tab.ptw3 || !c->tab.dly_w) return fail(c, MG_ERR_OOM, "table allocation failed");
+    if (!c->tab.tw || !c->tab.twf || !c->tab.c3 || !c->tab.ptw || !c->tab.ptw3 || !c->tab.ptw5 || !c->tab.dly_w)
+      return fail(c, MG_ERR_OOM, "table allocation failed");
   }
   // loss resolutions
   c->hres.assign(c->nres, LossRes{});

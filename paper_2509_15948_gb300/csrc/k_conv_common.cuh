@@ -37,13 +37,13 @@ __device__ __forceinline__ int mirror_pos(int k2, int k1, int N1) { return k2 ==
 __device__ __forceinline__ int rows_len(const ProcDev& P) { return P.f << P.logN1; }
 __device__ __forceinline__ int64_t fft_len(const ProcDev& P) { return (int64_t)P.f << P.logN; }
 
-// Transposition twiddle exp(-+2 pi i m / N), m < N: the power-of-two tables, times exp(-2 pi i (m mod 3) / N)
-// when N = 3 2^logN.
+// Transposition twiddle exp(-+2 pi i m / N), m < N: the power-of-two tables, times exp(-2 pi i (m mod f) / N)
+// when N = f 2^logN, f = 3 or 5.
 __device__ __forceinline__ float2 twiddle_node(const ProcDev& P, unsigned m, bool inverse, const Tables& tab) {
   if (P.f == 1) return twiddle_tab(m, P.logN, inverse, tab);
-  const unsigned q = m / 3u, r = m - 3u * q;
+  const unsigned q = m / (unsigned)P.f, r = m - (unsigned)P.f * q;
   float2 w = twiddle_tab(q, P.logN, false, tab);
-  if (r) w = cmul(w, P.c3n[r]);
+  if (r) w = cmul(w, P.cfn[r]);
   if (inverse) w.y = -w.y;
   return w;
 }
@@ -54,7 +54,8 @@ template <bool INV, class LD = fftp::SmemIO, class ST = fftp::SmemIO>
 __device__ __forceinline__ void row_fft(float2* d, const ProcDev& P, int nb, int bs, const Tables& tab, LD ld = LD(),
                                         ST st = ST()) {
   if (P.f == 1) fft_p_io<INV, 1>(d, P.logN1, nb, bs, tab.ptw, ld, st);
-  else fft_p3_io<INV>(d, P.logN1, nb, bs, tab.ptw3, ld, st);
+  else if (P.f == 3) fft_pf_io<INV, 3>(d, P.logN1, nb, bs, tab.ptw3, ld, st);
+  else fft_pf_io<INV, 5>(d, P.logN1, nb, bs, tab.ptw5, ld, st);
 }
 
 // Tap value of the stereo FIR at circular position n (time n, or n - N for the negative taps).

@@ -36,15 +36,18 @@ __host__ __device__ inline int ptw_source(int e) {
   return ((1 << j) * k) << (13 - lp - logr);
 }
 
-// Pass twiddle table of the transforms of size M = 3 * 2^a (1 <= a <= kPtw3MaxA).  Region a starts at
-// 12 (2^a - 2); in it, the twiddled pass number j (p = 3 * 16^j, radix 16 except the last) starts at
-// 12 (16^j - 1) / 15 and owns logr rows of p entries: row r, entry k is exp(-2 pi i m / M),
-// m = (2^r k) 2^(a - 4 j - logr).
+// Pass twiddle tables of the transforms of size M = F 2^a, F = 3 (1 <= a <= kPtw3MaxA) or F = 5
+// (1 <= a <= kPtw5MaxA).  Region a starts at 4F (2^a - 2); in it, the twiddled pass number j (p = F 16^j,
+// radix 16 except the last) starts at 4F (16^j - 1) / 15 and owns logr rows of p entries: row r, entry k is
+// exp(-2 pi i m / M), m = (2^r k) 2^(a - 4 j - logr).
 constexpr int kPtw3MaxA = 10;
 constexpr int kPtw3Count = 12 * ((2 << kPtw3MaxA) - 2);
-__host__ __device__ constexpr int ptw3_base(int a, int lp2) {
-  return 12 * ((1 << a) - 2) + 12 * (((1 << lp2) - 1) / 15);
+constexpr int kPtw5MaxA = 9;
+constexpr int kPtw5Count = 20 * ((2 << kPtw5MaxA) - 2);
+__host__ __device__ constexpr int ptwf_base(int f, int a, int lp2) {
+  return 4 * f * ((1 << a) - 2) + 4 * f * (((1 << lp2) - 1) / 15);
 }
+__host__ __device__ constexpr int ptw3_base(int a, int lp2) { return ptwf_base(3, a, lp2); }
 
 namespace fftp {
 
@@ -250,7 +253,7 @@ __device__ __forceinline__ void pass(float2* __restrict__ d, int logM, int nb, i
   if constexpr (!is_io<ST>) __syncthreads();
 }
 
-// ---- transforms of size M = 3 * 2^a (one radix-3 pass, then radix 16 / 8 / 4 / 2) ----
+// ---- transforms of size M = F 2^a, F = 3 or 5 (one radix-F pass, then radix 16 / 8 / 4 / 2) ----
 
 template <bool INV>
 __device__ __forceinline__ void dft3(float2& x0, float2& x1, float2& x2) {
@@ -264,12 +267,46 @@ __device__ __forceinline__ void dft3(float2& x0, float2& x1, float2& x2) {
   x2 = INV ? csub(m, ihd) : cadd(m, ihd);
 }
 
-// First pass (p = 1, no twiddles): butterfly i < 2^a reads x[i + r 2^a], writes 3 i + q.
-template <bool INV, class LD = SmemIO>
-__device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int bs, LD ld = LD()) {
-  constexpr int PER = 6;                      // 16 elements per thread -> at most 16/3 butterflies
+// 5-point DFT: with s1 = x1 + x4, d1 = x1 - x4, s2 = x2 + x3, d2 = x2 - x3 and c1, c2, s1', s2' the cosines and
+// sines of 2 pi / 5 and 4 pi / 5, X1 = x0 + c1 s1 + c2 s2 - i (s1' d1 + s2' d2), X4 its counterpart with +i,
+// X2 = x0 + c2 s1 + c1 s2 - i (s2' d1 - s1' d2), X3 with +i (forward; the inverse swaps the signs of the i terms).
+template <bool INV>
+__device__ __forceinline__ void dft5(float2& x0, float2& x1, float2& x2, float2& x3, float2& x4) {
+  constexpr float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;   // cos(2 pi / 5), cos(4 pi / 5)
+  constexpr float q1 = 0.95105651629515357f, q2 = 0.58778525229247313f;    // sin(2 pi / 5), sin(4 pi / 5)
+  const float2 s1 = cadd(x1, x4), d1 = csub(x1, x4), s2 = cadd(x2, x3), d2 = csub(x2, x3);
+  const float2 a1 = make_float2(x0.x + c1 * s1.x + c2 * s2.x, x0.y + c1 * s1.y + c2 * s2.y);
+  const float2 a2 = make_float2(x0.x + c2 * s1.x + c1 * s2.x, x0.y + c2 * s1.y + c1 * s2.y);
+  const float2 b1 = make_float2(q1 * d1.x + q2 * d2.x, q1 * d1.y + q2 * d2.y);   // times -i below
+  const float2 b2 = make_float2(q2 * d1.x - q1 * d2.x, q2 * d1.y - q1 * d2.y);
+  const float2 ib1 = make_float2(-b1.y, b1.x), ib2 = make_float2(-b2.y, b2.x);  // i b
+  x0 = cadd(x0, cadd(s1, s2));
+  x1 = INV ? cadd(a1, ib1) : csub(a1, ib1);
+  x4 = INV ? csub(a1, ib1) : cadd(a1, ib1);
+  x2 = INV ? cadd(a2, ib2) : csub(a2, ib2);
+  x3 = INV ? csub(a2, ib2) : cadd(a2, ib2);
+}
+
+template <bool INV, int F>
+__device__ __forceinline__ void dftF(float2 (&v)[F]) {
+  if constexpr (F == 3) dft3<INV>(v[0], v[1], v[2]);
+  else dft5<INV>(v[0], v[1], v[2], v[3], v[4]);
+}
+
+// floor(x / F) for 0 <= x < 2^31: multiply-high by the rounded-up 2^33 / 3, resp. 2^34 / 5 (exact over that range)
+template <int F>
+__device__ __forceinline__ int divF(int x) {
+  if constexpr (F == 3) return (int)(__umulhi((unsigned)x, 0xAAAAAAABu) >> 1);
+  else return (int)(__umulhi((unsigned)x, 0xCCCCCCCDu) >> 2);
+}
+__device__ __forceinline__ int div3(int x) { return divF<3>(x); }
+
+// First pass (p = 1, no twiddles): butterfly i < 2^a reads x[i + r 2^a], writes F i + q.
+template <bool INV, int F, class LD = SmemIO>
+__device__ __forceinline__ void passF(float2* __restrict__ d, int a, int nb, int bs, LD ld = LD()) {
+  constexpr int PER = (16 + F - 1) / F;       // 16 elements per thread -> at most 16/F butterflies
   const int MR = 1 << a, total = nb << a, nth = blockDim.x, tid = threadIdx.x;
-  float2 v[PER][3];
+  float2 v[PER][F];
   int ob[PER];
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
@@ -279,13 +316,13 @@ __device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int
       const int b = it >> a, i = it & (MR - 1);
       if constexpr (is_io<LD>) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) v[s][r] = ld(b, i + r * MR);
+        for (int r = 0; r < F; ++r) v[s][r] = ld(b, i + r * MR);
       } else {
         const float2* src = d + b * bs;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) v[s][r] = src[pidx(i + r * MR)];
+        for (int r = 0; r < F; ++r) v[s][r] = src[pidx(i + r * MR)];
       }
-      dft3<INV>(v[s][0], v[s][1], v[s][2]);
+      dftF<INV, F>(v[s]);
       ob[s] = b * bs;
     }
   }
@@ -295,21 +332,18 @@ __device__ __forceinline__ void pass3(float2* __restrict__ d, int a, int nb, int
     if (ob[s] >= 0) {
       const int i = (tid + s * nth) & (MR - 1);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) d[ob[s] + pidx(3 * i + q)] = v[s][q];
+      for (int q = 0; q < F; ++q) d[ob[s] + pidx(F * i + q)] = v[s][q];
     }
   }
   __syncthreads();
 }
 
-// floor(x / 3) for 0 <= x < 2^31 (multiply by the rounded-up 2^33 / 3, exact over that range)
-__device__ __forceinline__ int div3(int x) { return (int)(__umulhi((unsigned)x, 0xAAAAAAABu) >> 1); }
-
-// Later passes: p = 3 * 2^lp2, radix R = 2^LOGR; butterfly i < M / R, k = i mod p, twiddle w_M^{r k M / (R p)}.
-template <bool INV, int R, int LOGR, class ST = SmemIO>
+// Later passes: p = F 2^lp2, radix R = 2^LOGR; butterfly i < M / R, k = i mod p, twiddle w_M^{r k M / (R p)}.
+template <bool INV, int R, int LOGR, int F, class ST = SmemIO>
 __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int bs, int lp2,
-                                      const float2* __restrict__ ptw3, ST st = ST()) {
+                                      const float2* __restrict__ ptwf, ST st = ST()) {
   constexpr int PER = 16 / R;
-  const int MR = 3 << (a - LOGR), p = 3 << lp2, total = nb * MR;
+  const int MR = F << (a - LOGR), p = F << lp2, total = nb * MR;
   const int nth = blockDim.x, tid = threadIdx.x;
   float2 v[PER][R];
   int ob[PER];
@@ -318,12 +352,12 @@ __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int
     const int it = tid + s * nth;
     ob[s] = -1;
     if (it < total) {
-      const int b = div3(it >> (a - LOGR)), i = it - b * MR;   // it / MR, MR = 3 * 2^(a - LOGR)
-      const int k = i - p * div3(i >> lp2);                       // i mod p, p = 3 * 2^lp2
+      const int b = divF<F>(it >> (a - LOGR)), i = it - b * MR;   // it / MR, MR = F 2^(a - LOGR)
+      const int k = i - p * divF<F>(i >> lp2);                      // i mod p, p = F 2^lp2
       const float2* src = d + b * bs;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[s][r] = src[pidx(i + r * MR)];
-      if (k) twiddle<INV, R>(v[s], ptw3 + ptw3_base(a, lp2) + k, p);
+      if (k) twiddle<INV, R>(v[s], ptwf + ptwf_base(F, a, lp2) + k, p);
       dftR<INV, R>(v[s]);
       ob[s] = b * bs + (i - k) * R + k;
     }
@@ -332,7 +366,7 @@ __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int
 #pragma unroll
   for (int s = 0; s < PER; ++s) {
     if (ob[s] >= 0) {
-      const int b = div3((tid + s * nth) >> (a - LOGR));
+      const int b = divF<F>((tid + s * nth) >> (a - LOGR));
       const int e0 = ob[s] - b * bs;
       if constexpr (is_io<ST>) {
 #pragma unroll
@@ -349,38 +383,38 @@ __device__ __forceinline__ void passm(float2* __restrict__ d, int a, int nb, int
 
 }  // namespace fftp
 
-// FFTs of size M = 3 * 2^a (a >= 1) over nb batches in the padded layout, in place; same contract as fft_p.
+// FFTs of size M = F 2^a (a >= 1) over nb batches in the padded layout, in place; same contract as fft_p.
 namespace fftp {
-// passm from p = 3 * 2^LP2 on, the last one writing through st
-template <bool INV, int A, int LP2, class ST>
-__device__ __forceinline__ void fft_p3_from(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw3,
+// passm from p = F 2^LP2 on, the last one writing through st
+template <bool INV, int F, int A, int LP2, class ST>
+__device__ __forceinline__ void fft_pf_from(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptwf,
                                             ST st) {
   constexpr int left = A - LP2;
   if constexpr (left > 4) {
-    passm<INV, 16, 4>(d, A, nb, bs, LP2, ptw3);
-    fft_p3_from<INV, A, LP2 + 4, ST>(d, nb, bs, ptw3, st);
+    passm<INV, 16, 4, F>(d, A, nb, bs, LP2, ptwf);
+    fft_pf_from<INV, F, A, LP2 + 4, ST>(d, nb, bs, ptwf, st);
   } else {
-    passm<INV, 1 << left, left, ST>(d, A, nb, bs, LP2, ptw3, st);
+    passm<INV, 1 << left, left, F, ST>(d, A, nb, bs, LP2, ptwf, st);
   }
 }
 
-template <bool INV, int A, class LD, class ST>
-__device__ __forceinline__ void fft_p3_fixed(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptw3,
+template <bool INV, int F, int A, class LD, class ST>
+__device__ __forceinline__ void fft_pf_fixed(float2* __restrict__ d, int nb, int bs, const float2* __restrict__ ptwf,
                                              LD ld, ST st) {
-  pass3<INV, LD>(d, A, nb, bs, ld);
-  fft_p3_from<INV, A, 0, ST>(d, nb, bs, ptw3, st);
+  passF<INV, F, LD>(d, A, nb, bs, ld);
+  fft_pf_from<INV, F, A, 0, ST>(d, nb, bs, ptwf, st);
 }
 
-template <bool INV>
-__device__ __forceinline__ void fft_p3_generic(float2* __restrict__ d, int a, int nb, int bs,
-                                               const float2* __restrict__ ptw3) {
-  pass3<INV>(d, a, nb, bs);
+template <bool INV, int F>
+__device__ __forceinline__ void fft_pf_generic(float2* __restrict__ d, int a, int nb, int bs,
+                                               const float2* __restrict__ ptwf) {
+  passF<INV, F>(d, a, nb, bs);
   int lp2 = 0;
-  for (; a - lp2 >= 4; lp2 += 4) passm<INV, 16, 4>(d, a, nb, bs, lp2, ptw3);
+  for (; a - lp2 >= 4; lp2 += 4) passm<INV, 16, 4, F>(d, a, nb, bs, lp2, ptwf);
   const int rem = a - lp2;
-  if (rem == 3) passm<INV, 8, 3>(d, a, nb, bs, lp2, ptw3);
-  else if (rem == 2) passm<INV, 4, 2>(d, a, nb, bs, lp2, ptw3);
-  else if (rem == 1) passm<INV, 2, 1>(d, a, nb, bs, lp2, ptw3);
+  if (rem == 3) passm<INV, 8, 3, F>(d, a, nb, bs, lp2, ptwf);
+  else if (rem == 2) passm<INV, 4, 2, F>(d, a, nb, bs, lp2, ptwf);
+  else if (rem == 1) passm<INV, 2, 1, F>(d, a, nb, bs, lp2, ptwf);
 }
 
 // Transforms of a size without a compile-time variant: the functors run as a staging loop before / after.
@@ -405,20 +439,36 @@ __device__ __forceinline__ void stage_out(const float2* __restrict__ d, int M, i
 }
 }  // namespace fftp
 
-// FFTs of size M = 3 * 2^a as fft_p3, with the inputs taken through ld and the outputs put through st (the
-// fftp::SmemIO defaults keep them in the buffer).  With st a functor the call ends without a barrier.
+// FFTs of size M = F 2^a (F = 3 or 5), with the inputs taken through ld and the outputs put through st (the
+// fftp::SmemIO defaults keep them in the buffer).  With st a functor the call ends without a barrier.  The row
+// lengths of the convolutions (F 2^a, a = 8..10 for F = 3, 7..9 for F = 5) run unrolled pass sequences.
+template <bool INV, int F, class LD = fftp::SmemIO, class ST = fftp::SmemIO>
+__device__ void fft_pf_io(float2* __restrict__ d, int a, int nb, int bs, const float2* __restrict__ ptwf,
+                          LD ld = LD(), ST st = ST()) {
+  if constexpr (F == 3) {
+    switch (a) {
+      case 10: fftp::fft_pf_fixed<INV, 3, 10>(d, nb, bs, ptwf, ld, st); return;
+      case 9: fftp::fft_pf_fixed<INV, 3, 9>(d, nb, bs, ptwf, ld, st); return;
+      case 8: fftp::fft_pf_fixed<INV, 3, 8>(d, nb, bs, ptwf, ld, st); return;
+      default: break;
+    }
+  } else {
+    switch (a) {
+      case 9: fftp::fft_pf_fixed<INV, 5, 9>(d, nb, bs, ptwf, ld, st); return;
+      case 8: fftp::fft_pf_fixed<INV, 5, 8>(d, nb, bs, ptwf, ld, st); return;
+      case 7: fftp::fft_pf_fixed<INV, 5, 7>(d, nb, bs, ptwf, ld, st); return;
+      default: break;
+    }
+  }
+  fftp::stage_in<INV>(d, F << a, nb, bs, ld);
+  fftp::fft_pf_generic<INV, F>(d, a, nb, bs, ptwf);
+  fftp::stage_out<INV>(d, F << a, nb, bs, st);
+}
+
 template <bool INV, class LD = fftp::SmemIO, class ST = fftp::SmemIO>
 __device__ void fft_p3_io(float2* __restrict__ d, int a, int nb, int bs, const float2* __restrict__ ptw3, LD ld = LD(),
                           ST st = ST()) {
-  switch (a) {
-    case 10: fftp::fft_p3_fixed<INV, 10>(d, nb, bs, ptw3, ld, st); return;
-    case 9: fftp::fft_p3_fixed<INV, 9>(d, nb, bs, ptw3, ld, st); return;
-    case 8: fftp::fft_p3_fixed<INV, 8>(d, nb, bs, ptw3, ld, st); return;
-    default: break;
-  }
-  fftp::stage_in<INV>(d, 3 << a, nb, bs, ld);
-  fftp::fft_p3_generic<INV>(d, a, nb, bs, ptw3);
-  fftp::stage_out<INV>(d, 3 << a, nb, bs, st);
+  fft_pf_io<INV, 3>(d, a, nb, bs, ptw3, ld, st);
 }
 
 // FFTs of size M = 3 * 2^a (a >= 1) over nb batches in the padded layout, in place; same contract as fft_p.

@@ -65,7 +65,7 @@ struct ProcDev {
   // N2 = 2^logN2 (columns), f in {1, 3}
   int logN, logN1, logN2, colG;            // colG: columns per column-pass work item
   int f;
-  float2 c3n[3];                           // exp(-2 pi i r / N), r < 3 (transposition twiddles when f = 3)
+  float2 cfn[5];                           // exp(-2 pi i r / N), r < f (transposition twiddles when f = 3, 5)
   int n0, Nh;                              // FIR: first tap time, number of taps
   float2* T1;
   float2* T2;
@@ -128,7 +128,8 @@ struct Tables {
   const float2* twf;                       // exp(-2 pi i j / 2^26), j < 8192 (fine factor of large-N twiddles)
   const float2* c3;                        // [14][3] exp(-2 pi i r / (3 2^a)): twiddles of 3 2^a-point FFTs
   const float2* ptw;                       // pass twiddles of the 2^a-point FFTs (layout of ptw_base)
-  const float2* ptw3;                      // pass twiddles of the 3 2^a-point FFTs (layout of ptw3_base)
+  const float2* ptw3;                      // pass twiddles of the 3 2^a-point FFTs (layout of ptwf_base)
+  const float2* ptw5;                      // pass twiddles of the 5 2^a-point FFTs
   const float* cos_eq;                     // cos(2 pi m / 2047), m < 2047
   const float* cos_dl;                     // cos(2 pi m / 39), m < 39
   const float* rev_win;                    // periodic Hann 384

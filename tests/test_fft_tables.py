@@ -1,7 +1,7 @@
 """Layout of the shared-memory FFTs' pass twiddle tables (host side of mg_fftp.cuh), no GPU: every pass of every
 power-of-two transform (2 .. 8192 points) reads exactly the 8192-point table entries its butterflies need, every
-table entry is read, and the 3 * 2^a regions neither overlap nor leave the table.  Compiled with nvcc as host
-code."""
+table entry is read, and the 3 * 2^a and 5 * 2^a regions neither overlap nor leave their tables.  Compiled with
+nvcc as host code."""
 import os
 import shutil
 import subprocess
@@ -39,18 +39,23 @@ int main() {
   }
   int unused = 0;
   for (int e = 0; e < kPtwCount; ++e) unused += !seen[e];
-  std::vector<int> own(kPtw3Count, 0);
   int bad3 = 0;
-  for (int a = 1; a <= kPtw3MaxA; ++a)
-    for (int lp2 = 0; lp2 < a; lp2 += 4) {
-      const int logr = std::min(4, a - lp2), p = 3 << lp2;
-      for (int r = 0; r < logr; ++r)
-        for (int k = 0; k < p; ++k) {
-          const int e = ptw3_base(a, lp2) + r * p + k;
-          if (e < 0 || e >= kPtw3Count || own[e]) ++bad3; else own[e] = 1;
-        }
-      if (logr < 4) break;
-    }
+  auto regions = [&](int f, int max_a, int count) {
+    std::vector<int> own(count, 0);
+    for (int a = 1; a <= max_a; ++a)
+      for (int lp2 = 0; lp2 < a; lp2 += 4) {
+        const int logr = std::min(4, a - lp2), p = f << lp2;
+        for (int r = 0; r < logr; ++r)
+          for (int k = 0; k < p; ++k) {
+            const int e = ptwf_base(f, a, lp2) + r * p + k;
+            if (e < 0 || e >= count || own[e]) ++bad3; else own[e] = 1;
+          }
+        if (logr < 4) break;
+      }
+  };
+  regions(3, kPtw3MaxA, kPtw3Count);
+  regions(5, kPtw5MaxA, kPtw5Count);
+  if (ptw3_base(7, 4) != ptwf_base(3, 7, 4)) ++bad3;
   printf("%d %d %d %d\n", n, bad, unused, bad3);
   return 0;
 }

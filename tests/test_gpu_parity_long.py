@@ -1,8 +1,8 @@
 """CUDA path vs the FP64 oracle at the sizes the throughput benchmark runs (GPU).
 
 * Single-track consoles of the multitap delay and the reverb (Sec. 3.4, 3.7) at lengths that reach each of the
-  five FFT size classes of the uneven 64-song batch (N = 3 2^17, 2^19, 3 2^18, 2^20, 3 2^19), with the
-  row/column split the autotuner picks and with the default split.
+  FFT size classes of the uneven 64-song batch (N = 3 2^17, 2^19, 5 2^17, 3 2^18, 2^20, 5 2^18, 3 2^19), with
+  the row/column split the autotuner picks and with the default split.
 * A batch of ten copies of a 4-track, 30 s song with every processor type, whose arena passes 4 GiB, so that
   the node buffers of the later songs sit at byte offsets beyond 2^32: every copy against the oracle's song.
 * Sampled songs of the benchmark's own console (64 songs, 1,143 tracks, 1,053 s of audio, autotuned splits,
@@ -27,8 +27,10 @@ pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 FS = 44100
-# (seconds, f, log2 N / f): the five size classes of the uneven batch's reverb and delay convolutions
-SIZE_CLASSES = [(6.5, 3, 17), (9.5, 1, 19), (15.0, 3, 18), (20.0, 1, 20), (30.0, 3, 19)]
+# (seconds, f, log2 N / f): the size classes of the uneven batch's reverb and delay convolutions
+# (N = f 2^k, f = 1, 3, 5, the smallest that holds the linear convolution)
+SIZE_CLASSES = [(6.5, 3, 17), (9.5, 1, 19), (11.0, 5, 17), (15.0, 3, 18), (20.0, 1, 20), (25.0, 5, 18),
+                (30.0, 3, 19)]
 
 
 def _free_device():
