@@ -216,9 +216,26 @@ def test_autotuned_splits_keep_parity():
     types = con.processor_types()
     for (f, logn, logn1), t in zip(sz, types):
         if t in "rd":
-            assert f in (1, 3) and 4 <= logn1 and logn - logn1 >= 3 and (f << logn1) <= (2048 if f == 1 else 3072)
+            assert f in (1, 3, 5) and 4 <= logn1 and logn - logn1 >= 3 and (f << logn1) <= {1: 2048, 3: 3072, 5: 2560}[f]
         else:
             assert f == 0
+
+
+@pytest.mark.parametrize("autotune", [0, 1])
+def test_factor5_transform_sizes(autotune):
+    """Transform sizes N = 5 2^k with rows of 5 2^a: a 1 s song (N = 5 2^15, default rows 5 2^7) and a 4.5 s song
+    (N = 5 2^16, default rows 5 2^8) of reverbs and delays, ragged lengths, with the default and the autotuned
+    splits."""
+    lays = [W.SongLayout(2, 0, [-1, -1], 44111), W.SongLayout(1, 0, [-1], 200003)]
+    case = make_case(lays, types="dr", seed=17)
+    con, _, _ = check(case, autotune=autotune)
+    sz = con.fft_sizes()
+    song = con.layout()[2]
+    for (f, logn, logn1), s in zip(sz, song):
+        assert int(f) == 5 and int(logn) == (15 if s == 0 else 16), (f, logn, s)
+        if not autotune:
+            assert int(logn1) == (7 if s == 0 else 8)
+    con.close()
 
 
 def test_full_console_plain_workload():
