@@ -188,7 +188,9 @@ mg_status mg_prune(mg_console* c, const uint8_t* h_keep);
 mg_status mg_get_present(const mg_console* c, uint8_t* h_present);
 
 /* Replace the audio of one song (same K and L): sources [K][L], target [2][L] (NULL keeps the old target);
- * recomputes the target spectrograms.  Copied (host or device). */
+ * recomputes the target spectrograms.  Copied (host or device), stream-ordered: device memory and page-locked
+ * host memory (cudaHostAlloc / cudaHostRegister, mapped) are read by a kernel and must stay valid until the
+ * console's stream reaches the call; pageable host memory is copied before the call returns. */
 mg_status mg_update_audio(mg_console* c, int32_t song, const float* sources, const float* target,
                           int32_t on_device);
 

@@ -123,8 +123,10 @@ class Console:
         raise ValueError(p.type)
 
     def _chain(self, song: int, chain: int, u: torch.Tensor, params, w, present, outs):
+        """Runs one chain; outs[i] receives processor i's output and outs[("in", i)] its input."""
         lg = torch.zeros((), dtype=F64)
         for p in self.by_song_chain.get((song, chain), []):
+            outs[("in", p.index)] = u
             if present is not None and not present[p.index]:
                 outs[p.index] = u
                 continue

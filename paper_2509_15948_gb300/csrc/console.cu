@@ -194,6 +194,8 @@ struct mg_console {
   int loss_per[3] = {0, 0, 0};     // frames per loss work item per resolution (packing tuner; 0: 8192 / n_fft)
   bool debug_sync = false;         // MG_DEBUG_SYNC=1 in the environment: synchronise and check after every launch
   bool dyn_tma = true;             // TMA staging of the compressor / gate forward (MG_DYN_TMA=0: plain loads)
+  float** d_track_in = nullptr;    // input buffer of every track, song-major (mg_update_audio's one-launch ingest)
+  std::vector<int> track_in_base;  // first entry of each song in d_track_in
   bool debug_reported = false;
   ProcDev* d_procs = nullptr;
   SongDev* d_songs = nullptr;
@@ -1956,6 +1958,16 @@ mg_status create_impl(mg_console* c, const mg_console_desc* d, const mg_song_des
     }
     if (tmp) cudaFree(tmp);
   }
+  {
+    std::vector<float*> ins;
+    for (size_t si = 0; si < c->songs.size(); ++si) {
+      const HostSong& hs = c->songs[si];
+      c->track_in_base.push_back((int)ins.size());
+      for (int k = 0; k < hs.K; ++k)
+        ins.push_back((float*)(c->arena + (c->is_graph ? c->o_src[k] : c->chains[hs.tracks_chain[k]].o_in)));
+    }
+    if (upload(c, ins, &c->d_track_in) != MG_OK) return MG_ERR_CUDA;
+  }
   // ---- tables of the node structure ----
   if (build_tables(c) != MG_OK) return MG_ERR_CUDA;
   // ---- reverb noise spectra ----
@@ -3027,11 +3039,25 @@ mg_status mg_update_audio(mg_console* c, int32_t song, const float* sources, con
   if (!c || song < 0 || song >= (int)c->songs.size() || !sources) return fail(c, MG_ERR_INVALID, "bad song or null sources");
   const HostSong& hs = c->songs[song];
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  // mono sources go to the left row of each track input, then ingest duplicates them to both rows
-  for (int t = 0; t < hs.K; ++t) {
-    float* dst = (float*)(c->arena + (c->is_graph ? c->o_src[t] : c->chains[hs.tracks_chain[t]].o_in));
-    CK(cudaMemcpyAsync(dst, sources + (size_t)t * hs.L, sizeof(float) * hs.L, k, c->stream));
-    CK(cudaMemcpyAsync(dst + hs.ld, sources + (size_t)t * hs.L, sizeof(float) * hs.L, k, c->stream));
+  // Sources the device can read (device memory, or page-locked host memory mapped into the address space) go
+  // into both rows of every track input in one kernel launch; pageable host memory is copied track by track
+  // (once across, then a device-side copy of the left row to the right one).
+  const float* readable = on_device ? sources : nullptr;
+  if (!on_device) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, sources) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer)
+      readable = static_cast<const float*>(a.devicePointer);
+    else
+      cudaGetLastError();   // pageable memory: not an error
+  }
+  if (readable && c->d_track_in) {
+    launch_ingest_song(c->stream, readable, c->d_track_in + c->track_in_base[song], hs.K, hs.L, hs.ld);
+  } else {
+    for (int t = 0; t < hs.K; ++t) {
+      float* dst = (float*)(c->arena + (c->is_graph ? c->o_src[t] : c->chains[hs.tracks_chain[t]].o_in));
+      CK(cudaMemcpyAsync(dst, sources + (size_t)t * hs.L, sizeof(float) * hs.L, k, c->stream));
+      CK(cudaMemcpyAsync(dst + hs.ld, dst, sizeof(float) * hs.L, cudaMemcpyDeviceToDevice, c->stream));
+    }
   }
   if (target) {
     CK(cudaMemcpy2DAsync(c->arena + hs.o_tgt, (size_t)hs.ld * sizeof(float), target, (size_t)hs.L * sizeof(float),

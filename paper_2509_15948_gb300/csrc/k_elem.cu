@@ -132,6 +132,18 @@ __global__ void k_ingest(const float* __restrict__ mono, float* __restrict__ st,
   }
 }
 
+// All K mono sources of one song ([K][L], device-readable: device memory or mapped pinned host memory) into
+// both rows of their tracks' input buffers, one launch: blockIdx.y is the track.
+__global__ void k_ingest_song(const float* __restrict__ mono, float* const* __restrict__ dst, int L, int ld) {
+  const float* src = mono + (size_t)blockIdx.y * L;
+  float* st = dst[blockIdx.y];
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < L; n += gridDim.x * blockDim.x) {
+    const float x = src[n];
+    st[n] = x;
+    st[ld + n] = x;
+  }
+}
+
 __global__ void k_copy_mix(const SongDev* songs, int nsongs, float* out, const int64_t* offs) {
   const int s = blockIdx.y;
   const SongDev& S = songs[s];
@@ -154,6 +166,9 @@ void launch_sum(cudaStream_t st, float* const* outs, const float* const* ins, co
 }
 void launch_ingest(cudaStream_t st, const float* mono, float* stereo, int L, int ld) {
   k_ingest<<<min(1024, (L + 255) / 256), 256, 0, st>>>(mono, stereo, L, ld);
+}
+void launch_ingest_song(cudaStream_t st, const float* mono, float* const* dst, int K, int L, int ld) {
+  if (K > 0 && L > 0) k_ingest_song<<<dim3(std::min(256, (L + 255) / 256), K), 256, 0, st>>>(mono, dst, L, ld);
 }
 void launch_copy_mix(cudaStream_t st, const SongDev* songs, int nsongs, float* out, const int64_t* offs) {
   if (nsongs) k_copy_mix<<<dim3(256, nsongs), 256, 0, st>>>(songs, nsongs, out, offs);

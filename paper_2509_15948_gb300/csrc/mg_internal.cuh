@@ -160,6 +160,7 @@ void launch_gs_bwd(const LaunchCtx&, const Item* items, int n);
 void launch_sum(cudaStream_t, float* const* outs, const float* const* ins, const int* in_beg, const int* L,
                 const int* ld, const Item* items, int n, int tile);
 void launch_ingest(cudaStream_t, const float* mono, float* stereo, int L, int ld);
+void launch_ingest_song(cudaStream_t, const float* mono, float* const* dst, int K, int L, int ld);
 // envelope scans: chained single-pass forward (items in chunk order) and backward (items in reverse chunk order)
 void launch_dyn_fwd(const LaunchCtx&, const Item* items, int n);
 void launch_dyn_bwd(const LaunchCtx&, const Item* items, int n);

@@ -68,8 +68,9 @@ def rel_l2(a, b) -> float:
 
 
 def oracle_with_delay_taps(case: Case, alpha_p: float):
-    """Oracle losses, gradients and mixes, plus for every delay processor the oracle's dL/dh (taps) and its
-    39-tap FIRs c_m (captured from the forward/backward of the same call)."""
+    """Oracle losses, gradients and mixes, plus for every delay processor, from the forward/backward of the same
+    call: (dL/dh, its 39-tap FIRs c_m, |u| its input's magnitude, dL/dy_bar = w dL/dy its wet adjoint)."""
+    import torch
     from oracle import processors as OP
     cap = []
     orig = OP.DelayScatter.apply
@@ -83,12 +84,33 @@ def oracle_with_delay_taps(case: Case, alpha_p: float):
 
     OP.DelayScatter.apply = hook
     try:
-        losses, grads, mixes = case.oracle.loss_and_grad(case.params, alpha_p=alpha_p)
+        x = torch.tensor(np.asarray(case.params, np.float64), dtype=torch.float64, requires_grad=True)
+        res = case.oracle.forward(x, alpha_p=alpha_p, keep_outputs=True)
+        dprocs = [p for p in case.oracle.procs if p.type == "d"]
+        for p in dprocs:
+            res[p.song]["outputs"][p.index].retain_grad()
+        sum(r["total"] for r in res).backward()
     finally:
         OP.DelayScatter.apply = orig
-    dprocs = [p for p in case.oracle.procs if p.type == "d"]
-    taps = {p.index: (t.grad.numpy(), c) for p, (t, c) in zip(dprocs, cap)}
+    losses = np.array([[float(r[k].detach()) for k in ("La", "Llr", "Lm", "Ls", "Lg", "Lp", "total")] for r in res])
+    grads = x.grad.detach().numpy().copy()
+    mixes = [r["mix"].detach().numpy() for r in res]
+    q = np.asarray(case.params, np.float64)[case.oracle.n_proc_params:]
+    taps = {}
+    for p, (t, c) in zip(dprocs, cap):
+        o = res[p.song]["outputs"]
+        u_abs = np.abs(o[("in", p.index)].detach().numpy())
+        dybar = o[p.index].grad.numpy() / (1.0 + np.exp(-q[p.index]))
+        taps[p.index] = (t.grad.numpy(), c, u_abs, dybar)
     return losses, grads, mixes, taps
+
+
+def lag_correlation(a, b, nh: int, n0: int = -19):
+    """c[j] = sum_n a[n] b[n - j] at the tap lags j = n0 .. n0 + nh - 1 (both [2][L]), per channel, FP64."""
+    L = a.shape[1]
+    M = 1 << int(np.ceil(np.log2(2 * L + nh)))
+    lags = (np.arange(nh) + n0) % M
+    return np.stack([np.fft.irfft(np.fft.rfft(a[ch], M) * np.conj(np.fft.rfft(b[ch], M)), M)[lags] for ch in range(2)])
 
 
 def delay_term_rms(case: Case, alpha_p: float = 1e-3, D: int = None, n0: int = -19) -> dict:
@@ -111,7 +133,7 @@ def delay_term_rms(case: Case, alpha_p: float = 1e-3, D: int = None, n0: int = -
         if p.type != "d":
             continue
         o = res[p.song]["outputs"]
-        u = np.abs(o[p.index - 1].detach().numpy())
+        u = np.abs(o[("in", p.index)].detach().numpy())
         db = np.abs(o[p.index].grad.numpy()) / (1.0 + np.exp(-q[p.index]))
         L = u.shape[1]
         nh = 20 * D + 38                      # taps of Eq. (17): 20 slots of D plus the 39-tap FIR span
@@ -135,7 +157,7 @@ def delay_slot_conditioning(case: Case, taps: dict, D: int = None, term_rms: dic
     for p in case.oracle.procs:
         if p.type != "d":
             continue
-        dh, cvals = taps[p.index]
+        dh, cvals = taps[p.index][:2]
         kap = np.zeros((2, 20))
         for ch in range(2):
             rms = term_rms[p.index][ch] if term_rms is not None else np.sqrt(np.mean(dh[ch] ** 2))
