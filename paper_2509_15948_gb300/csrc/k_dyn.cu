@@ -236,9 +236,10 @@ __device__ __forceinline__ float chain_link(const LaunchCtx& c, const ProcDev& P
 
 __device__ __forceinline__ float q_at(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
 
-// ---- TMA staging of a forward chunk ----
-// With a tensor map of the node's input u (rows of 32 floats = 128 bytes, both channels: 2 ld / 32 rows), one
-// thread stages the chunk's 128 rows of each channel into shared memory with two bulk tensor copies
+// ---- TMA staging of a scan chunk ----
+// With a tensor map of a node's [2][ld] buffer (its input u, or in the backward also its adjoint dL/dy: rows of
+// 32 floats = 128 bytes, both channels: 2 ld / 32 rows), one thread stages the chunk's 128 rows of each channel
+// into shared memory with two bulk tensor copies
 // (cp.async.bulk.tensor, 128-byte swizzle) completing on an mbarrier.  Rows past the tensor read as zeros; rows of
 // the left channel past its ld read the right channel's first rows, and every sample at or beyond L is masked
 // anyway.  The swizzle stores the 16-byte chunk c of row r at chunk c ^ (r mod 8), so the quads a thread reads

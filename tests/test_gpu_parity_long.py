@@ -1,8 +1,9 @@
 """CUDA path vs the FP64 oracle at the sizes the throughput benchmark runs (GPU).
 
 * Single-track consoles of the multitap delay and the reverb (Sec. 3.4, 3.7) at lengths that reach each of the
-  FFT size classes of the uneven 64-song batch (N = 3 2^17, 2^19, 5 2^17, 3 2^18, 2^20, 5 2^18, 3 2^19), with
-  the row/column split the autotuner picks and with the default split.
+  FFT size classes of the uneven 64-song batch (N = 3 2^17, 2^19, 5 2^17, 3 2^18, 2^20, 5 2^18, 3 2^19) and at
+  the largest sizes of the factors 5 and 3 (57 s: N = 5 2^19, 60 s: N = 3 2^20, rows at the row kernels' limits
+  of 2560 and 3072 points), with the row/column split the autotuner picks and with the default split.
 * A batch of ten copies of a 4-track, 30 s song with every processor type, whose arena passes 4 GiB, so that
   the node buffers of the later songs sit at byte offsets beyond 2^32: every copy against the oracle's song.
 * Sampled songs of the benchmark's own console (64 songs, 1,143 tracks, 1,053 s of audio, autotuned splits,
@@ -31,6 +32,8 @@ FS = 44100
 # (N = f 2^k, f = 1, 3, 5, the smallest that holds the linear convolution)
 SIZE_CLASSES = [(6.5, 3, 17), (9.5, 1, 19), (11.0, 5, 17), (15.0, 3, 18), (20.0, 1, 20), (25.0, 5, 18),
                 (30.0, 3, 19)]
+# the largest transforms of each factor: rows of 5 2^9 = 2560 and 3 2^10 = 3072 points (the row kernels' limits)
+MAX_CLASSES = [(57.0, 5, 19), (60.0, 3, 20)]
 
 
 def _free_device():
@@ -49,7 +52,7 @@ def _song_slices(con, s):
     return procs, pidx
 
 
-@pytest.mark.parametrize("seconds,f,logn", SIZE_CLASSES)
+@pytest.mark.parametrize("seconds,f,logn", SIZE_CLASSES + MAX_CLASSES)
 def test_reverb_and_delay_at_benchmark_fft_sizes(seconds, f, logn):
     _free_device()
     L = int(seconds * FS)
