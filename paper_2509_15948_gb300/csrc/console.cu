@@ -660,6 +660,8 @@ void run_procs(mg_console* c, int fam, const ProcList& L, F&& f) {
   for (size_t i = 0; i < L.h.size(); ++i) run(c, fam, [&] { f(L.d + i, 1); });
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
 LaunchCtx make_ctx(mg_console* c, const uint8_t* mask) {
   LaunchCtx x{};
   x.stream = c->stream;
@@ -673,6 +675,7 @@ LaunchCtx make_ctx(mg_console* c, const uint8_t* mask) {
   x.chain = c->d_chain;
   x.err = c->d_err;
   x.chain_hold = c->chain_hold;
+  x.dyn_tma = c->dyn_tma && tensor_map_encoder() != nullptr;
   x.tab = c->tab;
   return x;
 }

@@ -565,12 +565,12 @@ void init_dyn_attributes() {
 void launch_dyn_fwd(const LaunchCtx& c, const Item* items, int n) {
   if (!n) return;
   k_chain_begin<<<1, 1, 0, c.stream>>>(c.chain);
-  k_dyn_fwd<<<n, kThreads, kDynFwdSmem, c.stream>>>(c, items);
+  k_dyn_fwd<<<n, kThreads, c.dyn_tma ? kDynFwdSmem : 0, c.stream>>>(c, items);   // no stage without maps
 }
 void launch_dyn_bwd(const LaunchCtx& c, const Item* items, int n) {
   if (!n) return;
   k_chain_begin<<<1, 1, 0, c.stream>>>(c.chain);
-  k_dyn_bwd<<<n, kThreads, kDynBwdSmem, c.stream>>>(c, items);
+  k_dyn_bwd<<<n, kThreads, c.dyn_tma ? kDynBwdSmem : 0, c.stream>>>(c, items);
 }
 
 }  // namespace mg

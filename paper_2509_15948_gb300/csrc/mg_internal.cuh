@@ -151,6 +151,7 @@ struct LaunchCtx {
   unsigned* chain;                         // device [2]: launch generation and work ticket of the chained scans
   int* err;                                // host-mapped error word: 1 = a chained scan's wait ran out
   int chain_hold;                          // test hook: the first work item does not publish its state
+  int dyn_tma;                             // the scans' nodes may carry tensor maps (their launches reserve the stage)
   Tables tab;
 };
 
