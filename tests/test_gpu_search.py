@@ -222,3 +222,45 @@ def test_consistency_check_runs_the_protocol():
                                   finetune_steps=3, seed=1)
     assert set(scores) >= {"mu"} and all(0.0 <= v <= 1.0 for d in scores.values() for v in d.values())
     print("consistency", {k: round(v["f1"], 3) for k, v in scores.items()})
+
+
+def test_config1_trained_round_replayed_through_oracle():
+    """The single-song search configuration (16 tracks x 10 s, 4 subgroups of 4): 2,000 Adam steps at lr 1e-2
+    on the GPU from the N(0, 0.1^2) initialisation, then one dry/wet round (Alg. 3, tau = 0.01) from the trained
+    parameters.  The oracle replays the round's trial sequence at the same parameters (the pruned-set identity
+    protocol): every trial's L_a and d = L_a - L_min against the oracle's FP64 values, and the same decision
+    wherever d is not a near tie, so with no near tie the accepted set is the oracle's."""
+    tau = 0.01
+    case = make_case([W.layout_single_search()], seed=11)
+    con = gpu_console(case)
+    con.set_params(case.params)
+    for _ in range(2000):
+        con.train_step(1e-2)
+    params = con.get_params().cpu().numpy()
+    P = con.n_processors
+    l_min_g = float(con.prune_scores(np.ones((1, P), np.uint8))[0, 0])
+    _, _, trials = GS.dry_wet_round(con, [l_min_g], tau, [GS.SplitMix64(GS.song_seed(7, 0))])
+    assert len(trials) >= 5
+    full, floor = la_floor(case, params)
+    l_min_o = full[0, 0]
+    assert abs(l_min_g - l_min_o) <= LA_TOL * abs(l_min_o) + floor
+    removed, near_ties, accepted = set(), 0, 0
+    for t in trials:
+        mask = np.ones(P, np.uint8)
+        mask[list(removed | set(t.candidates))] = 0
+        la_o = case.oracle.losses(params, mask=mask)[0][0, 0]
+        assert abs(t.la - la_o) <= LA_TOL * abs(la_o) + floor, (t, la_o, floor)
+        d_g, d_o = t.la - l_min_g, la_o - l_min_o
+        tol = D_TOL * abs(d_o) + 1e-6 * abs(la_o) + floor
+        assert abs(d_g - d_o) <= tol, (t, d_g, d_o, tol)
+        if abs(d_o - tau) <= 2 * tol:
+            near_ties += 1
+        else:
+            assert (d_o < tau) == t.accepted, (t, d_o)
+        if t.accepted:
+            accepted += 1
+            l_min_o, l_min_g = min(l_min_o, la_o), min(l_min_g, t.la)
+            removed |= set(t.candidates)
+    print(f"config-1 round: {len(trials)} trials, {accepted} accepted, {len(removed)} of {P} pruned, "
+          f"near ties {near_ties}, L_a {full[0, 0]:.4f} after training")
+    con.close()
