@@ -117,17 +117,12 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
       }
     }
     __syncthreads();
-    // band values from the magnitudes, one thread per (frame, band, channel)
+    // band values from the magnitudes: with narrow bands (few Mel weights per band on average) one thread per
+    // (frame, band, channel); with wide ones one warp per (frame, band), its lanes striding the band's bins and
+    // the four channel sums reduced over the warp (a fixed xor order), so a wide high band no longer holds the
+    // whole block at the barrier behind one thread
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int e = threadIdx.x; e < nb * nbands * 4; e += blockDim.x) {
-      const int f = e / (nbands * 4), r = e - f * (nbands * 4), b = r >> 2, ch = r & 3;
-      const float* Zf = reinterpret_cast<const float*>(sm + f * bs);
-      float yh = 0.f;
-      for (int q = R.band_beg[b]; q < R.band_beg[b + 1]; ++q) {
-        const int k = R.band_bin[q];
-        const int slot = ch < 2 ? pidx(k) : mag_slot2(k, n);
-        yh = fmaf(R.band_w[q], Zf[2 * slot + (ch & 1)], yh);
-      }
+    auto band_out = [&](int f, int b, int ch, float yh) {
       const int set = ch < 2 ? 0 : ch - 1;
       const size_t yi = ((size_t)(t0 + f) * nbands + b) * 4 + ch;
       float* ydst = Yt + yi;
@@ -140,6 +135,40 @@ __global__ void __launch_bounds__(kLossThreads, 2) k_loss_frames(LaunchCtx c, co
         acc[2 * set] += fabsf(logf(y + kLogEps) - logf(yh + kLogEps));
         const float d = y - yh;
         acc[2 * set + 1] += d * d;
+      }
+    };
+    if (R.band_beg[nbands] >= 16 * nbands) {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int e = wid; e < nb * nbands; e += nw) {
+        const int f = e / nbands, b = e - f * nbands;
+        const float2* Zf = sm + f * bs;
+        float y4[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = R.band_beg[b] + lane; q < R.band_beg[b + 1]; q += 32) {
+          const int k = R.band_bin[q];
+          const float wq = R.band_w[q];
+          const float2 lr = Zf[pidx(k)], ms = Zf[mag_slot2(k, n)];
+          y4[0] = fmaf(wq, lr.x, y4[0]);
+          y4[1] = fmaf(wq, lr.y, y4[1]);
+          y4[2] = fmaf(wq, ms.x, y4[2]);
+          y4[3] = fmaf(wq, ms.y, y4[3]);
+        }
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) y4[c4] += __shfl_xor_sync(0xffffffffu, y4[c4], o);
+        if (lane < 4) band_out(f, b, lane, lane == 0 ? y4[0] : lane == 1 ? y4[1] : lane == 2 ? y4[2] : y4[3]);
+      }
+    } else {
+      for (int e = threadIdx.x; e < nb * nbands * 4; e += blockDim.x) {
+        const int f = e / (nbands * 4), r = e - f * (nbands * 4), b = r >> 2, ch = r & 3;
+        const float* Zf = reinterpret_cast<const float*>(sm + f * bs);
+        float yh = 0.f;
+        for (int q = R.band_beg[b]; q < R.band_beg[b + 1]; ++q) {
+          const int k = R.band_bin[q];
+          const int slot = ch < 2 ? pidx(k) : mag_slot2(k, n);
+          yh = fmaf(R.band_w[q], Zf[2 * slot + (ch & 1)], yh);
+        }
+        band_out(f, b, ch, yh);
       }
     }
     float out[6];
