@@ -189,8 +189,8 @@ class ClockSampler:
 KERNEL_BYTES_PER_POINT = {"row_bwd2": 40, "row_conv": 32, "row_hz": 16}
 # ncu DRAM bytes (read + write) per grid point of k_row_bwd2, from the one-song capture summarised in
 # profiles/, valid while the kernel's sources hash to KERNEL_SRC_SHA1 (otherwise the traffic is reported null)
-ROW_BWD2_DRAM_BYTES_PER_POINT = 32.50
-KERNEL_SRC_SHA1 = "c07680324480ef0c346b061645ce47f7a3c1ce27"
+ROW_BWD2_DRAM_BYTES_PER_POINT = 32.46
+KERNEL_SRC_SHA1 = "394c99fdfa5d785c1b617b5e76eb85ba5c8fde5a"
 KERNEL_SRCS = ("k_conv_rowbwd.cu", "k_conv_common.cuh", "mg_fftp.cuh", "mg_fft.cuh", "mg_internal.cuh")
 
 
